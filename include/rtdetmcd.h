@@ -1,0 +1,174 @@
+/*
+ * rtdetmcd.h - C ABI of the GB300 (sm_103a) RT-DetMCD engine.
+ *
+ * RT-DetMCD is the real-time deterministic Minimum Covariance Determinant
+ * outlier detector of De Ketelaere, Hubert, Raymaekers, Rousseeuw and Vranckx
+ * (arXiv 1910.05615).  Given n observations x_i in R^p (the n x p data matrix
+ * X of Section 2) and a coverage h with [(n+p+1)/2] <= h < n (Section 2.1),
+ * it returns a robust centre and scatter and flags as outliers the rows whose
+ * robust distance exceeds the cutoff sqrt(chi2_{p,q}), q = 0.975 by default
+ * (Section 2.1).
+ *
+ * Conventions shared by every entry point
+ *   - Row data are float32, row-major, row stride `ld` floats (ld >= p).
+ *     Every data / output pointer may be device memory or host memory
+ *     (pageable or pinned); host buffers are staged through the workspace.
+ *   - `workspace` is device memory owned by the caller, at least the size
+ *     returned by the matching *_workspace_size call, 256-byte aligned.  No
+ *     entry point allocates device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is issued on that stream; the calls return after the
+ *     stream has finished their work, so outputs are valid on return.
+ *   - The return value is a status code (RTD_OK = 0).  Invalid arguments are
+ *     rejected before any device work.  Data-dependent failures (non-finite
+ *     input, degenerate columns, every start ill-conditioned) are detected on
+ *     the device and returned; warnings are reported in rtd_result.warnings.
+ *   - p <= RTD_MAX_P, n < 2^31.
+ */
+#ifndef RTDETMCD_H
+#define RTDETMCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTD_MAX_P 64
+
+/* status codes */
+#define RTD_OK            0
+#define RTD_EINVAL        1  /* bad argument: h out of range, p < 1 or > 64, ld < p, n <= 2p, ... */
+#define RTD_ENONFINITE    2  /* a NaN or Inf in the rows */
+#define RTD_EILLCOND      3  /* every start of every block was dropped (Section 3.3 step 2 / Section 3.4) */
+#define RTD_EDEGENERATE   4  /* zero univariate MCD scale, or a fitted scatter not positive definite */
+#define RTD_EWORKSPACE    5  /* workspace too small or misaligned */
+#define RTD_ECUDA         6  /* a CUDA runtime error */
+#define RTD_EINTERNAL     7  /* an internal consistency check failed */
+
+/* warning bits (rtd_result.warnings) */
+#define RTD_WARN_MAXITER        1  /* a C-step chain stopped at max_csteps */
+#define RTD_WARN_DROPPED_START  2  /* at least one start was dropped as ill-conditioned */
+#define RTD_WARN_CSTEP_REFUSED  4  /* the condition monitor stopped a chain (Section 3.4) */
+#define RTD_WARN_NO_BLOCK_FIT   8  /* at least one block had no fit */
+
+/* arithmetic of the row passes (distances, Grams, sort keys) */
+#define RTD_FP64 0   /* plain FP64 form */
+#define RTD_FP32 1   /* FP32 row passes, FP64 p x p algebra, FP64 recompute near every threshold */
+
+typedef struct {
+    int32_t  precision;            /* RTD_FP32 (default) or RTD_FP64 */
+    int32_t  omega;                /* eq. partitionsize, default 4096 */
+    int32_t  q_override;           /* number of blocks; 0 = q = max(floor(n/(p omega)), 1) */
+    int32_t  max_csteps;           /* C-step cap per start, default 100 */
+    double   cutoff_q;             /* chi-square quantile of the cutoff, default 0.975 */
+    double   kappa_max;            /* condition threshold, default 1000 (Sections 3.3, 3.4) */
+    uint64_t seed;                 /* random partition of Section 4, default 0 */
+    int32_t  reweight_consistency; /* 0: plain covariance of the reweighted set;
+                                      1 (default): times 0.975 / F_{chi2_{p+2}}(chi2_{p,0.975});
+                                      2: times c(|W|/n) at the kept fraction */
+    int32_t  reserved;
+    /* optional per-row output (nullable, device or host, n bytes, original row
+       order): bit0 = row is in the final h-subset of its block's chosen start,
+       bit1 = row is in the reweighting set W. */
+    uint8_t* subset_out;
+    /* optional diagnostics (nullable, device or host), rtdetmcd_diag_size()
+       bytes of doubles laid out as documented at rtdetmcd_diag_size. */
+    double*  diag_out;
+} rtd_options;
+
+typedef struct {
+    int32_t status;        /* same as the return value */
+    int32_t warnings;      /* RTD_WARN_* bits */
+    int32_t p, q;          /* dimension, number of blocks */
+    int64_t n, m, h, h_b;  /* rows, rows per block, coverage, coverage per block */
+    double  mu[RTD_MAX_P];                 /* reweighted centre, X units */
+    double  sigma[RTD_MAX_P * RTD_MAX_P];  /* reweighted scatter, row-major p x p (stride p) */
+    double  mu_raw[RTD_MAX_P];             /* raw (aggregated) centre */
+    double  sigma_raw[RTD_MAX_P * RTD_MAX_P];
+    double  logdet;        /* log det sigma */
+    double  logdet_raw;
+    double  cutoff_d2;     /* chi2_{p,cutoff_q} */
+    int64_t n_flagged;     /* rows with d2 > cutoff_d2 */
+    int64_t n_reweight;    /* |W| */
+    int32_t csteps_max;    /* largest number of C-steps over all chains */
+    int32_t chains_ok;     /* chains that produced a fit */
+} rtd_result;
+
+/* Fill *opt with the defaults listed above. */
+void rtdetmcd_default_options(rtd_options* opt);
+
+/* Bytes of workspace rtdetmcd_fit needs for an n x p problem under *opt
+   (opt may be NULL for the defaults).  Returns 0 for invalid n, p. */
+size_t rtdetmcd_workspace_size(int64_t n, int32_t p, const rtd_options* opt);
+
+/* Bytes of diagnostics written to opt->diag_out for q blocks (q as in
+   rtd_result.q).  Layout, all doubles, Z = standardised units (Section 4,
+   eq. standardization):
+     [0, p)          mu_uni   (univariate MCD location of each column)
+     [p, 2p)         sigma_uni
+     then for each chain c = 2 l + k (block l, start k = 0 wrapping,
+     k = 1 GSSCM), a record of 3 p^2 + 2 p + 6 doubles:
+        S_init[p^2]      initial scatter S~_k (Section 3.2)
+        Sigma_start[p^2] refined start Sigma_k (Section 3.3)
+        mu_start[p]
+        Sigma[p^2]       final C-step scatter Lambda/(h_b-1), without c(alpha)
+        mu[p]
+        logdet, steps, status (0 ok, 1 dropped at refinement, 2 refused by the
+        condition monitor before any step, 3 max steps), full_recomputes,
+        last_swaps, kappa1
+     then for each block l: chosen start (-1 none), KL deviation, kept (0/1). */
+size_t rtdetmcd_diag_size(int32_t p, int32_t q);
+
+/*
+ * Full RT-DetMCD fit (Section 4, steps 1-10, with the Section 3 serial
+ * improvements inside each block; q = 1 is the serial algorithm).
+ *   X          n rows of p floats, stride ld
+ *   h          coverage, [(n+p+1)/2] <= h < n
+ *   opt        options (NULL = defaults)
+ *   out        host pointer, filled on return (required)
+ *   d2_out     nullable, n floats: final squared robust distances, original order
+ *   flags_out  nullable, n bytes: 1 where d2 > cutoff_d2 (Section 4 step 10)
+ */
+int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h,
+                 const rtd_options* opt, void* workspace, size_t ws_bytes,
+                 void* stream, rtd_result* out, float* d2_out, uint8_t* flags_out);
+
+/* Bytes of workspace rtdetmcd_distances needs. */
+size_t rtdetmcd_distances_workspace_size(int64_t n, int32_t p);
+
+/*
+ * Squared statistical distances d2_i = (x_i - mu)^T Sigma^-1 (x_i - mu)
+ * (Section 2.1) computed as ||L^-1 (x_i - mu)||^2 with Sigma = L L^T
+ * (Section 3.4): the scoring step of Section 6.
+ *   mu_host     p doubles (host)
+ *   sigma_host  p x p doubles, row-major (host); must be positive definite
+ *               (RTD_EDEGENERATE otherwise)
+ *   precision   RTD_FP32 or RTD_FP64 arithmetic for the row pass
+ *   d2_out      n floats
+ */
+int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld,
+                       const double* mu_host, const double* sigma_host,
+                       int32_t precision, float* d2_out,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Outlier flags of Section 4 step 10: flags_out[i] = (d2[i] > cutoff_d2).
+ * n_flagged (nullable, host) receives the count.  workspace >= 256 bytes.
+ */
+int rtdetmcd_flag(const float* d2, int64_t n, double cutoff_d2,
+                  uint8_t* flags_out, int64_t* n_flagged,
+                  void* workspace, size_t ws_bytes, void* stream);
+
+/* chi2_{p, q} quantile as used for the cutoff (computed by the library's own
+   incomplete-gamma routines). */
+double rtdetmcd_chi2_quantile(int32_t p, double q);
+
+/* Human-readable name of a status code. */
+const char* rtdetmcd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTDETMCD_H */

@@ -1,0 +1,277 @@
+"""GB300 (sm_103a) RT-DetMCD engine: Python binding of the C ABI in
+include/rtdetmcd.h.
+
+The functions below only marshal arguments (tensor pointers, strides, the
+current CUDA stream, a workspace tensor) and call the CUDA library; every
+step of the method runs in its kernels.  Importing this module fails loudly
+if the library has not been built (`paper_1910_05615_gb300.build.build()`).
+
+Method: De Ketelaere, Hubert, Raymaekers, Rousseeuw, Vranckx, "Real-time
+outlier detection for large datasets by RT-DetMCD" (arXiv 1910.05615).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = [
+    "RTD_FP32", "RTD_FP64", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
+    "rtdetmcd_flag", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
+    "rtdetmcd_diag_size", "parse_diag",
+]
+
+RTD_FP64 = 0
+RTD_FP32 = 1
+RTD_MAX_P = 64
+
+STATUS = {0: "RTD_OK", 1: "RTD_EINVAL", 2: "RTD_ENONFINITE", 3: "RTD_EILLCOND", 4: "RTD_EDEGENERATE",
+          5: "RTD_EWORKSPACE", 6: "RTD_ECUDA", 7: "RTD_EINTERNAL"}
+
+
+class RtdError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("omega", ctypes.c_int32),
+                ("q_override", ctypes.c_int32), ("max_csteps", ctypes.c_int32),
+                ("cutoff_q", ctypes.c_double), ("kappa_max", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("reweight_consistency", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
+                ("diag_out", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("warnings", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("m", ctypes.c_int64), ("h", ctypes.c_int64), ("h_b", ctypes.c_int64),
+                ("mu", ctypes.c_double * RTD_MAX_P), ("sigma", ctypes.c_double * (RTD_MAX_P * RTD_MAX_P)),
+                ("mu_raw", ctypes.c_double * RTD_MAX_P),
+                ("sigma_raw", ctypes.c_double * (RTD_MAX_P * RTD_MAX_P)),
+                ("logdet", ctypes.c_double), ("logdet_raw", ctypes.c_double),
+                ("cutoff_d2", ctypes.c_double), ("n_flagged", ctypes.c_int64),
+                ("n_reweight", ctypes.c_int64), ("csteps_max", ctypes.c_int32),
+                ("chains_ok", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build_mod.LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"RT-DetMCD CUDA library not built ({path}); run "
+                          "paper_1910_05615_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+    lib.rtdetmcd_default_options.argtypes = [ctypes.POINTER(_Options)]
+    lib.rtdetmcd_workspace_size.argtypes = [i64, i32, ctypes.POINTER(_Options)]
+    lib.rtdetmcd_workspace_size.restype = sz
+    lib.rtdetmcd_diag_size.argtypes = [i32, i32]
+    lib.rtdetmcd_diag_size.restype = sz
+    lib.rtdetmcd_fit.argtypes = [vp, i64, i32, i64, i64, ctypes.POINTER(_Options), vp, sz, vp,
+                                 ctypes.POINTER(_Result), vp, vp]
+    lib.rtdetmcd_fit.restype = i32
+    lib.rtdetmcd_distances_workspace_size.argtypes = [i64, i32]
+    lib.rtdetmcd_distances_workspace_size.restype = sz
+    lib.rtdetmcd_distances.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp, sz, vp]
+    lib.rtdetmcd_distances.restype = i32
+    lib.rtdetmcd_flag.argtypes = [vp, i64, dbl, vp, ctypes.POINTER(i64), vp, sz, vp]
+    lib.rtdetmcd_flag.restype = i32
+    lib.rtdetmcd_chi2_quantile.argtypes = [i32, dbl]
+    lib.rtdetmcd_chi2_quantile.restype = dbl
+    lib.rtdetmcd_status_string.argtypes = [i32]
+    lib.rtdetmcd_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------ marshalling
+def _torch():
+    import torch
+    return torch
+
+
+def _rows(X):
+    """(pointer, n, p, ld, device_or_None, keepalive) of a float32 row-major
+    array: a torch tensor (cuda or cpu) or a numpy array."""
+    torch = _torch()
+    if isinstance(X, torch.Tensor):
+        if X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError("X must be a 2-D float32 tensor with unit column stride")
+        dev = X.device if X.is_cuda else None
+        return X.data_ptr(), X.shape[0], X.shape[1], X.stride(0), dev, X
+    A = np.asarray(X)
+    if A.dtype != np.float32 or A.ndim != 2 or A.strides[1] != 4:
+        A = np.ascontiguousarray(A, dtype=np.float32)
+    return A.ctypes.data, A.shape[0], A.shape[1], A.strides[0] // 4, None, A
+
+
+def _stream_ptr(device, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if device is None:
+        return ctypes.c_void_p(0)
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+def _out(n, dtype, device):
+    if device is None:
+        return np.empty(n, dtype=dtype)
+    torch = _torch()
+    tdt = {np.float32: torch.float32, np.uint8: torch.uint8, np.float64: torch.float64}[dtype]
+    return torch.empty(n, dtype=tdt, device=device)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def rtdetmcd_workspace_size(n, p, precision=RTD_FP32, omega=4096, q=0):
+    lib = _load()
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision, o.omega, o.q_override = precision, omega, q
+    return lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o))
+
+
+def rtdetmcd_diag_size(p, q):
+    return _load().rtdetmcd_diag_size(p, q)
+
+
+def rtdetmcd_chi2_quantile(p, q=0.975):
+    return _load().rtdetmcd_chi2_quantile(p, q)
+
+
+def rtdetmcd_status_string(code):
+    return _load().rtdetmcd_status_string(code).decode()
+
+
+def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100,
+                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, d2=True, flags=True,
+                 subset=False, diag=False, stream=None, workspace=None, check=True):
+    """RT-DetMCD fit of the rows of X (float32, row-major) with coverage h.
+
+    X on a CUDA device: outputs are CUDA tensors on the same device.  X in
+    host memory (numpy array or CPU tensor, pinned or not): the library
+    copies it in and returns host (numpy) outputs.  Returns a dict with the
+    reweighted and raw fits (X units, float64 numpy), the flags and squared
+    distances, and optional per-row subset bits and diagnostics.
+    """
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision, o.omega, o.q_override, o.seed = precision, omega, q, seed
+    o.max_csteps, o.cutoff_q, o.kappa_max = max_csteps, cutoff_q, kappa_max
+    o.reweight_consistency = reweight_consistency
+    ws_need = lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o))
+    if ws_need == 0:
+        raise RtdError(1, "invalid n, p or options")
+    ws = workspace if workspace is not None else _workspace(ws_need, dev)
+    d2_out = _out(n, np.float32, dev) if d2 else None
+    fl_out = _out(n, np.uint8, dev) if flags else None
+    sub_out = _out(n, np.uint8, dev) if subset else None
+    o.subset_out = _ptr(sub_out)
+    qq = q if q else max(min(n // (p * omega), 1024), 1)
+    dg = _out(lib.rtdetmcd_diag_size(p, qq) // 8, np.float64, dev) if diag else None
+    o.diag_out = _ptr(dg)
+    res = _Result()
+    st = lib.rtdetmcd_fit(ptr, n, p, ld, h, ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                          _stream_ptr(dev, stream), ctypes.byref(res), _ptr(d2_out), _ptr(fl_out))
+    del keep
+    if st != 0 and check:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    pp = p
+    out = {
+        "status": st, "warnings": res.warnings, "n": res.n, "p": res.p, "q": res.q, "m": res.m,
+        "h": res.h, "h_b": res.h_b,
+        "mu": np.array(res.mu[:pp]), "Sigma": np.array(res.sigma[:pp * pp]).reshape(pp, pp),
+        "mu_raw": np.array(res.mu_raw[:pp]),
+        "Sigma_raw": np.array(res.sigma_raw[:pp * pp]).reshape(pp, pp),
+        "logdet": res.logdet, "logdet_raw": res.logdet_raw, "cutoff_d2": res.cutoff_d2,
+        "n_flagged": res.n_flagged, "n_reweight": res.n_reweight, "csteps_max": res.csteps_max,
+        "chains_ok": res.chains_ok, "d2": d2_out, "flags": fl_out, "subset": sub_out,
+    }
+    if diag:
+        a = dg.cpu().numpy() if not isinstance(dg, np.ndarray) else dg
+        out["diag"] = parse_diag(a, pp, res.q)
+    return out
+
+
+def parse_diag(a, p, q):
+    """Unpack the diagnostics record documented at rtdetmcd_diag_size."""
+    a = np.asarray(a, dtype=np.float64)
+    rec = 3 * p * p + 2 * p + 6
+    d = {"mu_uni": a[:p].copy(), "sigma_uni": a[p:2 * p].copy(), "chains": [], "blocks": []}
+    for c in range(2 * q):
+        r = a[2 * p + c * rec: 2 * p + (c + 1) * rec]
+        t = r[3 * p * p + 2 * p:]
+        d["chains"].append({
+            "S_init": r[:p * p].reshape(p, p), "Sigma_start": r[p * p:2 * p * p].reshape(p, p),
+            "mu_start": r[2 * p * p:2 * p * p + p], "Sigma": r[2 * p * p + p:3 * p * p + p].reshape(p, p),
+            "mu": r[3 * p * p + p:3 * p * p + 2 * p], "logdet": t[0], "steps": int(t[1]),
+            "status": int(t[2]), "full_recomputes": int(t[3]), "last_swaps": int(t[4]), "kappa1": t[5]})
+    b = a[2 * p + 2 * q * rec:]
+    for l in range(q):
+        d["blocks"].append({"chosen": int(b[3 * l]), "kl": b[3 * l + 1], "kept": int(b[3 * l + 2])})
+    return d
+
+
+def rtdetmcd_distances(X, mu, Sigma, *, precision=RTD_FP32, stream=None, workspace=None):
+    """Squared robust distances of the rows of X to the fit (mu, Sigma)."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    S = np.ascontiguousarray(Sigma, dtype=np.float64)
+    ws = workspace if workspace is not None else _workspace(lib.rtdetmcd_distances_workspace_size(n, p), dev)
+    d2 = _out(n, np.float32, dev)
+    st = lib.rtdetmcd_distances(ptr, n, p, ld, mu.ctypes.data, S.ctypes.data, precision, _ptr(d2),
+                                ws.data_ptr(), ws.numel(), _stream_ptr(dev, stream))
+    del keep
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return d2
+
+
+def rtdetmcd_flag(d2, cutoff_d2, *, stream=None, workspace=None):
+    """flags = d2 > cutoff_d2 and their count."""
+    lib = _load()
+    torch = _torch()
+    if isinstance(d2, torch.Tensor) and d2.is_cuda:
+        dev, ptr, n = d2.device, d2.data_ptr(), d2.numel()
+    else:
+        d2 = np.ascontiguousarray(d2, dtype=np.float32)
+        dev, ptr, n = None, d2.ctypes.data, d2.size
+    fl = _out(n, np.uint8, dev)
+    ws = workspace if workspace is not None else _workspace(n * 5 + 1024, dev)
+    cnt = ctypes.c_int64(0)
+    st = lib.rtdetmcd_flag(ptr, n, float(cutoff_d2), _ptr(fl), ctypes.byref(cnt), ws.data_ptr(),
+                           ws.numel(), _stream_ptr(dev, stream))
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return fl, cnt.value

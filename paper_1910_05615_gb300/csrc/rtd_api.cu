@@ -1,0 +1,474 @@
+// rtd_api.cu - C ABI entry points and host orchestration of RT-DetMCD.
+//
+// The host validates arguments, lays out the caller's workspace, and issues
+// the device stages on the caller's stream.  The only values that come back
+// to the host before the end of a fit are the status word (to stop early on
+// bad data) and the number of chains still iterating (C-step loop control).
+#include <stdio.h>
+#include <string.h>
+
+#include "rtd_internal.cuh"
+
+using namespace rtd;
+
+namespace {
+
+constexpr int TARGET_CTAS = 1024;     // row-kernel CTAs per pass (all blocks)
+constexpr int MIN_ROWS_PER_CTA = 256;
+constexpr int MAX_BLOCKS = 1024;
+
+struct Region {
+    size_t off, bytes;
+};
+
+struct Layout {
+    size_t total = 0;
+    Region add(size_t bytes) {
+        total = (total + 255) & ~(size_t)255;
+        Region r{total, bytes};
+        total += bytes;
+        return r;
+    }
+};
+
+struct Shape {
+    long long n, h, ld;
+    int p, pb, q, m, hb, precision, cpb, key_bytes, max_steps;
+    size_t slot_doubles;
+};
+
+struct Regions {
+    Region st, cs, ch, rule, fitrp, res, xstage, d2stage, flagstage, substage, diagstage,
+        Xp, perm, arenaA, arenaB, sort_hist, uni, gss, dkeys, memb, cand, band, hist, swaps,
+        partial, wset, chosen, kept, kl, scratch;
+};
+
+rtd_options defaults() {
+    rtd_options o;
+    memset(&o, 0, sizeof(o));
+    o.precision = RTD_FP32;
+    o.omega = 4096;
+    o.q_override = 0;
+    o.max_csteps = 100;
+    o.cutoff_q = 0.975;
+    o.kappa_max = 1000.0;
+    o.seed = 0;
+    o.reweight_consistency = 1;
+    o.subset_out = nullptr;
+    o.diag_out = nullptr;
+    return o;
+}
+
+int make_shape(long long n, int p, long long ld, long long h, const rtd_options& o, Shape& S) {
+    if (p < 1 || p > RTD_MAX_P) return RTD_EINVAL;
+    if (n <= 2LL * p || n >= (1LL << 31)) return RTD_EINVAL;
+    if (ld < p) return RTD_EINVAL;
+    if (o.precision != RTD_FP32 && o.precision != RTD_FP64) return RTD_EINVAL;
+    if (o.omega < 1 || o.max_csteps < 1 || o.q_override < 0) return RTD_EINVAL;
+    if (!(o.cutoff_q > 0.0 && o.cutoff_q < 1.0) || !(o.kappa_max > 1.0)) return RTD_EINVAL;
+    if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
+    S.n = n; S.h = h; S.ld = ld; S.p = p; S.pb = pad_p(p);
+    S.precision = o.precision;
+    S.max_steps = o.max_csteps;
+    long long q = o.q_override ? o.q_override : n / ((long long)p * o.omega);
+    if (q < 1) q = 1;
+    if (q > MAX_BLOCKS) q = MAX_BLOCKS;
+    S.q = (int)q;
+    S.m = (int)(n / q);
+    S.hb = (q == 1) ? (int)h : (int)((h * (long long)S.m) / n);
+    S.key_bytes = (o.precision == RTD_FP64) ? 8 : 4;
+    long long cpb = (TARGET_CTAS + S.q - 1) / S.q;
+    long long lim = (S.m + MIN_ROWS_PER_CTA - 1) / MIN_ROWS_PER_CTA;
+    if (cpb > lim) cpb = lim;
+    if (cpb < 1) cpb = 1;
+    S.cpb = (int)cpb;
+    S.slot_doubles = (size_t)gram_nblk(S.pb) * 16;
+    return RTD_OK;
+}
+
+int check_h(const Shape& S) {
+    // Section 2.1: [(n+p+1)/2] <= h < n; each block needs h_b > p and m > 2p.
+    if (S.h < (S.n + S.p + 1) / 2 || S.h >= S.n) return RTD_EINVAL;
+    if (S.hb <= S.p || S.m <= 2 * S.p || S.hb >= S.m) return RTD_EINVAL;
+    return RTD_OK;
+}
+
+size_t tiles_of(long long L) { return (size_t)((L + 4095) / 4096); }
+
+size_t layout(const Shape& S, Regions& R) {
+    Layout L;
+    const size_t n = (size_t)S.n, p = (size_t)S.p, q = (size_t)S.q, m = (size_t)S.m;
+    const size_t qm = q * m, K = (size_t)S.key_bytes;
+    R.st = L.add(sizeof(Status));
+    R.cs = L.add(sizeof(Consts));
+    R.ch = L.add(2 * q * sizeof(Chain));
+    R.rule = L.add(2 * q * sizeof(SelRule));
+    R.fitrp = L.add(2 * sizeof(RowParams));
+    R.res = L.add(sizeof(rtd_result));
+    R.xstage = L.add(n * p * sizeof(float));
+    R.d2stage = L.add(n * sizeof(float));
+    R.flagstage = L.add(n);
+    R.substage = L.add(n);
+    R.diagstage = L.add(rtdetmcd_diag_size((int)p, (int)q));
+    R.Xp = L.add(qm * (size_t)S.pb * sizeof(float));
+    R.perm = L.add(qm * sizeof(int));
+    size_t arena = p * n * 4;
+    if (2 * p * qm * K > arena) arena = 2 * p * qm * K;
+    if (qm * K > arena) arena = qm * K;
+    R.arenaA = L.add(arena);
+    R.arenaB = L.add(arena);
+    size_t hs = p * 256 * tiles_of(S.n);
+    size_t h2 = 2 * p * q * 256 * tiles_of(S.m);
+    if (h2 > hs) hs = h2;
+    R.sort_hist = L.add(hs * sizeof(unsigned));
+    R.uni = L.add(4 * ((2 * p * q > p) ? 2 * p * q : p) * sizeof(double));
+    R.gss = L.add(2 * q * sizeof(double));
+    R.dkeys = L.add(2 * qm * K);
+    R.memb = L.add(2 * qm);
+    R.cand = L.add(2 * qm * sizeof(Cand));
+    R.band = L.add(2 * qm * sizeof(Cand));
+    R.hist = L.add(2 * q * HIST_BINS * sizeof(unsigned));
+    R.swaps = L.add(2 * q * sizeof(int));
+    R.partial = L.add(q * (size_t)S.cpb * 2 * S.slot_doubles * sizeof(double));
+    R.wset = L.add(qm);
+    R.chosen = L.add(q * sizeof(int));
+    R.kept = L.add(q * sizeof(int));
+    R.kl = L.add(q * sizeof(double));
+    R.scratch = L.add(1024 * q * sizeof(double));
+    return (L.total + 255) & ~(size_t)255;
+}
+
+template <typename T>
+T* at(void* base, const Region& r) {
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(base) + r.off);
+}
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define RTD_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) { return RTD_ECUDA; }    \
+    } while (0)
+
+int fetch_status(Status* dev, cudaStream_t s, Status& h) {
+    RTD_CUDA(cudaMemcpyAsync(&h, dev, sizeof(Status), cudaMemcpyDeviceToHost, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    RTD_CUDA(cudaGetLastError());
+    return RTD_OK;
+}
+
+void feistel_setup(Feistel& F, long long n, unsigned long long seed, bool identity) {
+    int k = 2;
+    while ((1LL << k) < n) k += 2;
+    F.half = k / 2;
+    F.mask = (1ull << F.half) - 1ull;
+    for (int r = 0; r < 4; ++r) F.key[r] = splitmix64(seed + (unsigned long long)r);
+    F.identity = identity ? 1 : 0;
+    F.n = n;
+}
+
+int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s,
+            rtd_result* out, float* d2_out, uint8_t* flags_out) {
+    Regions R;
+    layout(S, R);
+    Plan P;
+    memset(&P, 0, sizeof(P));
+    P.n = S.n; P.h = S.h; P.ld = S.ld; P.p = S.p; P.pb = S.pb; P.q = S.q; P.m = S.m; P.hb = S.hb;
+    P.precision = S.precision; P.cpb = S.cpb; P.max_steps = S.max_steps; P.key_bytes = S.key_bytes;
+    int dev = 0;
+    RTD_CUDA(cudaGetDevice(&dev));
+    RTD_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, dev));
+    feistel_setup(P.F, S.n, o.seed, S.q == 1);
+    P.st = at<Status>(ws, R.st);
+    P.cs = at<Consts>(ws, R.cs);
+    P.ch = at<Chain>(ws, R.ch);
+    P.rule = at<SelRule>(ws, R.rule);
+    P.fitrp = at<RowParams>(ws, R.fitrp);
+    P.Xp = at<float>(ws, R.Xp);
+    P.perm = at<int>(ws, R.perm);
+    P.arenaA = at<void>(ws, R.arenaA);
+    P.arenaB = at<void>(ws, R.arenaB);
+    P.sort_hist = at<unsigned>(ws, R.sort_hist);
+    P.uni = at<double>(ws, R.uni);
+    P.gss = at<double>(ws, R.gss);
+    P.dkeys = at<void>(ws, R.dkeys);
+    P.memb = at<uint8_t>(ws, R.memb);
+    P.cand = at<Cand>(ws, R.cand);
+    P.band = at<Cand>(ws, R.band);
+    P.hist = at<unsigned>(ws, R.hist);
+    P.swaps = at<int>(ws, R.swaps);
+    P.partial = at<double>(ws, R.partial);
+    P.slot_doubles = S.slot_doubles;
+    P.wset = at<uint8_t>(ws, R.wset);
+    P.chosen = at<int>(ws, R.chosen);
+    P.kept = at<int>(ws, R.kept);
+    P.kl = at<double>(ws, R.kl);
+    P.scratch = at<double>(ws, R.scratch);
+
+    // rows: stage host data through the workspace
+    if (is_device_ptr(X)) {
+        P.X = X;
+    } else {
+        float* xs = at<float>(ws, R.xstage);
+        RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)S.p * sizeof(float), X, (size_t)S.ld * sizeof(float),
+                                   (size_t)S.p * sizeof(float), (size_t)S.n, cudaMemcpyHostToDevice, s));
+        P.X = xs;
+        P.ld = S.p;
+    }
+    const size_t q2 = 2 * (size_t)S.q, qm = (size_t)S.q * S.m;
+    RTD_CUDA(cudaMemsetAsync(P.st, 0, sizeof(Status), s));
+    RTD_CUDA(cudaMemsetAsync(P.cs, 0, sizeof(Consts), s));
+    RTD_CUDA(cudaMemsetAsync(P.ch, 0, q2 * sizeof(Chain), s));
+    RTD_CUDA(cudaMemsetAsync(P.rule, 0, q2 * sizeof(SelRule), s));
+    RTD_CUDA(cudaMemsetAsync(P.hist, 0, q2 * HIST_BINS * sizeof(unsigned), s));
+    RTD_CUDA(cudaMemsetAsync(P.memb, 0, 2 * qm, s));
+    RTD_CUDA(cudaMemsetAsync(P.wset, 0, qm, s));
+    RTD_CUDA(cudaMemsetAsync(P.swaps, 0, q2 * sizeof(int), s));
+
+    Status hs;
+    // Sections 3.1 and 4: setup, partition, univariate MCD of every column
+    launch_setup(P, o, s);
+    launch_gather(P, s);
+    launch_col_keys(P, (uint32_t*)P.arenaA, s);
+    sort_segments(P, P.arenaA, P.arenaB, 4, S.p, S.n, s);
+    launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
+    launch_uni_finish(P, s);
+    { int e = fetch_status(P.st, s, hs); if (e) return e; }
+    if (hs.code) goto finish;
+    // Section 3.2: initial estimators per block
+    launch_start1(P, s);
+    sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, S.q, S.m, s);
+    launch_gsscm(P, P.arenaA, s);
+    launch_start2(P, s);
+    launch_start_reduce(P, s);
+    // Section 3.3: refinement
+    launch_refine_eigen(P, s);
+    launch_transform(P, 0, s);
+    sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
+    launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
+    launch_refine_mid(P, s);
+    launch_transform(P, 1, s);
+    sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
+    launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
+    launch_refine_end(P, s);
+    // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
+    for (int it = 0; it <= S.max_steps; ++it) {
+        launch_chol_prep(P, s);
+        launch_dist(P, s);
+        launch_select_bucket(P, s);
+        launch_compact(P, s);
+        launch_select_finish(P, s);
+        launch_memb(P, s);
+        RTD_CUDA(cudaMemsetAsync(&P.st->active, 0, sizeof(int), s));
+        launch_cstep_finalize(P, s);
+        int e = fetch_status(P.st, s, hs);
+        if (e) return e;
+        if (hs.code || hs.active == 0) break;
+    }
+    if (hs.code) goto finish;
+    // Section 4 steps 4-7
+    launch_block_choose(P, s);
+    launch_aggregate(P, s);
+    launch_fit_prep(P, 0, s);
+    // steps 8-9
+    launch_rew(P, s);
+    launch_rew_finalize(P, s);
+    launch_fit_prep(P, 1, s);
+    {
+        int e = fetch_status(P.st, s, hs);
+        if (e) return e;
+        if (hs.code) goto finish;
+    }
+    // step 10
+    {
+        bool d2dev = is_device_ptr(d2_out), fldev = is_device_ptr(flags_out);
+        float* d2 = d2_out ? (d2dev ? d2_out : at<float>(ws, R.d2stage)) : nullptr;
+        uint8_t* fl = flags_out ? (fldev ? flags_out : at<uint8_t>(ws, R.flagstage)) : nullptr;
+        launch_final(P, d2, fl, s);
+        if (d2_out && !d2dev)
+            RTD_CUDA(cudaMemcpyAsync(d2_out, d2, (size_t)S.n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (flags_out && !fldev)
+            RTD_CUDA(cudaMemcpyAsync(flags_out, fl, (size_t)S.n, cudaMemcpyDeviceToHost, s));
+        if (o.subset_out) {
+            bool sdev = is_device_ptr(o.subset_out);
+            uint8_t* so = sdev ? o.subset_out : at<uint8_t>(ws, R.substage);
+            RTD_CUDA(cudaMemsetAsync(so, 0, (size_t)S.n, s));
+            launch_subset_out(P, so, s);
+            if (!sdev) RTD_CUDA(cudaMemcpyAsync(o.subset_out, so, (size_t)S.n, cudaMemcpyDeviceToHost, s));
+        }
+    }
+finish:
+    {
+        rtd_result* dres = at<rtd_result>(ws, R.res);
+        RTD_CUDA(cudaMemsetAsync(dres, 0, sizeof(rtd_result), s));
+        double* diag = nullptr;
+        bool ddev = false;
+        if (o.diag_out) {
+            ddev = is_device_ptr(o.diag_out);
+            diag = ddev ? o.diag_out : at<double>(ws, R.diagstage);
+        }
+        launch_result(P, dres, diag, s);
+        RTD_CUDA(cudaGetLastError());
+        RTD_CUDA(cudaMemcpyAsync(out, dres, sizeof(rtd_result), cudaMemcpyDeviceToHost, s));
+        if (o.diag_out && !ddev)
+            RTD_CUDA(cudaMemcpyAsync(o.diag_out, diag, rtdetmcd_diag_size(S.p, S.q), cudaMemcpyDeviceToHost, s));
+        RTD_CUDA(cudaStreamSynchronize(s));
+        RTD_CUDA(cudaGetLastError());
+    }
+    return out->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rtdetmcd_default_options(rtd_options* opt) {
+    if (opt) *opt = defaults();
+}
+
+size_t rtdetmcd_diag_size(int32_t p, int32_t q) {
+    if (p < 1 || q < 1) return 0;
+    size_t rec = 3 * (size_t)p * p + 2 * (size_t)p + 6;
+    return (2 * (size_t)p + 2 * (size_t)q * rec + 3 * (size_t)q) * sizeof(double);
+}
+
+size_t rtdetmcd_workspace_size(int64_t n, int32_t p, const rtd_options* opt) {
+    rtd_options o = opt ? *opt : defaults();
+    Shape S;
+    if (make_shape(n, p, p, (n + p + 1) / 2, o, S) != RTD_OK) return 0;
+    Regions R;
+    return layout(S, R);
+}
+
+int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                 void* workspace, size_t ws_bytes, void* stream, rtd_result* out, float* d2_out,
+                 uint8_t* flags_out) {
+    if (!out) return RTD_EINVAL;
+    memset(out, 0, sizeof(*out));
+    rtd_options o = opt ? *opt : defaults();
+    Shape S;
+    int e = make_shape(n, p, ld, h, o, S);
+    if (!e) e = check_h(S);
+    if (!X) e = RTD_EINVAL;
+    if (e) { out->status = e; return e; }
+    Regions R;
+    size_t need = layout(S, R);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        out->status = RTD_EWORKSPACE;
+        return RTD_EWORKSPACE;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int r = run_fit(X, S, o, workspace, s, out, d2_out, flags_out);
+    out->status = r;
+    return r;
+}
+
+size_t rtdetmcd_distances_workspace_size(int64_t n, int32_t p) {
+    if (n < 1 || p < 1 || p > RTD_MAX_P) return 0;
+    Layout L;
+    L.add(sizeof(Status));
+    L.add(sizeof(RowParams));
+    L.add((size_t)RTD_MAX_P * (RTD_MAX_P + 1) * sizeof(double));
+    L.add((size_t)n * p * sizeof(float));
+    L.add((size_t)n * sizeof(float));
+    return (L.total + 255) & ~(size_t)255;
+}
+
+int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld, const double* mu_host,
+                       const double* sigma_host, int32_t precision, float* d2_out, void* workspace,
+                       size_t ws_bytes, void* stream) {
+    if (!X || !mu_host || !sigma_host || !d2_out || n < 1 || p < 1 || p > RTD_MAX_P || ld < p ||
+        (precision != RTD_FP32 && precision != RTD_FP64) || n >= (1LL << 31))
+        return RTD_EINVAL;
+    size_t need = rtdetmcd_distances_workspace_size(n, p);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Layout L;
+    Region rst = L.add(sizeof(Status));
+    Region rrp = L.add(sizeof(RowParams));
+    Region rms = L.add((size_t)RTD_MAX_P * (RTD_MAX_P + 1) * sizeof(double));
+    Region rxs = L.add((size_t)n * p * sizeof(float));
+    Region rds = L.add((size_t)n * sizeof(float));
+    Status* st = at<Status>(workspace, rst);
+    RowParams* rp = at<RowParams>(workspace, rrp);
+    double* ms = at<double>(workspace, rms);
+    RTD_CUDA(cudaMemsetAsync(st, 0, sizeof(Status), s));
+    RTD_CUDA(cudaMemcpyAsync(ms, mu_host, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, s));
+    RTD_CUDA(cudaMemcpyAsync(ms + RTD_MAX_P, sigma_host, (size_t)p * p * sizeof(double), cudaMemcpyHostToDevice, s));
+    const float* Xd = X;
+    long long ldd = ld;
+    if (!is_device_ptr(X)) {
+        float* xs = at<float>(workspace, rxs);
+        RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)p * sizeof(float), X, (size_t)ld * sizeof(float),
+                                   (size_t)p * sizeof(float), (size_t)n, cudaMemcpyHostToDevice, s));
+        Xd = xs;
+        ldd = p;
+    }
+    bool ddev = is_device_ptr(d2_out);
+    float* d2 = ddev ? d2_out : at<float>(workspace, rds);
+    launch_score_prep(ms, ms + RTD_MAX_P, p, rp, st, s);
+    launch_score(Xd, n, p, ldd, rp, precision, d2, s);
+    if (!ddev) RTD_CUDA(cudaMemcpyAsync(d2_out, d2, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    Status hs;
+    int e = fetch_status(st, s, hs);
+    if (e) return e;
+    return hs.code;
+}
+
+int rtdetmcd_flag(const float* d2, int64_t n, double cutoff_d2, uint8_t* flags_out, int64_t* n_flagged,
+                  void* workspace, size_t ws_bytes, void* stream) {
+    if (!d2 || n < 1 || !(cutoff_d2 == cutoff_d2)) return RTD_EINVAL;
+    Layout L;
+    Region rst = L.add(sizeof(Status));
+    Region rd = L.add((size_t)n * sizeof(float));
+    Region rf = L.add((size_t)n);
+    bool d2dev = is_device_ptr(d2), fdev = is_device_ptr(flags_out);
+    size_t need = 256;
+    if (!d2dev || (flags_out && !fdev)) need = (L.total + 255) & ~(size_t)255;
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Status* st = at<Status>(workspace, rst);
+    RTD_CUDA(cudaMemsetAsync(st, 0, sizeof(Status), s));
+    const float* dd = d2;
+    if (!d2dev) {
+        float* ds = at<float>(workspace, rd);
+        RTD_CUDA(cudaMemcpyAsync(ds, d2, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s));
+        dd = ds;
+    }
+    uint8_t* fl = flags_out ? (fdev ? flags_out : at<uint8_t>(workspace, rf)) : nullptr;
+    launch_flag(dd, n, cutoff_d2, fl, &st->n_flagged, s);
+    if (flags_out && !fdev) RTD_CUDA(cudaMemcpyAsync(flags_out, fl, (size_t)n, cudaMemcpyDeviceToHost, s));
+    Status hs;
+    int e = fetch_status(st, s, hs);
+    if (e) return e;
+    if (n_flagged) *n_flagged = (int64_t)hs.n_flagged;
+    return hs.code;
+}
+
+double rtdetmcd_chi2_quantile(int32_t p, double q) {
+    if (p < 1) return NAN;
+    return chi2_quantile(p, q);
+}
+
+const char* rtdetmcd_status_string(int status) {
+    switch (status) {
+        case RTD_OK: return "ok";
+        case RTD_EINVAL: return "invalid argument";
+        case RTD_ENONFINITE: return "non-finite value in the rows";
+        case RTD_EILLCOND: return "every start of every block was ill-conditioned";
+        case RTD_EDEGENERATE: return "degenerate data (zero scale or singular scatter)";
+        case RTD_EWORKSPACE: return "workspace too small or misaligned";
+        case RTD_ECUDA: return "CUDA runtime error";
+        case RTD_EINTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// rtd_linalg.cuh - CTA-cooperative FP64 dense algebra for p x p matrices
+// (p <= 64) held in shared memory with leading dimension LD.
+#pragma once
+#include "rtd_common.cuh"
+
+namespace rtd {
+
+constexpr int LD = PMAX + 1;   // padded leading dimension of shared matrices
+
+// In-place Cholesky A = L L^T (lower triangle overwritten by L; the strict
+// upper triangle is zeroed).  Returns false (uniformly) if A is not
+// numerically positive definite.
+__device__ inline bool cta_cholesky(double* A, int p) {
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int k = 0; k < p; ++k) {
+        if (threadIdx.x == 0) {
+            double d = A[k * LD + k];
+            if (!(d > 0.0) || !isfinite(d)) fail = 1;
+            else A[k * LD + k] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) break;
+        double dkk = A[k * LD + k];
+        for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) A[i * LD + k] /= dkk;
+        __syncthreads();
+        int rem = p - k - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            int i = k + 1 + e / rem, j = k + 1 + e % rem;
+            if (j <= i) A[i * LD + j] -= A[i * LD + k] * A[j * LD + k];
+        }
+        __syncthreads();
+    }
+    bool ok = !fail;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        if (j > i) A[i * LD + j] = 0.0;
+    }
+    __syncthreads();
+    return ok;
+}
+
+// Li = L^-1 for lower-triangular L (column-parallel forward substitution).
+__device__ inline void cta_tri_inverse(const double* L, double* Li, int p) {
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        for (int i = 0; i < j; ++i) Li[i * LD + j] = 0.0;
+        Li[j * LD + j] = 1.0 / L[j * LD + j];
+        for (int i = j + 1; i < p; ++i) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s += L[i * LD + k] * Li[k * LD + j];
+            Li[i * LD + j] = -s / L[i * LD + i];
+        }
+    }
+    __syncthreads();
+}
+
+// Block-wide reductions (blockDim.x a multiple of 32, <= 1024).
+__device__ inline double cta_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum_d(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (l < nw) ? red[l] : 0.0;
+        r = warp_sum_d(r);
+        if (l == 0) red[0] = r;
+    }
+    __syncthreads();
+    r = red[0];
+    __syncthreads();
+    return r;
+}
+__device__ inline double cta_max(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double r = -INFINITY;
+    if (threadIdx.x < 32) {
+        r = (l < nw) ? red[l] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (l == 0) red[0] = r;
+    }
+    __syncthreads();
+    r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// kappa_1 = ||S||_1 ||S^-1||_1 with S^-1 = Li^T Li (Section 3.4; exact).
+__device__ inline double cta_kappa1(const double* S, const double* Li, int p) {
+    double n1 = 0.0, n1i = 0.0;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double cs = 0.0, csi = 0.0;
+        for (int i = 0; i < p; ++i) {
+            cs += fabs(S[i * LD + j]);
+            int k0 = i > j ? i : j;
+            double v = 0.0;
+            for (int k = k0; k < p; ++k) v += Li[k * LD + i] * Li[k * LD + j];
+            csi += fabs(v);
+        }
+        n1 = fmax(n1, cs);
+        n1i = fmax(n1i, csi);
+    }
+    n1 = cta_max(n1);
+    n1i = cta_max(n1i);
+    return n1 * n1i;
+}
+
+// Symmetric eigen-decomposition by cyclic Jacobi rotations in the
+// round-robin (tournament) order, so that the p/2 rotations of one round act
+// on disjoint index pairs and are applied in parallel.  On return A's
+// diagonal holds the eigenvalues, V (columns) the eigenvectors; lam/Vs hold
+// them sorted by decreasing eigenvalue.
+__device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, double* Vs) {
+    __shared__ double rc[PMAX / 2 + 1], rs[PMAX / 2 + 1];
+    __shared__ int ri[PMAX / 2 + 1], rj[PMAX / 2 + 1];
+    __shared__ int order[PMAX];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        V[i * LD + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int P = p + (p & 1);
+    const int half = P / 2;
+    for (int sweep = 0; sweep < 60 && p > 1; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            double a = A[i * LD + j];
+            if (i != j) off += a * a; else dg += a * a;
+        }
+        off = cta_sum(off);
+        dg = cta_sum(dg);
+        if (off <= 1e-32 * dg || off == 0.0) break;
+        for (int round = 0; round < P - 1; ++round) {
+            if (threadIdx.x < half) {
+                int k = threadIdx.x;
+                // positions: 0 fixed, others rotate
+                int a = (k == 0) ? 0 : 1 + (k - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - k + round) % (P - 1);
+                int i = a < b ? a : b, j = a < b ? b : a;
+                double c = 1.0, s = 0.0;
+                if (j < p) {
+                    double aij = A[i * LD + j];
+                    if (aij != 0.0) {
+                        double th = (A[j * LD + j] - A[i * LD + i]) / (2.0 * aij);
+                        double t;
+                        if (fabs(th) > 1e150) t = 0.5 / th;
+                        else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    }
+                }
+                rc[k] = c; rs[k] = s; ri[k] = i; rj[k] = (j < p) ? j : -1;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+                int k = e / p, r = e % p;
+                int i = ri[k], j = rj[k];
+                if (j < 0 || rs[k] == 0.0) continue;
+                double c = rc[k], s = rs[k];
+                double a = A[r * LD + i], b = A[r * LD + j];
+                A[r * LD + i] = c * a - s * b;
+                A[r * LD + j] = s * a + c * b;
+                a = V[r * LD + i]; b = V[r * LD + j];
+                V[r * LD + i] = c * a - s * b;
+                V[r * LD + j] = s * a + c * b;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+                int k = e / p, r = e % p;
+                int i = ri[k], j = rj[k];
+                if (j < 0 || rs[k] == 0.0) continue;
+                double c = rc[k], s = rs[k];
+                double a = A[i * LD + r], b = A[j * LD + r];
+                A[i * LD + r] = c * a - s * b;
+                A[j * LD + r] = s * a + c * b;
+            }
+            __syncthreads();
+            // exact zero of the annihilated pair, symmetric copy
+            if (threadIdx.x < half) {
+                int k = threadIdx.x;
+                if (rj[k] >= 0 && rs[k] != 0.0) {
+                    A[ri[k] * LD + rj[k]] = 0.0;
+                    A[rj[k] * LD + ri[k]] = 0.0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < p; ++i) order[i] = i;
+        for (int i = 1; i < p; ++i) {       // stable insertion sort, decreasing
+            int v = order[i];
+            double dv = A[v * LD + v];
+            int j = i - 1;
+            while (j >= 0 && A[order[j] * LD + order[j]] < dv) { order[j + 1] = order[j]; --j; }
+            order[j + 1] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        Vs[i * LD + j] = V[i * LD + order[j]];
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) lam[j] = A[order[j] * LD + order[j]];
+    __syncthreads();
+}
+
+// log|det A| by LU with partial pivoting (A overwritten).  -inf if singular.
+__device__ inline double cta_logabsdet(double* A, int p) {
+    __shared__ int piv;
+    __shared__ double acc;
+    if (threadIdx.x == 0) acc = 0.0;
+    __syncthreads();
+    for (int k = 0; k < p; ++k) {
+        if (threadIdx.x == 0) {
+            int best = k;
+            double bv = fabs(A[k * LD + k]);
+            for (int i = k + 1; i < p; ++i) {
+                double v = fabs(A[i * LD + k]);
+                if (v > bv) { bv = v; best = i; }
+            }
+            piv = best;
+            if (bv == 0.0) acc = -INFINITY;
+            else acc += log(bv);
+        }
+        __syncthreads();
+        if (acc == -INFINITY) break;
+        int pr = piv;
+        if (pr != k) {
+            for (int j = threadIdx.x; j < p; j += blockDim.x) {
+                double t = A[k * LD + j];
+                A[k * LD + j] = A[pr * LD + j];
+                A[pr * LD + j] = t;
+            }
+        }
+        __syncthreads();
+        double d = A[k * LD + k];
+        int rem = p - k - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            int i = k + 1 + e / rem, j = k + 1 + e % rem;
+            A[i * LD + j] -= A[i * LD + k] / d * A[k * LD + j];
+        }
+        __syncthreads();
+    }
+    double r = acc;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace rtd

@@ -1,0 +1,191 @@
+// rtd_rows.cu - row kernels that do not depend on the padded width, and the
+// dispatch of the width-templated ones (instantiated in rtd_rows_pb*.cu).
+#include "rtd_rows.cuh"
+#include "rtd_rows_api.cuh"
+
+namespace rtd {
+
+// =====================================================================
+// Partition (Section 4): permuted, padded copy of the rows.
+// =====================================================================
+__global__ void k_gather(const float* __restrict__ X, long long ld, int p, int pb, long long nq,
+                         Feistel F, float* __restrict__ Xp, int* __restrict__ perm, Status* st) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = tid; e < nq * pb; e += stride) {
+        long long t = e / pb;
+        int j = (int)(e - t * pb);
+        long long src = feistel_perm(F, t);
+        if (src < 0) { set_error(st, RTD_EINTERNAL); Xp[e] = 0.f; continue; }
+        if (j == 0) perm[t] = (int)src;
+        Xp[e] = (j < p) ? X[src * ld + j] : 0.f;
+    }
+}
+
+void launch_gather(const Plan& P, cudaStream_t s) {
+    long long nq = (long long)P.q * P.m;
+    int grid = P.nsm * 8;
+    k_gather<<<grid, NT, 0, s>>>(P.X, P.ld, P.p, P.pb, nq, P.F, P.Xp, P.perm, P.st);
+}
+
+// =====================================================================
+// Whole-X column keys for the univariate MCD (Sections 3.1, 4) and the
+// non-finite check.
+// =====================================================================
+__global__ void k_col_keys(const float* __restrict__ X, long long ld, int p, long long n,
+                           uint32_t* __restrict__ keys, Status* st) {
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float* row = X + i * ld;
+        bool bad = false;
+        for (int j = 0; j < p; ++j) {
+            float v = row[j];
+            bad |= !isfinite(v);
+            keys[(long long)j * n + i] = f2key(v);
+        }
+        if (bad) set_error(st, RTD_ENONFINITE);
+    }
+}
+
+void launch_col_keys(const Plan& P, uint32_t* keys, cudaStream_t s) {
+    k_col_keys<<<P.nsm * 8, NT, 0, s>>>(P.X, P.ld, P.p, P.n, keys, P.st);
+}
+
+// =====================================================================
+// Candidate compaction of the radix select: rows whose coarse key lies in
+// the bucket of rank h_b (widened by the FP64 band in the FP32 form) are
+// appended to the chain's candidate list; rows below are counted.
+// =====================================================================
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_compact(const T* __restrict__ dkeys, int m, int cpb, long long qm,
+                                                const Chain* __restrict__ ch, SelRule* __restrict__ rule,
+                                                Cand* __restrict__ cand) {
+    const int l = blockIdx.y;
+    int r0, r1;
+    block_rows(m, cpb, r0, r1);
+    for (int k = 0; k < 2; ++k) {
+        const int c = 2 * l + k;
+        if (!ch[c].active) continue;
+        const unsigned long long lo = rule[c].lo, hi = rule[c].hi;
+        const T* in = dkeys + (size_t)k * qm;
+        Cand* out = cand + (size_t)c * m;
+        int below = 0;
+        // whole warps iterate together so that the ballot below is full
+        for (int base = r0; base < r1; base += NT) {
+            int row = base + threadIdx.x;
+            bool valid = row < r1;
+            T d = valid ? in[row] : (T)0;
+            unsigned long long ck = coarse_key(d);
+            below += (valid && ck < lo) ? 1 : 0;
+            bool take = valid && ck >= lo && ck <= hi;
+            unsigned mask = __ballot_sync(0xffffffffu, take);
+            if (mask) {
+                int lane = threadIdx.x & 31;
+                int leader = __ffs(mask) - 1;
+                int basei = 0;
+                if (lane == leader) basei = atomicAdd(&rule[c].cand, __popc(mask));
+                basei = __shfl_sync(0xffffffffu, basei, leader);
+                if (take) {
+                    int idx = basei + __popc(mask & ((1u << lane) - 1u));
+                    if (idx < m) {
+                        Cand e;
+                        e.key = full_key(d);
+                        e.pos = (unsigned)(row - l * m);
+                        e.pad = 0;
+                        out[idx] = e;
+                    }
+                }
+            }
+        }
+        below = cta_sum_int(below);
+        if (threadIdx.x == 0 && below) atomicAdd(&rule[c].below, below);
+    }
+}
+
+void launch_compact(const Plan& P, cudaStream_t s) {
+    dim3 grid(P.cpb, P.q);
+    long long qm = (long long)P.q * P.m;
+    if (P.precision == RTD_FP64)
+        k_compact<double><<<grid, NT, 0, s>>>((const double*)P.dkeys, P.m, P.cpb, qm, P.ch, P.rule, P.cand);
+    else
+        k_compact<float><<<grid, NT, 0, s>>>((const float*)P.dkeys, P.m, P.cpb, qm, P.ch, P.rule, P.cand);
+}
+
+
+
+
+
+
+
+
+// ---------------------------------------------------------------- flags
+__global__ void k_flag(const float* __restrict__ d2, long long n, double cut, uint8_t* __restrict__ flags,
+                       unsigned long long* __restrict__ count) {
+    int nf = 0;
+    long long stride = (long long)gridDim.x * NT;
+    for (long long base = (long long)blockIdx.x * NT; base < n; base += stride) {
+        long long i = base + threadIdx.x;
+        if (i < n) {
+            bool o = (double)d2[i] > cut;
+            if (flags) flags[i] = o ? 1 : 0;
+            nf += o ? 1 : 0;
+        }
+    }
+    nf = cta_sum_int(nf);
+    if (threadIdx.x == 0 && nf && count) atomicAdd(count, (unsigned long long)nf);
+}
+
+void launch_flag(const float* d2, long long n, double cut, uint8_t* flags, unsigned long long* count,
+                 cudaStream_t s) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (n + NT - 1) / NT;
+    int grid = (int)(blocks < (long long)nsm * 16 ? blocks : (long long)nsm * 16);
+    if (grid < 1) grid = 1;
+    k_flag<<<grid, NT, 0, s>>>(d2, n, cut, flags, count);
+}
+
+// ------------------------------------------------------- subset output
+__global__ void k_subset_out(const int* __restrict__ perm, const uint8_t* __restrict__ memb,
+                             const uint8_t* __restrict__ wset, const Chain* __restrict__ ch,
+                             const int* __restrict__ chosen, int m, long long qm, uint8_t* __restrict__ out) {
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < qm; t += stride) {
+        int l = (int)(t / m);
+        int k = chosen[l];
+        uint8_t v = 0;
+        if (k >= 0) v |= memb[(size_t)(2 * l + k) * m + (t - (long long)l * m)] & 1;
+        v |= wset[t] & 2;
+        out[perm[t]] = v;
+    }
+}
+
+void launch_subset_out(const Plan& P, uint8_t* out, cudaStream_t s) {
+    long long qm = (long long)P.q * P.m;
+    k_subset_out<<<P.nsm * 8, NT, 0, s>>>(P.perm, P.memb, P.wset, P.ch, P.chosen, P.m, qm, out);
+}
+
+
+void launch_start1(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, start1, P, s); }
+void launch_start2(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, start2, P, s); }
+void launch_transform(const Plan& P, int which, cudaStream_t s) { (void)which; RTD_PB_CALL(P.pb, transform, P, s); }
+void launch_dist(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist, P, s); }
+void launch_memb(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, memb, P, s); }
+void launch_rew(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, rew, P, s); }
+
+void launch_final(const Plan& P, float* d2_out, uint8_t* flags_out, cudaStream_t s) {
+    RTD_PB_CALL(P.pb, final, P.X, P.n, P.p, P.ld, P.precision, P.fitrp + 1, &P.cs->cutoff_d2, 1,
+                d2_out, flags_out, &P.st->n_flagged, P.nsm, s);
+}
+
+void launch_score(const float* X, long long n, int p, long long ld, const RowParams* rp,
+                  int precision, float* d2_out, cudaStream_t s) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    RTD_PB_CALL(pad_p(p), final, X, n, p, ld, precision, rp, nullptr, 0, d2_out, nullptr, nullptr, nsm, s);
+}
+
+}  // namespace rtd

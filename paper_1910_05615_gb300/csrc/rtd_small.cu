@@ -1,0 +1,804 @@
+// rtd_small.cu - FP64 p x p stages of RT-DetMCD: one CTA per chain, block
+// or fit.  All matrices are in standardised (Z) units unless noted; the row
+// passes receive M = L^-1 D^-1 and mu_x = mu_uni + D mu so that
+// standardisation never touches the rows.
+#include "rtd_internal.cuh"
+#include "rtd_linalg.cuh"
+
+namespace rtd {
+
+constexpr int CT = 256;     // threads of the per-chain kernels
+constexpr size_t MAT = (size_t)PMAX * LD;   // doubles of one shared matrix
+
+template <typename K>
+inline void big_smem(K kernel, size_t bytes) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Sum of the Gram slots of chain slot k of block l over its CTAs, in order.
+__device__ inline void sum_slots(const double* __restrict__ partial, size_t slot_d, int nvals,
+                                 int l, int cpb, int k, double* __restrict__ out) {
+    for (int e = threadIdx.x; e < nvals; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < cpb; ++b) s += partial[(((size_t)l * cpb + b) * 2 + k) * slot_d + e];
+        out[e] = s;
+    }
+    __syncthreads();
+}
+
+// =====================================================================
+// Constants of Section 2.1 (c(alpha), chi-square cutoffs) and of the
+// univariate MCD (Section 3.1).
+// =====================================================================
+__global__ void k_setup(Consts* cs, long long n, int p, int pb, int q, int m, int hb, long long h,
+                        int precision, int max_steps, int rew_mode, double cutoff_q, double kappa_max) {
+    if (threadIdx.x != 0) return;
+    cs->n = (int)n; cs->p = p; cs->pb = pb; cs->q = q; cs->m = m; cs->hb = hb; cs->h = h;
+    cs->precision = precision; cs->max_steps = max_steps; cs->rew_mode = rew_mode;
+    cs->alpha = (double)h / (double)n;
+    cs->c_alpha = consistency(cs->alpha, p);
+    cs->cutoff_d2 = chi2_quantile(p, cutoff_q);
+    cs->c_rew = cutoff_q / chi2_cdf(cs->cutoff_d2, p + 2);
+    cs->kappa_max = kappa_max;
+    cs->uni_cut2 = chi2_quantile(1, cutoff_q);
+    cs->crew1 = cutoff_q / chi2_cdf(cs->uni_cut2, 3);
+    cs->c1_n = consistency((double)(n / 2 + 1) / (double)n, 1);
+    cs->c1_m = consistency((double)(m / 2 + 1) / (double)m, 1);
+    cs->chains_ok = 0;
+    cs->csteps_max = 0;
+}
+
+void launch_setup(const Plan& P, const rtd_options& o, cudaStream_t s) {
+    k_setup<<<1, 32, 0, s>>>(P.cs, P.n, P.p, P.pb, P.q, P.m, P.hb, P.h, P.precision, P.max_steps,
+                             o.reweight_consistency, o.cutoff_q, o.kappa_max);
+}
+
+__global__ void k_uni_finish(Consts* cs, const double* __restrict__ uni, int p, Status* st) {
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double mu = uni[4 * j], s2 = uni[4 * j + 1];
+        if (!(s2 > 0.0) || !isfinite(s2) || !isfinite(mu)) {
+            set_error(st, RTD_EDEGENERATE);
+            cs->mu_uni[j] = 0.0;
+            cs->s_uni[j] = 1.0;
+        } else {
+            cs->mu_uni[j] = mu;
+            cs->s_uni[j] = sqrt(s2);
+        }
+    }
+}
+
+void launch_uni_finish(const Plan& P, cudaStream_t s) {
+    k_uni_finish<<<1, 64, 0, s>>>(P.cs, P.uni, P.p, P.st);
+}
+
+// =====================================================================
+// Initial scatters (Section 3.2) from the Gram partials:
+//   S~_1 = covariance (n-1 denominator) of the wrapped rows,
+//   S~_2 = (1/m) sum xi^2 z z^T.
+// =====================================================================
+__global__ void __launch_bounds__(CT) k_start_reduce(Chain* ch, const Consts* __restrict__ cs,
+                                                     const double* __restrict__ partial, size_t slot_d,
+                                                     int cpb) {
+    extern __shared__ double ext[];
+    const int c = blockIdx.x, l = c / 2, k = c % 2;
+    const int p = cs->p, nb = gram_nb(cs->pb);
+    sum_slots(partial, slot_d, gram_nblk(cs->pb) * 16, l, cpb, k, ext);
+    Chain& C = ch[c];
+    const double cnt = gram_get(ext, p, p, nb);
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double g = gram_get(ext, i, j, nb);
+        double v;
+        if (k == 0) {
+            double si = gram_get(ext, i, p, nb), sj = gram_get(ext, j, p, nb);
+            v = (g - si * sj / cnt) / (cnt - 1.0);
+        } else {
+            v = g / (double)cs->m;
+        }
+        C.Sinit[i * PMAX + j] = v;
+    }
+    if (threadIdx.x == 0) {
+        C.status = CH_OK; C.active = 0; C.steps = 0; C.full = 1; C.full_count = 0;
+        C.swaps = 0; C.started = 0; C.logdet = NAN; C.kappa1 = NAN;
+    }
+}
+
+void launch_start_reduce(const Plan& P, cudaStream_t s) {
+    size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
+    auto k = k_start_reduce;
+    big_smem(k, sm);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.partial, P.slot_doubles, P.cpb);
+}
+
+// =====================================================================
+// Refinement (Section 3.3).
+// eigen: S~_k = V D V^T, drop when lambda_1/lambda_p > kappa_max, and the
+//        score transform W = V^T D_uni^-1 (T = Z V).
+// mid:   Sigma_k = V diag(sigma_uni^2(T_j)) V^T and the sphering transform
+//        W = Sigma_k^{-1/2} D_uni^-1.
+// end:   mu_k = Sigma_k^{1/2} (mu_uni(Z~_j))_j; the chain starts here.
+// Chain.G holds W while the refinement runs.
+// =====================================================================
+__global__ void __launch_bounds__(CT) k_refine_eigen(Chain* ch, const Consts* __restrict__ cs, Status* st) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* V = sm + MAT;
+    double* Vs = sm + 2 * MAT;
+    __shared__ double lam[PMAX];
+    __shared__ int bad;
+    Chain& C = ch[blockIdx.x];
+    const int p = cs->p;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = C.Sinit[i * PMAX + j];
+        if (!isfinite(v)) bad = 1;
+        A[i * LD + j] = v;
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) { C.status = CH_DROPPED; set_warning(st, RTD_WARN_DROPPED_START); }
+        return;
+    }
+    cta_jacobi(A, V, p, lam, Vs);
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        C.V[i * PMAX + j] = Vs[i * LD + j];
+        // W[j][i] = V_ij / sigma_uni_i  (output j = score j)
+        C.G[j * PMAX + i] = Vs[i * LD + j] / cs->s_uni[i];
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) C.lam[j] = lam[j];
+    if (threadIdx.x == 0) {
+        double l1 = lam[0], lp = lam[p - 1];
+        if (!(lp > 0.0) || l1 / lp > cs->kappa_max || !isfinite(l1)) {
+            C.status = CH_DROPPED;
+            set_warning(st, RTD_WARN_DROPPED_START);
+        }
+    }
+}
+
+void launch_refine_eigen(const Plan& P, cudaStream_t s) {
+    size_t sm = 3 * MAT * sizeof(double);
+    auto k = k_refine_eigen;
+    big_smem(k, sm);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.st);
+}
+
+__global__ void __launch_bounds__(CT) k_refine_mid(Chain* ch, const Consts* __restrict__ cs,
+                                                   const double* __restrict__ uni, Status* st) {
+    __shared__ double d[PMAX], dih[PMAX];
+    __shared__ int bad;
+    const int c = blockIdx.x;
+    Chain& C = ch[c];
+    if (C.status != CH_OK) return;
+    const int p = cs->p;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double v = uni[4 * ((size_t)c * p + j) + 1];
+        if (!(v > 0.0) || !isfinite(v)) bad = 1;
+        d[j] = v;
+        dih[j] = 1.0 / sqrt(v);
+        C.D[j] = v;
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) { C.status = CH_DROPPED; set_warning(st, RTD_WARN_DROPPED_START); }
+        return;
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double sg = 0.0, sh = 0.0;
+        for (int t = 0; t < p; ++t) {
+            double vi = C.V[i * PMAX + t], vj = C.V[j * PMAX + t];
+            sg += vi * d[t] * vj;
+            sh += vi * dih[t] * vj;
+        }
+        C.Sigma0[i * PMAX + j] = sg;
+        // W[i][j] = (Sigma^{-1/2})_ij / sigma_uni_j
+        C.G[i * PMAX + j] = sh / cs->s_uni[j];
+    }
+}
+
+void launch_refine_mid(const Plan& P, cudaStream_t s) {
+    k_refine_mid<<<2 * P.q, CT, 0, s>>>(P.ch, P.cs, P.uni, P.st);
+}
+
+__global__ void __launch_bounds__(CT) k_refine_end(Chain* ch, const Consts* __restrict__ cs,
+                                                   const double* __restrict__ uni, Status* st) {
+    __shared__ double mt[PMAX], u[PMAX];
+    __shared__ int bad;
+    const int c = blockIdx.x;
+    Chain& C = ch[c];
+    if (C.status != CH_OK) return;
+    const int p = cs->p;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double v = uni[4 * ((size_t)c * p + j)];
+        if (!isfinite(v)) bad = 1;
+        mt[j] = v;
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) { C.status = CH_DROPPED; set_warning(st, RTD_WARN_DROPPED_START); }
+        return;
+    }
+    // u = D^{1/2} V^T mu~ ;  mu = V u
+    for (int t = threadIdx.x; t < p; t += blockDim.x) {
+        double a = 0.0;
+        for (int i = 0; i < p; ++i) a += C.V[i * PMAX + t] * mt[i];
+        u[t] = a * sqrt(C.D[t]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        double a = 0.0;
+        for (int t = 0; t < p; ++t) a += C.V[i * PMAX + t] * u[t];
+        C.mu0[i] = a;
+        C.mu[i] = a;
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        C.Sigma[i * PMAX + j] = C.Sigma0[i * PMAX + j];
+    }
+    if (threadIdx.x == 0) { C.active = 1; C.full = 1; C.steps = 0; C.started = 1; }
+}
+
+void launch_refine_end(const Plan& P, cudaStream_t s) {
+    k_refine_end<<<2 * P.q, CT, 0, s>>>(P.ch, P.cs, P.uni, P.st);
+}
+
+// =====================================================================
+// Row parameters of a fit (mu, Sigma in Z units): Cholesky Sigma = L L^T
+// (Section 3.4), M = L^-1 D^-1, mu_x = mu_uni + D mu, FP32 copies with the
+// centre split into hi + lo.  Returns false if Sigma is not positive
+// definite.  Leaves L in A and L^-1 in Li.
+// =====================================================================
+__device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __restrict__ S_z,
+                               const double* __restrict__ mu_uni, const double* __restrict__ s_uni,
+                               int p, double* A, double* Li, RowParams& rp, double* logdet) {
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        A[i * LD + j] = S_z[i * PMAX + j];
+    }
+    __syncthreads();
+    if (!cta_cholesky(A, p)) return false;
+    cta_tri_inverse(A, Li, p);
+    double ld = 0.0;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) ld += log(A[j * LD + j]);
+    ld = 2.0 * cta_sum(ld);
+    *logdet = ld;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = (j <= i) ? Li[i * LD + j] / s_uni[j] : 0.0;
+        rp.M[i * PMAX + j] = v;
+        rp.Mf[i * PMAX + j] = (float)v;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double mx = mu_uni[j] + s_uni[j] * mu_z[j];
+        rp.mu[j] = mx;
+        float hi = (float)mx;
+        rp.mu_hi[j] = hi;
+        rp.mu_lo[j] = (float)(mx - (double)hi);
+    }
+    __syncthreads();
+    return true;
+}
+
+// Before each C-step: condition monitor (Section 3.4) and the row
+// parameters of the current (mu, Sigma).
+__global__ void __launch_bounds__(CT) k_chol_prep(Chain* ch, const Consts* __restrict__ cs, int* swaps,
+                                                  Status* st) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Li = sm + MAT;
+    double* S = sm + 2 * MAT;
+    __shared__ double s_ld;
+    const int c = blockIdx.x;
+    Chain& C = ch[c];
+    if (!C.active) return;
+    const int p = cs->p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        S[i * LD + j] = C.Sigma[i * PMAX + j];
+    }
+    if (threadIdx.x == 0) swaps[c] = 0;
+    __syncthreads();
+    bool ok = make_rowparams(C.mu, C.Sigma, cs->mu_uni, cs->s_uni, p, A, Li, C.rp, &s_ld);
+    double k1 = ok ? cta_kappa1(S, Li, p) : INFINITY;
+    if (!ok || !(k1 < cs->kappa_max)) {
+        if (threadIdx.x == 0) {
+            C.active = 0;
+            C.status = CH_REFUSED;
+            C.kappa1 = k1;
+            set_warning(st, RTD_WARN_CSTEP_REFUSED);
+        }
+        return;
+    }
+    if (C.full) {
+        for (int j = threadIdx.x; j < p; j += blockDim.x) {
+            C.rp.ref[j] = C.rp.mu[j];
+            C.rp.ref_hi[j] = C.rp.mu_hi[j];
+            C.rp.ref_lo[j] = C.rp.mu_lo[j];
+        }
+    }
+    if (threadIdx.x == 0) { C.logdet = s_ld; C.kappa1 = k1; }
+}
+
+void launch_chol_prep(const Plan& P, cudaStream_t s) {
+    size_t sm = 3 * MAT * sizeof(double);
+    auto k = k_chol_prep;
+    big_smem(k, sm);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.swaps, P.st);
+}
+
+// =====================================================================
+// End of a C-step: fold the Gram partials into (S, G) (Section 3.5 update,
+// or a fresh sum), new mu and Sigma = Lambda/(h_b-1) (eqs. cstep4a/b),
+// convergence when H_new = H_old (no swaps).
+// =====================================================================
+__global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* __restrict__ cs,
+                                                       const double* __restrict__ partial, size_t slot_d,
+                                                       int cpb, const int* __restrict__ swaps, Status* st) {
+    extern __shared__ double ext[];
+    __shared__ double dmu[PMAX];
+    __shared__ double s_m2;
+    const int c = blockIdx.x, l = c / 2, k = c % 2;
+    Chain& C = ch[c];
+    if (!C.active) return;
+    const int p = cs->p, nb = gram_nb(cs->pb);
+    const double hb = (double)cs->hb;
+    sum_slots(partial, slot_d, gram_nblk(cs->pb) * 16, l, cpb, k, ext);
+    const int full = C.full;
+    const double cnt = gram_get(ext, p, p, nb);
+    if (threadIdx.x == 0) {
+        double expect = full ? hb : 0.0;
+        if (fabs(cnt - expect) > 0.5) set_error(st, RTD_EINTERNAL);
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double v = gram_get(ext, j, p, nb);
+        C.S[j] = full ? v : C.S[j] + v;
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = gram_get(ext, i, j, nb);
+        C.G[i * PMAX + j] = full ? v : C.G[i * PMAX + j] + v;
+    }
+    __syncthreads();
+    const double* su = cs->s_uni;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double mx = C.rp.ref[j] + C.S[j] / hb;
+        C.mu[j] = (mx - cs->mu_uni[j]) / su[j];
+        dmu[j] = mx - C.rp.ref[j];
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double lam = C.G[i * PMAX + j] - C.S[i] * C.S[j] / hb;
+        C.Sigma[i * PMAX + j] = lam / (hb - 1.0) / (su[i] * su[j]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // squared distance of the centre's move from the reference, under
+        // the previous fit
+        double m2 = 0.0;
+        for (int i = 0; i < p; ++i) {
+            double a = 0.0;
+            for (int j = 0; j <= i; ++j) a += C.rp.M[i * PMAX + j] * dmu[j];
+            m2 += a * a;
+        }
+        s_m2 = m2;
+        int sw = swaps[c];
+        C.swaps = sw;
+        C.steps += 1;
+        C.full_count += full;
+        if (C.steps >= 2 && sw == 0) {
+            C.active = 0;
+            C.status = CH_OK;
+        } else if (C.steps >= cs->max_steps) {
+            C.active = 0;
+            C.status = CH_MAXITER;
+            set_warning(st, RTD_WARN_MAXITER);
+        } else {
+            C.full = ((C.steps >= 2 && 4.0 * sw > hb) || s_m2 > 1.0) ? 1 : 0;
+            atomicAdd(&st->active, 1);
+        }
+    }
+}
+
+void launch_cstep_finalize(const Plan& P, cudaStream_t s) {
+    size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
+    auto k = k_cstep_finalize;
+    big_smem(k, sm);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.partial, P.slot_doubles, P.cpb, P.swaps, P.st);
+}
+
+// =====================================================================
+// Section 4 step 4: the start with the lower determinant (start 1 on ties).
+// =====================================================================
+__global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, int* chosen, Status* st) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    __shared__ int okk[2];
+    __shared__ double ldk[2];
+    const int l = blockIdx.x, p = cs->p;
+    for (int k = 0; k < 2; ++k) {
+        Chain& C = ch[2 * l + k];
+        bool has = C.started && C.steps > 0 && C.status != CH_DROPPED;
+        __syncthreads();
+        if (threadIdx.x == 0) { okk[k] = 0; ldk[k] = NAN; }
+        __syncthreads();
+        if (!has) continue;
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            A[i * LD + j] = C.Sigma[i * PMAX + j];
+        }
+        __syncthreads();
+        bool ok = cta_cholesky(A, p);
+        double ld = 0.0;
+        for (int j = threadIdx.x; j < p; j += blockDim.x) ld += log(A[j * LD + j]);
+        ld = 2.0 * cta_sum(ld);
+        if (threadIdx.x == 0) {
+            okk[k] = ok ? 1 : 0;
+            ldk[k] = ld;
+            C.logdet = ok ? ld : NAN;
+            atomicMax(&cs->csteps_max, C.steps);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int ch_ = -1;
+        if (okk[0] && okk[1]) ch_ = (ldk[0] <= ldk[1]) ? 0 : 1;
+        else if (okk[0]) ch_ = 0;
+        else if (okk[1]) ch_ = 1;
+        chosen[l] = ch_;
+        if (ch_ < 0) set_warning(st, RTD_WARN_NO_BLOCK_FIT);
+        else atomicAdd(&cs->chains_ok, okk[0] + okk[1]);
+    }
+}
+
+void launch_block_choose(const Plan& P, cudaStream_t s) {
+    size_t sm = MAT * sizeof(double);
+    auto k = k_block_choose;
+    big_smem(k, sm);
+    k<<<P.q, CT, sm, s>>>(P.ch, P.cs, P.chosen, P.st);
+}
+
+// =====================================================================
+// Section 4 steps 5-7: entrywise median of the block fits, KL deviation of
+// each fit from the median (eq. KL, log|det|), keep the ceil(q/2) closest,
+// Bennett pooling of their h-subsets.  One CTA.
+// =====================================================================
+constexpr int AGG_T = 1024;
+
+__global__ void __launch_bounds__(AGG_T) k_aggregate(const Chain* __restrict__ ch, Consts* cs,
+                                                     const int* __restrict__ chosen, int* kept, double* kl,
+                                                     double* scratch, Status* st) {
+    extern __shared__ double sm[];
+    double* Smed = sm;
+    double* A = sm + MAT;
+    double* Li = sm + 2 * MAT;
+    double* Lam = sm + 3 * MAT;
+    __shared__ int fl[1024];
+    __shared__ int s_qf;
+    __shared__ double mumed[PMAX], mup[PMAX], dv[PMAX];
+    __shared__ double s_lad, s_np;
+    const int p = cs->p, q = cs->q;
+    const double ca = cs->c_alpha, hb = (double)cs->hb;
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int l = 0; l < q && n < 1024; ++l) {
+            kept[l] = 0;
+            kl[l] = NAN;
+            if (chosen[l] >= 0) fl[n++] = l;
+        }
+        s_qf = n;
+    }
+    __syncthreads();
+    const int qf = s_qf;
+    if (qf == 0) {
+        if (threadIdx.x == 0) set_error(st, RTD_EILLCOND);
+        return;
+    }
+    if (q == 1) {
+        const Chain& C = ch[chosen[0]];
+        for (int j = threadIdx.x; j < p; j += blockDim.x) cs->mu_raw[j] = C.mu[j];
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            cs->Sigma_raw[i * PMAX + j] = ca * C.Sigma[i * PMAX + j];
+        }
+        if (threadIdx.x == 0) { kept[0] = 1; kl[0] = 0.0; }
+        return;
+    }
+    // entrywise medians (insertion sort of the qf values of each entry)
+    double* vals = scratch;   // [AGG_T][qf] work rows
+    for (int e = threadIdx.x; e < p + p * p; e += blockDim.x) {
+        double* v = vals + (size_t)threadIdx.x * qf;
+        for (int t = 0; t < qf; ++t) {
+            const Chain& C = ch[2 * fl[t] + chosen[fl[t]]];
+            double x = (e < p) ? C.mu[e] : ca * C.Sigma[((e - p) / p) * PMAX + (e - p) % p];
+            int u = t - 1;
+            while (u >= 0 && v[u] > x) { v[u + 1] = v[u]; --u; }
+            v[u + 1] = x;
+        }
+        double med = (qf & 1) ? v[qf / 2] : 0.5 * (v[qf / 2 - 1] + v[qf / 2]);
+        if (e < p) mumed[e] = med;
+        else { int i = (e - p) / p, j = (e - p) % p; Smed[i * LD + j] = med; }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        A[i * LD + j] = Smed[i * LD + j];
+    }
+    __syncthreads();
+    double lad = cta_logabsdet(A, p);
+    if (threadIdx.x == 0) s_lad = lad;
+    __syncthreads();
+    // KL of each fitted block
+    for (int t = 0; t < qf; ++t) {
+        const int l = fl[t];
+        const Chain& C = ch[2 * l + chosen[l]];
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            A[i * LD + j] = ca * C.Sigma[i * PMAX + j];
+        }
+        __syncthreads();
+        bool ok = cta_cholesky(A, p);
+        if (!ok) { if (threadIdx.x == 0) kl[l] = INFINITY; __syncthreads(); continue; }
+        cta_tri_inverse(A, Li, p);
+        double ldb = 0.0;
+        for (int j = threadIdx.x; j < p; j += blockDim.x) ldb += log(A[j * LD + j]);
+        ldb = 2.0 * cta_sum(ldb);
+        for (int j = threadIdx.x; j < p; j += blockDim.x) dv[j] = mumed[j] - C.mu[j];
+        __syncthreads();
+        // B^-1 = Li^T Li ; tr(Smed B^-1) and d^T B^-1 d
+        double tr = 0.0, quad = 0.0;
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            int k0 = i > j ? i : j;
+            double bij = 0.0;
+            for (int kk = k0; kk < p; ++kk) bij += Li[kk * LD + i] * Li[kk * LD + j];
+            tr += Smed[j * LD + i] * bij;
+            quad += dv[i] * bij * dv[j];
+        }
+        tr = cta_sum(tr);
+        quad = cta_sum(quad);
+        if (threadIdx.x == 0) {
+            double v = tr - p - (s_lad - ldb) + quad;
+            kl[l] = isfinite(v) ? v : INFINITY;
+        }
+        __syncthreads();
+    }
+    // stable order by (KL, block); keep ceil(qf/2)
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < qf; ++i) {
+            int v = fl[i];
+            int u = i - 1;
+            while (u >= 0 && kl[fl[u]] > kl[v]) { fl[u + 1] = fl[u]; --u; }
+            fl[u + 1] = v;
+        }
+        for (int i = 0; i < (qf + 1) / 2; ++i) kept[fl[i]] = 1;
+    }
+    __syncthreads();
+    // Bennett pooling over the kept blocks in KL order, counts h_b
+    const int nk = (qf + 1) / 2;
+    {
+        const Chain& C0 = ch[2 * fl[0] + chosen[fl[0]]];
+        for (int j = threadIdx.x; j < p; j += blockDim.x) mup[j] = C0.mu[j];
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            Lam[i * LD + j] = (hb - 1.0) * C0.Sigma[i * PMAX + j];
+        }
+        if (threadIdx.x == 0) s_np = hb;
+        __syncthreads();
+    }
+    for (int t = 1; t < nk; ++t) {
+        const Chain& C = ch[2 * fl[t] + chosen[fl[t]]];
+        const double np_ = s_np;
+        for (int j = threadIdx.x; j < p; j += blockDim.x) dv[j] = C.mu[j] - mup[j];
+        __syncthreads();
+        const double wgt = np_ * hb / (np_ + hb);
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            Lam[i * LD + j] += (hb - 1.0) * C.Sigma[i * PMAX + j] + dv[i] * dv[j] * wgt;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < p; j += blockDim.x) mup[j] = (np_ * mup[j] + hb * C.mu[j]) / (np_ + hb);
+        __syncthreads();
+        if (threadIdx.x == 0) s_np = np_ + hb;
+        __syncthreads();
+    }
+    const double npool = s_np;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) cs->mu_raw[j] = mup[j];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        cs->Sigma_raw[i * PMAX + j] = ca * Lam[i * LD + j] / (npool - 1.0);
+    }
+}
+
+void launch_aggregate(const Plan& P, cudaStream_t s) {
+    size_t sm = 4 * MAT * sizeof(double);
+    auto k = k_aggregate;
+    big_smem(k, sm);
+    k<<<1, AGG_T, sm, s>>>(P.ch, P.cs, P.chosen, P.kept, P.kl, P.scratch, P.st);
+}
+
+// Row parameters of the raw (which = 0) or reweighted (which = 1) fit.
+__global__ void __launch_bounds__(CT) k_fit_prep(Consts* cs, RowParams* fitrp, int which, Status* st) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Li = sm + MAT;
+    __shared__ double s_ld;
+    const int p = cs->p;
+    const double* mu = which ? cs->mu_rew : cs->mu_raw;
+    const double* S = which ? cs->Sigma_rew : cs->Sigma_raw;
+    RowParams& rp = fitrp[which];
+    bool ok = make_rowparams(mu, S, cs->mu_uni, cs->s_uni, p, A, Li, rp, &s_ld);
+    if (!ok) {
+        if (threadIdx.x == 0) set_error(st, RTD_EDEGENERATE);
+        return;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        rp.ref[j] = rp.mu[j];
+        rp.ref_hi[j] = rp.mu_hi[j];
+        rp.ref_lo[j] = rp.mu_lo[j];
+    }
+    if (threadIdx.x == 0) {
+        if (which) cs->logdet_rew = s_ld;
+        else cs->logdet_raw = s_ld;
+    }
+}
+
+void launch_fit_prep(const Plan& P, int which, cudaStream_t s) {
+    size_t sm = 2 * MAT * sizeof(double);
+    auto k = k_fit_prep;
+    big_smem(k, sm);
+    k<<<1, CT, sm, s>>>(P.cs, P.fitrp, which, P.st);
+}
+
+// Section 4 steps 8-9: mean and covariance of the reweighting set (the
+// pooled per-block moments), times the reweighting consistency factor.
+__global__ void __launch_bounds__(1024) k_rew_finalize(Consts* cs, const RowParams* __restrict__ fitrp,
+                                                       const double* __restrict__ partial, size_t slot_d,
+                                                       int q, int cpb, Status* st) {
+    extern __shared__ double ext[];
+    const int p = cs->p, nb = gram_nb(cs->pb), nv = gram_nblk(cs->pb) * 16;
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+        double s = 0.0;
+        for (int l = 0; l < q; ++l)
+            for (int b = 0; b < cpb; ++b) s += partial[(((size_t)l * cpb + b) * 2 + 0) * slot_d + e];
+        ext[e] = s;
+    }
+    __syncthreads();
+    const double nw = gram_get(ext, p, p, nb);
+    if (!(nw > (double)p + 1.0)) {
+        if (threadIdx.x == 0) set_error(st, RTD_EDEGENERATE);
+        return;
+    }
+    double f = 1.0;
+    if (cs->rew_mode == 1) f = cs->c_rew;
+    else if (cs->rew_mode == 2) f = consistency(nw / (double)cs->n, p);
+    const RowParams& rp = fitrp[0];
+    const double* su = cs->s_uni;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        double mx = rp.ref[j] + gram_get(ext, j, p, nb) / nw;
+        cs->mu_rew[j] = (mx - cs->mu_uni[j]) / su[j];
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double si = gram_get(ext, i, p, nb), sj = gram_get(ext, j, p, nb);
+        double lam = gram_get(ext, i, j, nb) - si * sj / nw;
+        cs->Sigma_rew[i * PMAX + j] = f * lam / (nw - 1.0) / (su[i] * su[j]);
+    }
+    if (threadIdx.x == 0) cs->n_rew = (long long)(nw + 0.5);
+}
+
+void launch_rew_finalize(const Plan& P, cudaStream_t s) {
+    size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
+    auto k = k_rew_finalize;
+    big_smem(k, sm);
+    k<<<1, 1024, sm, s>>>(P.cs, P.fitrp, P.partial, P.slot_doubles, P.q, P.cpb, P.st);
+}
+
+// =====================================================================
+// Result assembly (X units: mu_x = mu_uni + D mu, Sigma_x = D Sigma D) and
+// the optional diagnostics record.
+// =====================================================================
+__global__ void k_result(const Consts* __restrict__ cs, const Status* __restrict__ st,
+                         const Chain* __restrict__ ch, const int* __restrict__ chosen,
+                         const int* __restrict__ kept, const double* __restrict__ kl,
+                         rtd_result* out, double* diag) {
+    const int p = cs->p;
+    const double* su = cs->s_uni;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        out->mu[j] = cs->mu_uni[j] + su[j] * cs->mu_rew[j];
+        out->mu_raw[j] = cs->mu_uni[j] + su[j] * cs->mu_raw[j];
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        out->sigma[e] = cs->Sigma_rew[i * PMAX + j] * su[i] * su[j];
+        out->sigma_raw[e] = cs->Sigma_raw[i * PMAX + j] * su[i] * su[j];
+    }
+    if (threadIdx.x == 0) {
+        double lds = 0.0;
+        for (int j = 0; j < p; ++j) lds += 2.0 * log(su[j]);
+        out->status = st->code;
+        out->warnings = st->warnings;
+        out->p = p; out->q = cs->q;
+        out->n = cs->n; out->m = cs->m; out->h = cs->h; out->h_b = cs->hb;
+        out->logdet = cs->logdet_rew + lds;
+        out->logdet_raw = cs->logdet_raw + lds;
+        out->cutoff_d2 = cs->cutoff_d2;
+        out->n_flagged = (int64_t)st->n_flagged;
+        out->n_reweight = cs->n_rew;
+        out->csteps_max = cs->csteps_max;
+        out->chains_ok = cs->chains_ok;
+    }
+    if (!diag) return;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) { diag[j] = cs->mu_uni[j]; diag[p + j] = su[j]; }
+    const size_t rec = 3 * (size_t)p * p + 2 * p + 6;
+    const int q = cs->q;
+    for (int c = 0; c < 2 * q; ++c) {
+        const Chain& C = ch[c];
+        double* r = diag + 2 * p + (size_t)c * rec;
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            r[e] = C.Sinit[i * PMAX + j];
+            r[p * p + e] = C.Sigma0[i * PMAX + j];
+            r[2 * p * p + p + e] = C.Sigma[i * PMAX + j];
+        }
+        for (int j = threadIdx.x; j < p; j += blockDim.x) {
+            r[2 * p * p + j] = C.mu0[j];
+            r[3 * p * p + p + j] = C.mu[j];
+        }
+        if (threadIdx.x == 0) {
+            double* t = r + 3 * p * p + 2 * p;
+            t[0] = C.logdet;
+            t[1] = C.steps;
+            int stt = C.status;
+            if (stt == CH_REFUSED && C.steps > 0) stt = CH_OK;
+            t[2] = stt;
+            t[3] = C.full_count;
+            t[4] = C.swaps;
+            t[5] = C.kappa1;
+        }
+    }
+    double* b = diag + 2 * p + (size_t)2 * q * rec;
+    for (int l = threadIdx.x; l < q; l += blockDim.x) {
+        b[3 * l] = chosen[l];
+        b[3 * l + 1] = kl[l];
+        b[3 * l + 2] = kept[l];
+    }
+}
+
+void launch_result(const Plan& P, rtd_result* dev_out, double* diag, cudaStream_t s) {
+    k_result<<<1, 256, 0, s>>>(P.cs, P.st, P.ch, P.chosen, P.kept, P.kl, dev_out, diag);
+}
+
+// Scoring: row parameters of a caller fit (X units, D = I).
+__global__ void __launch_bounds__(CT) k_score_prep(const double* __restrict__ mu, const double* __restrict__ S,
+                                                   int p, RowParams* rp, Status* st) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Li = sm + MAT;
+    __shared__ double one[PMAX], zero[PMAX], Sp[PMAX * PMAX];
+    __shared__ double s_ld;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) { one[j] = 1.0; zero[j] = 0.0; }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        Sp[i * PMAX + j] = S[e];
+    }
+    __syncthreads();
+    // mu_x = 0 + 1 * mu
+    bool ok = make_rowparams(mu, Sp, zero, one, p, A, Li, *rp, &s_ld);
+    if (!ok && threadIdx.x == 0) set_error(st, RTD_EDEGENERATE);
+}
+
+void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* rp, Status* st, cudaStream_t s) {
+    size_t sm = 2 * MAT * sizeof(double);
+    auto k = k_score_prep;
+    big_smem(k, sm);
+    k<<<1, CT, sm, s>>>(mu, Sigma, p, rp, st);
+}
+
+}  // namespace rtd

@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads and exports every symbol include/rtdetmcd.h
+declares; host-side argument checks and the library's own chi-square
+routines (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rtdetmcd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1910_05615_gb300 import build as b
+    path = b.build()
+    import paper_1910_05615_gb300 as m
+    L = m._load()
+    assert os.path.samefile(path, m.library_path())
+    return L
+
+
+def declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rtdetmcd_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_chi2_quantile_matches_oracle(lib):
+    for p in (1, 2, 3, 5, 8, 20, 40, 64):
+        for q in (0.5, 0.6, 0.75, 0.975, 0.99):
+            assert lib.rtdetmcd_chi2_quantile(p, q) == pytest.approx(O.chi2_ppf(q, p), rel=1e-12)
+
+
+def test_status_strings(lib):
+    import paper_1910_05615_gb300 as m
+    for code in range(8):
+        assert m.rtdetmcd_status_string(code) != "unknown status"
+    assert m.rtdetmcd_status_string(99) == "unknown status"
+
+
+def test_workspace_size(lib):
+    import paper_1910_05615_gb300 as m
+    a = m.rtdetmcd_workspace_size(1_000_000, 20)
+    b = m.rtdetmcd_workspace_size(1_000_000, 20, precision=m.RTD_FP64)
+    assert 0 < a < b < 4 << 30
+    assert m.rtdetmcd_workspace_size(10, 20) == 0          # n <= 2p
+    assert m.rtdetmcd_workspace_size(1000, 65) == 0        # p > 64
+    assert m.rtdetmcd_diag_size(5, 1) == 8 * (10 + 2 * (75 + 10 + 6) + 3)
+
+
+@pytest.mark.parametrize("n,p,ld,h,code", [
+    (1000, 5, 5, 502, 1),      # h < [(n+p+1)/2] = 503
+    (1000, 5, 5, 1000, 1),     # h = n
+    (1000, 0, 5, 700, 1),      # p < 1
+    (1000, 65, 65, 700, 1),    # p > 64
+    (1000, 5, 4, 700, 1),      # ld < p
+    (10, 5, 5, 8, 1),          # n <= 2p
+    (1000, 5, 5, 700, 5),      # valid, but no workspace
+])
+def test_fit_rejects_before_device_work(lib, n, p, ld, h, code):
+    import paper_1910_05615_gb300 as m
+    X = np.zeros((n, max(ld, 1)), np.float32)
+    res = m._Result()
+    st = lib.rtdetmcd_fit(X.ctypes.data, n, p, ld, h, None, None, 0, None, ctypes.byref(res), None, None)
+    assert st == code and res.status == code
+
+
+def test_distances_rejects_bad_arguments(lib):
+    X = np.zeros((10, 3), np.float32)
+    mu = np.zeros(3)
+    S = np.eye(3)
+    out = np.zeros(10, np.float32)
+    st = lib.rtdetmcd_distances(X.ctypes.data, 10, 3, 2, mu.ctypes.data, S.ctypes.data, 1,
+                                out.ctypes.data, None, 0, None)
+    assert st == 1
+    st = lib.rtdetmcd_distances(X.ctypes.data, 10, 3, 3, mu.ctypes.data, S.ctypes.data, 7,
+                                out.ctypes.data, None, 0, None)
+    assert st == 1

@@ -1,0 +1,118 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle as O
+from parity import TOL, compare_fit, rel_center, rel_mat, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rtd():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1910_05615_gb300 as m
+    return m
+
+
+def _spd(p, rng, cond=50.0):
+    Q, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    ev = np.logspace(0, np.log10(cond), p)
+    return (Q * ev) @ Q.T
+
+
+# ----------------------------------------------------------- scoring (Section 6)
+@pytest.mark.parametrize("p", [1, 3, 5, 20, 37, 64])
+@pytest.mark.parametrize("host", [False, True])
+def test_distances(rtd, p, host):
+    rng = np.random.default_rng(p)
+    n = 5003 + 7 * p
+    X = (rng.standard_normal((n, p)) * 2 + 1).astype(np.float32)
+    mu = rng.standard_normal(p)
+    S = _spd(p, rng)
+    ref = O.mahalanobis_d2_plain(X, mu, S)
+    src = X if host else torch.from_numpy(X).cuda()
+    for prec, tol in ((rtd.RTD_FP64, 1e-6), (rtd.RTD_FP32, 2e-4)):
+        d2 = to_np(rtd.rtdetmcd_distances(src, mu, S, precision=prec))
+        # FP64 form: exact up to the float32 store of the result
+        err = np.max(np.abs(d2 - ref) / np.maximum(ref, 1e-3))
+        assert err < tol, (prec, err)
+
+
+def test_distances_strided(rtd):
+    rng = np.random.default_rng(0)
+    n, p, ld = 3001, 6, 11
+    buf = rng.standard_normal((n, ld)).astype(np.float32)
+    X = torch.from_numpy(buf).cuda()[:, :p]
+    mu = np.zeros(p)
+    S = _spd(p, rng)
+    d2 = to_np(rtd.rtdetmcd_distances(X, mu, S, precision=rtd.RTD_FP64))
+    ref = O.mahalanobis_d2_plain(buf[:, :p], mu, S)
+    assert np.max(np.abs(d2 - ref) / np.maximum(ref, 1e-3)) < 1e-6
+
+
+def test_flag_bit_exact(rtd):
+    rng = np.random.default_rng(1)
+    d2 = (rng.chisquare(5, 100_003)).astype(np.float32)
+    cut = O.chi2_ppf(0.975, 5)
+    d2[:10] = np.float32(cut)                      # exactly at the cutoff: not flagged
+    fl, cnt = rtd.rtdetmcd_flag(torch.from_numpy(d2).cuda(), cut)
+    ref = d2.astype(np.float64) > cut
+    assert np.array_equal(to_np(fl).astype(bool), ref) and cnt == int(ref.sum())
+    fl2, cnt2 = rtd.rtdetmcd_flag(d2, cut)         # host buffers
+    assert np.array_equal(fl2.astype(bool), ref) and cnt2 == cnt
+
+
+# ------------------------------------------------------------- whole fits
+def _fit_both(rtd, fr, form, host=False, **kw):
+    X = fr.X if host else torch.from_numpy(fr.X).cuda()
+    prec = rtd.RTD_FP32 if form == "fp32" else rtd.RTD_FP64
+    got = rtd.rtdetmcd_fit(X, fr.h, precision=prec, subset=True, diag=True, **kw)
+    ref = O.fit(fr.X, fr.h, **{k: v for k, v in kw.items() if k in ("omega", "seed", "q")})
+    return got, ref
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
+def test_fit_small_case(rtd, form):
+    """n=10,000, p=5, 10% point outliers at 10 v_min (serial algorithm, q=1)."""
+    fr = datagen.small_fp64_case()
+    got, ref = _fit_both(rtd, fr, form)
+    assert got["q"] == ref.q == 1
+    d = got["diag"]
+    np.testing.assert_allclose(d["mu_uni"], ref.mu_uni, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(d["sigma_uni"], ref.s_uni, rtol=1e-10)
+    ok, rep = compare_fit(got, ref, fr.X, form)
+    assert ok, rep
+    assert got["n_flagged"] == int(ref.flags.sum())
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
+def test_fit_blocks(rtd, form):
+    """Parallel algorithm: q = 9 blocks of a ragged n (discarded rows)."""
+    fr = datagen.contaminated_gaussian(184_331, 5, eps=0.15, kind="shift", shift=6.0, seed=4)
+    got, ref = _fit_both(rtd, fr, form)
+    assert got["q"] == ref.q == 9 and got["m"] == ref.m
+    d = got["diag"]
+    for l, b in enumerate(ref.blocks):
+        for k in range(2):
+            c = d["chains"][2 * l + k]
+            oc = b.chains[k]
+            # initial scatters S~_k are continuous functions of the data
+            assert rel_mat(c["S_init"], b.S[k]) < (1e-4 if form == "fp32" else 1e-8)
+            if oc is not None and oc.ok and c["status"] == 0:
+                assert rel_mat(c["Sigma"], oc.Sigma) < TOL[form] * 10
+        assert d["blocks"][l]["chosen"] == b.chosen
+    ok, rep = compare_fit(got, ref, fr.X, form)
+    assert ok, rep
+
+
+def test_fit_host_buffers(rtd):
+    fr = datagen.contaminated_gaussian(20_000, 6, eps=0.2, kind="cluster", shift=6.0, seed=2)
+    got, ref = _fit_both(rtd, fr, "fp32", host=True)
+    assert isinstance(got["flags"], np.ndarray)
+    ok, rep = compare_fit(got, ref, fr.X, "fp32")
+    assert ok, rep
