@@ -76,7 +76,34 @@ typedef struct {
     /* optional diagnostics (nullable, device or host), rtdetmcd_diag_size()
        bytes of doubles laid out as documented at rtdetmcd_diag_size. */
     double*  diag_out;
+    /* optional stage profile (nullable, host), filled on return */
+    struct rtd_profile* profile;
 } rtd_options;
+
+/* Stages of a fit, for rtd_profile. */
+#define RTD_STAGE_PARTITION   0   /* random partition copy (Section 4) */
+#define RTD_STAGE_UNIVARIATE  1   /* column univariate MCD (Sections 3.1, 4) */
+#define RTD_STAGE_STARTS      2   /* wrapping and GSSCM scatters (Section 3.2) */
+#define RTD_STAGE_REFINE      3   /* refinement (Section 3.3) */
+#define RTD_STAGE_CPREP       4   /* Cholesky and condition monitor per C-step (Section 3.4) */
+#define RTD_STAGE_CDIST       5   /* C-step distances + top-digit histogram */
+#define RTD_STAGE_CSELECT     6   /* radix select of the h_b smallest */
+#define RTD_STAGE_CUPDATE     7   /* membership update and Gram update (Section 3.5) */
+#define RTD_STAGE_AGGREGATE   8   /* block choice, median, KL, pooling (Section 4 steps 4-7) */
+#define RTD_STAGE_REWEIGHT    9   /* reweighting (steps 8-9) */
+#define RTD_STAGE_FINAL      10   /* final distances and flags (step 10) */
+#define RTD_NSTAGES          11
+
+/* Per-stage device time (CUDA events recorded on the fit's stream around
+   each stage), algorithmic bytes (each row and key read or written once per
+   pass) and kernel launches of one rtdetmcd_fit call. */
+typedef struct rtd_profile {
+    double  ms[RTD_NSTAGES];
+    double  bytes[RTD_NSTAGES];
+    int64_t launches[RTD_NSTAGES];
+    int32_t csteps;        /* C-step iterations run (all chains in lockstep) */
+    int32_t reserved;
+} rtd_profile;
 
 typedef struct {
     int32_t status;        /* same as the return value */

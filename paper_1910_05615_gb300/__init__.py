@@ -44,7 +44,17 @@ class _Options(ctypes.Structure):
                 ("cutoff_q", ctypes.c_double), ("kappa_max", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("reweight_consistency", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
-                ("diag_out", ctypes.c_void_p)]
+                ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p)]
+
+
+STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_dist",
+          "cstep_select", "cstep_update", "aggregate", "reweight", "final"]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("bytes", ctypes.c_double * len(STAGES)),
+                ("launches", ctypes.c_int64 * len(STAGES)), ("csteps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
@@ -173,7 +183,7 @@ def rtdetmcd_status_string(code):
 
 def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100,
                  cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, d2=True, flags=True,
-                 subset=False, diag=False, stream=None, workspace=None, check=True):
+                 subset=False, diag=False, profile=False, stream=None, workspace=None, check=True):
     """RT-DetMCD fit of the rows of X (float32, row-major) with coverage h.
 
     X on a CUDA device: outputs are CUDA tensors on the same device.  X in
@@ -200,6 +210,8 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     qq = q if q else max(min(n // (p * omega), 1024), 1)
     dg = _out(lib.rtdetmcd_diag_size(p, qq) // 8, np.float64, dev) if diag else None
     o.diag_out = _ptr(dg)
+    prof = _Profile() if profile else None
+    o.profile = ctypes.cast(ctypes.pointer(prof), ctypes.c_void_p) if profile else None
     res = _Result()
     st = lib.rtdetmcd_fit(ptr, n, p, ld, h, ctypes.byref(o), ws.data_ptr(), ws.numel(),
                           _stream_ptr(dev, stream), ctypes.byref(res), _ptr(d2_out), _ptr(fl_out))
@@ -220,6 +232,10 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     if diag:
         a = dg.cpu().numpy() if not isinstance(dg, np.ndarray) else dg
         out["diag"] = parse_diag(a, pp, res.q)
+    if profile:
+        out["profile"] = {"csteps": prof.csteps, "stages": {
+            name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i]}
+            for i, name in enumerate(STAGES)}}
     return out
 
 

@@ -40,7 +40,7 @@ struct Shape {
 struct Regions {
     Region st, cs, ch, rule, fitrp, res, xstage, d2stage, flagstage, substage, diagstage,
         Xp, perm, arenaA, arenaB, sort_hist, uni, gss, dkeys, memb, cand, band, hist, swaps,
-        partial, wset, chosen, kept, kl, scratch;
+        blk, partial, wset, chosen, kept, kl, scratch;
 };
 
 rtd_options defaults() {
@@ -56,6 +56,7 @@ rtd_options defaults() {
     o.reweight_consistency = 1;
     o.subset_out = nullptr;
     o.diag_out = nullptr;
+    o.profile = nullptr;
     return o;
 }
 
@@ -129,6 +130,7 @@ size_t layout(const Shape& S, Regions& R) {
     R.band = L.add(2 * qm * sizeof(Cand));
     R.hist = L.add(2 * q * HIST_BINS * sizeof(unsigned));
     R.swaps = L.add(2 * q * sizeof(int));
+    R.blk = L.add(q * sizeof(int));
     R.partial = L.add(q * (size_t)S.cpb * 2 * S.slot_doubles * sizeof(double));
     R.wset = L.add(qm);
     R.chosen = L.add(q * sizeof(int));
@@ -174,6 +176,52 @@ void feistel_setup(Feistel& F, long long n, unsigned long long seed, bool identi
     F.n = n;
 }
 
+// Stage profile: CUDA events recorded on the fit's stream around each stage,
+// read back at the host synchronisation points the fit already has.
+struct Prof {
+    rtd_profile* out = nullptr;
+    cudaStream_t s = nullptr;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    Rec recs[64];
+    int nrec = 0;
+    int cur = -1;
+    cudaEvent_t ea = nullptr;
+    void init(rtd_profile* o, cudaStream_t st) {
+        out = o;
+        s = st;
+        if (out) memset(out, 0, sizeof(*out));
+    }
+    void begin(int stage) {
+        if (!out) return;
+        cudaEventCreate(&ea);
+        cudaEventRecord(ea, s);
+        cur = stage;
+    }
+    void end(int launches, double bytes) {
+        if (!out) return;
+        cudaEvent_t eb;
+        cudaEventCreate(&eb);
+        cudaEventRecord(eb, s);
+        if (nrec == 64) collect();
+        recs[nrec++] = Rec{cur, ea, eb};
+        out->launches[cur] += launches;
+        out->bytes[cur] += bytes;
+    }
+    // after a stream synchronisation
+    void collect() {
+        if (!out) return;
+        for (int i = 0; i < nrec; ++i) {
+            float ms = 0.f;
+            cudaEventSynchronize(recs[i].b);
+            if (cudaEventElapsedTime(&ms, recs[i].a, recs[i].b) == cudaSuccess) out->ms[recs[i].stage] += ms;
+            cudaEventDestroy(recs[i].a);
+            cudaEventDestroy(recs[i].b);
+        }
+        nrec = 0;
+    }
+    ~Prof() { collect(); }
+};
+
 int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s,
             rtd_result* out, float* d2_out, uint8_t* flags_out) {
     Regions R;
@@ -204,6 +252,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     P.band = at<Cand>(ws, R.band);
     P.hist = at<unsigned>(ws, R.hist);
     P.swaps = at<int>(ws, R.swaps);
+    P.blk_active = at<int>(ws, R.blk);
     P.partial = at<double>(ws, R.partial);
     P.slot_doubles = S.slot_doubles;
     P.wset = at<uint8_t>(ws, R.wset);
@@ -233,22 +282,35 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     RTD_CUDA(cudaMemsetAsync(P.swaps, 0, q2 * sizeof(int), s));
 
     Status hs;
-    // Sections 3.1 and 4: setup, partition, univariate MCD of every column
-    launch_setup(P, o, s);
+    Prof pf;
+    pf.init(o.profile, s);
+    const double n_ = (double)S.n, p_ = (double)S.p, qm_ = (double)qm, K_ = (double)S.key_bytes;
+    // Section 4: random partition copy
+    pf.begin(RTD_STAGE_PARTITION);
     launch_gather(P, s);
+    pf.end(1, qm_ * p_ * 4 + qm_ * S.pb * 4);
+    // Sections 3.1 and 4: setup, univariate MCD of every column
+    pf.begin(RTD_STAGE_UNIVARIATE);
+    launch_setup(P, o, s);
     launch_col_keys(P, (uint32_t*)P.arenaA, s);
     sort_segments(P, P.arenaA, P.arenaB, 4, S.p, S.n, s);
     launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
     launch_uni_finish(P, s);
+    // rows read, keys written, 4 sort passes (read + write), window scan read
+    pf.end(4 + 3 * 4, n_ * p_ * (4 + 4 + 4 * 8 + 4));
     { int e = fetch_status(P.st, s, hs); if (e) return e; }
+    pf.collect();
     if (hs.code) goto finish;
     // Section 3.2: initial estimators per block
+    pf.begin(RTD_STAGE_STARTS);
     launch_start1(P, s);
     sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, S.q, S.m, s);
     launch_gsscm(P, P.arenaA, s);
     launch_start2(P, s);
     launch_start_reduce(P, s);
+    pf.end(4 + 3 * S.key_bytes, 2 * qm_ * p_ * 4 + qm_ * K_ * (1 + 2 * S.key_bytes));
     // Section 3.3: refinement
+    pf.begin(RTD_STAGE_REFINE);
     launch_refine_eigen(P, s);
     launch_transform(P, 0, s);
     sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
@@ -258,32 +320,60 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
     launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
     launch_refine_end(P, s);
+    pf.end(7 + 6 * S.key_bytes,
+           2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * (1 + 2 * S.key_bytes + 1)));
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
-    for (int it = 0; it <= S.max_steps; ++it) {
-        launch_chol_prep(P, s);
-        launch_dist(P, s);
-        launch_select_bucket(P, s);
-        launch_compact(P, s);
-        launch_select_finish(P, s);
-        launch_memb(P, s);
-        RTD_CUDA(cudaMemsetAsync(&P.st->active, 0, sizeof(int), s));
-        launch_cstep_finalize(P, s);
-        int e = fetch_status(P.st, s, hs);
-        if (e) return e;
-        if (hs.code || hs.active == 0) break;
+    {
+        int act_chains = 2 * S.q, act_blocks = S.q;
+        for (int it = 0; it <= S.max_steps; ++it) {
+            const double mch = (double)S.m * act_chains;
+            pf.begin(RTD_STAGE_CPREP);
+            launch_chol_prep(P, s);
+            pf.end(1, 0.0);
+            pf.begin(RTD_STAGE_CDIST);
+            launch_dist(P, s);
+            pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_);
+            pf.begin(RTD_STAGE_CSELECT);
+            launch_select_bucket(P, s);
+            launch_compact(P, s);
+            launch_select_finish(P, s);
+            pf.end(3, mch * K_);
+            pf.begin(RTD_STAGE_CUPDATE);
+            RTD_CUDA(cudaMemsetAsync(&P.st->active, 0, 3 * sizeof(int), s));
+            RTD_CUDA(cudaMemsetAsync(&P.st->gram_rows, 0, sizeof(unsigned long long), s));
+            RTD_CUDA(cudaMemsetAsync(P.blk_active, 0, (size_t)S.q * sizeof(int), s));
+            launch_memb(P, s);
+            launch_cstep_finalize(P, s);
+            pf.end(2, mch * (K_ + 2));
+            int e = fetch_status(P.st, s, hs);
+            if (e) return e;
+            if (o.profile) {
+                o.profile->bytes[RTD_STAGE_CUPDATE] += (double)hs.gram_rows * p_ * 4;
+                o.profile->csteps = it + 1;
+            }
+            pf.collect();
+            act_chains = hs.active;
+            act_blocks = hs.active_blocks;
+            if (hs.code || hs.active == 0) break;
+        }
     }
     if (hs.code) goto finish;
     // Section 4 steps 4-7
+    pf.begin(RTD_STAGE_AGGREGATE);
     launch_block_choose(P, s);
     launch_aggregate(P, s);
     launch_fit_prep(P, 0, s);
+    pf.end(3, 2 * qm_);
     // steps 8-9
+    pf.begin(RTD_STAGE_REWEIGHT);
     launch_rew(P, s);
     launch_rew_finalize(P, s);
     launch_fit_prep(P, 1, s);
+    pf.end(3, qm_ * p_ * 4 + qm_);
     {
         int e = fetch_status(P.st, s, hs);
         if (e) return e;
+        pf.collect();
         if (hs.code) goto finish;
     }
     // step 10
@@ -291,7 +381,9 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         bool d2dev = is_device_ptr(d2_out), fldev = is_device_ptr(flags_out);
         float* d2 = d2_out ? (d2dev ? d2_out : at<float>(ws, R.d2stage)) : nullptr;
         uint8_t* fl = flags_out ? (fldev ? flags_out : at<uint8_t>(ws, R.flagstage)) : nullptr;
+        pf.begin(RTD_STAGE_FINAL);
         launch_final(P, d2, fl, s);
+        pf.end(1, n_ * p_ * 4 + (d2 ? n_ * 4 : 0) + (fl ? n_ : 0));
         if (d2_out && !d2dev)
             RTD_CUDA(cudaMemcpyAsync(d2_out, d2, (size_t)S.n * sizeof(float), cudaMemcpyDeviceToHost, s));
         if (flags_out && !fldev)
@@ -321,6 +413,7 @@ finish:
             RTD_CUDA(cudaMemcpyAsync(o.diag_out, diag, rtdetmcd_diag_size(S.p, S.q), cudaMemcpyDeviceToHost, s));
         RTD_CUDA(cudaStreamSynchronize(s));
         RTD_CUDA(cudaGetLastError());
+        pf.collect();
     }
     return out->status;
 }

@@ -26,8 +26,11 @@ struct Status {
     int code;          // first RTD_E* error seen on the device
     int warnings;      // RTD_WARN_* bits
     int active;        // chains still iterating (C-step loop control)
+    int active_blocks; // blocks with an iterating chain (written by the last finalize CTA)
+    int done;          // finalize CTAs finished in this step
     int pad;
     unsigned long long n_flagged;
+    unsigned long long gram_rows;   // rows the last step's Gram update touched
 };
 
 // Per-fit constants, written by the setup kernels.

@@ -48,6 +48,7 @@ struct Plan {
     Cand* band;             // [2q][m]
     unsigned* hist;         // [2q][HIST_BINS]
     int* swaps;             // [2q]
+    int* blk_active;        // [q] iterating chains per block after a step
     double* partial;        // Gram partial slots
     size_t slot_doubles;    // doubles per slot
     uint8_t* wset;          // [q*m] reweighting set

@@ -338,15 +338,36 @@ void launch_chol_prep(const Plan& P, cudaStream_t s) {
 // or a fresh sum), new mu and Sigma = Lambda/(h_b-1) (eqs. cstep4a/b),
 // convergence when H_new = H_old (no swaps).
 // =====================================================================
+// Last of the 2q finalize CTAs: count the blocks that still iterate.
+__device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Status* st) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&st->done, 1) == 2 * q - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int a = 0;
+    for (int l = threadIdx.x; l < q; l += blockDim.x) {
+        volatile const int* b = blk;
+        a += b[l] > 0 ? 1 : 0;
+    }
+    a = (int)cta_sum((double)a);
+    if (threadIdx.x == 0) st->active_blocks = a;
+}
+
 __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* __restrict__ cs,
                                                        const double* __restrict__ partial, size_t slot_d,
-                                                       int cpb, const int* __restrict__ swaps, Status* st) {
+                                                       int cpb, const int* __restrict__ swaps, int* blk,
+                                                       Status* st) {
     extern __shared__ double ext[];
     __shared__ double dmu[PMAX];
     __shared__ double s_m2;
     const int c = blockIdx.x, l = c / 2, k = c % 2;
     Chain& C = ch[c];
-    if (!C.active) return;
+    if (!C.active) { count_active_blocks(ch, cs->q, blk, st); return; }
     const int p = cs->p, nb = gram_nb(cs->pb);
     const double hb = (double)cs->hb;
     sum_slots(partial, slot_d, gram_nblk(cs->pb) * 16, l, cpb, k, ext);
@@ -390,6 +411,7 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
         s_m2 = m2;
         int sw = swaps[c];
         C.swaps = sw;
+        atomicAdd(&st->gram_rows, (unsigned long long)(full ? cs->hb : sw));
         C.steps += 1;
         C.full_count += full;
         if (C.steps >= 2 && sw == 0) {
@@ -402,26 +424,43 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
         } else {
             C.full = ((C.steps >= 2 && 4.0 * sw > hb) || s_m2 > 1.0) ? 1 : 0;
             atomicAdd(&st->active, 1);
+            atomicAdd(&blk[l], 1);
         }
     }
+    count_active_blocks(ch, cs->q, blk, st);
 }
 
 void launch_cstep_finalize(const Plan& P, cudaStream_t s) {
     size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
     auto k = k_cstep_finalize;
     big_smem(k, sm);
-    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.partial, P.slot_doubles, P.cpb, P.swaps, P.st);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.partial, P.slot_doubles, P.cpb, P.swaps, P.blk_active, P.st);
 }
 
 // =====================================================================
 // Section 4 step 4: the start with the lower determinant (start 1 on ties).
 // =====================================================================
-__global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, int* chosen, Status* st) {
+__global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, const uint8_t* __restrict__ memb,
+                                                     int* chosen, Status* st) {
     extern __shared__ double sm[];
     double* A = sm;
     __shared__ int okk[2];
     __shared__ double ldk[2];
-    const int l = blockIdx.x, p = cs->p;
+    __shared__ int ndiff;
+    const int l = blockIdx.x, p = cs->p, m = cs->m;
+    // Two starts that reach the same h-subset have equal determinants; the
+    // comparison is then decided exactly (start 1 wins ties, as "<=").
+    if (threadIdx.x == 0) ndiff = 0;
+    __syncthreads();
+    {
+        const uint8_t* a = memb + (size_t)(2 * l) * m;
+        const uint8_t* b = memb + (size_t)(2 * l + 1) * m;
+        int d = 0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) d += ((a[t] ^ b[t]) & 1);
+        d = (int)cta_sum((double)d);
+        if (threadIdx.x == 0) ndiff = d;
+        __syncthreads();
+    }
     for (int k = 0; k < 2; ++k) {
         Chain& C = ch[2 * l + k];
         bool has = C.started && C.steps > 0 && C.status != CH_DROPPED;
@@ -448,7 +487,7 @@ __global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, int*
     }
     if (threadIdx.x == 0) {
         int ch_ = -1;
-        if (okk[0] && okk[1]) ch_ = (ldk[0] <= ldk[1]) ? 0 : 1;
+        if (okk[0] && okk[1]) ch_ = (ndiff == 0 || ldk[0] <= ldk[1]) ? 0 : 1;
         else if (okk[0]) ch_ = 0;
         else if (okk[1]) ch_ = 1;
         chosen[l] = ch_;
@@ -461,7 +500,7 @@ void launch_block_choose(const Plan& P, cudaStream_t s) {
     size_t sm = MAT * sizeof(double);
     auto k = k_block_choose;
     big_smem(k, sm);
-    k<<<P.q, CT, sm, s>>>(P.ch, P.cs, P.chosen, P.st);
+    k<<<P.q, CT, sm, s>>>(P.ch, P.cs, P.memb, P.chosen, P.st);
 }
 
 // =====================================================================

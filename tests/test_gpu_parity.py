@@ -116,3 +116,82 @@ def test_fit_host_buffers(rtd):
     assert isinstance(got["flags"], np.ndarray)
     ok, rep = compare_fit(got, ref, fr.X, "fp32")
     assert ok, rep
+
+
+# ----------------------------------------------------- full-size workload
+@pytest.fixture(scope="module")
+def main_case():
+    fr = datagen.main_case()
+    return fr, O.fit(fr.X, fr.h)
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
+def test_fit_main_case(rtd, main_case, form):
+    """n=1,000,000, p=20, h=floor(0.75n), 20% cluster outliers (q = 12)."""
+    fr, ref = main_case
+    X = torch.from_numpy(fr.X).cuda()
+    got = rtd.rtdetmcd_fit(X, fr.h, precision=rtd.RTD_FP32 if form == "fp32" else rtd.RTD_FP64,
+                           subset=True, diag=True)
+    assert got["q"] == ref.q == 12
+    ok, rep = compare_fit(got, ref, fr.X, form)
+    assert ok, rep
+    for l, b in enumerate(ref.blocks):
+        assert got["diag"]["blocks"][l]["chosen"] == b.chosen
+        assert got["diag"]["blocks"][l]["kept"] == int(l in ref.kept)
+
+
+# ------------------------------------------------------------ edge cases
+def test_nonfinite_rows(rtd):
+    fr = datagen.contaminated_gaussian(5000, 4, eps=0.0, kind="point", shift=0.0, seed=0)
+    X = fr.X.copy()
+    X[1234, 2] = np.nan
+    with pytest.raises(rtd.RtdError) as e:
+        rtd.rtdetmcd_fit(torch.from_numpy(X).cuda(), fr.h)
+    assert e.value.code == 2
+    X[1234, 2] = np.inf
+    r = rtd.rtdetmcd_fit(torch.from_numpy(X).cuda(), fr.h, check=False)
+    assert r["status"] == 2
+
+
+def test_degenerate_column(rtd):
+    fr = datagen.contaminated_gaussian(5000, 4, eps=0.0, kind="point", shift=0.0, seed=0)
+    X = fr.X.copy()
+    X[:3000, 1] = 1.0           # more than half the values equal: zero univariate MCD scale
+    with pytest.raises(O.OracleError):
+        O.fit(X, fr.h)
+    r = rtd.rtdetmcd_fit(torch.from_numpy(X).cuda(), fr.h, check=False)
+    assert r["status"] == 4
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,p,alpha,seed", [
+    (3001, 1, 0.75, 0),        # univariate data
+    (9, 3, 0.75, 1),           # the smallest sizes the definition allows here
+    (4999, 64, 0.75, 2),       # maximum dimension
+    (12_288, 3, 0.5, 3),       # h = [(n+p+1)/2], q = 1 exactly at n = p omega
+    (61_447, 2, 0.6, 5),       # q = 7, ragged tail
+])
+def test_fit_edges(rtd, form, n, p, alpha, seed):
+    fr = datagen.contaminated_gaussian(n, p, eps=0.1, kind="point", shift=9.0, seed=seed, alpha=alpha)
+    h = max(fr.h, (n + p + 1) // 2)
+    try:
+        ref = O.fit(fr.X, h)
+    except O.OracleError:
+        r = rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), h, check=False)
+        assert r["status"] != 0
+        return
+    got = rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), h,
+                           precision=rtd.RTD_FP32 if form == "fp32" else rtd.RTD_FP64,
+                           subset=True, diag=True)
+    assert got["q"] == ref.q
+    ok, rep = compare_fit(got, ref, fr.X, form)
+    assert ok, rep
+
+
+def test_fit_deterministic(rtd):
+    fr = datagen.contaminated_gaussian(50_000, 8, eps=0.2, kind="cluster", shift=7.0, seed=9)
+    X = torch.from_numpy(fr.X).cuda()
+    a = rtd.rtdetmcd_fit(X, fr.h, subset=True)
+    b = rtd.rtdetmcd_fit(X, fr.h, subset=True)
+    assert np.array_equal(a["mu"], b["mu"]) and np.array_equal(a["Sigma"], b["Sigma"])
+    assert torch.equal(a["flags"], b["flags"]) and torch.equal(a["subset"], b["subset"])
