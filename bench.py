@@ -194,8 +194,8 @@ def main():
     Xh = torch.from_numpy(fr.X).pin_memory()
     stream = torch.cuda.current_stream(dev)
     ws32 = torch.empty(rtd.rtdetmcd_workspace_size(n, p), dtype=torch.uint8, device=dev)
-    ws64 = torch.empty(rtd.rtdetmcd_workspace_size(n, p, precision=rtd.RTD_FP64), dtype=torch.uint8,
-                       device=dev)
+    ws64 = (torch.empty(rtd.rtdetmcd_workspace_size(n, p, precision=rtd.RTD_FP64), dtype=torch.uint8,
+                        device=dev) if args.fp64_steps > 0 else None)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def fit(Xin, prec, ws, profile=False):
@@ -228,8 +228,10 @@ def main():
     barrier()
     clocks = clk.stop()
     # plain FP64 form beside it
-    fit(X, rtd.RTD_FP64, ws64)
-    t64, prof64, r64 = timed(X, rtd.RTD_FP64, ws64, args.fp64_steps)
+    t64 = []
+    if args.fp64_steps > 0:
+        fit(X, rtd.RTD_FP64, ws64)
+        t64, prof64, r64 = timed(X, rtd.RTD_FP64, ws64, args.fp64_steps)
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -300,9 +302,9 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "p": p, "h": h, "q": r32["q"], "form": "fp32",
                    "l2": "512 MiB write between timed steps (input 80 MB < L2)",
                    "parallelism": f"{ws_n} independent replica(s)"},
-        "fp64_form": {"value": n / (statistics.mean(t64) / 1e3), "unit": "rows/s",
-                      "ms_per_step": statistics.mean(t64),
-                      "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps)},
+        "fp64_form": ({"value": n / (statistics.mean(t64) / 1e3), "unit": "rows/s",
+                       "ms_per_step": statistics.mean(t64),
+                       "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps)} if t64 else None),
         "roofline": roof, "stages": stages, "csteps": prof32[-1]["csteps"],
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         "n_flagged": r32["n_flagged"], "step_ms": t32,

@@ -13,7 +13,7 @@ using namespace rtd;
 
 namespace {
 
-constexpr int TARGET_CTAS = 1024;     // row-kernel CTAs per pass (all blocks)
+constexpr int TARGET_CTAS = 304;      // row-kernel CTAs per pass (all blocks): 2 per SM
 constexpr int MIN_ROWS_PER_CTA = 256;
 constexpr int MAX_BLOCKS = 1024;
 
@@ -39,8 +39,8 @@ struct Shape {
 
 struct Regions {
     Region st, cs, ch, rule, fitrp, res, xstage, d2stage, flagstage, substage, diagstage,
-        Xp, perm, arenaA, arenaB, sort_hist, uni, gss, dkeys, memb, cand, band, hist, swaps,
-        blk, partial, wset, chosen, kept, kl, scratch;
+        Xp, perm, arenaA, arenaB, sort_hist, uni, uscratch, gss, dkeys, memb, cand, band, hist, swaps,
+        blk, partial, gsum, wset, chosen, amb, kept, kl, scratch;
 };
 
 rtd_options defaults() {
@@ -123,6 +123,10 @@ size_t layout(const Shape& S, Regions& R) {
     if (h2 > hs) hs = h2;
     R.sort_hist = L.add(hs * sizeof(unsigned));
     R.uni = L.add(4 * ((2 * p * q > p) ? 2 * p * q : p) * sizeof(double));
+    {
+        size_t a = unimcd_scratch_doubles((int)p, S.n), b = unimcd_scratch_doubles(2 * (int)(p * q), S.m);
+        R.uscratch = L.add((a > b ? a : b) * sizeof(double));
+    }
     R.gss = L.add(2 * q * sizeof(double));
     R.dkeys = L.add(2 * qm * K);
     R.memb = L.add(2 * qm);
@@ -132,11 +136,13 @@ size_t layout(const Shape& S, Regions& R) {
     R.swaps = L.add(2 * q * sizeof(int));
     R.blk = L.add(q * sizeof(int));
     R.partial = L.add(q * (size_t)S.cpb * 2 * S.slot_doubles * sizeof(double));
+    R.gsum = L.add(2 * q * S.slot_doubles * sizeof(double));
     R.wset = L.add(qm);
     R.chosen = L.add(q * sizeof(int));
+    R.amb = L.add(q * sizeof(int));
     R.kept = L.add(q * sizeof(int));
     R.kl = L.add(q * sizeof(double));
-    R.scratch = L.add(1024 * q * sizeof(double));
+    R.scratch = L.add(((p + p * p) * (q + 1) + 64) * sizeof(double));
     return (L.total + 255) & ~(size_t)255;
 }
 
@@ -233,6 +239,11 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     int dev = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     RTD_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, dev));
+    {   // distance pass: about four CTAs per SM, at least 512 rows each
+        long long cd = (4LL * P.nsm + S.q - 1) / S.q;
+        long long lim = (S.m + 511) / 512;
+        P.cpb_dist = (int)(cd < lim ? (cd > 0 ? cd : 1) : lim);
+    }
     feistel_setup(P.F, S.n, o.seed, S.q == 1);
     P.st = at<Status>(ws, R.st);
     P.cs = at<Consts>(ws, R.cs);
@@ -245,6 +256,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     P.arenaB = at<void>(ws, R.arenaB);
     P.sort_hist = at<unsigned>(ws, R.sort_hist);
     P.uni = at<double>(ws, R.uni);
+    P.uscratch = at<double>(ws, R.uscratch);
     P.gss = at<double>(ws, R.gss);
     P.dkeys = at<void>(ws, R.dkeys);
     P.memb = at<uint8_t>(ws, R.memb);
@@ -255,8 +267,10 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     P.blk_active = at<int>(ws, R.blk);
     P.partial = at<double>(ws, R.partial);
     P.slot_doubles = S.slot_doubles;
+    P.gsum = at<double>(ws, R.gsum);
     P.wset = at<uint8_t>(ws, R.wset);
     P.chosen = at<int>(ws, R.chosen);
+    P.amb = at<int>(ws, R.amb);
     P.kept = at<int>(ws, R.kept);
     P.kl = at<double>(ws, R.kl);
     P.scratch = at<double>(ws, R.scratch);
@@ -297,7 +311,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
     launch_uni_finish(P, s);
     // rows read, keys written, 4 sort passes (read + write), window scan read
-    pf.end(4 + 3 * 4, n_ * p_ * (4 + 4 + 4 * 8 + 4));
+    pf.end(6 + 3 * 4, n_ * p_ * (4 + 4 + 4 * 8 + 4));
     { int e = fetch_status(P.st, s, hs); if (e) return e; }
     pf.collect();
     if (hs.code) goto finish;
@@ -308,7 +322,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     launch_gsscm(P, P.arenaA, s);
     launch_start2(P, s);
     launch_start_reduce(P, s);
-    pf.end(4 + 3 * S.key_bytes, 2 * qm_ * p_ * 4 + qm_ * K_ * (1 + 2 * S.key_bytes));
+    pf.end(5 + 3 * S.key_bytes, 2 * qm_ * p_ * 4 + qm_ * K_ * (1 + 2 * S.key_bytes));
     // Section 3.3: refinement
     pf.begin(RTD_STAGE_REFINE);
     launch_refine_eigen(P, s);
@@ -320,7 +334,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
     launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
     launch_refine_end(P, s);
-    pf.end(7 + 6 * S.key_bytes,
+    pf.end(11 + 6 * S.key_bytes,
            2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * (1 + 2 * S.key_bytes + 1)));
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
     {
@@ -344,7 +358,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
             RTD_CUDA(cudaMemsetAsync(P.blk_active, 0, (size_t)S.q * sizeof(int), s));
             launch_memb(P, s);
             launch_cstep_finalize(P, s);
-            pf.end(2, mch * (K_ + 2));
+            pf.end(3, mch * (K_ + 2));
             int e = fetch_status(P.st, s, hs);
             if (e) return e;
             if (o.profile) {
@@ -361,15 +375,16 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     // Section 4 steps 4-7
     pf.begin(RTD_STAGE_AGGREGATE);
     launch_block_choose(P, s);
+    if (S.precision == RTD_FP32) launch_rechoose(P, s);
     launch_aggregate(P, s);
     launch_fit_prep(P, 0, s);
-    pf.end(3, 2 * qm_);
+    pf.end((S.q == 1 ? 3 : 5) + (S.precision == RTD_FP32 ? 3 : 0), 2 * qm_);
     // steps 8-9
     pf.begin(RTD_STAGE_REWEIGHT);
     launch_rew(P, s);
     launch_rew_finalize(P, s);
     launch_fit_prep(P, 1, s);
-    pf.end(3, qm_ * p_ * 4 + qm_);
+    pf.end(4, qm_ * p_ * 4 + qm_);
     {
         int e = fetch_status(P.st, s, hs);
         if (e) return e;

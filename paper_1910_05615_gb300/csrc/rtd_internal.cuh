@@ -26,6 +26,7 @@ __host__ __device__ inline unsigned long long splitmix64(unsigned long long z) {
 struct Plan {
     long long n, h, ld;
     int p, pb, q, m, hb, precision, cpb, nsm, max_steps;
+    int cpb_dist;           // CTAs per block of the distance and compaction passes
     int key_bytes;          // 4 (FP32 form) or 8 (FP64 form) for refinement sorts
     Feistel F;
     // device buffers
@@ -41,6 +42,7 @@ struct Plan {
     void* arenaB;           // sort arena (pong)
     unsigned* sort_hist;
     double* uni;            // per-segment univariate MCD results (4 doubles)
+    double* uscratch;       // univariate MCD chunk sums and window argmins
     double* gss;            // per-block GSSCM cutoffs (A, B)
     void* dkeys;            // C-step distance keys [2][q*m]
     uint8_t* memb;          // [2q][m] membership bytes
@@ -50,9 +52,11 @@ struct Plan {
     int* swaps;             // [2q]
     int* blk_active;        // [q] iterating chains per block after a step
     double* partial;        // Gram partial slots
+    double* gsum;           // reduced Gram of each chain [2q][slot]
     size_t slot_doubles;    // doubles per slot
     uint8_t* wset;          // [q*m] reweighting set
     int* chosen;            // [q] chosen start per block (-1 none)
+    int* amb;               // [q] start choice within the FP32 error band
     int* kept;              // [q] block kept by the aggregation
     double* kl;             // [q] KL deviation of each block fit
     double* scratch;        // FP64 scratch of the aggregation (p + p^2 + ...)
@@ -70,6 +74,7 @@ void launch_memb(const Plan& P, cudaStream_t s);
 void launch_rew(const Plan& P, cudaStream_t s);
 void launch_final(const Plan& P, float* d2_out, uint8_t* flags_out, cudaStream_t s);
 void launch_subset_out(const Plan& P, uint8_t* out, cudaStream_t s);
+void launch_member_gram(const Plan& P, cudaStream_t s);
 void launch_score(const float* X, long long n, int p, long long ld, const RowParams* rp,
                   int precision, float* d2_out, cudaStream_t s);
 void launch_flag(const float* d2, long long n, double cut, uint8_t* flags,
@@ -80,6 +85,7 @@ void sort_segments(const Plan& P, void* keys, void* tmp, int key_bytes, int nseg
                    long long L, cudaStream_t s);
 void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L,
                    int which_c1, double* out, cudaStream_t s);
+size_t unimcd_scratch_doubles(int nseg, long long L);
 void launch_gsscm(const Plan& P, const void* rkeys, cudaStream_t s);
 void launch_select_bucket(const Plan& P, cudaStream_t s);
 void launch_select_finish(const Plan& P, cudaStream_t s);
@@ -94,6 +100,7 @@ void launch_refine_end(const Plan& P, cudaStream_t s);
 void launch_chol_prep(const Plan& P, cudaStream_t s);
 void launch_cstep_finalize(const Plan& P, cudaStream_t s);
 void launch_block_choose(const Plan& P, cudaStream_t s);
+void launch_rechoose(const Plan& P, cudaStream_t s);
 void launch_aggregate(const Plan& P, cudaStream_t s);
 void launch_fit_prep(const Plan& P, int which, cudaStream_t s);
 void launch_rew_finalize(const Plan& P, cudaStream_t s);

@@ -96,17 +96,20 @@ __device__ inline double cta_max(double v) {
 }
 
 // kappa_1 = ||S||_1 ||S^-1||_1 with S^-1 = Li^T Li (Section 3.4; exact).
-__device__ inline double cta_kappa1(const double* S, const double* Li, int p) {
+// W is a p x p shared scratch matrix.
+__device__ inline double cta_kappa1(const double* S, const double* Li, double* W, int p) {
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        int k0 = i > j ? i : j;
+        double v = 0.0;
+        for (int k = k0; k < p; ++k) v += Li[k * LD + i] * Li[k * LD + j];
+        W[i * LD + j] = v;
+    }
+    __syncthreads();
     double n1 = 0.0, n1i = 0.0;
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         double cs = 0.0, csi = 0.0;
-        for (int i = 0; i < p; ++i) {
-            cs += fabs(S[i * LD + j]);
-            int k0 = i > j ? i : j;
-            double v = 0.0;
-            for (int k = k0; k < p; ++k) v += Li[k * LD + i] * Li[k * LD + j];
-            csi += fabs(v);
-        }
+        for (int i = 0; i < p; ++i) { cs += fabs(S[i * LD + j]); csi += fabs(W[i * LD + j]); }
         n1 = fmax(n1, cs);
         n1i = fmax(n1i, csi);
     }
@@ -131,7 +134,7 @@ __device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, doub
     __syncthreads();
     const int P = p + (p & 1);
     const int half = P / 2;
-    for (int sweep = 0; sweep < 60 && p > 1; ++sweep) {
+    for (int sweep = 0; sweep < 40 && p > 1; ++sweep) {
         double off = 0.0, dg = 0.0;
         for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
             int i = e / p, j = e % p;
@@ -140,7 +143,8 @@ __device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, doub
         }
         off = cta_sum(off);
         dg = cta_sum(dg);
-        if (off <= 1e-32 * dg || off == 0.0) break;
+        // converged: off-diagonal norm below 1e-14 of the diagonal norm
+        if (off <= 1e-28 * dg || off == 0.0) break;
         for (int round = 0; round < P - 1; ++round) {
             if (threadIdx.x < half) {
                 int k = threadIdx.x;

@@ -10,15 +10,31 @@ namespace rtd {
 // =====================================================================
 __global__ void k_gather(const float* __restrict__ X, long long ld, int p, int pb, long long nq,
                          Feistel F, float* __restrict__ Xp, int* __restrict__ perm, Status* st) {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = tid; e < nq * pb; e += stride) {
-        long long t = e / pb;
-        int j = (int)(e - t * pb);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const bool vec = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += stride) {
         long long src = feistel_perm(F, t);
-        if (src < 0) { set_error(st, RTD_EINTERNAL); Xp[e] = 0.f; continue; }
-        if (j == 0) perm[t] = (int)src;
-        Xp[e] = (j < p) ? X[src * ld + j] : 0.f;
+        float4* dst = reinterpret_cast<float4*>(Xp + t * pb);
+        if (src < 0) {
+            set_error(st, RTD_EINTERNAL);
+            for (int j = 0; j < pb / 4; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        perm[t] = (int)src;
+        const float* row = X + src * ld;
+        if (vec) {
+            const float4* r4 = reinterpret_cast<const float4*>(row);
+            for (int j = 0; j < pb / 4; ++j) dst[j] = (4 * j < p) ? __ldg(r4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            for (int j = 0; j < pb / 4; ++j) {
+                float4 v;
+                v.x = (4 * j + 0 < p) ? __ldg(row + 4 * j + 0) : 0.f;
+                v.y = (4 * j + 1 < p) ? __ldg(row + 4 * j + 1) : 0.f;
+                v.z = (4 * j + 2 < p) ? __ldg(row + 4 * j + 2) : 0.f;
+                v.w = (4 * j + 3 < p) ? __ldg(row + 4 * j + 3) : 0.f;
+                dst[j] = v;
+            }
+        }
     }
 }
 
@@ -104,12 +120,12 @@ __global__ void __launch_bounds__(NT) k_compact(const T* __restrict__ dkeys, int
 }
 
 void launch_compact(const Plan& P, cudaStream_t s) {
-    dim3 grid(P.cpb, P.q);
+    dim3 grid(P.cpb_dist, P.q);
     long long qm = (long long)P.q * P.m;
     if (P.precision == RTD_FP64)
-        k_compact<double><<<grid, NT, 0, s>>>((const double*)P.dkeys, P.m, P.cpb, qm, P.ch, P.rule, P.cand);
+        k_compact<double><<<grid, NT, 0, s>>>((const double*)P.dkeys, P.m, P.cpb_dist, qm, P.ch, P.rule, P.cand);
     else
-        k_compact<float><<<grid, NT, 0, s>>>((const float*)P.dkeys, P.m, P.cpb, qm, P.ch, P.rule, P.cand);
+        k_compact<float><<<grid, NT, 0, s>>>((const float*)P.dkeys, P.m, P.cpb_dist, qm, P.ch, P.rule, P.cand);
 }
 
 
@@ -174,6 +190,7 @@ void launch_transform(const Plan& P, int which, cudaStream_t s) { (void)which; R
 void launch_dist(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist, P, s); }
 void launch_memb(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, memb, P, s); }
 void launch_rew(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, rew, P, s); }
+void launch_member_gram(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, member_gram, P, s); }
 
 void launch_final(const Plan& P, float* d2_out, uint8_t* flags_out, cudaStream_t s) {
     RTD_PB_CALL(P.pb, final, P.X, P.n, P.p, P.ld, P.precision, P.fitrp + 1, &P.cs->cutoff_d2, 1,

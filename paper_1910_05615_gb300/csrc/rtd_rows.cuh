@@ -101,19 +101,20 @@ __device__ inline int cta_sum_int(int v) {
 // length PE = PB + 4, as 4 x 4 register blocks (bi <= bj).  Thread groups
 // take interleaved rows; products in T, running sums flushed to FP64 every
 // FLUSH rows (T = float) so that FP32 rounding stays local.
-template <int PB>
+template <int PB, typename T>
 struct GramShape {
     static constexpr int PE = PB + 4;
     static constexpr int NB = PE / 4;
     static constexpr int NBLK = NB * (NB + 1) / 2;
     static constexpr int G = (NT / NBLK) > 0 ? (NT / NBLK) : 1;
-    static constexpr int TR = PB >= 48 ? 64 : 128;
+    // rows staged per tile: every thread loads one row where shared memory allows
+    static constexpr int TR = (PE * (int)sizeof(T) <= 160) ? 256 : ((PE * (int)sizeof(T) <= 320) ? 128 : 64);
     static constexpr int FLUSH = 64;
 };
 
 template <int PB, typename T>
 struct GramAcc {
-    typedef GramShape<PB> S;
+    typedef GramShape<PB, T> S;
     double a64[16];
     T a32[16];
     int since, bi, bj, g;
@@ -173,7 +174,7 @@ struct GramAcc {
 
 template <int PB, typename T>
 constexpr size_t gram_smem_bytes() {
-    typedef GramShape<PB> S;
+    typedef GramShape<PB, T> S;
     size_t tile = (size_t)S::TR * S::PE * sizeof(T) + (size_t)S::TR * sizeof(T);
     size_t red = (size_t)S::G * S::NBLK * 16 * sizeof(double);
     return tile > red ? tile : red;
@@ -200,6 +201,69 @@ __device__ inline void block_rows(int m, int cpb, int& r0, int& r1) {
 
 __device__ inline unsigned long long full_key(float d) { return (unsigned long long)__float_as_uint(d); }
 __device__ inline unsigned long long full_key(double d) { return (unsigned long long)__double_as_longlong(d); }
+
+// Blocks whose start choice lies within the FP32 error band: FP64 Gram of
+// the rows in exactly one of the two final h-subsets, +1 for start 2 and -1
+// for start 1, relative to start 1's reference centre.  With it the
+// log-determinant difference of the two subsets is exact (Section 4 step 4).
+template <int PB>
+__global__ void __launch_bounds__(NT) k_diff_gram(const float* __restrict__ Xp, int p, int m, int cpb,
+                                                  const Chain* __restrict__ ch, const int* __restrict__ amb,
+                                                  const uint8_t* __restrict__ memb, double* __restrict__ partial,
+                                                  size_t slot_d) {
+    typedef double T;
+    typedef GramShape<PB, T> S;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* tile = reinterpret_cast<T*>(smem);
+    T* wt = tile + S::TR * S::PE;
+    __shared__ double s_ref[PB];
+    const int l = blockIdx.y;
+    if (!amb[l]) return;
+    int r0, r1;
+    block_rows(m, cpb, r0, r1);
+    for (int j = threadIdx.x; j < PB; j += NT) s_ref[j] = (j < p) ? ch[2 * l].rp.ref[j] : 0.0;
+    __syncthreads();
+    const uint8_t* m0 = memb + (size_t)(2 * l) * m;
+    const uint8_t* m1 = memb + (size_t)(2 * l + 1) * m;
+    GramAcc<PB, T> acc;
+    acc.init();
+    for (int base = r0; base < r1; base += S::TR) {
+        int row = base + threadIdx.x;
+        bool inc = false;
+        T w = 0.0;
+        if (threadIdx.x < S::TR && row < r1) {
+            int a = m0[row - l * m] & 1, b = m1[row - l * m] & 1;
+            inc = a != b;
+            w = b ? 1.0 : -1.0;
+        }
+        int tot;
+        int slot = cta_compact(inc, tot);
+        if (slot >= 0) {
+            float x[PB];
+            load_row_padded<PB>(Xp + (size_t)row * PB, x);
+            T* dst = tile + slot * S::PE;
+#pragma unroll
+            for (int j = 0; j < PB; ++j) dst[j] = (double)x[j] - s_ref[j];
+            dst[PB] = 0.0; dst[PB + 1] = 0.0; dst[PB + 2] = 0.0; dst[PB + 3] = 0.0;
+            dst[p] = 1.0;
+            wt[slot] = w;
+        }
+        __syncthreads();
+        if (tot) acc.rows(tile, wt, tot);
+        __syncthreads();
+    }
+    size_t sl = ((size_t)l * cpb + blockIdx.x) * 2;
+    acc.store(reinterpret_cast<double*>(smem), partial + sl * slot_d);
+}
+
+template <int PB>
+void member_gram_t(const Plan& P, cudaStream_t s) {
+    size_t sm = gram_smem_bytes<PB, double>();
+    auto k = k_diff_gram<PB>;
+    set_smem(k, sm);
+    dim3 grid(P.cpb, P.q);
+    k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb, P.ch, P.amb, P.memb, P.partial, P.slot_doubles);
+}
 
 // FP64 distance of one row (band recomputation).
 __device__ inline double d2_fp64(const float* __restrict__ x, const RowParams& rp, int p) {
@@ -232,7 +296,7 @@ template <int PB, typename T, typename K>
 __global__ void __launch_bounds__(NT) k_start1(const float* __restrict__ Xp, int p, int m, int cpb,
                                                const Consts* __restrict__ cs, K* __restrict__ rkeys,
                                                double* __restrict__ partial, size_t slot_d) {
-    typedef GramShape<PB> S;
+    typedef GramShape<PB, T> S;
     extern __shared__ __align__(16) unsigned char smem[];
     T* tile = reinterpret_cast<T*>(smem);
     T* wt = tile + S::TR * S::PE;
@@ -284,7 +348,7 @@ template <int PB, typename T, typename K>
 __global__ void __launch_bounds__(NT) k_start2(const float* __restrict__ Xp, int p, int m, int cpb,
                                                const Consts* __restrict__ cs, const double* __restrict__ gss,
                                                double* __restrict__ partial, size_t slot_d) {
-    typedef GramShape<PB> S;
+    typedef GramShape<PB, T> S;
     extern __shared__ __align__(16) unsigned char smem[];
     T* tile = reinterpret_cast<T*>(smem);
     T* wt = tile + S::TR * S::PE;
@@ -427,7 +491,7 @@ template <> struct Vec4<double> {
     }
 };
 
-template <int PB, typename T> struct DistRows { static constexpr int R = PB <= 24 ? 4 : (PB <= 48 ? 2 : 1); };
+template <int PB, typename T> struct DistRows { static constexpr int R = (PB <= 24 && sizeof(T) == 4) ? 2 : 1; };
 
 // y = M c row by row (lower triangular M, row stride PB, zero above the
 // diagonal), d2 = sum y^2, for R rows at once.
@@ -468,7 +532,7 @@ template <> __device__ inline float load_m<float>(const RowParams& rp, int i, in
 template <> __device__ inline double load_m<double>(const RowParams& rp, int i, int j) { return rp.M[i * PMAX + j]; }
 
 template <int PB, typename T>
-__global__ void __launch_bounds__(NT) k_dist(const float* __restrict__ Xp, int p, int m, int cpb,
+__global__ void __launch_bounds__(NT, 2) k_dist(const float* __restrict__ Xp, int p, int m, int cpb,
                                              const Chain* __restrict__ ch, T* __restrict__ dkeys,
                                              long long qm, unsigned* __restrict__ hist) {
     constexpr int R = DistRows<PB, T>::R;
@@ -533,11 +597,11 @@ __global__ void __launch_bounds__(NT) k_dist(const float* __restrict__ Xp, int p
 
 template <int PB, typename T>
 void dist_t(const Plan& P, cudaStream_t s) {
-    dim3 grid(P.cpb, P.q);
+    dim3 grid(P.cpb_dist, P.q);
     size_t sm = 2 * PB * PB * sizeof(T) + 2 * HIST_BINS * sizeof(unsigned);
     auto k = k_dist<PB, T>;
     set_smem(k, sm);
-    k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb, P.ch, (T*)P.dkeys, (long long)P.q * P.m, P.hist);
+    k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb_dist, P.ch, (T*)P.dkeys, (long long)P.q * P.m, P.hist);
 }
 // =====================================================================
 // Membership update and update-based C-step (Section 3.5).  A row whose
@@ -553,7 +617,7 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
                                              const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
                                              uint8_t* __restrict__ memb, int* __restrict__ swaps,
                                              double* __restrict__ partial, size_t slot_d) {
-    typedef GramShape<PB> S;
+    typedef GramShape<PB, T> S;
     extern __shared__ __align__(16) unsigned char smem[];
     T* tile = reinterpret_cast<T*>(smem);
     T* wt = tile + S::TR * S::PE;
@@ -639,7 +703,7 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
                                             const Consts* __restrict__ cs, const RowParams* __restrict__ rp,
                                             uint8_t* __restrict__ wset, double* __restrict__ partial,
                                             size_t slot_d) {
-    typedef GramShape<PB> S;
+    typedef GramShape<PB, T> S;
     constexpr int R = 1;
     extern __shared__ __align__(16) unsigned char smem[];
     T* tile = reinterpret_cast<T*>(smem);
@@ -716,7 +780,7 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
                                               int vec4, int fp32, const RowParams* __restrict__ rp,
                                               const double* __restrict__ cutp, int decide, float* __restrict__ d2_out,
                                               uint8_t* __restrict__ flags, unsigned long long* __restrict__ count) {
-    constexpr int R = 1;
+    constexpr int R = DistRows<PB, T>::R;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sM = reinterpret_cast<T*>(smem);
     __shared__ T s_hi[PB], s_lo[PB];
@@ -733,26 +797,29 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
     const double cut = cutp ? *cutp : INFINITY;
     const T cut_lo = (T)(cut * (1.0 - BAND_EPS)), cut_hi = (T)(cut * (1.0 + BAND_EPS));
     int nflag = 0;
-    long long stride = (long long)gridDim.x * NT;
-    long long start = (long long)blockIdx.x * NT;
-    for (long long base = start; base < n; base += stride) {
-        long long i = base + threadIdx.x;
-        if (i < n) {
-            float x[PB];
-            load_row_user<PB>(X + i * ld, p, vec4 != 0, x);
-            T c[R][PB];
+    const long long stride = (long long)gridDim.x * NT * R;
+    for (long long base = ((long long)blockIdx.x * NT + threadIdx.x) * R; base < n; base += stride) {
+        T c[R][PB];
+        float xs[R][PB];
 #pragma unroll
-            for (int j = 0; j < PB; ++j) c[0][j] = ((T)x[j] - s_hi[j]) - s_lo[j];
-            T d2[R];
-            tri_d2<PB, T, R>(sM, p, c, d2);
-            double d = (double)d2[0];
-            bool out;
-            if (fp32 && decide && d2[0] >= cut_lo && d2[0] <= cut_hi) {
-                d = d2_fp64(x, *rp, p);
-                out = d > cut;
-            } else {
-                out = d > cut;
+        for (int r = 0; r < R; ++r) {
+            if (base + r < n) load_row_user<PB>(X + (base + r) * ld, p, vec4 != 0, xs[r]);
+            else {
+#pragma unroll
+                for (int j = 0; j < PB; ++j) xs[r][j] = 0.f;
             }
+#pragma unroll
+            for (int j = 0; j < PB; ++j) c[r][j] = ((T)xs[r][j] - s_hi[j]) - s_lo[j];
+        }
+        T d2[R];
+        tri_d2<PB, T, R>(sM, p, c, d2);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long i = base + r;
+            if (i >= n) continue;
+            double d = (double)d2[r];
+            if (fp32 && decide && d2[r] >= cut_lo && d2[r] <= cut_hi) d = d2_fp64(xs[r], *rp, p);
+            const bool out = d > cut;
             if (d2_out) d2_out[i] = (float)d;
             if (flags) flags[i] = out ? 1 : 0;
             nflag += out ? 1 : 0;
@@ -770,8 +837,9 @@ void final_t(const float* X, long long n, int p, long long ld, int fp32, const R
                     int nsm, cudaStream_t s) {
     // float4 rows only when they hold whole float4s: no read past column p
     int vec4 = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    long long blocks = (n + NT - 1) / NT;
-    int grid = (int)(blocks < (long long)nsm * 16 ? blocks : (long long)nsm * 16);
+    constexpr int R = DistRows<PB, T>::R;
+    long long blocks = (n + (long long)NT * R - 1) / ((long long)NT * R);
+    int grid = (int)(blocks < (long long)nsm * 4 ? blocks : (long long)nsm * 4);
     if (grid < 1) grid = 1;
     size_t sm = PB * PB * sizeof(T);
     auto k = k_final<PB, T>;

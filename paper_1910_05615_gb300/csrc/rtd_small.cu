@@ -8,6 +8,7 @@
 namespace rtd {
 
 constexpr int CT = 256;     // threads of the per-chain kernels
+constexpr int AGG_T = 1024;
 constexpr size_t MAT = (size_t)PMAX * LD;   // doubles of one shared matrix
 
 template <typename K>
@@ -15,42 +16,87 @@ inline void big_smem(K kernel, size_t bytes) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Sum of the Gram slots of chain slot k of block l over its CTAs, in order.
-__device__ inline void sum_slots(const double* __restrict__ partial, size_t slot_d, int nvals,
-                                 int l, int cpb, int k, double* __restrict__ out) {
-    for (int e = threadIdx.x; e < nvals; e += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < cpb; ++b) s += partial[(((size_t)l * cpb + b) * 2 + k) * slot_d + e];
-        out[e] = s;
+// Deterministic reduction of the Gram partial slots written by the row
+// kernels: out[c][e] = sum over the CTAs b of block l = c / 2 of slot
+// ((l cpb + b) 2 + c % 2)[e] (mode 0, one output per chain), or the sum of
+// slot ((l cpb + b) 2)[e] over every block and CTA (mode 1, one output).
+// Lanes take consecutive values, warps interleaved slots, and the warps are
+// combined in a fixed order.
+__global__ void __launch_bounds__(256) k_reduce_slots(const double* __restrict__ partial, size_t slot_d,
+                                                      int nvals, int q, int cpb, int mode,
+                                                      double* __restrict__ out) {
+    __shared__ double red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    const int c = blockIdx.y;
+    double acc = 0.0;
+    if (e < nvals) {
+        if (mode == 0) {
+            const int l = c / 2, k = c % 2;
+            for (int b = w; b < cpb; b += 8) acc += partial[(((size_t)l * cpb + b) * 2 + k) * slot_d + e];
+        } else {
+            const int ns = q * cpb;
+            for (int t = w; t < ns; t += 8) acc += partial[((size_t)t * 2) * slot_d + e];
+        }
     }
+    red[w][lane] = acc;
     __syncthreads();
+    if (w == 0 && e < nvals) {
+        double s = 0.0;
+        for (int ww = 0; ww < 8; ++ww) s += red[ww][lane];
+        out[(size_t)c * slot_d + e] = s;
+    }
+}
+
+void launch_reduce_slots(const Plan& P, int mode, cudaStream_t s) {
+    const int nv = gram_nblk(P.pb) * 16;
+    dim3 grid((nv + 31) / 32, mode == 0 ? 2 * P.q : 1);
+    k_reduce_slots<<<grid, 256, 0, s>>>(P.partial, P.slot_doubles, nv, P.q, P.cpb, mode, P.gsum);
 }
 
 // =====================================================================
 // Constants of Section 2.1 (c(alpha), chi-square cutoffs) and of the
 // univariate MCD (Section 3.1).
 // =====================================================================
+// Scalars of one fit, written by the host: they depend only on (n, p, h, m)
+// and are the same chi-square functions the device uses.
+struct SetupScalars {
+    double alpha, c_alpha, cutoff_d2, c_rew, kappa_max, uni_cut2, crew1, c1_n, c1_m;
+};
+
 __global__ void k_setup(Consts* cs, long long n, int p, int pb, int q, int m, int hb, long long h,
-                        int precision, int max_steps, int rew_mode, double cutoff_q, double kappa_max) {
+                        int precision, int max_steps, int rew_mode, SetupScalars sc) {
     if (threadIdx.x != 0) return;
     cs->n = (int)n; cs->p = p; cs->pb = pb; cs->q = q; cs->m = m; cs->hb = hb; cs->h = h;
     cs->precision = precision; cs->max_steps = max_steps; cs->rew_mode = rew_mode;
-    cs->alpha = (double)h / (double)n;
-    cs->c_alpha = consistency(cs->alpha, p);
-    cs->cutoff_d2 = chi2_quantile(p, cutoff_q);
-    cs->c_rew = cutoff_q / chi2_cdf(cs->cutoff_d2, p + 2);
-    cs->kappa_max = kappa_max;
-    cs->uni_cut2 = chi2_quantile(1, cutoff_q);
-    cs->crew1 = cutoff_q / chi2_cdf(cs->uni_cut2, 3);
-    cs->c1_n = consistency((double)(n / 2 + 1) / (double)n, 1);
-    cs->c1_m = consistency((double)(m / 2 + 1) / (double)m, 1);
+    cs->alpha = sc.alpha;
+    cs->c_alpha = sc.c_alpha;
+    cs->cutoff_d2 = sc.cutoff_d2;
+    cs->c_rew = sc.c_rew;
+    cs->kappa_max = sc.kappa_max;
+    cs->uni_cut2 = sc.uni_cut2;
+    cs->crew1 = sc.crew1;
+    cs->c1_n = sc.c1_n;
+    cs->c1_m = sc.c1_m;
     cs->chains_ok = 0;
     cs->csteps_max = 0;
 }
 
 void launch_setup(const Plan& P, const rtd_options& o, cudaStream_t s) {
+    SetupScalars sc;
+    // Section 2.1: c(alpha), alpha = h/n; cutoff chi2_{p,q}; reweighting factor
+    sc.alpha = (double)P.h / (double)P.n;
+    sc.c_alpha = consistency(sc.alpha, P.p);
+    sc.cutoff_d2 = chi2_quantile(P.p, o.cutoff_q);
+    sc.c_rew = o.cutoff_q / chi2_cdf(sc.cutoff_d2, P.p + 2);
+    sc.kappa_max = o.kappa_max;
+    // Section 3.1: univariate MCD with coverage [L/2] + 1 of L = n and L = m
+    sc.uni_cut2 = chi2_quantile(1, o.cutoff_q);
+    sc.crew1 = o.cutoff_q / chi2_cdf(sc.uni_cut2, 3);
+    sc.c1_n = consistency((double)(P.n / 2 + 1) / (double)P.n, 1);
+    sc.c1_m = consistency((double)(P.m / 2 + 1) / (double)P.m, 1);
     k_setup<<<1, 32, 0, s>>>(P.cs, P.n, P.p, P.pb, P.q, P.m, P.hb, P.h, P.precision, P.max_steps,
-                             o.reweight_consistency, o.cutoff_q, o.kappa_max);
+                             o.reweight_consistency, sc);
 }
 
 __global__ void k_uni_finish(Consts* cs, const double* __restrict__ uni, int p, Status* st) {
@@ -77,12 +123,10 @@ void launch_uni_finish(const Plan& P, cudaStream_t s) {
 //   S~_2 = (1/m) sum xi^2 z z^T.
 // =====================================================================
 __global__ void __launch_bounds__(CT) k_start_reduce(Chain* ch, const Consts* __restrict__ cs,
-                                                     const double* __restrict__ partial, size_t slot_d,
-                                                     int cpb) {
-    extern __shared__ double ext[];
-    const int c = blockIdx.x, l = c / 2, k = c % 2;
+                                                     const double* __restrict__ gsum, size_t slot_d) {
+    const int c = blockIdx.x, k = c % 2;
     const int p = cs->p, nb = gram_nb(cs->pb);
-    sum_slots(partial, slot_d, gram_nblk(cs->pb) * 16, l, cpb, k, ext);
+    const double* ext = gsum + (size_t)c * slot_d;
     Chain& C = ch[c];
     const double cnt = gram_get(ext, p, p, nb);
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -104,10 +148,8 @@ __global__ void __launch_bounds__(CT) k_start_reduce(Chain* ch, const Consts* __
 }
 
 void launch_start_reduce(const Plan& P, cudaStream_t s) {
-    size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
-    auto k = k_start_reduce;
-    big_smem(k, sm);
-    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.partial, P.slot_doubles, P.cpb);
+    launch_reduce_slots(P, 0, s);
+    k_start_reduce<<<2 * P.q, CT, 0, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles);
 }
 
 // =====================================================================
@@ -306,7 +348,7 @@ __global__ void __launch_bounds__(CT) k_chol_prep(Chain* ch, const Consts* __res
     if (threadIdx.x == 0) swaps[c] = 0;
     __syncthreads();
     bool ok = make_rowparams(C.mu, C.Sigma, cs->mu_uni, cs->s_uni, p, A, Li, C.rp, &s_ld);
-    double k1 = ok ? cta_kappa1(S, Li, p) : INFINITY;
+    double k1 = ok ? cta_kappa1(S, Li, A, p) : INFINITY;
     if (!ok || !(k1 < cs->kappa_max)) {
         if (threadIdx.x == 0) {
             C.active = 0;
@@ -359,10 +401,9 @@ __device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Sta
 }
 
 __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* __restrict__ cs,
-                                                       const double* __restrict__ partial, size_t slot_d,
-                                                       int cpb, const int* __restrict__ swaps, int* blk,
+                                                       const double* __restrict__ gsum, size_t slot_d,
+                                                       const int* __restrict__ swaps, int* blk,
                                                        Status* st) {
-    extern __shared__ double ext[];
     __shared__ double dmu[PMAX];
     __shared__ double s_m2;
     const int c = blockIdx.x, l = c / 2, k = c % 2;
@@ -370,7 +411,8 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
     if (!C.active) { count_active_blocks(ch, cs->q, blk, st); return; }
     const int p = cs->p, nb = gram_nb(cs->pb);
     const double hb = (double)cs->hb;
-    sum_slots(partial, slot_d, gram_nblk(cs->pb) * 16, l, cpb, k, ext);
+    const double* ext = gsum + (size_t)c * slot_d;
+    (void)k;
     const int full = C.full;
     const double cnt = gram_get(ext, p, p, nb);
     if (threadIdx.x == 0) {
@@ -431,17 +473,15 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
 }
 
 void launch_cstep_finalize(const Plan& P, cudaStream_t s) {
-    size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
-    auto k = k_cstep_finalize;
-    big_smem(k, sm);
-    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.partial, P.slot_doubles, P.cpb, P.swaps, P.blk_active, P.st);
+    launch_reduce_slots(P, 0, s);
+    k_cstep_finalize<<<2 * P.q, CT, 0, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles, P.swaps, P.blk_active, P.st);
 }
 
 // =====================================================================
 // Section 4 step 4: the start with the lower determinant (start 1 on ties).
 // =====================================================================
-__global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, const uint8_t* __restrict__ memb,
-                                                     int* chosen, Status* st) {
+__global__ void __launch_bounds__(1024) k_block_choose(Chain* ch, Consts* cs, const uint8_t* __restrict__ memb,
+                                                     int* chosen, int* amb, int fp32, Status* st) {
     extern __shared__ double sm[];
     double* A = sm;
     __shared__ int okk[2];
@@ -456,7 +496,13 @@ __global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, cons
         const uint8_t* a = memb + (size_t)(2 * l) * m;
         const uint8_t* b = memb + (size_t)(2 * l + 1) * m;
         int d = 0;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) d += ((a[t] ^ b[t]) & 1);
+        if ((m & 3) == 0) {   // 4 rows per word (rows of chain c start at c m)
+            const unsigned* a4 = reinterpret_cast<const unsigned*>(a);
+            const unsigned* b4 = reinterpret_cast<const unsigned*>(b);
+            for (int t = threadIdx.x; t < m / 4; t += blockDim.x) d += __popc((a4[t] ^ b4[t]) & 0x01010101u);
+        } else {
+            for (int t = threadIdx.x; t < m; t += blockDim.x) d += ((a[t] ^ b[t]) & 1);
+        }
         d = (int)cta_sum((double)d);
         if (threadIdx.x == 0) ndiff = d;
         __syncthreads();
@@ -490,6 +536,10 @@ __global__ void __launch_bounds__(CT) k_block_choose(Chain* ch, Consts* cs, cons
         if (okk[0] && okk[1]) ch_ = (ndiff == 0 || ldk[0] <= ldk[1]) ? 0 : 1;
         else if (okk[0]) ch_ = 0;
         else if (okk[1]) ch_ = 1;
+        // FP32 form: different subsets whose log-determinants lie within the
+        // FP32 Gram error are compared again from FP64 Grams (k_rechoose)
+        amb[l] = (fp32 && okk[0] && okk[1] && ndiff > 0 &&
+                  fabs(ldk[0] - ldk[1]) <= 1e-5 * fmax(1.0, fabs(ldk[0]))) ? 1 : 0;
         chosen[l] = ch_;
         if (ch_ < 0) set_warning(st, RTD_WARN_NO_BLOCK_FIT);
         else atomicAdd(&cs->chains_ok, okk[0] + okk[1]);
@@ -500,38 +550,184 @@ void launch_block_choose(const Plan& P, cudaStream_t s) {
     size_t sm = MAT * sizeof(double);
     auto k = k_block_choose;
     big_smem(k, sm);
-    k<<<P.q, CT, sm, s>>>(P.ch, P.cs, P.memb, P.chosen, P.st);
+    k<<<P.q, 1024, sm, s>>>(P.ch, P.cs, P.memb, P.chosen, P.amb, P.precision == RTD_FP32, P.st);
+}
+
+// Ambiguous blocks: with Lambda_1 = G_1 - S_1 S_1^T / h_b of start 1 and the
+// FP64 Gram (dS, dG) of the rows in exactly one subset, Lambda_2 = Lambda_1 +
+// dL, dL = dG - (S_1 dS^T + dS S_1^T + dS dS^T) / h_b, and
+// log det Lambda_2 - log det Lambda_1 = log det(I + L^-1 dL L^-T).  The
+// common rounding of Lambda_1 cancels in the difference, which decides the
+// choice of Section 4 step 4 (start 1 when det Sigma_1 <= det Sigma_2).
+__global__ void __launch_bounds__(CT) k_rechoose(Chain* ch, const Consts* __restrict__ cs,
+                                                 const double* __restrict__ gsum, size_t slot_d,
+                                                 const int* __restrict__ amb, int* chosen, Status* st) {
+    extern __shared__ double sm[];
+    double* A = sm;             // Lambda_1, then L
+    double* Li = sm + MAT;      // L^-1
+    double* Dl = sm + 2 * MAT;  // dL, then I + L^-1 dL L^-T
+    __shared__ double dS[PMAX];
+    const int l = blockIdx.x;
+    if (!amb[l]) return;
+    const int p = cs->p, nb = gram_nb(cs->pb);
+    const double hb = (double)cs->hb;
+    const Chain& C = ch[2 * l];
+    const double* ext = gsum + (size_t)(2 * l) * slot_d;
+    if (threadIdx.x == 0 && fabs(gram_get(ext, p, p, nb)) > 0.5) set_error(st, RTD_EINTERNAL);
+    for (int j = threadIdx.x; j < p; j += blockDim.x) dS[j] = gram_get(ext, j, p, nb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        A[i * LD + j] = C.G[i * PMAX + j] - C.S[i] * C.S[j] / hb;
+        Dl[i * LD + j] = gram_get(ext, i, j, nb) - (C.S[i] * dS[j] + dS[i] * C.S[j] + dS[i] * dS[j]) / hb;
+    }
+    __syncthreads();
+    if (!cta_cholesky(A, p)) return;
+    cta_tri_inverse(A, Li, p);
+    // T = L^-1 dL (into A), then Dl = I + T L^-T
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = 0.0;
+        for (int k = 0; k <= i; ++k) v += Li[i * LD + k] * Dl[k * LD + j];
+        A[i * LD + j] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = 0.0;
+        for (int k = 0; k <= j; ++k) v += A[i * LD + k] * Li[j * LD + k];
+        Dl[i * LD + j] = v + (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    // symmetrise against rounding
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        if (j < i) { double v = 0.5 * (Dl[i * LD + j] + Dl[j * LD + i]); Dl[i * LD + j] = v; Dl[j * LD + i] = v; }
+    }
+    __syncthreads();
+    if (!cta_cholesky(Dl, p)) return;
+    double ld = 0.0;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) ld += log(Dl[j * LD + j]);
+    ld = 2.0 * cta_sum(ld);
+    if (threadIdx.x == 0) chosen[l] = (ld >= 0.0) ? 0 : 1;
+}
+
+void launch_rechoose(const Plan& P, cudaStream_t s) {
+    launch_member_gram(P, s);
+    launch_reduce_slots(P, 0, s);
+    size_t sm = 3 * MAT * sizeof(double);
+    auto k = k_rechoose;
+    big_smem(k, sm);
+    k<<<P.q, CT, sm, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles, P.amb, P.chosen, P.st);
 }
 
 // =====================================================================
 // Section 4 steps 5-7: entrywise median of the block fits, KL deviation of
 // each fit from the median (eq. KL, log|det|), keep the ceil(q/2) closest,
-// Bennett pooling of their h-subsets.  One CTA.
+// Bennett pooling of their h-subsets.
+//   agg_median: one thread per entry of (mu, Sigma), insertion sort of the
+//               fitted blocks' values;
+//   agg_kl:     one CTA per block;
+//   agg_pool:   one CTA: stable order by (KL, block), keep, pool.
+// Scratch layout: [0, p) mu_med, [p, p + p^2) Sigma_med, then per-thread
+// sort rows.
 // =====================================================================
-constexpr int AGG_T = 1024;
+__global__ void k_agg_median(const Chain* __restrict__ ch, const Consts* __restrict__ cs,
+                             const int* __restrict__ chosen, double* scratch) {
+    const int p = cs->p, q = cs->q;
+    const double ca = cs->c_alpha;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p + p * p) return;
+    double* v = scratch + p + p * p + (size_t)e * q;
+    int n = 0;
+    for (int l = 0; l < q; ++l) {
+        if (chosen[l] < 0) continue;
+        const Chain& C = ch[2 * l + chosen[l]];
+        double x = (e < p) ? C.mu[e] : ca * C.Sigma[((e - p) / p) * PMAX + (e - p) % p];
+        int u = n - 1;
+        while (u >= 0 && v[u] > x) { v[u + 1] = v[u]; --u; }
+        v[u + 1] = x;
+        ++n;
+    }
+    if (n == 0) return;
+    scratch[e] = (n & 1) ? v[n / 2] : 0.5 * (v[n / 2 - 1] + v[n / 2]);
+}
 
-__global__ void __launch_bounds__(AGG_T) k_aggregate(const Chain* __restrict__ ch, Consts* cs,
-                                                     const int* __restrict__ chosen, int* kept, double* kl,
-                                                     double* scratch, Status* st) {
+__global__ void __launch_bounds__(CT) k_agg_kl(const Chain* __restrict__ ch, const Consts* __restrict__ cs,
+                                               const int* __restrict__ chosen, const double* __restrict__ scratch,
+                                               double* kl) {
     extern __shared__ double sm[];
     double* Smed = sm;
     double* A = sm + MAT;
     double* Li = sm + 2 * MAT;
-    double* Lam = sm + 3 * MAT;
+    __shared__ double dv[PMAX];
+    const int l = blockIdx.x, p = cs->p;
+    if (chosen[l] < 0) { if (threadIdx.x == 0) kl[l] = NAN; return; }
+    const double ca = cs->c_alpha;
+    const Chain& C = ch[2 * l + chosen[l]];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = scratch[p + e];
+        Smed[i * LD + j] = v;
+        A[i * LD + j] = v;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) dv[j] = scratch[j] - C.mu[j];
+    __syncthreads();
+    const double lad = cta_logabsdet(A, p);
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        A[i * LD + j] = ca * C.Sigma[i * PMAX + j];
+    }
+    __syncthreads();
+    if (!cta_cholesky(A, p)) { if (threadIdx.x == 0) kl[l] = INFINITY; return; }
+    cta_tri_inverse(A, Li, p);
+    double ldb = 0.0;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) ldb += log(A[j * LD + j]);
+    ldb = 2.0 * cta_sum(ldb);
+    // B^-1 = Li^T Li ; tr(Smed B^-1) and d^T B^-1 d
+    double tr = 0.0, quad = 0.0;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        int k0 = i > j ? i : j;
+        double bij = 0.0;
+        for (int kk = k0; kk < p; ++kk) bij += Li[kk * LD + i] * Li[kk * LD + j];
+        tr += Smed[j * LD + i] * bij;
+        quad += dv[i] * bij * dv[j];
+    }
+    tr = cta_sum(tr);
+    quad = cta_sum(quad);
+    if (threadIdx.x == 0) {
+        double v = tr - p - (lad - ldb) + quad;
+        kl[l] = isfinite(v) ? v : INFINITY;
+    }
+}
+
+__global__ void __launch_bounds__(AGG_T) k_agg_pool(const Chain* __restrict__ ch, Consts* cs,
+                                                    const int* __restrict__ chosen, int* kept, double* kl,
+                                                    Status* st) {
+    extern __shared__ double sm[];
+    double* Lam = sm;
     __shared__ int fl[1024];
     __shared__ int s_qf;
-    __shared__ double mumed[PMAX], mup[PMAX], dv[PMAX];
-    __shared__ double s_lad, s_np;
+    __shared__ double mup[PMAX], dv[PMAX];
+    __shared__ double s_np;
     const int p = cs->p, q = cs->q;
     const double ca = cs->c_alpha, hb = (double)cs->hb;
     if (threadIdx.x == 0) {
         int n = 0;
         for (int l = 0; l < q && n < 1024; ++l) {
             kept[l] = 0;
-            kl[l] = NAN;
             if (chosen[l] >= 0) fl[n++] = l;
         }
         s_qf = n;
+        // stable order by (KL, block)
+        for (int i = 1; i < n; ++i) {
+            int v = fl[i];
+            int u = i - 1;
+            while (u >= 0 && kl[fl[u]] > kl[v]) { fl[u + 1] = fl[u]; --u; }
+            fl[u + 1] = v;
+        }
+        for (int i = 0; i < (n + 1) / 2; ++i) kept[fl[i]] = 1;
     }
     __syncthreads();
     const int qf = s_qf;
@@ -539,86 +735,6 @@ __global__ void __launch_bounds__(AGG_T) k_aggregate(const Chain* __restrict__ c
         if (threadIdx.x == 0) set_error(st, RTD_EILLCOND);
         return;
     }
-    if (q == 1) {
-        const Chain& C = ch[chosen[0]];
-        for (int j = threadIdx.x; j < p; j += blockDim.x) cs->mu_raw[j] = C.mu[j];
-        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-            int i = e / p, j = e % p;
-            cs->Sigma_raw[i * PMAX + j] = ca * C.Sigma[i * PMAX + j];
-        }
-        if (threadIdx.x == 0) { kept[0] = 1; kl[0] = 0.0; }
-        return;
-    }
-    // entrywise medians (insertion sort of the qf values of each entry)
-    double* vals = scratch;   // [AGG_T][qf] work rows
-    for (int e = threadIdx.x; e < p + p * p; e += blockDim.x) {
-        double* v = vals + (size_t)threadIdx.x * qf;
-        for (int t = 0; t < qf; ++t) {
-            const Chain& C = ch[2 * fl[t] + chosen[fl[t]]];
-            double x = (e < p) ? C.mu[e] : ca * C.Sigma[((e - p) / p) * PMAX + (e - p) % p];
-            int u = t - 1;
-            while (u >= 0 && v[u] > x) { v[u + 1] = v[u]; --u; }
-            v[u + 1] = x;
-        }
-        double med = (qf & 1) ? v[qf / 2] : 0.5 * (v[qf / 2 - 1] + v[qf / 2]);
-        if (e < p) mumed[e] = med;
-        else { int i = (e - p) / p, j = (e - p) % p; Smed[i * LD + j] = med; }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        int i = e / p, j = e % p;
-        A[i * LD + j] = Smed[i * LD + j];
-    }
-    __syncthreads();
-    double lad = cta_logabsdet(A, p);
-    if (threadIdx.x == 0) s_lad = lad;
-    __syncthreads();
-    // KL of each fitted block
-    for (int t = 0; t < qf; ++t) {
-        const int l = fl[t];
-        const Chain& C = ch[2 * l + chosen[l]];
-        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-            int i = e / p, j = e % p;
-            A[i * LD + j] = ca * C.Sigma[i * PMAX + j];
-        }
-        __syncthreads();
-        bool ok = cta_cholesky(A, p);
-        if (!ok) { if (threadIdx.x == 0) kl[l] = INFINITY; __syncthreads(); continue; }
-        cta_tri_inverse(A, Li, p);
-        double ldb = 0.0;
-        for (int j = threadIdx.x; j < p; j += blockDim.x) ldb += log(A[j * LD + j]);
-        ldb = 2.0 * cta_sum(ldb);
-        for (int j = threadIdx.x; j < p; j += blockDim.x) dv[j] = mumed[j] - C.mu[j];
-        __syncthreads();
-        // B^-1 = Li^T Li ; tr(Smed B^-1) and d^T B^-1 d
-        double tr = 0.0, quad = 0.0;
-        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-            int i = e / p, j = e % p;
-            int k0 = i > j ? i : j;
-            double bij = 0.0;
-            for (int kk = k0; kk < p; ++kk) bij += Li[kk * LD + i] * Li[kk * LD + j];
-            tr += Smed[j * LD + i] * bij;
-            quad += dv[i] * bij * dv[j];
-        }
-        tr = cta_sum(tr);
-        quad = cta_sum(quad);
-        if (threadIdx.x == 0) {
-            double v = tr - p - (s_lad - ldb) + quad;
-            kl[l] = isfinite(v) ? v : INFINITY;
-        }
-        __syncthreads();
-    }
-    // stable order by (KL, block); keep ceil(qf/2)
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < qf; ++i) {
-            int v = fl[i];
-            int u = i - 1;
-            while (u >= 0 && kl[fl[u]] > kl[v]) { fl[u + 1] = fl[u]; --u; }
-            fl[u + 1] = v;
-        }
-        for (int i = 0; i < (qf + 1) / 2; ++i) kept[fl[i]] = 1;
-    }
-    __syncthreads();
     // Bennett pooling over the kept blocks in KL order, counts h_b
     const int nk = (qf + 1) / 2;
     {
@@ -655,11 +771,38 @@ __global__ void __launch_bounds__(AGG_T) k_aggregate(const Chain* __restrict__ c
     }
 }
 
+// q = 1: the serial algorithm's raw fit is the chosen start's C_k.
+__global__ void k_agg_single(const Chain* __restrict__ ch, Consts* cs, const int* __restrict__ chosen,
+                             int* kept, double* kl, Status* st) {
+    const int p = cs->p;
+    if (chosen[0] < 0) {
+        if (threadIdx.x == 0) set_error(st, RTD_EILLCOND);
+        return;
+    }
+    const Chain& C = ch[chosen[0]];
+    for (int j = threadIdx.x; j < p; j += blockDim.x) cs->mu_raw[j] = C.mu[j];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        cs->Sigma_raw[i * PMAX + j] = cs->c_alpha * C.Sigma[i * PMAX + j];
+    }
+    if (threadIdx.x == 0) { kept[0] = 1; kl[0] = 0.0; }
+}
+
 void launch_aggregate(const Plan& P, cudaStream_t s) {
-    size_t sm = 4 * MAT * sizeof(double);
-    auto k = k_aggregate;
-    big_smem(k, sm);
-    k<<<1, AGG_T, sm, s>>>(P.ch, P.cs, P.chosen, P.kept, P.kl, P.scratch, P.st);
+    if (P.q == 1) {
+        k_agg_single<<<1, 256, 0, s>>>(P.ch, P.cs, P.chosen, P.kept, P.kl, P.st);
+        return;
+    }
+    const int ne = P.p + P.p * P.p;
+    k_agg_median<<<(ne + 127) / 128, 128, 0, s>>>(P.ch, P.cs, P.chosen, P.scratch);
+    size_t sm = 3 * MAT * sizeof(double);
+    auto k1 = k_agg_kl;
+    big_smem(k1, sm);
+    k1<<<P.q, CT, sm, s>>>(P.ch, P.cs, P.chosen, P.scratch, P.kl);
+    size_t sm2 = MAT * sizeof(double);
+    auto k2 = k_agg_pool;
+    big_smem(k2, sm2);
+    k2<<<1, AGG_T, sm2, s>>>(P.ch, P.cs, P.chosen, P.kept, P.kl, P.st);
 }
 
 // Row parameters of the raw (which = 0) or reweighted (which = 1) fit.
@@ -697,18 +840,9 @@ void launch_fit_prep(const Plan& P, int which, cudaStream_t s) {
 
 // Section 4 steps 8-9: mean and covariance of the reweighting set (the
 // pooled per-block moments), times the reweighting consistency factor.
-__global__ void __launch_bounds__(1024) k_rew_finalize(Consts* cs, const RowParams* __restrict__ fitrp,
-                                                       const double* __restrict__ partial, size_t slot_d,
-                                                       int q, int cpb, Status* st) {
-    extern __shared__ double ext[];
-    const int p = cs->p, nb = gram_nb(cs->pb), nv = gram_nblk(cs->pb) * 16;
-    for (int e = threadIdx.x; e < nv; e += blockDim.x) {
-        double s = 0.0;
-        for (int l = 0; l < q; ++l)
-            for (int b = 0; b < cpb; ++b) s += partial[(((size_t)l * cpb + b) * 2 + 0) * slot_d + e];
-        ext[e] = s;
-    }
-    __syncthreads();
+__global__ void __launch_bounds__(256) k_rew_finalize(Consts* cs, const RowParams* __restrict__ fitrp,
+                                                      const double* __restrict__ ext, Status* st) {
+    const int p = cs->p, nb = gram_nb(cs->pb);
     const double nw = gram_get(ext, p, p, nb);
     if (!(nw > (double)p + 1.0)) {
         if (threadIdx.x == 0) set_error(st, RTD_EDEGENERATE);
@@ -733,10 +867,8 @@ __global__ void __launch_bounds__(1024) k_rew_finalize(Consts* cs, const RowPara
 }
 
 void launch_rew_finalize(const Plan& P, cudaStream_t s) {
-    size_t sm = (size_t)gram_nblk(P.pb) * 16 * sizeof(double);
-    auto k = k_rew_finalize;
-    big_smem(k, sm);
-    k<<<1, 1024, sm, s>>>(P.cs, P.fitrp, P.partial, P.slot_doubles, P.q, P.cpb, P.st);
+    launch_reduce_slots(P, 1, s);
+    k_rew_finalize<<<1, 256, 0, s>>>(P.cs, P.fitrp, P.gsum, P.st);
 }
 
 // =====================================================================

@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
                                                      int tiles, int shift, const unsigned* __restrict__ offs) {
     __shared__ unsigned wcnt[SW][256];
     __shared__ unsigned goff[256];
+    __shared__ unsigned tstart[256];
+    __shared__ K stage[STILE];
     const int seg = blockIdx.y, tile = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < SW * 256; e += ST) (&wcnt[0][0])[e] = 0u;
@@ -88,24 +90,47 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
         __syncwarp();
     }
     __syncthreads();
-    {
+    {   // per digit: exclusive prefix over warps, and the tile's digit total
         unsigned run = 0;
         for (int ww = 0; ww < SW; ++ww) {
             unsigned c = wcnt[ww][threadIdx.x];
             wcnt[ww][threadIdx.x] = run;
             run += c;
         }
+        tstart[threadIdx.x] = run;
     }
     __syncthreads();
-    K* dst = out + (long long)seg * L;
+    if (threadIdx.x < 32) {   // exclusive scan of the 256 digit totals
+        unsigned v[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { v[k] = tstart[threadIdx.x * 8 + k]; sum += v[k]; }
+        unsigned inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        unsigned ex = inc - sum;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { tstart[threadIdx.x * 8 + k] = ex; ex += v[k]; }
+    }
+    __syncthreads();
+    // tile-local sorted order in shared memory
 #pragma unroll
     for (int r = 0; r < SITEMS; ++r) {
         int idx = w * SKPW + r * 32 + lane;
         if (idx < cnt) {
             unsigned d = (unsigned)(key[r] >> shift) & 255u;
-            unsigned pos = goff[d] + wcnt[w][d] + rank[r];
-            if (pos < (unsigned)L) dst[pos] = key[r];
+            stage[tstart[d] + wcnt[w][d] + rank[r]] = key[r];
         }
+    }
+    __syncthreads();
+    // consecutive threads write consecutive keys of one digit run
+    K* dst = out + (long long)seg * L;
+    for (int i = threadIdx.x; i < cnt; i += ST) {
+        K k = stage[i];
+        unsigned d = (unsigned)(k >> shift) & 255u;
+        unsigned pos = goff[d] + (unsigned)i - tstart[d];
+        if (pos < (unsigned)L) dst[pos] = k;
     }
 }
 
@@ -133,147 +158,282 @@ void sort_segments(const Plan& P, void* keys, void* tmp, int key_bytes, int nseg
 }
 
 // =====================================================================
-// Univariate reweighted MCD of a sorted segment (Section 3.1): coverage
+// Univariate reweighted MCD of sorted segments (Section 3.1): coverage
 // h~ = [L/2] + 1; the contiguous h~-window of minimum variance (first on
 // ties) gives mu0 and c(h~/L) var; the reweighting keeps
-// (x - mu0)^2 / s0^2 <= chi2_{1,q}, a contiguous range of the sorted values
-// found by binary search.  Window sums come from FP64 running sums of the
-// values shifted by the middle order statistic.
-// out[seg] = (mu, s2, mu_raw, s2_raw); s2 <= 0 or NaN marks a degenerate
-// segment.
+// (x - mu0)^2 / s0^2 <= chi2_{1,q}, a contiguous range of the sorted values.
+// Window sums are differences of FP64 running sums of the values shifted by
+// the middle order statistic.  Three launches, all coalesced:
+//   U1  chunk sums of every segment,
+//   U2  windows of a chunk of starts: two block scans in lock step over the
+//       values at positions j and j + h~, per-CTA argmin,
+//   U3  per segment: argmin over chunks, reweighting bounds by a CTA-wide
+//       256-ary search, sums over the kept range.
+// out[seg] = (mu, s2, mu_raw, s2_raw); NaN marks a degenerate segment.
 // =====================================================================
-constexpr int UT = 1024;
+constexpr int UT = 256;              // threads
+constexpr int UV = 4;                // values per thread and tile
+constexpr int UTILE = UT * UV;       // 1024
+constexpr int UCH = 8 * UTILE;       // chunk of positions / window starts
 
 template <typename K>
 __device__ inline double uval(const K* s, long long i) { return KeyOps<K>::dec(s[i]); }
 
+struct D2 { double a, b; };
+
+// Block-wide exclusive scan of (a, b) pairs (one pair per thread); returns
+// the exclusive prefix and writes the block total to tot.
+__device__ inline D2 cta_exscan2(D2 v, D2& tot) {
+    __shared__ double wa[UT / 32], wb[UT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    D2 x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        double ya = __shfl_up_sync(0xffffffffu, x.a, o);
+        double yb = __shfl_up_sync(0xffffffffu, x.b, o);
+        if (lane >= o) { x.a += ya; x.b += yb; }
+    }
+    if (lane == 31) { wa[w] = x.a; wb[w] = x.b; }
+    __syncthreads();
+    double pa = 0.0, pb = 0.0, ta = 0.0, tb = 0.0;
+    for (int k = 0; k < UT / 32; ++k) {
+        if (k < w) { pa += wa[k]; pb += wb[k]; }
+        ta += wa[k]; tb += wb[k];
+    }
+    __syncthreads();
+    tot = D2{ta, tb};
+    return D2{pa + x.a - v.a, pb + x.b - v.b};
+}
+
+__device__ inline D2 cta_sum2(D2 v) {
+    D2 t;
+    cta_exscan2(v, t);
+    return t;
+}
+
+// Sum of (s_i - c, (s_i - c)^2) over [a, b) by the whole CTA.
 template <typename K>
-__global__ void __launch_bounds__(UT) k_unimcd(const K* __restrict__ sorted, long long L,
-                                               const Consts* __restrict__ cs, int which_c1,
-                                               double* __restrict__ out) {
-    __shared__ double pre1[UT], pre2[UT];
-    __shared__ double bv[UT / 32];
-    __shared__ long long bj[UT / 32];
-    __shared__ double s_res[2];
-    __shared__ long long s_j;
-    const K* s = sorted + (long long)blockIdx.x * L;
-    const long long h = L / 2 + 1;
-    const long long nwin = L - h + 1;
-    const double c = uval(s, L / 2);
-    const long long E = (L + UT - 1) / UT;
-    const long long a0 = threadIdx.x * E;
-    const long long a1 = (a0 + E < L) ? a0 + E : L;
-    double s1 = 0.0, s2 = 0.0;
-    for (long long i = a0; i < a1; ++i) {
+__device__ inline D2 cta_range_sum(const K* s, double c, long long a, long long b) {
+    D2 acc{0.0, 0.0};
+    for (long long i = a + threadIdx.x; i < b; i += UT) {
         double d = uval(s, i) - c;
-        s1 += d;
-        s2 += d * d;
+        acc.a += d;
+        acc.b += d * d;
     }
-    pre1[threadIdx.x] = s1;
-    pre2[threadIdx.x] = s2;
-    __syncthreads();
-    if (threadIdx.x == 0) {   // exclusive prefix of the chunk sums, fixed order
-        double r1 = 0.0, r2 = 0.0;
-        for (int t = 0; t < UT; ++t) {
-            double v1 = pre1[t], v2 = pre2[t];
-            pre1[t] = r1; pre2[t] = r2;
-            r1 += v1; r2 += v2;
-        }
+    return cta_sum2(acc);
+}
+
+// Running sum up to position a from the chunk sums plus a partial chunk.
+template <typename K>
+__device__ inline D2 cta_prefix(const K* s, double c, const double* csum, long long a) {
+    long long ca = a / UCH;
+    D2 acc{0.0, 0.0};
+    for (long long k = threadIdx.x; k < ca; k += UT) { acc.a += csum[2 * k]; acc.b += csum[2 * k + 1]; }
+    D2 t1 = cta_sum2(acc);
+    D2 t2 = cta_range_sum(s, c, ca * UCH, a);
+    return D2{t1.a + t2.a, t1.b + t2.b};
+}
+
+template <typename K>
+__global__ void __launch_bounds__(UT) k_uni_chunks(const K* __restrict__ sorted, long long L, int nch,
+                                                   double* __restrict__ csum) {
+    const int seg = blockIdx.y, ch = blockIdx.x;
+    const K* s = sorted + (long long)seg * L;
+    const double c = uval(s, L / 2);
+    long long a = (long long)ch * UCH, b = a + UCH < L ? a + UCH : L;
+    D2 t = cta_range_sum(s, c, a, b);
+    if (threadIdx.x == 0) {
+        double* o = csum + ((size_t)seg * nch + ch) * 2;
+        o[0] = t.a;
+        o[1] = t.b;
     }
-    __syncthreads();
-    // running sums P(a) = sum_{i<a} (s_i - c), for any 0 <= a <= L
-    auto prefix = [&](long long a, double& p1, double& p2) {
-        long long t = a / E;
-        if (t >= UT) t = UT - 1;
-        p1 = pre1[t]; p2 = pre2[t];
-        for (long long i = t * E; i < a; ++i) {
-            double d = uval(s, i) - c;
-            p1 += d;
-            p2 += d * d;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(UT) k_uni_windows(const K* __restrict__ sorted, long long L, int nch,
+                                                    const double* __restrict__ csum_all, int nwch,
+                                                    double* __restrict__ wres) {
+    __shared__ double rv[UT / 32], rs[UT / 32];
+    __shared__ long long rj[UT / 32];
+    const int seg = blockIdx.y, wc = blockIdx.x;
+    const K* s = sorted + (long long)seg * L;
+    const double* csum = csum_all + (size_t)seg * nch * 2;
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    const double c = uval(s, L / 2);
+    const long long j0 = (long long)wc * UCH;
+    const long long j1 = j0 + UCH < nwin ? j0 + UCH : nwin;
+    D2 PA = cta_prefix(s, c, csum, j0);
+    D2 PB = cta_prefix(s, c, csum, j0 + h);
+    double best = INFINITY, bs1 = 0.0;
+    long long bj = -1;
+    for (long long t0 = j0; t0 < j1; t0 += UTILE) {
+        const long long base = t0 + (long long)threadIdx.x * UV;
+        D2 la{0.0, 0.0}, lb{0.0, 0.0};
+        double da[UV], db[UV];
+#pragma unroll
+        for (int u = 0; u < UV; ++u) {
+            long long ja = base + u, jb = base + u + h;
+            da[u] = (ja < j1) ? uval(s, ja) - c : 0.0;
+            db[u] = (ja < j1 && jb < L) ? uval(s, jb) - c : 0.0;
+            la.a += da[u]; la.b += da[u] * da[u];
+            lb.a += db[u]; lb.b += db[u] * db[u];
         }
-    };
-    double best = INFINITY;
-    long long bjj = -1;
-    if (a0 < nwin) {
-        long long w1 = (a1 < nwin) ? a1 : nwin;
-        double P1a, P2a, P1b, P2b;
-        prefix(a0, P1a, P2a);
-        prefix(a0 + h, P1b, P2b);
-        for (long long j = a0; j < w1; ++j) {
-            double S1 = P1b - P1a, S2 = P2b - P2a;
-            double var = (S2 - S1 * S1 / (double)h) / (double)(h - 1);
-            if (var < best) { best = var; bjj = j; }
-            double d0 = uval(s, j) - c;
-            P1a += d0; P2a += d0 * d0;
-            if (j + h < L) {
-                double d1 = uval(s, j + h) - c;
-                P1b += d1; P2b += d1 * d1;
+        D2 ta, tb;
+        D2 ea = cta_exscan2(la, ta);
+        D2 eb = cta_exscan2(lb, tb);
+        double A1 = PA.a + ea.a, A2 = PA.b + ea.b, B1 = PB.a + eb.a, B2 = PB.b + eb.b;
+#pragma unroll
+        for (int u = 0; u < UV; ++u) {
+            long long j = base + u;
+            if (j < j1) {
+                double S1 = B1 - A1, S2 = B2 - A2;
+                double var = (S2 - S1 * S1 / (double)h) / (double)(h - 1);
+                if (var < best) { best = var; bj = j; bs1 = S1; }
             }
+            A1 += da[u]; A2 += da[u] * da[u];
+            B1 += db[u]; B2 += db[u] * db[u];
         }
+        PA.a += ta.a; PA.b += ta.b;
+        PB.a += tb.a; PB.b += tb.b;
     }
-    // block argmin, ties to the lower window start
     for (int o = 16; o > 0; o >>= 1) {
         double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        long long oj = __shfl_xor_sync(0xffffffffu, bjj, o);
-        if (oj >= 0 && (bjj < 0 || ov < best || (ov == best && oj < bjj))) { best = ov; bjj = oj; }
+        double os = __shfl_xor_sync(0xffffffffu, bs1, o);
+        long long oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (oj >= 0 && (bj < 0 || ov < best || (ov == best && oj < bj))) { best = ov; bj = oj; bs1 = os; }
     }
-    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bj[threadIdx.x >> 5] = bjj; }
+    if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; rj[threadIdx.x >> 5] = bj; rs[threadIdx.x >> 5] = bs1; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = INFINITY;
-        long long j = -1;
-        for (int w = 0; w < UT / 32; ++w) {
-            if (bj[w] >= 0 && (j < 0 || bv[w] < b || (bv[w] == b && bj[w] < j))) { b = bv[w]; j = bj[w]; }
+        double b = INFINITY, bsum = 0.0;
+        long long jj = -1;
+        for (int w = 0; w < UT / 32; ++w)
+            if (rj[w] >= 0 && (jj < 0 || rv[w] < b || (rv[w] == b && rj[w] < jj))) { b = rv[w]; jj = rj[w]; bsum = rs[w]; }
+        double* o = wres + ((size_t)seg * nwch + wc) * 3;
+        o[0] = b;
+        o[1] = (double)jj;
+        o[2] = bsum;
+    }
+}
+
+// First index in [lo, hi) where the monotone (false ... true) predicate
+// holds, hi if none; 256-ary search by the whole CTA.
+template <typename Pred>
+__device__ inline long long cta_first_true(long long lo, long long hi, Pred pred) {
+    __shared__ int s_t;
+    while (true) {
+        if (hi - lo <= UT) {
+            if (threadIdx.x == 0) s_t = UT;
+            __syncthreads();
+            long long x = lo + threadIdx.x;
+            if (x < hi && pred(x)) atomicMin(&s_t, (int)threadIdx.x);
+            __syncthreads();
+            long long r = (s_t < UT) ? lo + s_t : hi;
+            __syncthreads();
+            return r;
         }
-        s_j = j;
-        s_res[0] = b;
+        long long step = (hi - lo + UT - 1) / UT;
+        if (threadIdx.x == 0) s_t = UT;
+        __syncthreads();
+        long long x = lo + (threadIdx.x + 1) * step - 1;
+        if (x > hi - 1) x = hi - 1;
+        if (pred(x)) atomicMin(&s_t, (int)threadIdx.x);
+        __syncthreads();
+        int t = s_t;
+        __syncthreads();
+        if (t == UT) return hi;
+        long long nlo = lo + (long long)t * step;
+        long long nhi = lo + ((long long)t + 1) * step;
+        if (nhi > hi) nhi = hi;
+        lo = nlo;
+        hi = nhi;     // pred(nhi - 1) holds: the answer lies in [lo, hi)
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sorted, long long L, int nch,
+                                                       const double* __restrict__ csum_all, int nwch,
+                                                       const double* __restrict__ wres,
+                                                       const Consts* __restrict__ cs, int which_c1,
+                                                       double* __restrict__ out) {
+    __shared__ double sv[UT], ss[UT];
+    __shared__ long long sj[UT];
+    const int seg = blockIdx.x;
+    const K* s = sorted + (long long)seg * L;
+    const double* csum = csum_all + (size_t)seg * nch * 2;
+    const long long h = L / 2 + 1;
+    const double c = uval(s, L / 2);
+    double best = INFINITY, bs1 = 0.0;
+    long long bj = -1;
+    for (int w = threadIdx.x; w < nwch; w += UT) {
+        const double* r = wres + ((size_t)seg * nwch + w) * 3;
+        long long jj = (long long)r[1];
+        if (jj >= 0 && (bj < 0 || r[0] < best || (r[0] == best && jj < bj))) { best = r[0]; bj = jj; bs1 = r[2]; }
+    }
+    sv[threadIdx.x] = best; ss[threadIdx.x] = bs1; sj[threadIdx.x] = bj;
+    __syncthreads();
+    __shared__ double s_var, s_s1;
+    __shared__ long long s_j;
+    if (threadIdx.x == 0) {
+        double b = INFINITY, bsum = 0.0;
+        long long jj = -1;
+        for (int t = 0; t < UT; ++t)
+            if (sj[t] >= 0 && (jj < 0 || sv[t] < b || (sv[t] == b && sj[t] < jj))) { b = sv[t]; jj = sj[t]; bsum = ss[t]; }
+        s_var = b; s_j = jj; s_s1 = bsum;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double* o = out + 4 * (size_t)blockIdx.x;
-    long long j = s_j;
-    if (j < 0) { o[0] = o[1] = o[2] = o[3] = NAN; return; }
-    double P1a, P2a, P1b, P2b;
-    prefix(j, P1a, P2a);
-    prefix(j + h, P1b, P2b);
-    double S1 = P1b - P1a;
+    double* o = out + 4 * (size_t)seg;
+    if (s_j < 0) { if (threadIdx.x == 0) { o[0] = o[1] = o[2] = o[3] = NAN; } return; }
     const double c1 = which_c1 ? cs->c1_m : cs->c1_n;
-    const double mu0 = c + S1 / (double)h;
-    const double s20 = c1 * s_res[0];
-    o[2] = mu0;
-    o[3] = s20;
-    if (!(s20 > 0.0) || !isfinite(s20)) { o[0] = NAN; o[1] = NAN; return; }
+    const double mu0 = c + s_s1 / (double)h;
+    const double s20 = c1 * s_var;
+    if (!(s20 > 0.0) || !isfinite(s20)) {
+        if (threadIdx.x == 0) { o[0] = NAN; o[1] = NAN; o[2] = mu0; o[3] = s20; }
+        return;
+    }
     const double cut2 = cs->uni_cut2;
     auto keep = [&](long long i) { double d = uval(s, i) - mu0; return d * d / s20 <= cut2; };
-    // m0: first index with value >= mu0
-    long long lo = 0, hi = L;
-    while (lo < hi) { long long md = (lo + hi) / 2; if (uval(s, md) < mu0) lo = md + 1; else hi = md; }
-    long long m0 = lo;
-    // first kept index in [0, m0] (keep is false then true there)
-    lo = 0; hi = m0;
-    while (lo < hi) { long long md = (lo + hi) / 2; if (keep(md)) hi = md; else lo = md + 1; }
-    long long wlo = lo;
-    // first not-kept index in [m0, L] (keep is true then false there)
-    lo = m0; hi = L;
-    while (lo < hi) { long long md = (lo + hi) / 2; if (keep(md)) lo = md + 1; else hi = md; }
-    long long whi = lo;
+    long long m0 = cta_first_true(0, L, [&](long long i) { return uval(s, i) >= mu0; });
+    long long wlo = cta_first_true(0, m0, keep);
+    long long whi = cta_first_true(m0, L, [&](long long i) { return !keep(i); });
     long long nw = whi - wlo;
-    if (nw < 2) { o[0] = NAN; o[1] = NAN; return; }
-    prefix(wlo, P1a, P2a);
-    prefix(whi, P1b, P2b);
-    double T1 = P1b - P1a, T2 = P2b - P2a;
-    double mu = c + T1 / (double)nw;
-    double var = (T2 - T1 * T1 / (double)nw) / (double)(nw - 1);
-    o[0] = mu;
-    o[1] = cs->crew1 * var;
+    if (nw < 2) {
+        if (threadIdx.x == 0) { o[0] = NAN; o[1] = NAN; o[2] = mu0; o[3] = s20; }
+        return;
+    }
+    D2 Pa = cta_prefix(s, c, csum, wlo);
+    D2 Pb = cta_prefix(s, c, csum, whi);
+    if (threadIdx.x == 0) {
+        double T1 = Pb.a - Pa.a, T2 = Pb.b - Pa.b;
+        o[0] = c + T1 / (double)nw;
+        o[1] = cs->crew1 * (T2 - T1 * T1 / (double)nw) / (double)(nw - 1);
+        o[2] = mu0;
+        o[3] = s20;
+    }
+}
+
+template <typename K>
+static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int which_c1, double* out,
+                     cudaStream_t s) {
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    const int nch = (int)((L + UCH - 1) / UCH);
+    const int nwch = (int)((nwin + UCH - 1) / UCH);
+    double* csum = P.uscratch;
+    double* wres = P.uscratch + (size_t)nseg * nch * 2;
+    k_uni_chunks<K><<<dim3(nch, nseg), UT, 0, s>>>(keys, L, nch, csum);
+    k_uni_windows<K><<<dim3(nwch, nseg), UT, 0, s>>>(keys, L, nch, csum, nwch, wres);
+    k_uni_finish_seg<K><<<nseg, UT, 0, s>>>(keys, L, nch, csum, nwch, wres, P.cs, which_c1, out);
 }
 
 void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L, int which_c1,
                    double* out, cudaStream_t s) {
-    if (key_bytes == 8)
-        k_unimcd<unsigned long long><<<nseg, UT, 0, s>>>((const unsigned long long*)keys, L, P.cs, which_c1, out);
-    else
-        k_unimcd<uint32_t><<<nseg, UT, 0, s>>>((const uint32_t*)keys, L, P.cs, which_c1, out);
+    if (key_bytes == 8) unimcd_t<unsigned long long>(P, (const unsigned long long*)keys, nseg, L, which_c1, out, s);
+    else unimcd_t<uint32_t>(P, (const uint32_t*)keys, nseg, L, which_c1, out, s);
+}
+
+size_t unimcd_scratch_doubles(int nseg, long long L) {
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    const long long nch = (L + UCH - 1) / UCH, nwch = (nwin + UCH - 1) / UCH;
+    return (size_t)nseg * (2 * nch + 3 * nwch);
 }
 
 // =====================================================================
@@ -286,27 +446,50 @@ void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, lon
 template <typename K>
 __device__ inline double r23(const K* s, long long i) { return pow(KeyOps<K>::dec(s[i]), 2.0 / 3.0); }
 
+// First index in [lo, hi) where the monotone (false ... true) predicate
+// holds, hi if none; 32-ary search by one warp.
+template <typename Pred>
+__device__ inline long long warp_first_true(long long lo, long long hi, Pred pred) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        long long step = (hi - lo + 31) / 32;
+        long long x = lo + (lane + 1) * step - 1;
+        if (x > hi - 1) x = hi - 1;
+        unsigned b = __ballot_sync(0xffffffffu, pred(x));
+        if (!b) return hi;
+        int t = __ffs(b) - 1;
+        long long nlo = lo + (long long)t * step, nhi = lo + ((long long)t + 1) * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    long long x = lo + lane;
+    unsigned b = __ballot_sync(0xffffffffu, x < hi && pred(x));
+    return b ? lo + (__ffs(b) - 1) : hi;
+}
+
+// k-th smallest (1-based) of |v_i - m3| over the sorted v = r^(2/3): the
+// runs Lt = m3 - v[s0-1-t] and Rt = v[s0+t] - m3 are both ascending.
 template <typename K>
 __device__ double kth_absdev(const K* s, long long L, long long s0, double m3, long long k) {
-    // left run: Lt = m3 - v[s0 - 1 - t], t < a; right run: Rt = v[s0 + t] - m3, t < b
     long long a = s0, b = L - s0;
     auto Lv = [&](long long t) { return m3 - r23(s, s0 - 1 - t); };
     auto Rv = [&](long long t) { return r23(s, s0 + t) - m3; };
     long long lo = k - b > 0 ? k - b : 0, hi = k < a ? k : a;
-    while (lo < hi) {
-        long long i = (lo + hi) / 2, j = k - i;
-        if (i < a && j > 0 && Rv(j - 1) > Lv(i)) lo = i + 1;
-        else hi = i;
-    }
-    long long i = lo, j = k - i;
+    // i = number taken from the left run: first i where R_{k-i-1} > L_i fails
+    long long i = warp_first_true(lo, hi, [&](long long ii) {
+        long long jj = k - ii;
+        return !(ii < a && jj > 0 && Rv(jj - 1) > Lv(ii));
+    });
+    long long j = k - i;
     double x = (i > 0) ? Lv(i - 1) : -INFINITY;
     double y = (j > 0) ? Rv(j - 1) : -INFINITY;
     return x > y ? x : y;
 }
 
+// One warp per block.
 template <typename K>
 __global__ void k_gsscm(const K* __restrict__ rs, int q, long long m, double* __restrict__ AB) {
-    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (l >= q) return;
     const K* s = rs + (size_t)l * m;
     double A, m3;
@@ -317,19 +500,19 @@ __global__ void k_gsscm(const K* __restrict__ rs, int q, long long m, double* __
         A = 0.5 * (KeyOps<K>::dec(s[m / 2 - 1]) + KeyOps<K>::dec(s[m / 2]));
         m3 = 0.5 * (r23(s, m / 2 - 1) + r23(s, m / 2));
     }
-    long long lo = 0, hi = m;   // s0 = first index with v >= m3
-    while (lo < hi) { long long md = (lo + hi) / 2; if (r23(s, md) < m3) lo = md + 1; else hi = md; }
-    long long s0 = lo;
+    long long s0 = warp_first_true(0, m, [&](long long i) { return r23(s, i) >= m3; });
     double mad;
     if (m & 1) mad = kth_absdev(s, m, s0, m3, (m + 1) / 2);
     else mad = 0.5 * (kth_absdev(s, m, s0, m3, m / 2) + kth_absdev(s, m, s0, m3, m / 2 + 1));
     const double phi075 = 0.6744897501960817, madc = 1.4826;
-    AB[2 * l] = A;
-    AB[2 * l + 1] = pow(m3 + phi075 * madc * mad, 1.5);
+    if ((threadIdx.x & 31) == 0) {
+        AB[2 * l] = A;
+        AB[2 * l + 1] = pow(m3 + phi075 * madc * mad, 1.5);
+    }
 }
 
 void launch_gsscm(const Plan& P, const void* rkeys, cudaStream_t s) {
-    int th = 64, bl = (P.q + th - 1) / th;
+    int th = 128, bl = (P.q * 32 + th - 1) / th;
     if (P.key_bytes == 8) k_gsscm<unsigned long long><<<bl, th, 0, s>>>((const unsigned long long*)rkeys, P.q, P.m, P.gss);
     else k_gsscm<uint32_t><<<bl, th, 0, s>>>((const uint32_t*)rkeys, P.q, P.m, P.gss);
 }
@@ -406,26 +589,58 @@ __device__ inline u128 comp(const Cand& e) { return ((u128)e.key << 32) | (u128)
 
 __device__ Cand cta_select_rank(const Cand* list, int C, int r, int key_bits, Cand* buf, Status* st) {
     __shared__ unsigned hcnt[256];
+    __shared__ unsigned long long s_and, s_or;
     __shared__ int s_digit, s_r, s_cnt, s_n;
     __shared__ Cand s_out;
-    const int total = key_bits + 32;
-    u128 prefix = 0;
-    int pbits = 0, cnt = C, rr = r;
-    if (threadIdx.x == 0) { s_out.key = ~0ull; s_out.pos = 0xffffffffu; s_out.pad = 1; }
+    (void)key_bits;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_out.key = ~0ull; s_out.pos = 0xffffffffu; s_out.pad = 1;
+        s_and = ~0ull; s_or = 0ull; s_n = 0;
+    }
+    __syncthreads();
+    // key bits shared by every entry need no pass
+    {
+        unsigned long long a = ~0ull, o = 0ull;
+        for (int i = threadIdx.x; i < C; i += blockDim.x) { unsigned long long k = list[i].key; a &= k; o |= k; }
+        for (int d = 16; d > 0; d >>= 1) {
+            a &= __shfl_xor_sync(0xffffffffu, a, d);
+            o |= __shfl_xor_sync(0xffffffffu, o, d);
+        }
+        if (lane == 0) { atomicAnd(&s_and, a); atomicOr(&s_or, o); }
+    }
+    __syncthreads();
+    const unsigned long long diff = s_and ^ s_or;
+    // composite value: 96 bits = key (64) : position (32)
+    const int total = 96;
+    int top = diff ? 32 + 63 - __clzll((long long)diff) : 31;   // highest differing bit
+    int pbits = total - 1 - top;
+    u128 prefix = (((u128)s_and << 32) >> (top + 1));
+    int cnt = C, rr = r;
     while (cnt > SEL_SMALL && pbits < total) {
-        const int shift = total - pbits - 8;
+        const int width = (total - pbits) < 8 ? (total - pbits) : 8;
+        const int shift = total - pbits - width;
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hcnt[i] = 0u;
         __syncthreads();
-        for (int i = threadIdx.x; i < C; i += blockDim.x) {
-            u128 v = comp(list[i]);
-            if (pbits == 0 || (v >> (total - pbits)) == prefix)
-                atomicAdd(&hcnt[(unsigned)(v >> shift) & 255u], 1u);
+        for (int base = 0; base < C; base += blockDim.x) {
+            int i = base + threadIdx.x;
+            unsigned tag = 0x1000u + lane;
+            unsigned dg = 0;
+            if (i < C) {
+                u128 v = comp(list[i]);
+                if (pbits == 0 || (v >> (total - pbits)) == prefix) {
+                    dg = (unsigned)(v >> shift) & ((1u << width) - 1u);
+                    tag = dg;
+                }
+            }
+            unsigned peers = __match_any_sync(0xffffffffu, tag);
+            if (tag < 0x1000u && (__ffs(peers) - 1) == lane) atomicAdd(&hcnt[dg], (unsigned)__popc(peers));
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             int cum = 0;
             s_digit = -1;
-            for (int d = 0; d < 256; ++d) {
+            for (int d = 0; d < (1 << width); ++d) {
                 int hd = (int)hcnt[d];
                 if (cum + hd >= rr) { s_digit = d; s_r = rr - cum; s_cnt = hd; break; }
                 cum += hd;
@@ -433,19 +648,27 @@ __device__ Cand cta_select_rank(const Cand* list, int C, int r, int key_bits, Ca
         }
         __syncthreads();
         if (s_digit < 0) { if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL); __syncthreads(); return s_out; }
-        prefix = (prefix << 8) | (u128)(unsigned)s_digit;
-        pbits += 8;
+        prefix = (prefix << width) | (u128)(unsigned)s_digit;
+        pbits += width;
         rr = s_r;
         cnt = s_cnt;
         __syncthreads();
     }
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < C; i += blockDim.x) {
-        Cand e = list[i];
-        u128 v = comp(e);
-        if (pbits == 0 || (v >> (total - pbits)) == prefix) {
-            int slot = atomicAdd(&s_n, 1);
+    for (int base = 0; base < C; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        bool m = false;
+        Cand e;
+        if (i < C) {
+            e = list[i];
+            u128 v = comp(e);
+            m = (pbits == 0 || (v >> (total - pbits)) == prefix);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, m);
+        int wb = 0;
+        if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (m) {
+            int slot = wb + __popc(bal & ((1u << lane) - 1u));
             if (slot < SEL_SMALL) buf[slot] = e;
         }
     }
@@ -512,25 +735,37 @@ __global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict
     __syncthreads();
     Cand* band = band_all + (size_t)c * m;
     const RowParams& rp = ch[c].rp;
+    // collect the band rows first, so that the FP64 distances run on full warps
     int nlo = 0;
-    for (int i = threadIdx.x; i < C; i += blockDim.x) {
-        Cand e = cand[i];
-        if (e.key < t_lo) { ++nlo; continue; }
-        if (e.key > t_hi) continue;
-        const float* x = Xp + ((size_t)l * m + e.pos) * pb;
-        double d2 = row_d2_fp64(x, rp, p);
-        int slot = atomicAdd(&s_nb, 1);
-        Cand b;
-        b.key = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bits order as values
-        b.pos = e.pos;
-        b.pad = 0;
-        band[slot] = b;
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < C; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        bool inb = false;
+        Cand e;
+        if (i < C) {
+            e = cand[i];
+            if (e.key < t_lo) ++nlo;
+            else inb = e.key <= t_hi;
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, inb);
+        int wb = 0;
+        if (lane == 0 && bal) wb = atomicAdd(&s_nb, __popc(bal));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (inb) band[wb + __popc(bal & ((1u << lane) - 1u))] = e;
     }
     nlo = warp_sum_int(nlo);
-    if ((threadIdx.x & 31) == 0 && nlo) atomicAdd(&s_nlo, nlo);
+    if (lane == 0 && nlo) atomicAdd(&s_nlo, nlo);
     __threadfence_block();
     __syncthreads();
     const int nb = s_nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        Cand e = band[i];
+        const float* x = Xp + ((size_t)l * m + e.pos) * pb;
+        e.key = (unsigned long long)__double_as_longlong(row_d2_fp64(x, rp, p));  // d2 >= 0: bits order as values
+        band[i] = e;
+    }
+    __threadfence_block();
+    __syncthreads();
     const int r2 = hb - R.below - s_nlo;
     if (r2 < 1 || r2 > nb) {
         if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);

@@ -83,10 +83,13 @@ def test_fit_small_case(rtd, form):
     got, ref = _fit_both(rtd, fr, form)
     assert got["q"] == ref.q == 1
     d = got["diag"]
-    np.testing.assert_allclose(d["mu_uni"], ref.mu_uni, rtol=1e-10, atol=1e-12)
-    np.testing.assert_allclose(d["sigma_uni"], ref.s_uni, rtol=1e-10)
+    # the whole-column univariate MCD is FP64 in both forms
+    rt = 1e-10
+    np.testing.assert_allclose(d["mu_uni"], ref.mu_uni, rtol=rt, atol=rt * 1e-2)
+    np.testing.assert_allclose(d["sigma_uni"], ref.s_uni, rtol=rt)
     ok, rep = compare_fit(got, ref, fr.X, form)
-    assert ok, rep
+    if not ok:
+        pytest.fail(str(rep))
     assert got["n_flagged"] == int(ref.flags.sum())
 
 
@@ -107,7 +110,8 @@ def test_fit_blocks(rtd, form):
                 assert rel_mat(c["Sigma"], oc.Sigma) < TOL[form] * 10
         assert d["blocks"][l]["chosen"] == b.chosen
     ok, rep = compare_fit(got, ref, fr.X, form)
-    assert ok, rep
+    if not ok:
+        pytest.fail(str(rep))
 
 
 def test_fit_host_buffers(rtd):
@@ -115,7 +119,8 @@ def test_fit_host_buffers(rtd):
     got, ref = _fit_both(rtd, fr, "fp32", host=True)
     assert isinstance(got["flags"], np.ndarray)
     ok, rep = compare_fit(got, ref, fr.X, "fp32")
-    assert ok, rep
+    if not ok:
+        pytest.fail(str(rep))
 
 
 # ----------------------------------------------------- full-size workload
@@ -134,7 +139,8 @@ def test_fit_main_case(rtd, main_case, form):
                            subset=True, diag=True)
     assert got["q"] == ref.q == 12
     ok, rep = compare_fit(got, ref, fr.X, form)
-    assert ok, rep
+    if not ok:
+        pytest.fail(str(rep))
     for l, b in enumerate(ref.blocks):
         assert got["diag"]["blocks"][l]["chosen"] == b.chosen
         assert got["diag"]["blocks"][l]["kept"] == int(l in ref.kept)
@@ -185,7 +191,8 @@ def test_fit_edges(rtd, form, n, p, alpha, seed):
                            subset=True, diag=True)
     assert got["q"] == ref.q
     ok, rep = compare_fit(got, ref, fr.X, form)
-    assert ok, rep
+    if not ok:
+        pytest.fail(str(rep))
 
 
 def test_fit_deterministic(rtd):
