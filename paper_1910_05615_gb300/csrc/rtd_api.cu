@@ -311,7 +311,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
     launch_uni_finish(P, s);
     // rows read, keys written, 4 sort passes (read + write), window scan read
-    pf.end(6 + 3 * 4, n_ * p_ * (4 + 4 + 4 * 8 + 4));
+    pf.end(9 + 3 * 4, n_ * p_ * (4 + 4 + 4 * 8 + 4));
     { int e = fetch_status(P.st, s, hs); if (e) return e; }
     pf.collect();
     if (hs.code) goto finish;
@@ -334,7 +334,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
     launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
     launch_refine_end(P, s);
-    pf.end(11 + 6 * S.key_bytes,
+    pf.end(17 + 6 * S.key_bytes,
            2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * (1 + 2 * S.key_bytes + 1)));
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
     {

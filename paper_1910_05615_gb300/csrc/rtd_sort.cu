@@ -162,156 +162,270 @@ void sort_segments(const Plan& P, void* keys, void* tmp, int key_bytes, int nseg
 // h~ = [L/2] + 1; the contiguous h~-window of minimum variance (first on
 // ties) gives mu0 and c(h~/L) var; the reweighting keeps
 // (x - mu0)^2 / s0^2 <= chi2_{1,q}, a contiguous range of the sorted values.
-// Window sums are differences of FP64 running sums of the values shifted by
-// the middle order statistic.  Three launches, all coalesced:
-//   U1  chunk sums of every segment,
-//   U2  windows of a chunk of starts: two block scans in lock step over the
-//       values at positions j and j + h~, per-CTA argmin,
-//   U3  per segment: argmin over chunks, reweighting bounds by a CTA-wide
-//       256-ary search, sums over the kept range.
+// All sums are FP64 over the values shifted by the middle order statistic c;
+// q_j = h S2_j - S1_j^2 = h (h-1) var_j orders the windows.
+//
+// Windows are grouped in ranges of UW starts.  Every window of a range
+// contains the core of sorted positions shared by all of them, and for any
+// subset C of a window  sum_window (x - mean)^2 >= (|C| - 1) var(C), so
+// q_j >= h q_C / |C| bounds the whole range from below (C taken on the chunk
+// grid so that it comes from chunk prefix sums).  Ranges whose bound exceeds
+// the exact q of some window are skipped; the others are evaluated window by
+// window.  Kernels:
+//   U1 chunk sums (UC positions)        U2 exclusive scan of chunk sums
+//   U3 per range: bound and q at its first window
+//   U4 per segment: least first-window q     U5 per range: exact windows
+//   U6 per segment: argmin, reweighting bounds by a 256-ary search, sums.
 // out[seg] = (mu, s2, mu_raw, s2_raw); NaN marks a degenerate segment.
 // =====================================================================
 constexpr int UT = 256;              // threads
-constexpr int UV = 4;                // values per thread and tile
-constexpr int UTILE = UT * UV;       // 1024
-constexpr int UCH = 8 * UTILE;       // chunk of positions / window starts
+constexpr int UC = 256;              // chunk of positions (prefix anchors)
+constexpr int UW = 256;              // range of window starts
+
+// float or double value of a sort key as a double; for 32-bit keys the
+// conversion is done with integer operations (exact for every float).
+__device__ inline double kval(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;    // float bits
+    uint32_t e = (u >> 23) & 0xffu, mant = u & 0x7fffffu;
+    unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (e == 0u) {
+        if (mant == 0u) return __longlong_as_double((long long)sign);
+        return (double)__uint_as_float(u);                       // subnormal: rare
+    }
+    if (e == 0xffu) return (double)__uint_as_float(u);            // inf / nan
+    unsigned long long b = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)mant << 29);
+    return __longlong_as_double((long long)b);
+}
+__device__ inline double kval(unsigned long long k) { return key2d(k); }
 
 template <typename K>
-__device__ inline double uval(const K* s, long long i) { return KeyOps<K>::dec(s[i]); }
+__device__ inline double uval(const K* s, long long i) { return kval(s[i]); }
 
 struct D2 { double a, b; };
 
-// Block-wide exclusive scan of (a, b) pairs (one pair per thread); returns
-// the exclusive prefix and writes the block total to tot.
-__device__ inline D2 cta_exscan2(D2 v, D2& tot) {
-    __shared__ double wa[UT / 32], wb[UT / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    D2 x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        double ya = __shfl_up_sync(0xffffffffu, x.a, o);
-        double yb = __shfl_up_sync(0xffffffffu, x.b, o);
-        if (lane >= o) { x.a += ya; x.b += yb; }
+__device__ inline D2 warp_sum2(D2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.a += __shfl_xor_sync(0xffffffffu, v.a, o);
+        v.b += __shfl_xor_sync(0xffffffffu, v.b, o);
     }
-    if (lane == 31) { wa[w] = x.a; wb[w] = x.b; }
-    __syncthreads();
-    double pa = 0.0, pb = 0.0, ta = 0.0, tb = 0.0;
-    for (int k = 0; k < UT / 32; ++k) {
-        if (k < w) { pa += wa[k]; pb += wb[k]; }
-        ta += wa[k]; tb += wb[k];
-    }
-    __syncthreads();
-    tot = D2{ta, tb};
-    return D2{pa + x.a - v.a, pb + x.b - v.b};
+    return v;
 }
 
 __device__ inline D2 cta_sum2(D2 v) {
-    D2 t;
-    cta_exscan2(v, t);
+    __shared__ double wa[UT / 32], wb[UT / 32];
+    v = warp_sum2(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { wa[w] = v.a; wb[w] = v.b; }
+    __syncthreads();
+    D2 t{0.0, 0.0};
+    for (int k = 0; k < UT / 32; ++k) { t.a += wa[k]; t.b += wb[k]; }
+    __syncthreads();
     return t;
 }
 
-// Sum of (s_i - c, (s_i - c)^2) over [a, b) by the whole CTA.
+// Sum of (s_i - c, (s_i - c)^2) over [a, b) by one warp / by the CTA.
+template <typename K>
+__device__ inline D2 warp_range_sum(const K* s, double c, long long a, long long b) {
+    D2 acc{0.0, 0.0};
+    for (long long i = a + (threadIdx.x & 31); i < b; i += 32) {
+        double d = uval(s, i) - c;
+        acc.a += d;
+        acc.b = fma(d, d, acc.b);
+    }
+    return warp_sum2(acc);
+}
 template <typename K>
 __device__ inline D2 cta_range_sum(const K* s, double c, long long a, long long b) {
     D2 acc{0.0, 0.0};
     for (long long i = a + threadIdx.x; i < b; i += UT) {
         double d = uval(s, i) - c;
         acc.a += d;
-        acc.b += d * d;
+        acc.b = fma(d, d, acc.b);
     }
     return cta_sum2(acc);
 }
 
-// Running sum up to position a from the chunk sums plus a partial chunk.
-template <typename K>
-__device__ inline D2 cta_prefix(const K* s, double c, const double* csum, long long a) {
-    long long ca = a / UCH;
-    D2 acc{0.0, 0.0};
-    for (long long k = threadIdx.x; k < ca; k += UT) { acc.a += csum[2 * k]; acc.b += csum[2 * k + 1]; }
-    D2 t1 = cta_sum2(acc);
-    D2 t2 = cta_range_sum(s, c, ca * UCH, a);
-    return D2{t1.a + t2.a, t1.b + t2.b};
-}
-
+// U1: warp per chunk.
 template <typename K>
 __global__ void __launch_bounds__(UT) k_uni_chunks(const K* __restrict__ sorted, long long L, int nch,
                                                    double* __restrict__ csum) {
-    const int seg = blockIdx.y, ch = blockIdx.x;
+    const int seg = blockIdx.y;
+    const int ch = blockIdx.x * (UT / 32) + (threadIdx.x >> 5);
+    if (ch >= nch) return;
     const K* s = sorted + (long long)seg * L;
     const double c = uval(s, L / 2);
-    long long a = (long long)ch * UCH, b = a + UCH < L ? a + UCH : L;
-    D2 t = cta_range_sum(s, c, a, b);
-    if (threadIdx.x == 0) {
+    long long a = (long long)ch * UC, b = a + UC < L ? a + UC : L;
+    D2 t = warp_range_sum(s, c, a, b);
+    if ((threadIdx.x & 31) == 0) {
         double* o = csum + ((size_t)seg * nch + ch) * 2;
         o[0] = t.a;
         o[1] = t.b;
     }
 }
 
+// U2: cpre[seg][k] = sum of chunks < k, k = 0..nch (one CTA per segment).
+__global__ void __launch_bounds__(1024) k_uni_prefix(const double* __restrict__ csum, int nch,
+                                                     double* __restrict__ cpre) {
+    __shared__ double pa[1024], pb[1024];
+    const int seg = blockIdx.x;
+    const double* c = csum + (size_t)seg * nch * 2;
+    double* o = cpre + (size_t)seg * (nch + 1) * 2;
+    const int per = (nch + 1023) / 1024;
+    const int b0 = threadIdx.x * per, b1 = b0 + per < nch ? b0 + per : nch;
+    double sa = 0.0, sb = 0.0;
+    for (int k = b0; k < b1; ++k) { sa += c[2 * k]; sb += c[2 * k + 1]; }
+    pa[threadIdx.x] = sa;
+    pb[threadIdx.x] = sb;
+    __syncthreads();
+    if (threadIdx.x == 0) {   // fixed order
+        double ra = 0.0, rb = 0.0;
+        for (int t = 0; t < 1024; ++t) {
+            double va = pa[t], vb = pb[t];
+            pa[t] = ra; pb[t] = rb;
+            ra += va; rb += vb;
+        }
+        o[2 * nch] = ra;
+        o[2 * nch + 1] = rb;
+    }
+    __syncthreads();
+    double ra = pa[threadIdx.x], rb = pb[threadIdx.x];
+    for (int k = b0; k < b1; ++k) {
+        o[2 * k] = ra;
+        o[2 * k + 1] = rb;
+        ra += c[2 * k];
+        rb += c[2 * k + 1];
+    }
+}
+
+// Running sums up to position x (exact FP64): anchor plus a partial chunk.
 template <typename K>
-__global__ void __launch_bounds__(UT) k_uni_windows(const K* __restrict__ sorted, long long L, int nch,
-                                                    const double* __restrict__ csum_all, int nwch,
-                                                    double* __restrict__ wres) {
-    __shared__ double rv[UT / 32], rs[UT / 32];
-    __shared__ long long rj[UT / 32];
-    const int seg = blockIdx.y, wc = blockIdx.x;
+__device__ inline D2 warp_prefix(const K* s, double c, const double* cpre, long long x) {
+    long long k = x / UC;
+    D2 t = warp_range_sum(s, c, k * UC, x);
+    return D2{cpre[2 * k] + t.a, cpre[2 * k + 1] + t.b};
+}
+template <typename K>
+__device__ inline D2 cta_prefix(const K* s, double c, const double* cpre, long long x) {
+    long long k = x / UC;
+    D2 t = cta_range_sum(s, c, k * UC, x);
+    return D2{cpre[2 * k] + t.a, cpre[2 * k + 1] + t.b};
+}
+
+// U3: warp per range: lower bound over the range and q at its first window.
+template <typename K>
+__global__ void __launch_bounds__(UT) k_uni_bound(const K* __restrict__ sorted, long long L, int nch, int nwr,
+                                                  const double* __restrict__ cpre_all, double* __restrict__ wb) {
+    const int seg = blockIdx.y;
+    const int r = blockIdx.x * (UT / 32) + (threadIdx.x >> 5);
+    if (r >= nwr) return;
     const K* s = sorted + (long long)seg * L;
-    const double* csum = csum_all + (size_t)seg * nch * 2;
+    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
     const long long h = L / 2 + 1, nwin = L - h + 1;
-    const double c = uval(s, L / 2);
-    const long long j0 = (long long)wc * UCH;
-    const long long j1 = j0 + UCH < nwin ? j0 + UCH : nwin;
-    D2 PA = cta_prefix(s, c, csum, j0);
-    D2 PB = cta_prefix(s, c, csum, j0 + h);
-    double best = INFINITY, bs1 = 0.0;
-    long long bj = -1;
-    for (long long t0 = j0; t0 < j1; t0 += UTILE) {
-        const long long base = t0 + (long long)threadIdx.x * UV;
-        D2 la{0.0, 0.0}, lb{0.0, 0.0};
-        double da[UV], db[UV];
-#pragma unroll
-        for (int u = 0; u < UV; ++u) {
-            long long ja = base + u, jb = base + u + h;
-            da[u] = (ja < j1) ? uval(s, ja) - c : 0.0;
-            db[u] = (ja < j1 && jb < L) ? uval(s, jb) - c : 0.0;
-            la.a += da[u]; la.b += da[u] * da[u];
-            lb.a += db[u]; lb.b += db[u] * db[u];
-        }
-        D2 ta, tb;
-        D2 ea = cta_exscan2(la, ta);
-        D2 eb = cta_exscan2(lb, tb);
-        double A1 = PA.a + ea.a, A2 = PA.b + ea.b, B1 = PB.a + eb.a, B2 = PB.b + eb.b;
-#pragma unroll
-        for (int u = 0; u < UV; ++u) {
-            long long j = base + u;
-            if (j < j1) {
-                double S1 = B1 - A1, S2 = B2 - A2;
-                double var = (S2 - S1 * S1 / (double)h) / (double)(h - 1);
-                if (var < best) { best = var; bj = j; bs1 = S1; }
-            }
-            A1 += da[u]; A2 += da[u] * da[u];
-            B1 += db[u]; B2 += db[u] * db[u];
-        }
-        PA.a += ta.a; PA.b += ta.b;
-        PB.a += tb.a; PB.b += tb.b;
+    const double hd = (double)h, c = uval(s, L / 2);
+    const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
+    // aligned core [lo, hi) inside [b - 1, a + h)
+    const long long lo = ((b - 1 + UC - 1) / UC) * UC, hi = ((a + h) / UC) * UC;
+    double lb = -INFINITY;
+    if (hi - lo >= 2) {
+        double n = (double)(hi - lo);
+        double s1 = cpre[2 * (hi / UC)] - cpre[2 * (lo / UC)];
+        double s2 = cpre[2 * (hi / UC) + 1] - cpre[2 * (lo / UC) + 1];
+        lb = hd * (n * s2 - s1 * s1) / n;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        double os = __shfl_xor_sync(0xffffffffu, bs1, o);
-        long long oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if (oj >= 0 && (bj < 0 || ov < best || (ov == best && oj < bj))) { best = ov; bj = oj; bs1 = os; }
+    D2 pb = warp_prefix(s, c, cpre, a + h);
+    double S1 = pb.a - cpre[2 * (a / UC)], S2 = pb.b - cpre[2 * (a / UC) + 1];
+    double qa = hd * S2 - S1 * S1;
+    if ((threadIdx.x & 31) == 0) {
+        double* o = wb + ((size_t)seg * nwr + r) * 2;
+        o[0] = lb;
+        o[1] = qa;
     }
-    if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; rj[threadIdx.x >> 5] = bj; rs[threadIdx.x >> 5] = bs1; }
+}
+
+// U4: least first-window q of each segment.
+__global__ void __launch_bounds__(UT) k_uni_ub(const double* __restrict__ wb, int nwr, double* __restrict__ ub) {
+    __shared__ double red[UT / 32];
+    const int seg = blockIdx.x;
+    double m = INFINITY;
+    for (int r = threadIdx.x; r < nwr; r += UT) m = fmin(m, wb[((size_t)seg * nwr + r) * 2 + 1]);
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = INFINITY, bsum = 0.0;
+        double v = INFINITY;
+        for (int k = 0; k < UT / 32; ++k) v = fmin(v, red[k]);
+        ub[seg] = v;
+    }
+}
+
+// U5: exact windows of the ranges the bound does not exclude.
+template <typename K>
+__global__ void __launch_bounds__(UT) k_uni_eval(const K* __restrict__ sorted, long long L, int nch, int nwr,
+                                                 const double* __restrict__ cpre_all, const double* __restrict__ wb,
+                                                 const double* __restrict__ ub, double* __restrict__ wres) {
+    __shared__ double sw[UT / 32][4];
+    __shared__ double sq[UT / 32], ss[UT / 32];
+    __shared__ long long sj[UT / 32];
+    __shared__ double s_pb[2];
+    const int seg = blockIdx.y, r = blockIdx.x;
+    double* o = wres + ((size_t)seg * nwr + r) * 3;
+    const double lb = wb[((size_t)seg * nwr + r) * 2];
+    if (lb > ub[seg] * (1.0 + 1e-12)) {
+        if (threadIdx.x == 0) { o[0] = INFINITY; o[1] = -1.0; o[2] = 0.0; }
+        return;
+    }
+    const K* s = sorted + (long long)seg * L;
+    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    const double hd = (double)h, c = uval(s, L / 2);
+    const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {
+        D2 pb = warp_prefix(s, c, cpre, a + h);
+        if (lane == 0) { s_pb[0] = pb.a; s_pb[1] = pb.b; }
+    }
+    const long long j = a + threadIdx.x;
+    double da = 0.0, db = 0.0;
+    if (j < b) {
+        da = uval(s, j) - c;
+        if (j + h < L) db = uval(s, j + h) - c;
+    }
+    // exclusive scans of (da, da^2, db, db^2) over the range
+    double x0 = da, x1 = da * da, x2 = db, x3 = db * db;
+    for (int off = 1; off < 32; off <<= 1) {
+        double y0 = __shfl_up_sync(0xffffffffu, x0, off), y1 = __shfl_up_sync(0xffffffffu, x1, off);
+        double y2 = __shfl_up_sync(0xffffffffu, x2, off), y3 = __shfl_up_sync(0xffffffffu, x3, off);
+        if (lane >= off) { x0 += y0; x1 += y1; x2 += y2; x3 += y3; }
+    }
+    if (lane == 31) { sw[w][0] = x0; sw[w][1] = x1; sw[w][2] = x2; sw[w][3] = x3; }
+    __syncthreads();
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    for (int k = 0; k < w; ++k) { p0 += sw[k][0]; p1 += sw[k][1]; p2 += sw[k][2]; p3 += sw[k][3]; }
+    const double A1 = cpre[2 * (a / UC)] + p0 + x0 - da, A2 = cpre[2 * (a / UC) + 1] + p1 + x1 - da * da;
+    const double B1 = s_pb[0] + p2 + x2 - db, B2 = s_pb[1] + p3 + x3 - db * db;
+    double q = INFINITY, s1 = 0.0;
+    long long bj = -1;
+    if (j < b) {
+        s1 = B1 - A1;
+        q = hd * (B2 - A2) - s1 * s1;
+        bj = j;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        double oq = __shfl_xor_sync(0xffffffffu, q, off);
+        double os = __shfl_xor_sync(0xffffffffu, s1, off);
+        long long oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        if (oj >= 0 && (bj < 0 || oq < q || (oq == q && oj < bj))) { q = oq; bj = oj; s1 = os; }
+    }
+    if (lane == 0) { sq[w] = q; sj[w] = bj; ss[w] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bq = INFINITY, bs = 0.0;
         long long jj = -1;
-        for (int w = 0; w < UT / 32; ++w)
-            if (rj[w] >= 0 && (jj < 0 || rv[w] < b || (rv[w] == b && rj[w] < jj))) { b = rv[w]; jj = rj[w]; bsum = rs[w]; }
-        double* o = wres + ((size_t)seg * nwch + wc) * 3;
-        o[0] = b;
+        for (int k = 0; k < UT / 32; ++k)
+            if (sj[k] >= 0 && (jj < 0 || sq[k] < bq || (sq[k] == bq && sj[k] < jj))) { bq = sq[k]; jj = sj[k]; bs = ss[k]; }
+        o[0] = bq;
         o[1] = (double)jj;
-        o[2] = bsum;
+        o[2] = bs;
     }
 }
 
@@ -349,43 +463,47 @@ __device__ inline long long cta_first_true(long long lo, long long hi, Pred pred
     }
 }
 
+// U6
 template <typename K>
-__global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sorted, long long L, int nch,
-                                                       const double* __restrict__ csum_all, int nwch,
+__global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sorted, long long L, int nch, int nwr,
+                                                       const double* __restrict__ cpre_all,
                                                        const double* __restrict__ wres,
                                                        const Consts* __restrict__ cs, int which_c1,
                                                        double* __restrict__ out) {
     __shared__ double sv[UT], ss[UT];
     __shared__ long long sj[UT];
+    __shared__ double s_q, s_s1;
+    __shared__ long long s_j;
     const int seg = blockIdx.x;
     const K* s = sorted + (long long)seg * L;
-    const double* csum = csum_all + (size_t)seg * nch * 2;
+    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
     const long long h = L / 2 + 1;
+    const double hd = (double)h;
     const double c = uval(s, L / 2);
     double best = INFINITY, bs1 = 0.0;
     long long bj = -1;
-    for (int w = threadIdx.x; w < nwch; w += UT) {
-        const double* r = wres + ((size_t)seg * nwch + w) * 3;
-        long long jj = (long long)r[1];
-        if (jj >= 0 && (bj < 0 || r[0] < best || (r[0] == best && jj < bj))) { best = r[0]; bj = jj; bs1 = r[2]; }
+    for (int r = threadIdx.x; r < nwr; r += UT) {
+        const double* x = wres + ((size_t)seg * nwr + r) * 3;
+        long long jj = (long long)x[1];
+        if (jj >= 0 && (bj < 0 || x[0] < best || (x[0] == best && jj < bj))) { best = x[0]; bj = jj; bs1 = x[2]; }
     }
     sv[threadIdx.x] = best; ss[threadIdx.x] = bs1; sj[threadIdx.x] = bj;
     __syncthreads();
-    __shared__ double s_var, s_s1;
-    __shared__ long long s_j;
     if (threadIdx.x == 0) {
         double b = INFINITY, bsum = 0.0;
         long long jj = -1;
         for (int t = 0; t < UT; ++t)
             if (sj[t] >= 0 && (jj < 0 || sv[t] < b || (sv[t] == b && sj[t] < jj))) { b = sv[t]; jj = sj[t]; bsum = ss[t]; }
-        s_var = b; s_j = jj; s_s1 = bsum;
+        s_q = b; s_j = jj; s_s1 = bsum;
     }
     __syncthreads();
     double* o = out + 4 * (size_t)seg;
     if (s_j < 0) { if (threadIdx.x == 0) { o[0] = o[1] = o[2] = o[3] = NAN; } return; }
     const double c1 = which_c1 ? cs->c1_m : cs->c1_n;
-    const double mu0 = c + s_s1 / (double)h;
-    const double s20 = c1 * s_var;
+    const double mu0 = c + s_s1 / hd;
+    // a window of equal values has variance exactly 0 (degenerate column)
+    const bool flat = uval(s, s_j) == uval(s, s_j + h - 1);
+    const double s20 = flat ? 0.0 : c1 * (s_q / (hd * (hd - 1.0)));
     if (!(s20 > 0.0) || !isfinite(s20)) {
         if (threadIdx.x == 0) { o[0] = NAN; o[1] = NAN; o[2] = mu0; o[3] = s20; }
         return;
@@ -400,8 +518,8 @@ __global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sor
         if (threadIdx.x == 0) { o[0] = NAN; o[1] = NAN; o[2] = mu0; o[3] = s20; }
         return;
     }
-    D2 Pa = cta_prefix(s, c, csum, wlo);
-    D2 Pb = cta_prefix(s, c, csum, whi);
+    D2 Pa = cta_prefix(s, c, cpre, wlo);
+    D2 Pb = cta_prefix(s, c, cpre, whi);
     if (threadIdx.x == 0) {
         double T1 = Pb.a - Pa.a, T2 = Pb.b - Pa.b;
         o[0] = c + T1 / (double)nw;
@@ -411,17 +529,28 @@ __global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sor
     }
 }
 
+struct UniDims { int nch, nwr; };
+inline UniDims uni_dims(long long L) {
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    return UniDims{(int)((L + UC - 1) / UC), (int)((nwin + UW - 1) / UW)};
+}
+
 template <typename K>
 static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int which_c1, double* out,
                      cudaStream_t s) {
-    const long long h = L / 2 + 1, nwin = L - h + 1;
-    const int nch = (int)((L + UCH - 1) / UCH);
-    const int nwch = (int)((nwin + UCH - 1) / UCH);
+    const UniDims D = uni_dims(L);
     double* csum = P.uscratch;
-    double* wres = P.uscratch + (size_t)nseg * nch * 2;
-    k_uni_chunks<K><<<dim3(nch, nseg), UT, 0, s>>>(keys, L, nch, csum);
-    k_uni_windows<K><<<dim3(nwch, nseg), UT, 0, s>>>(keys, L, nch, csum, nwch, wres);
-    k_uni_finish_seg<K><<<nseg, UT, 0, s>>>(keys, L, nch, csum, nwch, wres, P.cs, which_c1, out);
+    double* cpre = csum + (size_t)nseg * D.nch * 2;
+    double* wb = cpre + (size_t)nseg * (D.nch + 1) * 2;
+    double* ub = wb + (size_t)nseg * D.nwr * 2;
+    double* wres = ub + nseg;
+    const int wpb = UT / 32;
+    k_uni_chunks<K><<<dim3((D.nch + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, csum);
+    k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, cpre);
+    k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
+    k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub);
+    k_uni_eval<K><<<dim3(D.nwr, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
+    k_uni_finish_seg<K><<<nseg, UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wres, P.cs, which_c1, out);
 }
 
 void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L, int which_c1,
@@ -431,9 +560,8 @@ void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, lon
 }
 
 size_t unimcd_scratch_doubles(int nseg, long long L) {
-    const long long h = L / 2 + 1, nwin = L - h + 1;
-    const long long nch = (L + UCH - 1) / UCH, nwch = (nwin + UCH - 1) / UCH;
-    return (size_t)nseg * (2 * nch + 3 * nwch);
+    const UniDims D = uni_dims(L);
+    return (size_t)nseg * (2 * (size_t)D.nch + 2 * ((size_t)D.nch + 1) + 2 * (size_t)D.nwr + 1 + 3 * (size_t)D.nwr);
 }
 
 // =====================================================================
