@@ -128,6 +128,18 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_throughput(local_total_ms, rows_per_rank, steps, world, pg=None, device=None):
+    """Whole-job rows/s of independent replicas: the rows of every rank over
+    the slowest rank's timed total (max over ranks)."""
+    tot = float(local_total_ms)
+    if pg is not None and world > 1:
+        import torch
+        t = torch.tensor([tot], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tot = float(t.item())
+    return steps * rows_per_rank * world / (tot / 1e3), tot
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -252,12 +264,7 @@ def main():
                "h2d_bytes_per_step": n * p * 4, "d2h_bytes_per_step": n * 4 + n + 67_000,
                "path": "rtdetmcd_fit with pinned host X, host d2 and flags outputs"}
 
-    tot32 = sum(t32)
-    if pg is not None:
-        tt = torch.tensor([tot32], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        tot32 = float(tt.item())
-    value = args.steps * n * ws_n / (tot32 / 1e3)
+    value, tot32 = replica_throughput(sum(t32), n, args.steps, ws_n, pg, dev)
     if rank != 0:
         pg.destroy_process_group()
         return 0

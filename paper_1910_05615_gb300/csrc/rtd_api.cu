@@ -280,8 +280,11 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         P.X = X;
     } else {
         float* xs = at<float>(ws, R.xstage);
-        RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)S.p * sizeof(float), X, (size_t)S.ld * sizeof(float),
-                                   (size_t)S.p * sizeof(float), (size_t)S.n, cudaMemcpyHostToDevice, s));
+        if (S.ld == S.p)   // contiguous rows: one copy
+            RTD_CUDA(cudaMemcpyAsync(xs, X, (size_t)S.n * S.p * sizeof(float), cudaMemcpyHostToDevice, s));
+        else
+            RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)S.p * sizeof(float), X, (size_t)S.ld * sizeof(float),
+                                       (size_t)S.p * sizeof(float), (size_t)S.n, cudaMemcpyHostToDevice, s));
         P.X = xs;
         P.ld = S.p;
     }
@@ -514,8 +517,11 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld, const d
     long long ldd = ld;
     if (!is_device_ptr(X)) {
         float* xs = at<float>(workspace, rxs);
-        RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)p * sizeof(float), X, (size_t)ld * sizeof(float),
-                                   (size_t)p * sizeof(float), (size_t)n, cudaMemcpyHostToDevice, s));
+        if (ld == p)
+            RTD_CUDA(cudaMemcpyAsync(xs, X, (size_t)n * p * sizeof(float), cudaMemcpyHostToDevice, s));
+        else
+            RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)p * sizeof(float), X, (size_t)ld * sizeof(float),
+                                       (size_t)p * sizeof(float), (size_t)n, cudaMemcpyHostToDevice, s));
         Xd = xs;
         ldd = p;
     }
