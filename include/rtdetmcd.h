@@ -180,6 +180,32 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld,
                        int32_t precision, float* d2_out,
                        void* workspace, size_t ws_bytes, void* stream);
 
+/* Size of the fixed device array used by rtdetmcd_distances_noalloc. */
+#define RTD_NOALLOC_SCRATCH_BYTES (96 * 1024)
+
+/*
+ * Scoring without allocating: the squared distances of rtdetmcd_distances,
+ * for callers that cannot allocate device memory when they score (a sorting
+ * line that must not wait on an allocator between frames, code that runs in
+ * a fixed memory budget, or a process whose device memory is owned by
+ * another component).  The paper has no counterpart; this is an interface
+ * convenience.
+ *   X, d2_out  device pointers (RTD_EINVAL for host memory: staging host rows
+ *              would need memory proportional to n)
+ *   p          <= RTD_MAX_P, the largest fit the array holds (RTD_EINVAL above)
+ * The working state (factorised fit, status word) lives in one file-scope
+ * device array of RTD_NOALLOC_SCRATCH_BYTES that every GPU using the library
+ * keeps until the process exits.  The first call on a device looks up that
+ * array's device address; make that first call before capturing any stream
+ * into a CUDA graph.  All calls on a device share the array and it keeps the
+ * last call's contents: calls whose device work overlaps (several threads or
+ * streams at the same time) race on it and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or other allocation is made.
+ */
+int rtdetmcd_distances_noalloc(const float* X, int64_t n, int32_t p, int64_t ld,
+                               const double* mu_host, const double* sigma_host,
+                               int32_t precision, float* d2_out, void* stream);
+
 /*
  * Outlier flags of Section 4 step 10: flags_out[i] = (d2[i] > cutoff_d2).
  * n_flagged (nullable, host) receives the count.  workspace >= 256 bytes.

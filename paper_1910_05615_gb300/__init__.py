@@ -20,7 +20,7 @@ from . import build as _build_mod
 
 __all__ = [
     "RTD_FP32", "RTD_FP64", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
-    "rtdetmcd_flag", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
+    "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
     "rtdetmcd_diag_size", "parse_diag",
 ]
 
@@ -99,6 +99,8 @@ def _load():
     lib.rtdetmcd_distances_workspace_size.restype = sz
     lib.rtdetmcd_distances.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp, sz, vp]
     lib.rtdetmcd_distances.restype = i32
+    lib.rtdetmcd_distances_noalloc.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp]
+    lib.rtdetmcd_distances_noalloc.restype = i32
     lib.rtdetmcd_flag.argtypes = [vp, i64, dbl, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.rtdetmcd_flag.restype = i32
     lib.rtdetmcd_chi2_quantile.argtypes = [i32, dbl]
@@ -268,6 +270,25 @@ def rtdetmcd_distances(X, mu, Sigma, *, precision=RTD_FP32, stream=None, workspa
     d2 = _out(n, np.float32, dev)
     st = lib.rtdetmcd_distances(ptr, n, p, ld, mu.ctypes.data, S.ctypes.data, precision, _ptr(d2),
                                 ws.data_ptr(), ws.numel(), _stream_ptr(dev, stream))
+    del keep
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return d2
+
+
+def rtdetmcd_distances_noalloc(X, mu, Sigma, *, precision=RTD_FP32, out=None, stream=None):
+    """Squared distances like rtdetmcd_distances, for callers that cannot
+    allocate when they score: no workspace, the library uses a fixed device
+    array instead.  X (and out, if given) must be CUDA tensors."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    if dev is None:
+        raise ValueError("rtdetmcd_distances_noalloc needs X on a CUDA device")
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    S = np.ascontiguousarray(Sigma, dtype=np.float64)
+    d2 = out if out is not None else _out(n, np.float32, dev)
+    st = lib.rtdetmcd_distances_noalloc(ptr, n, p, ld, mu.ctypes.data, S.ctypes.data, precision, _ptr(d2),
+                                        _stream_ptr(dev, stream))
     del keep
     if st != 0:
         raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
