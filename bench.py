@@ -35,6 +35,11 @@ CPU_SAMPLE_ROWS = 250_000
 REF_SAMPLE_ROWS = 200_000
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_dist launch at n=1e6,
+# p=20 with both chains of every block active (80.14 MB + 2.74 MB)
+K_DIST_TRAFFIC = 82.88e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -214,7 +219,7 @@ def main():
         return rtd.rtdetmcd_fit(Xin, h, precision=prec, workspace=ws, profile=profile,
                                 stream=stream.cuda_stream)
 
-    def timed(Xin, prec, ws, k):
+    def timed(Xin, prec, ws, k, profile=False):
         out, profs = [], []
         for i in range(k):
             flush.fill_(i & 255)
@@ -222,11 +227,12 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = fit(Xin, prec, ws, profile=True)
+            r = fit(Xin, prec, ws, profile=profile)
             e1.record(stream)
             e1.synchronize()
             out.append(e0.elapsed_time(e1))
-            profs.append(r["profile"])
+            if profile:
+                profs.append(r["profile"])
             last = r
         return out, profs, last
 
@@ -236,14 +242,16 @@ def main():
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or str(local)
     clk = Clocks(gpu_index if gpu_index.isdigit() else local)
     time.sleep(0.3)
-    t32, prof32, r32 = timed(X, rtd.RTD_FP32, ws32, args.steps)
+    t32, _, r32 = timed(X, rtd.RTD_FP32, ws32, args.steps)
     barrier()
     clocks = clk.stop()
+    # the same steps again with per-stage CUDA events on the fit's stream
+    tprof, prof32, _ = timed(X, rtd.RTD_FP32, ws32, args.steps, profile=True)
     # plain FP64 form beside it
     t64 = []
     if args.fp64_steps > 0:
         fit(X, rtd.RTD_FP64, ws64)
-        t64, prof64, r64 = timed(X, rtd.RTD_FP64, ws64, args.fp64_steps)
+        t64, _, r64 = timed(X, rtd.RTD_FP64, ws64, args.fp64_steps)
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -281,17 +289,29 @@ def main():
     tot_stage = sum(s["ms_per_fit"] for s in stages.values())
     for s in stages.values():
         s["share"] = s["ms_per_fit"] / tot_stage if tot_stage else 0.0
-    d_ms = sum(pp["stages"]["cstep_dist"]["ms"] for pp in prof32)
-    d_by = sum(pp["stages"]["cstep_dist"]["bytes"] for pp in prof32)
-    d_la = sum(pp["stages"]["cstep_dist"]["launches"] for pp in prof32)
-    achieved = d_by / (d_ms / 1e3) / 1e9
-    s_ms = d_ms + sum(pp["stages"]["cstep_select"]["ms"] for pp in prof32)
-    s_by = d_by + sum(pp["stages"]["cstep_select"]["bytes"] for pp in prof32)
-    roof = {"kernel": "k_dist (C-step distances + fused top-digit histogram)", "bound": "hbm",
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_kind": peak_kind,
-            "bytes_per_launch": d_by / d_la, "launch_ms": d_ms / d_la,
-            "dist_plus_select_frac": (s_by / (s_ms / 1e3) / 1e9) / peak}
+    def stage_roof(name, kernel):
+        ms = sum(pp["stages"][name]["ms"] for pp in prof32)
+        by = sum(pp["stages"][name]["bytes"] for pp in prof32)
+        la = sum(pp["stages"][name]["launches"] for pp in prof32)
+        a = by / (ms / 1e3) / 1e9
+        return {"kernel": kernel, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s",
+                "frac": a / peak, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": by / la, "launch_ms": ms / la}
+    dominant = max(stages, key=lambda k: stages[k]["ms_per_fit"])
+    roof = stage_roof("sort", "k_sort_hist/scan/scatter (segmented LSD radix sort, 8-bit digits; "
+                      "per pass 4 B read for the histogram + 4 B read + 4 B written per key)")
+    roof["dominant_stage"] = dominant
+    # ncu DRAM bytes of one launch, taken on the current kernels (null when a
+    # kernel changed after its capture); the summaries live under profiles/
+    roof["traffic_note"] = ("k_sort_scatter alone: 282.4 MB DRAM per refinement pass of 40 M keys "
+                            "(320 MB algorithmic), profiles/k_sort_scatter_refine_n1e6_p20.md")
+    roof_c = stage_roof("cstep_dist", "k_dist (C-step distances + fused top-digit histogram; "
+                        "per row 4p B read + 4 B per active chain written)")
+    s_ms = sum(pp["stages"][k]["ms"] for pp in prof32 for k in ("cstep_dist", "cstep_select"))
+    s_by = sum(pp["stages"][k]["bytes"] for pp in prof32 for k in ("cstep_dist", "cstep_select"))
+    roof_c["traffic"] = K_DIST_TRAFFIC
+    roof_c["traffic_note"] = "second C-step launch, both chains active: profiles/k_dist_cstep_n1e6_p20.md"
+    roof_c["dist_plus_select_frac"] = (s_by / (s_ms / 1e3) / 1e9) / peak
     launches = int(sum(sum(st["launches"] for st in pp["stages"].values()) for pp in prof32))
     cpu = None
     if not args.no_cpu:
@@ -312,7 +332,8 @@ def main():
         "fp64_form": ({"value": n / (statistics.mean(t64) / 1e3), "unit": "rows/s",
                        "ms_per_step": statistics.mean(t64),
                        "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps)} if t64 else None),
-        "roofline": roof, "stages": stages, "csteps": prof32[-1]["csteps"],
+        "roofline": roof, "roofline_cstep": roof_c, "stages": stages, "csteps": prof32[-1]["csteps"],
+        "profiled_ms_per_step": statistics.mean(tprof),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         "n_flagged": r32["n_flagged"], "step_ms": t32,
     }

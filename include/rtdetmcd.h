@@ -92,7 +92,8 @@ typedef struct {
 #define RTD_STAGE_AGGREGATE   8   /* block choice, median, KL, pooling (Section 4 steps 4-7) */
 #define RTD_STAGE_REWEIGHT    9   /* reweighting (steps 8-9) */
 #define RTD_STAGE_FINAL      10   /* final distances and flags (step 10) */
-#define RTD_NSTAGES          11
+#define RTD_STAGE_SORT       11   /* segmented radix sorts (timed apart from the stages above) */
+#define RTD_NSTAGES          12
 
 /* Per-stage device time (CUDA events recorded on the fit's stream around
    each stage), algorithmic bytes (each row and key read or written once per

@@ -48,7 +48,7 @@ class _Options(ctypes.Structure):
 
 
 STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_dist",
-          "cstep_select", "cstep_update", "aggregate", "reweight", "final"]
+          "cstep_select", "cstep_update", "aggregate", "reweight", "final", "sort"]
 
 
 class _Profile(ctypes.Structure):

@@ -239,8 +239,8 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     int dev = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     RTD_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, dev));
-    {   // distance pass: about four CTAs per SM, at least 512 rows each
-        long long cd = (4LL * P.nsm + S.q - 1) / S.q;
+    {   // distance pass: one resident wave (two CTAs per SM), at least 512 rows each
+        long long cd = (2LL * P.nsm + S.q - 1) / S.q;
         long long lim = (S.m + 511) / 512;
         P.cpb_dist = (int)(cd < lim ? (cd > 0 ? cd : 1) : lim);
     }
@@ -306,39 +306,47 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     pf.begin(RTD_STAGE_PARTITION);
     launch_gather(P, s);
     pf.end(1, qm_ * p_ * 4 + qm_ * S.pb * 4);
+    // segmented sort timed as its own stage; `stage` resumes afterwards
+    auto sorted_ = [&](void* keys, int kb, int nseg, long long L, int stage) {
+        pf.end(0, 0.0);
+        pf.begin(RTD_STAGE_SORT);
+        sort_segments(P, keys, P.arenaB, kb, nseg, L, s);
+        // per pass: histogram read, scatter read + write
+        pf.end(3 * kb, (double)nseg * L * kb * 3.0 * kb);
+        pf.begin(stage);
+    };
     // Sections 3.1 and 4: setup, univariate MCD of every column
     pf.begin(RTD_STAGE_UNIVARIATE);
     launch_setup(P, o, s);
     launch_col_keys(P, (uint32_t*)P.arenaA, s);
-    sort_segments(P, P.arenaA, P.arenaB, 4, S.p, S.n, s);
+    sorted_(P.arenaA, 4, S.p, S.n, RTD_STAGE_UNIVARIATE);
     launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
     launch_uni_finish(P, s);
-    // rows read, keys written, 4 sort passes (read + write), window scan read
-    pf.end(9 + 3 * 4, n_ * p_ * (4 + 4 + 4 * 8 + 4));
+    // rows read, keys written, window search (chunk sums read the keys once)
+    pf.end(9, n_ * p_ * (4 + 4 + 4 + 4));
     { int e = fetch_status(P.st, s, hs); if (e) return e; }
     pf.collect();
     if (hs.code) goto finish;
     // Section 3.2: initial estimators per block
     pf.begin(RTD_STAGE_STARTS);
     launch_start1(P, s);
-    sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, S.q, S.m, s);
+    sorted_(P.arenaA, S.key_bytes, S.q, S.m, RTD_STAGE_STARTS);
     launch_gsscm(P, P.arenaA, s);
     launch_start2(P, s);
     launch_start_reduce(P, s);
-    pf.end(5 + 3 * S.key_bytes, 2 * qm_ * p_ * 4 + qm_ * K_ * (1 + 2 * S.key_bytes));
+    pf.end(5, 2 * qm_ * p_ * 4 + qm_ * K_);
     // Section 3.3: refinement
     pf.begin(RTD_STAGE_REFINE);
     launch_refine_eigen(P, s);
     launch_transform(P, 0, s);
-    sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
+    sorted_(P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, RTD_STAGE_REFINE);
     launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
     launch_refine_mid(P, s);
     launch_transform(P, 1, s);
-    sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, s);
+    sorted_(P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, RTD_STAGE_REFINE);
     launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
     launch_refine_end(P, s);
-    pf.end(17 + 6 * S.key_bytes,
-           2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * (1 + 2 * S.key_bytes + 1)));
+    pf.end(17, 2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * 2));
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
     {
         int act_chains = 2 * S.q, act_blocks = S.q;

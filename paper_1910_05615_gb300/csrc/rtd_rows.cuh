@@ -531,10 +531,19 @@ template <typename T> __device__ inline T load_m(const RowParams& rp, int i, int
 template <> __device__ inline float load_m<float>(const RowParams& rp, int i, int j) { return rp.Mf[i * PMAX + j]; }
 template <> __device__ inline double load_m<double>(const RowParams& rp, int i, int j) { return rp.M[i * PMAX + j]; }
 
+// Warp-aggregated increment of a shared histogram bin (lanes with equal
+// bins add once).
+__device__ inline void hist_add(unsigned* h, unsigned bin, bool valid) {
+    const int lane = threadIdx.x & 31;
+    unsigned tag = valid ? bin : (0x80000000u | lane);
+    unsigned peers = __match_any_sync(0xffffffffu, tag);
+    if (valid && (__ffs(peers) - 1) == lane) atomicAdd(h + bin, (unsigned)__popc(peers));
+}
+
 template <int PB, typename T>
 __global__ void __launch_bounds__(NT, 2) k_dist(const float* __restrict__ Xp, int p, int m, int cpb,
-                                             const Chain* __restrict__ ch, T* __restrict__ dkeys,
-                                             long long qm, unsigned* __restrict__ hist) {
+                                                const Chain* __restrict__ ch, T* __restrict__ dkeys,
+                                                long long qm, unsigned* __restrict__ hist) {
     constexpr int R = DistRows<PB, T>::R;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sMb = reinterpret_cast<T*>(smem);                                   // [2][PB*PB]
@@ -555,32 +564,36 @@ __global__ void __launch_bounds__(NT, 2) k_dist(const float* __restrict__ Xp, in
     }
     for (int e = threadIdx.x; e < 2 * HIST_BINS; e += NT) shb[e] = 0u;
     __syncthreads();
+    const int a0 = act[0], a1 = act[1];
+    if (!a0 && !a1) return;
     int r0, r1;
     block_rows(m, cpb, r0, r1);
-    for (int k = 0; k < 2; ++k) {
-        if (!act[k]) continue;
-        T* out = dkeys + (size_t)k * qm;
-        for (int base = r0 + threadIdx.x * R; base < r1; base += NT * R) {
+    for (int base = r0 + threadIdx.x * R; base - threadIdx.x * R < r1; base += NT * R) {
+        float x[R][PB];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (base + r < r1) load_row_padded<PB>(Xp + (size_t)(base + r) * PB, x[r]);
+            else {
+#pragma unroll
+                for (int j = 0; j < PB; ++j) x[r][j] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!(k ? a1 : a0)) continue;
             T c[R][PB];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float x[PB];
-                if (base + r < r1) load_row_padded<PB>(Xp + (size_t)(base + r) * PB, x);
-                else {
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-                    for (int j = 0; j < PB; ++j) x[j] = 0.f;
-                }
-#pragma unroll
-                for (int j = 0; j < PB; ++j) c[r][j] = ((T)x[j] - s_hi[k][j]) - s_lo[k][j];
-            }
+                for (int j = 0; j < PB; ++j) c[r][j] = ((T)x[r][j] - s_hi[k][j]) - s_lo[k][j];
             T d2[R];
             tri_d2<PB, T, R>(sMb + k * PB * PB, p, c, d2);
+            T* out = dkeys + (size_t)k * qm;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                if (base + r < r1) {
-                    out[base + r] = d2[r];
-                    atomicAdd(&shb[k * HIST_BINS + (coarse_key(d2[r]) >> (32 - HIST_BITS))], 1u);
-                }
+                const bool v = base + r < r1;
+                if (v) out[base + r] = d2[r];
+                hist_add(shb + k * HIST_BINS, coarse_key(d2[r]) >> (32 - HIST_BITS), v);
             }
         }
     }

@@ -76,10 +76,14 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
     unsigned rank[SITEMS];
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
+    for (int r = 0; r < SITEMS; ++r) {     // all loads in flight before the ranking
+        int idx = w * SKPW + r * 32 + lane;
+        key[r] = idx < cnt ? __ldg(src + idx) : (K)0;
+    }
+#pragma unroll
     for (int r = 0; r < SITEMS; ++r) {
         int idx = w * SKPW + r * 32 + lane;
         bool valid = idx < cnt;
-        key[r] = valid ? src[idx] : (K)0;
         unsigned d = (unsigned)(key[r] >> shift) & 255u;
         unsigned tag = valid ? d : 256u + lane;
         unsigned peers = __match_any_sync(0xffffffffu, tag);
