@@ -40,6 +40,15 @@ REF_SAMPLE_ROWS = 200_000
 K_DIST_TRAFFIC = 82.88e6
 
 
+def selection_stats(pp):
+    """Window-path counters of one profiled fit (chain steps summed)."""
+    ws = pp.get("win_steps", 0)
+    steps = max(1, ws)
+    return {"window_chain_steps": ws, "window_misses": pp.get("win_miss", 0),
+            "candidates_per_window_step": pp.get("sel_cand", 0) / steps,
+            "band_rows_total": pp.get("sel_band", 0)}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -333,6 +342,7 @@ def main():
                        "ms_per_step": statistics.mean(t64),
                        "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps)} if t64 else None),
         "roofline": roof, "roofline_cstep": roof_c, "stages": stages, "csteps": prof32[-1]["csteps"],
+        "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         "n_flagged": r32["n_flagged"], "step_ms": t32,

@@ -103,7 +103,11 @@ typedef struct rtd_profile {
     double  bytes[RTD_NSTAGES];
     int64_t launches[RTD_NSTAGES];
     int32_t csteps;        /* C-step iterations run (all chains in lockstep) */
+    int32_t win_steps;     /* chain steps whose selection used the predicted window (FP32 form) */
+    int32_t win_miss;      /* of those, steps whose window missed (histogram path taken) */
     int32_t reserved;
+    int64_t sel_cand;      /* selection candidates listed, summed over chain steps */
+    int64_t sel_band;      /* rows decided in FP64 inside the band, summed over chain steps */
 } rtd_profile;
 
 typedef struct {

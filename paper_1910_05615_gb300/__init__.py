@@ -54,7 +54,8 @@ STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_di
 class _Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("bytes", ctypes.c_double * len(STAGES)),
                 ("launches", ctypes.c_int64 * len(STAGES)), ("csteps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("win_steps", ctypes.c_int32), ("win_miss", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sel_cand", ctypes.c_int64), ("sel_band", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):
@@ -235,7 +236,8 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
         a = dg.cpu().numpy() if not isinstance(dg, np.ndarray) else dg
         out["diag"] = parse_diag(a, pp, res.q)
     if profile:
-        out["profile"] = {"csteps": prof.csteps, "stages": {
+        out["profile"] = {"csteps": prof.csteps, "win_steps": prof.win_steps, "win_miss": prof.win_miss,
+                          "sel_cand": prof.sel_cand, "sel_band": prof.sel_band, "stages": {
             name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i]}
             for i, name in enumerate(STAGES)}}
     return out

@@ -1,3 +1,4 @@
+#include <vector>
 // rtd_api.cu - C ABI entry points and host orchestration of RT-DetMCD.
 //
 // The host validates arguments, lays out the caller's workspace, and issues
@@ -243,6 +244,13 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         long long cd = (2LL * P.nsm + S.q - 1) / S.q;
         long long lim = (S.m + 511) / 512;
         P.cpb_dist = (int)(cd < lim ? (cd > 0 ? cd : 1) : lim);
+        // window-path distance pass: exactly one resident wave (two CTAs per
+        // SM, one at the widest rows), at least 256 rows each
+        long long per_sm = S.pb >= 48 ? 1 : 2;
+        long long cw = per_sm * P.nsm / S.q;
+        long long limw = (S.m + 255) / 256;
+        if (cw > limw) cw = limw;
+        P.cpb_win = (int)(cw > 0 ? cw : 1);
     }
     feistel_setup(P.F, S.n, o.seed, S.q == 1);
     P.st = at<Status>(ws, R.st);
@@ -350,19 +358,33 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
     {
         int act_chains = 2 * S.q, act_blocks = S.q;
+        pf.begin(RTD_STAGE_CPREP);
+        launch_chol_prep(P, s);   // later steps are prepared by the previous step's finalize
+        pf.end(1, 0.0);
         for (int it = 0; it <= S.max_steps; ++it) {
             const double mch = (double)S.m * act_chains;
-            pf.begin(RTD_STAGE_CPREP);
-            launch_chol_prep(P, s);
-            pf.end(1, 0.0);
+            // FP32 form from the second step on: classification against the
+            // predicted window, selection from the window's rows; chains whose
+            // window missed take the histogram path below
+            const bool win = S.precision == RTD_FP32 && it > 0;
             pf.begin(RTD_STAGE_CDIST);
-            launch_dist(P, s);
-            pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_);
+            if (win) launch_dist_win(P, s);
+            else launch_dist(P, s);
+            // rows read, keys written (+ membership bytes read and written)
+            pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_ + (win ? 2 * mch : 0));
             pf.begin(RTD_STAGE_CSELECT);
+            if (win) {
+                launch_select_win(P, s);
+                launch_hist_keys(P, s);
+            }
             launch_select_bucket(P, s);
             launch_compact(P, s);
             launch_select_finish(P, s);
-            pf.end(3, mch * K_);
+            if (S.precision == RTD_FP32) {
+                launch_band64(P, s);
+                launch_select_band(P, s);
+            }
+            pf.end(3 + (win ? 2 : 0) + (S.precision == RTD_FP32 ? 2 : 0), win ? 0.0 : mch * K_);
             pf.begin(RTD_STAGE_CUPDATE);
             RTD_CUDA(cudaMemsetAsync(&P.st->active, 0, 3 * sizeof(int), s));
             RTD_CUDA(cudaMemsetAsync(&P.st->gram_rows, 0, sizeof(unsigned long long), s));
@@ -380,6 +402,17 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
             act_chains = hs.active;
             act_blocks = hs.active_blocks;
             if (hs.code || hs.active == 0) break;
+        }
+    }
+    if (o.profile) {   // selection counters of the C-steps (profiling only: one more copy)
+        std::vector<SelRule> hr((size_t)2 * S.q);
+        RTD_CUDA(cudaMemcpyAsync(hr.data(), P.rule, hr.size() * sizeof(SelRule), cudaMemcpyDeviceToHost, s));
+        RTD_CUDA(cudaStreamSynchronize(s));
+        for (const SelRule& r : hr) {
+            o.profile->win_steps += r.acc_win;
+            o.profile->win_miss += r.acc_miss;
+            o.profile->sel_cand += r.acc_cand;
+            o.profile->sel_band += r.acc_band;
         }
     }
     if (hs.code) goto finish;

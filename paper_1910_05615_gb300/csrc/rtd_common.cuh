@@ -61,6 +61,9 @@ struct RowParams {
     // reference centre of the Gram accumulation (X units)
     double ref[PMAX];
     float  ref_hi[PMAX], ref_lo[PMAX];
+    // centre folded into the product for rows centred at the FP32 univariate
+    // centre u: y = M (x - u) - bf with bf = M (mu - u) (FP64, rounded once)
+    float  bf[PMAX];
 };
 
 // C-step chain (one per block and start).
@@ -90,7 +93,26 @@ struct SelRule {
     int below;                      // rows with coarse key < lo (atomic)
     int cand;                       // candidates (atomic)
     int band;
+    // FP32 form, from the second step on: rows are classified against a
+    // window [w_lo, w_hi] of FP32 keys predicted from the last thresholds.
+    // When the h_b-th key and its FP64 band fall inside the window the
+    // selection needs only the window's rows (fast); otherwise the
+    // histogram path runs for this chain.
+    unsigned int w_lo, w_hi;
+    int w_sh;                       // window bin of a key: (key - w_lo) >> w_sh, < WIN_BINS
+    int win;                        // this step classifies against the window
+    int fast;                       // the window held
+    int need_hist;                  // the window missed: histogram from the keys
+    int nlo;                        // rows below the band (window path)
+    int have_t;                     // t_prev holds the last threshold
+    float t_prev, t_prev2;          // FP32 thresholds of the last two steps
+    int bandsel;                    // histogram path: band listed, FP64 ranking pending
+    int band_off;                   // offset of the band list in the chain's band buffer
+    // counters over the whole fit (profiling)
+    int acc_win, acc_miss;
+    long long acc_cand, acc_band;
 };
+constexpr int WIN_BINS = 1024;      // bins of the window histogram
 
 struct Cand {
     unsigned long long key;

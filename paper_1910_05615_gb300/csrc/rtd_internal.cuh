@@ -27,6 +27,7 @@ struct Plan {
     long long n, h, ld;
     int p, pb, q, m, hb, precision, cpb, nsm, max_steps;
     int cpb_dist;           // CTAs per block of the distance and compaction passes
+    int cpb_win;            // CTAs per block of the window-path distance pass
     int key_bytes;          // 4 (FP32 form) or 8 (FP64 form) for refinement sorts
     Feistel F;
     // device buffers
@@ -69,6 +70,9 @@ void launch_start1(const Plan& P, cudaStream_t s);
 void launch_start2(const Plan& P, cudaStream_t s);
 void launch_transform(const Plan& P, int which, cudaStream_t s);
 void launch_dist(const Plan& P, cudaStream_t s);
+void launch_dist_win(const Plan& P, cudaStream_t s);
+void launch_hist_keys(const Plan& P, cudaStream_t s);
+void launch_band64(const Plan& P, cudaStream_t s);
 void launch_compact(const Plan& P, cudaStream_t s);
 void launch_memb(const Plan& P, cudaStream_t s);
 void launch_rew(const Plan& P, cudaStream_t s);
@@ -89,6 +93,8 @@ size_t unimcd_scratch_doubles(int nseg, long long L);
 void launch_gsscm(const Plan& P, const void* rkeys, cudaStream_t s);
 void launch_select_bucket(const Plan& P, cudaStream_t s);
 void launch_select_finish(const Plan& P, cudaStream_t s);
+void launch_select_win(const Plan& P, cudaStream_t s);
+void launch_select_band(const Plan& P, cudaStream_t s);
 
 // ---- small FP64 kernels (rtd_small.cu)
 void launch_setup(const Plan& P, const rtd_options& o, cudaStream_t s);

@@ -9,30 +9,34 @@ constexpr int LD = PMAX + 1;   // padded leading dimension of shared matrices
 
 // In-place Cholesky A = L L^T (lower triangle overwritten by L; the strict
 // upper triangle is zeroed).  Returns false (uniformly) if A is not
-// numerically positive definite.
+// numerically positive definite.  Right-looking, one barrier per column:
+// step k updates the trailing block from the unscaled column k, and column
+// k - 1 is scaled in step k (no thread reads it any more).
 __device__ inline bool cta_cholesky(double* A, int p) {
-    __shared__ int fail;
-    if (threadIdx.x == 0) fail = 0;
     __syncthreads();
+    bool ok = true;
+    double d_prev = 0.0, r_prev = 0.0;
     for (int k = 0; k < p; ++k) {
-        if (threadIdx.x == 0) {
-            double d = A[k * LD + k];
-            if (!(d > 0.0) || !isfinite(d)) fail = 1;
-            else A[k * LD + k] = sqrt(d);
+        const double akk = A[k * LD + k];
+        if (!(akk > 0.0) || !isfinite(akk)) { ok = false; break; }   // same value in every thread
+        const double dk = sqrt(akk), rk = 1.0 / dk, rk2 = rk * rk;
+        if (k > 0) {
+            for (int i = k + threadIdx.x; i < p; i += blockDim.x) A[i * LD + (k - 1)] *= r_prev;
+            if (threadIdx.x == 0) A[(k - 1) * LD + (k - 1)] = d_prev;
         }
-        __syncthreads();
-        if (fail) break;
-        double dkk = A[k * LD + k];
-        for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) A[i * LD + k] /= dkk;
-        __syncthreads();
-        int rem = p - k - 1;
+        const int rem = p - k - 1;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            int i = k + 1 + e / rem, j = k + 1 + e % rem;
-            if (j <= i) A[i * LD + j] -= A[i * LD + k] * A[j * LD + k];
+            const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+            if (j <= i) A[i * LD + j] -= A[i * LD + k] * A[j * LD + k] * rk2;
         }
+        d_prev = dk;
+        r_prev = rk;
         __syncthreads();
     }
-    bool ok = !fail;
+    if (ok && p > 0) {
+        if (threadIdx.x == 0) A[(p - 1) * LD + (p - 1)] = d_prev;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         if (j > i) A[i * LD + j] = 0.0;
@@ -41,15 +45,24 @@ __device__ inline bool cta_cholesky(double* A, int p) {
     return ok;
 }
 
-// Li = L^-1 for lower-triangular L (column-parallel forward substitution).
+// Li = L^-1 for lower-triangular L (column-parallel forward substitution
+// with the reciprocal diagonal).
 __device__ inline void cta_tri_inverse(const double* L, double* Li, int p) {
+    __shared__ double rd[PMAX];
+    for (int j = threadIdx.x; j < p; j += blockDim.x) rd[j] = 1.0 / L[j * LD + j];
+    __syncthreads();
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         for (int i = 0; i < j; ++i) Li[i * LD + j] = 0.0;
-        Li[j * LD + j] = 1.0 / L[j * LD + j];
+        Li[j * LD + j] = rd[j];
         for (int i = j + 1; i < p; ++i) {
-            double s = 0.0;
-            for (int k = j; k < i; ++k) s += L[i * LD + k] * Li[k * LD + j];
-            Li[i * LD + j] = -s / L[i * LD + i];
+            double s0 = 0.0, s1 = 0.0;
+            int k = j;
+            for (; k + 1 < i; k += 2) {
+                s0 = fma(L[i * LD + k], Li[k * LD + j], s0);
+                s1 = fma(L[i * LD + k + 1], Li[(k + 1) * LD + j], s1);
+            }
+            if (k < i) s0 = fma(L[i * LD + k], Li[k * LD + j], s0);
+            Li[i * LD + j] = -(s0 + s1) * rd[i];
         }
     }
     __syncthreads();

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NT) k_compact(const T* __restrict__ dkeys, int
     block_rows(m, cpb, r0, r1);
     for (int k = 0; k < 2; ++k) {
         const int c = 2 * l + k;
-        if (!ch[c].active) continue;
+        if (!ch[c].active || rule[c].fast) continue;
         const unsigned long long lo = rule[c].lo, hi = rule[c].hi;
         const T* in = dkeys + (size_t)k * qm;
         Cand* out = cand + (size_t)c * m;
@@ -134,6 +134,43 @@ void launch_compact(const Plan& P, cudaStream_t s) {
 
 
 
+
+// Top-digit histogram of the keys of chains whose window missed (the
+// distance pass of the window path does not build it).
+__global__ void __launch_bounds__(NT) k_hist_keys(const float* __restrict__ dkeys, int m, int cpb, long long qm,
+                                                  const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
+                                                  unsigned* __restrict__ hist) {
+    __shared__ unsigned sh[HIST_BINS];
+    const int l = blockIdx.y;
+    int r0, r1;
+    block_rows(m, cpb, r0, r1);
+    for (int k = 0; k < 2; ++k) {
+        const int c = 2 * l + k;
+        if (!ch[c].active || !rule[c].need_hist) continue;   // uniform
+        __syncthreads();
+        for (int b = threadIdx.x; b < HIST_BINS; b += NT) sh[b] = 0u;
+        __syncthreads();
+        const float* in = dkeys + (size_t)k * qm;
+        for (int base = r0; base < r1; base += NT) {
+            const int row = base + threadIdx.x;
+            const bool v = row < r1;
+            const float d = v ? in[row] : 0.f;
+            hist_add(sh, coarse_key(d) >> (32 - HIST_BITS), v);
+        }
+        __syncthreads();
+        unsigned* gh = hist + (size_t)c * HIST_BINS;
+        for (int b = threadIdx.x; b < HIST_BINS; b += NT) {
+            const unsigned v = sh[b];
+            if (v) atomicAdd(gh + b, v);
+        }
+    }
+}
+
+void launch_hist_keys(const Plan& P, cudaStream_t s) {
+    dim3 grid(P.cpb_dist, P.q);
+    k_hist_keys<<<grid, NT, 0, s>>>((const float*)P.dkeys, P.m, P.cpb_dist, (long long)P.q * P.m, P.ch, P.rule,
+                                    P.hist);
+}
 
 // ---------------------------------------------------------------- flags
 __global__ void k_flag(const float* __restrict__ d2, long long n, double cut, uint8_t* __restrict__ flags,
@@ -188,6 +225,8 @@ void launch_start1(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, start1, P,
 void launch_start2(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, start2, P, s); }
 void launch_transform(const Plan& P, int which, cudaStream_t s) { (void)which; RTD_PB_CALL(P.pb, transform, P, s); }
 void launch_dist(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist, P, s); }
+void launch_dist_win(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist_win, P, s); }
+void launch_band64(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, band64, P, s); }
 void launch_memb(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, memb, P, s); }
 void launch_rew(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, rew, P, s); }
 void launch_member_gram(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, member_gram, P, s); }

@@ -6,6 +6,7 @@
 // zeros to pb floats (pb a multiple of 4) so that they load as float4.
 #pragma once
 #include "rtd_internal.cuh"
+#include "rtd_async.cuh"
 
 namespace rtd {
 
@@ -117,13 +118,15 @@ struct GramAcc {
     typedef GramShape<PB, T> S;
     double a64[16];
     T a32[16];
-    int since, bi, bj, g;
+    int since, bi, bj, g, ng;
     bool on;
-    __device__ void init() {
+    // ng groups of NBLK threads take interleaved rows (ng <= G)
+    __device__ void init(int groups = S::G) {
         int t = threadIdx.x;
+        ng = groups;
         g = t / S::NBLK;
         int blk = t % S::NBLK;
-        on = g < S::G;
+        on = g < ng;
         int b = blk;
         bi = 0;
         while (b >= S::NB - bi) { b -= S::NB - bi; ++bi; }
@@ -140,7 +143,7 @@ struct GramAcc {
     // tile: k rows of PE values, weights wt
     __device__ void rows(const T* tile, const T* wt, int k) {
         if (!on) return;
-        for (int r = g; r < k; r += S::G) {
+        for (int r = g; r < k; r += ng) {
             const T* row = tile + r * S::PE;
             T w = wt[r];
             T a[4], b[4];
@@ -165,7 +168,7 @@ struct GramAcc {
         __syncthreads();
         for (int e = threadIdx.x; e < S::NBLK * 16; e += NT) {
             double s = 0.0;
-            for (int gg = 0; gg < S::G; ++gg) s += red[gg * S::NBLK * 16 + e];
+            for (int gg = 0; gg < ng; ++gg) s += red[gg * S::NBLK * 16 + e];
             slot[e] = s;
         }
         __syncthreads();
@@ -617,6 +620,247 @@ void dist_t(const Plan& P, cudaStream_t s) {
     k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb_dist, P.ch, (T*)P.dkeys, (long long)P.q * P.m, P.hist);
 }
 // =====================================================================
+// C-step distances of the FP32 form from the second step on (Sections 2.1,
+// 3.4).  The block's rows stream through shared memory in tiles brought by
+// bulk asynchronous copies (two stages, one thread issues them).  Rows are
+// centred once at the FP32 univariate centre u; each start's
+// y = M (x - u) - bf, bf = M (mu - u), is formed with packed FP32 FMAs that
+// carry the even and odd columns of a row in the two halves.  Each key is
+// then classified against the chain's predicted window [w_lo, w_hi]: rows
+// below it are counted, rows inside it are listed as candidates and counted
+// in a histogram of WIN_BINS bins over the window.  The keys are written
+// for the membership pass and for the histogram path a missed window falls
+// back to.
+// =====================================================================
+template <int PB> struct DistWin {
+    static constexpr int R = 2;                      // rows per thread
+    static constexpr int NTW = PB <= 24 ? 256 : 128; // threads
+    static constexpr int TR = NTW * R;               // rows per tile
+    static constexpr int STAGES = 2;
+    static constexpr int PH = PB / 2;                // column pairs per row
+    static constexpr size_t TILE = (size_t)TR * PB * sizeof(float);
+    static constexpr size_t SMEM = STAGES * TILE + 2 * (size_t)PB * PB * sizeof(float) +
+                                   2 * (size_t)WIN_BINS * sizeof(unsigned);
+};
+
+// d2 of R rows for lower-triangular M stored as column pairs (row stride
+// PB / 2 pairs, zero above the diagonal); b the folded centre.  Column pairs
+// alternate between two accumulators per row to shorten dependence chains.
+template <int PB, int R>
+__device__ __forceinline__ void tri_d2_pk(const float2* __restrict__ sM, int p, const float2 (&c)[R][PB / 2],
+                                          const float* __restrict__ b, float (&d2)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) d2[r] = 0.f;
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+        if (i < p) {
+            const int npair = i / 2 + 1;                    // pairs holding columns 0..i
+            const float2 binit = make_float2(-b[i], 0.f);
+            float2 a0[R], a1[R];
+#pragma unroll
+            for (int g = 0; 4 * g <= i; ++g) {
+                const float4 mv = *reinterpret_cast<const float4*>(sM + i * (PB / 2) + 2 * g);
+                const float2 m0 = make_float2(mv.x, mv.y);
+                const float2 m1 = make_float2(mv.z, mv.w);
+#pragma unroll
+                for (int r = 0; r < R; ++r) a0[r] = __ffma2_rn(m0, c[r][2 * g], g == 0 ? binit : a0[r]);
+                if (2 * g + 1 < npair) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        a1[r] = (g == 0) ? __fmul2_rn(m1, c[r][1]) : __ffma2_rn(m1, c[r][2 * g + 1], a1[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 a = a0[r];
+                if (npair > 1) a = __fadd2_rn(a, a1[r]);
+                const float y = a.x + a.y;
+                d2[r] = fmaf(y, y, d2[r]);
+            }
+        }
+    }
+}
+
+template <int PB>
+__global__ void __launch_bounds__(DistWin<PB>::NTW, 2)
+    k_dist_win(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
+               const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys,
+               long long qm, Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st) {
+    typedef DistWin<PB> D;
+    constexpr int R = D::R, PH = D::PH, NTW = D::NTW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* tiles = reinterpret_cast<float*>(smem);
+    float2* sM = reinterpret_cast<float2*>(smem + D::STAGES * D::TILE);   // [2][PB][PH]
+    unsigned* sh = reinterpret_cast<unsigned*>(smem + D::STAGES * D::TILE + 2 * (size_t)PB * PB * sizeof(float));
+    __shared__ __align__(8) uint64_t bar[D::STAGES];
+    __shared__ float2 s_nu[PH];
+    __shared__ float s_b[2][PB];
+    __shared__ unsigned s_wlo[2], s_whi[2];
+    __shared__ int s_wsh[2], s_on[2], s_below[2], s_fail;
+    const int l = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    int r0, r1;
+    block_rows(m, cpb, r0, r1);
+    const int ntiles = (r1 - r0 + D::TR - 1) / D::TR;
+    if (threadIdx.x < 2) {
+        const int c = 2 * l + threadIdx.x;
+        s_on[threadIdx.x] = ch[c].active && rule[c].win;
+        s_wlo[threadIdx.x] = rule[c].w_lo;
+        s_whi[threadIdx.x] = rule[c].w_hi;
+        s_wsh[threadIdx.x] = rule[c].w_sh;
+        s_below[threadIdx.x] = 0;
+    }
+    for (int e = threadIdx.x; e < 2 * WIN_BINS; e += NTW) sh[e] = 0u;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < D::STAGES; ++s) mbar_init(&bar[s], 1);
+        mbar_init_fence();
+    }
+    for (int e = threadIdx.x; e < 2 * PB * PH; e += NTW) {
+        const int k = e / (PB * PH), i = (e / PH) % PB, h = e % PH;
+        const float* Mf = ch[2 * l + k].rp.Mf;
+        const int j0 = 2 * h, j1 = 2 * h + 1;
+        sM[e] = make_float2((i < p && j0 <= i) ? Mf[i * PMAX + j0] : 0.f, (i < p && j1 <= i) ? Mf[i * PMAX + j1] : 0.f);
+    }
+    for (int e = threadIdx.x; e < 2 * PB; e += NTW) {
+        const int k = e / PB, j = e % PB;
+        s_b[k][j] = (j < p) ? ch[2 * l + k].rp.bf[j] : 0.f;
+    }
+    for (int h = threadIdx.x; h < PH; h += NTW) {
+        const float a = (2 * h < p) ? -(float)cs->mu_uni[2 * h] : 0.f;
+        const float b = (2 * h + 1 < p) ? -(float)cs->mu_uni[2 * h + 1] : 0.f;
+        s_nu[h] = make_float2(a, b);
+    }
+    __syncthreads();
+    if ((!s_on[0] && !s_on[1]) || ntiles <= 0) return;   // uniform; nothing issued yet
+
+    auto issue = [&](int t, int s) {
+        const int row0 = r0 + t * D::TR;
+        const int rows = min(D::TR, r1 - row0);
+        const unsigned bytes = (unsigned)rows * PB * (unsigned)sizeof(float);
+        mbar_expect_tx(&bar[s], bytes);
+        bulk_load(tiles + (size_t)s * D::TR * PB, Xp + (size_t)row0 * PB, bytes, &bar[s]);
+    };
+    if (threadIdx.x == 0)
+        for (int s = 0; s < D::STAGES && s < ntiles; ++s) issue(s, s);
+
+    int below0 = 0, below1 = 0;
+    int t = 0;
+    for (; t < ntiles; ++t) {
+        const int s = t % D::STAGES;
+        const int row0 = r0 + t * D::TR;
+        const int rows = min(D::TR, r1 - row0);
+        const bool ok = mbar_wait(&bar[s], (unsigned)(t / D::STAGES) & 1u);
+        if (!ok) s_fail = 1;
+        if (ok) {
+            const float* T = tiles + (size_t)s * D::TR * PB;
+            float2 c[R][PH];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int j = r * NTW + threadIdx.x;
+                if (j < rows) {
+                    const float4* src = reinterpret_cast<const float4*>(T + (size_t)j * PB);
+#pragma unroll
+                    for (int q4 = 0; q4 < PB / 4; ++q4) {
+                        const float4 v = src[q4];
+                        c[r][2 * q4] = __fadd2_rn(make_float2(v.x, v.y), s_nu[2 * q4]);
+                        c[r][2 * q4 + 1] = __fadd2_rn(make_float2(v.z, v.w), s_nu[2 * q4 + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < PH; ++h) c[r][h] = make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!s_on[k]) continue;
+                float d2[R];
+                tri_d2_pk<PB, R>(sM + k * PB * PH, p, c, s_b[k], d2);
+                const int cidx = 2 * l + k;
+                const unsigned wlo = s_wlo[k], whi = s_whi[k];
+                const int wsh = s_wsh[k];
+                float* out = dkeys + (size_t)k * qm;
+                int nb = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int j = r * NTW + threadIdx.x;
+                    const int row = row0 + j;
+                    const unsigned key = __float_as_uint(d2[r]);
+                    bool cnd = false;
+                    if (j < rows) {
+                        const bool in = key < wlo;
+                        cnd = !in && key <= whi;
+                        nb += in ? 1 : 0;
+                        out[row] = d2[r];
+                        if (cnd) atomicAdd(&sh[k * WIN_BINS + ((key - wlo) >> wsh)], 1u);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, cnd);
+                    if (bal) {
+                        const int lead = __ffs(bal) - 1;
+                        int b0 = 0;
+                        if (lane == lead) b0 = atomicAdd(&rule[cidx].cand, __popc(bal));
+                        b0 = __shfl_sync(0xffffffffu, b0, lead);
+                        if (cnd) {
+                            const int idx = b0 + __popc(bal & ((1u << lane) - 1u));
+                            if (idx < m) {
+                                Cand e;
+                                e.key = key;
+                                e.pos = (unsigned)(row - l * m);
+                                e.pad = 0;
+                                cand[(size_t)cidx * m + idx] = e;
+                            }
+                        }
+                    }
+                }
+                if (k == 0) below0 += nb; else below1 += nb;
+            }
+        }
+        __syncthreads();                 // stage s read by every thread
+        if (s_fail) break;               // uniform after the barrier
+        if (threadIdx.x == 0 && t + D::STAGES < ntiles) {
+            async_proxy_fence();
+            issue(t + D::STAGES, s);
+        }
+    }
+    if (s_fail) {
+        // let the copies still in flight land before the CTA's shared memory is released
+        if (threadIdx.x == 0) {
+            for (int u = t; u < ntiles && u < t + D::STAGES; ++u)
+                (void)mbar_wait(&bar[u % D::STAGES], (unsigned)(u / D::STAGES) & 1u);
+            set_error(st, RTD_EINTERNAL);
+        }
+        return;
+    }
+    below0 = warp_sum_int(below0);
+    below1 = warp_sum_int(below1);
+    if (lane == 0) {
+        if (below0) atomicAdd(&s_below[0], below0);
+        if (below1) atomicAdd(&s_below[1], below1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 && s_on[threadIdx.x] && s_below[threadIdx.x])
+        atomicAdd(&rule[2 * l + threadIdx.x].below, s_below[threadIdx.x]);
+    for (int k = 0; k < 2; ++k) {
+        if (!s_on[k]) continue;
+        unsigned* gh = hist + (size_t)(2 * l + k) * HIST_BINS;
+        for (int b = threadIdx.x; b < WIN_BINS; b += NTW) {
+            const unsigned v = sh[k * WIN_BINS + b];
+            if (v) atomicAdd(gh + b, v);
+        }
+    }
+}
+
+template <int PB>
+void dist_win_t(const Plan& P, cudaStream_t s) {
+    typedef DistWin<PB> D;
+    dim3 grid(P.cpb_win, P.q);
+    auto k = k_dist_win<PB>;
+    set_smem(k, D::SMEM);
+    k<<<grid, D::NTW, D::SMEM, s>>>(P.Xp, P.p, P.m, P.cpb_win, P.cs, P.ch, P.rule, (float*)P.dkeys,
+                                    (long long)P.q * P.m, P.cand, P.hist, P.st);
+}
+
+// =====================================================================
 // Membership update and update-based C-step (Section 3.5).  A row whose
 // membership changed contributes delta * (x - ref)(x - ref)^T (delta = +1
 // entering, -1 leaving) to the chain's Gram; with the reference centre ref
@@ -624,6 +868,99 @@ void dist_t(const Plan& P, cudaStream_t s) {
 // swaps.  When Chain.full is set the Gram of the whole new subset is taken
 // instead (first step, or after a re-centring).
 // =====================================================================
+// =====================================================================
+// FP32 form: FP64 distances of the rows in a chain's band (Section 3.4
+// distances; the band decision of the selection).  M and mu of the chain
+// are staged in shared memory in FP64.
+// =====================================================================
+constexpr int BAND_CTAS = 16;    // CTAs per chain
+constexpr int BAND_T = 128;      // threads per CTA: one warp per band row, one lane per component
+
+template <int PB>
+__global__ void __launch_bounds__(BAND_T) k_band64(const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
+                                                   Cand* __restrict__ band_all, const float* __restrict__ Xp,
+                                                   int m, int p) {
+    constexpr int LDM = PB + 1;                  // padded row stride of M in shared memory
+    __shared__ double sM[PB * LDM];
+    __shared__ double smu[PB];
+    __shared__ double scc[BAND_T / 32][PB];
+    const int c = blockIdx.x;
+    if (!ch[c].active) return;
+    const SelRule& R = rule[c];
+    if (!(R.fast || R.bandsel)) return;
+    const int nb = R.band, l = c / 2;
+    if (nb <= (int)blockIdx.y) return;
+    const RowParams& rp = ch[c].rp;
+    for (int e = threadIdx.x; e < PB * PB; e += BAND_T) {
+        const int i = e / PB, j = e % PB;
+        sM[i * LDM + j] = (i < p && j <= i) ? rp.M[i * PMAX + j] : 0.0;
+    }
+    for (int j = threadIdx.x; j < PB; j += BAND_T) smu[j] = (j < p) ? rp.mu[j] : 0.0;
+    __syncthreads();
+    Cand* band = band_all + (size_t)c * m + R.band_off;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = BAND_T / 32;
+    // rows dealt round-robin over the chain's CTAs and their warps
+    for (int i = blockIdx.y + gridDim.y * w; i < nb; i += gridDim.y * NW) {
+        Cand e = band[i];
+        const float* x = Xp + ((size_t)l * m + e.pos) * PB;
+        for (int j = lane; j < PB; j += 32) scc[w][j] = (double)x[j] - smu[j];
+        __syncwarp();
+        double d2 = 0.0;
+        for (int ii = lane; ii < p; ii += 32) {
+            double a = 0.0;
+            for (int jj = 0; jj <= ii; ++jj) a = fma(sM[ii * LDM + jj], scc[w][jj], a);
+            d2 = fma(a, a, d2);
+        }
+        d2 = warp_sum_d(d2);
+        __syncwarp();
+        if (lane == 0) {
+            e.key = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bits order as values
+            band[i] = e;
+        }
+    }
+}
+
+template <int PB>
+void band64_t(const Plan& P, cudaStream_t s) {
+    k_band64<PB><<<dim3(2 * P.q, BAND_CTAS), BAND_T, 0, s>>>(P.ch, P.rule, P.band, P.Xp, P.m, P.p);
+}
+
+// Exclusive prefix sum over the CTA (NT threads, all must call it).
+__device__ inline int cta_excl_scan(int v, int& total) {
+    __shared__ int ws[NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+        int c = ws[i];
+        if (i < w) off += c;
+        tot += c;
+    }
+    __syncthreads();
+    total = tot;
+    return off + x - v;
+}
+
+constexpr int MEMB_U = 8;                 // rows per thread per scan chunk
+constexpr int MEMB_CHUNK = NT * MEMB_U;
+
+template <int PB, typename T>
+constexpr size_t memb_smem_bytes() { return align16(gram_smem_bytes<PB, T>()) + MEMB_CHUNK * sizeof(int); }
+
+// New membership of every row, then the Gram over the rows that changed
+// (or over all members when Chain.full is set).  A chunk of MEMB_CHUNK rows
+// is scanned first (membership from the key and, inside the FP32 band, from
+// the FP64 decision bit), the rows to add are listed in a fixed order, then
+// staged in tiles for the Gram.
 template <int PB, typename T>
 __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const T* __restrict__ dkeys,
                                              int p, int m, int cpb, long long qm, int fp32,
@@ -634,6 +971,7 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
     extern __shared__ __align__(16) unsigned char smem[];
     T* tile = reinterpret_cast<T*>(smem);
     T* wt = tile + S::TR * S::PE;
+    int* lst = reinterpret_cast<int*>(smem + align16(gram_smem_bytes<PB, T>()));
     __shared__ T s_hi[PB], s_lo[PB];
     const int l = blockIdx.y;
     int r0, r1;
@@ -654,41 +992,61 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
         const T* keys = dkeys + (size_t)k * qm;
         uint8_t* mb = memb + (size_t)c * m;
         GramAcc<PB, T> acc;
-        acc.init();
+        acc.init(full ? S::G : 1);     // few swapped rows: one group, little FP64 reduction
         int nswap = 0;
-        for (int base = r0; base < r1; base += S::TR) {
-            int row = base + threadIdx.x;
-            bool valid = threadIdx.x < S::TR && row < r1;
-            bool inc = false;
-            T w = 0;
-            if (valid) {
-                int t = row - l * m;
-                unsigned long long key = full_key(keys[row]);
-                uint8_t b = mb[t];
-                bool in;
-                if (fp32) in = key < R.t_lo || (key <= R.t_hi && (b & 2));
-                else in = key < R.t_key || (key == R.t_key && (unsigned)t <= R.t_pos);
-                bool old = b & 1;
-                nswap += (in != old);
-                if (full) { inc = in; w = (T)1; }
-                else { inc = in != old; w = in ? (T)1 : (T)-1; }
-                mb[t] = in ? 1 : 0;
-            }
-            int tot;
-            int slot = cta_compact(inc, tot);
-            if (slot >= 0) {
-                float x[PB];
-                load_row_padded<PB>(Xp + (size_t)row * PB, x);
-                T* dst = tile + slot * S::PE;
+        for (int c0 = r0; c0 < r1; c0 += MEMB_CHUNK) {
+            uint8_t bb[MEMB_U];
+            unsigned long long kk[MEMB_U];
 #pragma unroll
-                for (int j = 0; j < PB; ++j) dst[j] = ((T)x[j] - s_hi[j]) - s_lo[j];
-                dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
-                dst[p] = (T)1;
-                wt[slot] = w;
+            for (int u = 0; u < MEMB_U; ++u) {
+                const int row = c0 + u * NT + threadIdx.x;
+                bb[u] = (row < r1) ? mb[row - l * m] : (uint8_t)0;
+                kk[u] = (row < r1) ? full_key(keys[row]) : 0ull;
             }
+            unsigned incm = 0, negm = 0;
+#pragma unroll
+            for (int u = 0; u < MEMB_U; ++u) {
+                const int row = c0 + u * NT + threadIdx.x;
+                if (row >= r1) continue;
+                const int t = row - l * m;
+                const uint8_t b = bb[u];
+                bool in;
+                if (fp32) in = kk[u] < R.t_lo || (kk[u] <= R.t_hi && (b & 2));
+                else in = kk[u] < R.t_key || (kk[u] == R.t_key && (unsigned)t <= R.t_pos);
+                const bool old = b & 1;
+                nswap += (in != old);
+                const bool inc = full ? in : (in != old);
+                if (inc) {
+                    incm |= 1u << u;
+                    if (!full && !in) negm |= 1u << u;
+                }
+                const uint8_t nb = in ? 1 : 0;
+                if (b != nb) mb[t] = nb;
+            }
+            int total;
+            int off = cta_excl_scan(__popc(incm), total);
+#pragma unroll
+            for (int u = 0; u < MEMB_U; ++u)
+                if (incm >> u & 1u) lst[off++] = (c0 + u * NT + threadIdx.x) | (int)((negm >> u & 1u) << 31);
             __syncthreads();
-            if (tot) acc.rows(tile, wt, tot);
-            __syncthreads();
+            for (int b0 = 0; b0 < total; b0 += S::TR) {
+                const int nbat = min(S::TR, total - b0);
+                if (threadIdx.x < nbat) {
+                    const int e = lst[b0 + threadIdx.x];
+                    const int row = e & 0x7fffffff;
+                    float x[PB];
+                    load_row_padded<PB>(Xp + (size_t)row * PB, x);
+                    T* dst = tile + threadIdx.x * S::PE;
+#pragma unroll
+                    for (int j = 0; j < PB; ++j) dst[j] = ((T)x[j] - s_hi[j]) - s_lo[j];
+                    dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
+                    dst[p] = (T)1;
+                    wt[threadIdx.x] = (e < 0) ? (T)-1 : (T)1;
+                }
+                __syncthreads();
+                acc.rows(tile, wt, nbat);
+                __syncthreads();
+            }
         }
         nswap = cta_sum_int(nswap);
         if (threadIdx.x == 0 && nswap) atomicAdd(swaps + c, nswap);
@@ -699,7 +1057,7 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
 
 template <int PB, typename T>
 void memb_t(const Plan& P, cudaStream_t s) {
-    size_t sm = gram_smem_bytes<PB, T>();
+    size_t sm = memb_smem_bytes<PB, T>();
     auto k = k_memb<PB, T>;
     set_smem(k, sm);
     dim3 grid(P.cpb, P.q);

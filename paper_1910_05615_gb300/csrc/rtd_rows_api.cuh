@@ -9,6 +9,8 @@ namespace rtd {
     void start2_pb##N(const Plan& P, cudaStream_t s);                                               \
     void transform_pb##N(const Plan& P, cudaStream_t s);                                            \
     void dist_pb##N(const Plan& P, cudaStream_t s);                                                 \
+    void dist_win_pb##N(const Plan& P, cudaStream_t s);                                             \
+    void band64_pb##N(const Plan& P, cudaStream_t s);                                               \
     void memb_pb##N(const Plan& P, cudaStream_t s);                                                 \
     void rew_pb##N(const Plan& P, cudaStream_t s);                                                  \
     void member_gram_pb##N(const Plan& P, cudaStream_t s);                                          \

@@ -29,6 +29,8 @@ void RTD_FN(dist_pb)(const Plan& P, cudaStream_t s) {
     if (P.precision == RTD_FP64) dist_t<RTD_PB, double>(P, s);
     else dist_t<RTD_PB, float>(P, s);
 }
+void RTD_FN(dist_win_pb)(const Plan& P, cudaStream_t s) { dist_win_t<RTD_PB>(P, s); }
+void RTD_FN(band64_pb)(const Plan& P, cudaStream_t s) { band64_t<RTD_PB>(P, s); }
 void RTD_FN(memb_pb)(const Plan& P, cudaStream_t s) {
     if (P.precision == RTD_FP64) memb_t<RTD_PB, double>(P, s);
     else memb_t<RTD_PB, float>(P, s);

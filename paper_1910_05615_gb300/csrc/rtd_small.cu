@@ -300,11 +300,12 @@ void launch_refine_end(const Plan& P, cudaStream_t s) {
 __device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __restrict__ S_z,
                                const double* __restrict__ mu_uni, const double* __restrict__ s_uni,
                                int p, double* A, double* Li, RowParams& rp, double* logdet) {
+    __shared__ double inv_s[PMAX], dm[PMAX];
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         A[i * LD + j] = S_z[i * PMAX + j];
     }
-    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) inv_s[j] = 1.0 / s_uni[j];
     if (!cta_cholesky(A, p)) return false;
     cta_tri_inverse(A, Li, p);
     double ld = 0.0;
@@ -313,7 +314,7 @@ __device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __
     *logdet = ld;
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
-        double v = (j <= i) ? Li[i * LD + j] / s_uni[j] : 0.0;
+        double v = (j <= i) ? Li[i * LD + j] * inv_s[j] : 0.0;
         rp.M[i * PMAX + j] = v;
         rp.Mf[i * PMAX + j] = (float)v;
     }
@@ -323,29 +324,63 @@ __device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __
         float hi = (float)mx;
         rp.mu_hi[j] = hi;
         rp.mu_lo[j] = (float)(mx - (double)hi);
+        // centre offset from the FP32 univariate centre u, in Z units
+        dm[j] = (mx - (double)(float)mu_uni[j]) * inv_s[j];
+    }
+    __syncthreads();
+    // bf = M (mu - u) = Li D^-1 (mu - u)
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        double a = 0.0;
+        for (int j = 0; j <= i; ++j) a = fma(Li[i * LD + j], dm[j], a);
+        rp.bf[i] = (float)a;
     }
     __syncthreads();
     return true;
 }
 
-// Before each C-step: condition monitor (Section 3.4) and the row
-// parameters of the current (mu, Sigma).
-__global__ void __launch_bounds__(CT) k_chol_prep(Chain* ch, const Consts* __restrict__ cs, int* swaps,
-                                                  Status* st) {
-    extern __shared__ double sm[];
+// FP32 form: the window of keys the distance pass classifies against,
+// predicted from the chain's last two thresholds (none before the first
+// selection: the histogram path runs).
+__device__ inline void set_window(SelRule& R, int fp32) {
+    R.below = 0; R.cand = 0; R.band = 0; R.nlo = 0;
+    R.fast = 0; R.need_hist = 0; R.bandsel = 0; R.band_off = 0;
+    R.win = 0;
+    if (!fp32 || !R.have_t || !(R.t_prev >= 0.f) || !isfinite(R.t_prev)) return;
+    // half-width: twice the last relative change, within [4 eps, 1/2]; the
+    // first window (one threshold known) takes 1/2
+    float t = R.t_prev, d = 0.5f;
+    if (R.t_prev2 > 0.f && t > 0.f) d = 2.f * fabsf(t - R.t_prev2) / t;
+    d = fminf(fmaxf(d, 4.f * (float)BAND_EPS), 0.5f);
+    R.w_lo = __float_as_uint(t * (1.f - d));
+    R.w_hi = __float_as_uint(t * (1.f + d));
+    int sh = 0;
+    while (((R.w_hi - R.w_lo) >> sh) >= (unsigned)WIN_BINS) ++sh;
+    R.w_sh = sh;
+    R.win = 1;
+}
+
+__device__ inline void clear_rule(SelRule& R) {
+    R.win = 0; R.fast = 0; R.bandsel = 0; R.need_hist = 0; R.cand = 0; R.band = 0;
+}
+
+// Condition monitor (Section 3.4) and row parameters of a chain's current
+// (mu, Sigma), and the selection window of its next step.  False when the
+// chain is refused.  sm: 3 MAT doubles of shared memory.
+__device__ bool chain_prep(Chain& C, SelRule& R, const Consts* __restrict__ cs, int* swap_slot, Status* st,
+                           double* sm) {
     double* A = sm;
     double* Li = sm + MAT;
     double* S = sm + 2 * MAT;
     __shared__ double s_ld;
-    const int c = blockIdx.x;
-    Chain& C = ch[c];
-    if (!C.active) return;
     const int p = cs->p;
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         S[i * LD + j] = C.Sigma[i * PMAX + j];
     }
-    if (threadIdx.x == 0) swaps[c] = 0;
+    if (threadIdx.x == 0) {
+        *swap_slot = 0;
+        set_window(R, cs->precision == RTD_FP32);
+    }
     __syncthreads();
     bool ok = make_rowparams(C.mu, C.Sigma, cs->mu_uni, cs->s_uni, p, A, Li, C.rp, &s_ld);
     double k1 = ok ? cta_kappa1(S, Li, A, p) : INFINITY;
@@ -354,9 +389,11 @@ __global__ void __launch_bounds__(CT) k_chol_prep(Chain* ch, const Consts* __res
             C.active = 0;
             C.status = CH_REFUSED;
             C.kappa1 = k1;
+            clear_rule(R);
             set_warning(st, RTD_WARN_CSTEP_REFUSED);
         }
-        return;
+        __syncthreads();
+        return false;
     }
     if (C.full) {
         for (int j = threadIdx.x; j < p; j += blockDim.x) {
@@ -366,13 +403,28 @@ __global__ void __launch_bounds__(CT) k_chol_prep(Chain* ch, const Consts* __res
         }
     }
     if (threadIdx.x == 0) { C.logdet = s_ld; C.kappa1 = k1; }
+    __syncthreads();
+    return true;
+}
+
+// Before the first C-step.
+__global__ void __launch_bounds__(CT) k_chol_prep(Chain* ch, const Consts* __restrict__ cs, int* swaps,
+                                                  SelRule* rule, Status* st) {
+    extern __shared__ double sm[];
+    const int c = blockIdx.x;
+    Chain& C = ch[c];
+    if (!C.active) {
+        if (threadIdx.x == 0) clear_rule(rule[c]);   // a stopped chain selects nothing
+        return;
+    }
+    (void)chain_prep(C, rule[c], cs, swaps + c, st, sm);
 }
 
 void launch_chol_prep(const Plan& P, cudaStream_t s) {
     size_t sm = 3 * MAT * sizeof(double);
     auto k = k_chol_prep;
     big_smem(k, sm);
-    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.swaps, P.st);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.swaps, P.rule, P.st);
 }
 
 // =====================================================================
@@ -400,62 +452,77 @@ __device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Sta
     if (threadIdx.x == 0) st->active_blocks = a;
 }
 
+// End of a C-step and start of the next one: fold the Gram partials into
+// (S, G) (Section 3.5 update, or a fresh sum), new mu and
+// Sigma = Lambda/(h_b-1) (eqs. cstep4a/b), convergence when H_new = H_old
+// (no swaps); a chain that goes on gets its next row parameters and window.
 __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* __restrict__ cs,
                                                        const double* __restrict__ gsum, size_t slot_d,
-                                                       const int* __restrict__ swaps, int* blk,
-                                                       Status* st) {
-    __shared__ double dmu[PMAX];
+                                                       int* swaps, int* blk, SelRule* rule, Status* st) {
+    extern __shared__ double sm[];
+    __shared__ double dmu[PMAX], inv_s[PMAX];
     __shared__ double s_m2;
-    const int c = blockIdx.x, l = c / 2, k = c % 2;
+    __shared__ int s_cont;
+    const int c = blockIdx.x, l = c / 2;
     Chain& C = ch[c];
-    if (!C.active) { count_active_blocks(ch, cs->q, blk, st); return; }
+    if (!C.active) {
+        if (threadIdx.x == 0) clear_rule(rule[c]);
+        count_active_blocks(ch, cs->q, blk, st);
+        return;
+    }
     const int p = cs->p, nb = gram_nb(cs->pb);
-    const double hb = (double)cs->hb;
+    const double hb = (double)cs->hb, inv_hb = 1.0 / hb, inv_hb1 = 1.0 / (hb - 1.0);
     const double* ext = gsum + (size_t)c * slot_d;
-    (void)k;
     const int full = C.full;
-    const double cnt = gram_get(ext, p, p, nb);
     if (threadIdx.x == 0) {
+        const double cnt = gram_get(ext, p, p, nb);
         double expect = full ? hb : 0.0;
         if (fabs(cnt - expect) > 0.5) set_error(st, RTD_EINTERNAL);
     }
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         double v = gram_get(ext, j, p, nb);
         C.S[j] = full ? v : C.S[j] + v;
+        inv_s[j] = 1.0 / cs->s_uni[j];
     }
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         double v = gram_get(ext, i, j, nb);
         C.G[i * PMAX + j] = full ? v : C.G[i * PMAX + j] + v;
     }
+    // the previous M, for the centre's move below
+    double* Mo = sm;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        Mo[i * LD + j] = C.rp.M[i * PMAX + j];
+    }
     __syncthreads();
-    const double* su = cs->s_uni;
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        double mx = C.rp.ref[j] + C.S[j] / hb;
-        C.mu[j] = (mx - cs->mu_uni[j]) / su[j];
+        double mx = C.rp.ref[j] + C.S[j] * inv_hb;
+        C.mu[j] = (mx - cs->mu_uni[j]) * inv_s[j];
         dmu[j] = mx - C.rp.ref[j];
     }
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
-        double lam = C.G[i * PMAX + j] - C.S[i] * C.S[j] / hb;
-        C.Sigma[i * PMAX + j] = lam / (hb - 1.0) / (su[i] * su[j]);
+        double lam = C.G[i * PMAX + j] - C.S[i] * C.S[j] * inv_hb;
+        C.Sigma[i * PMAX + j] = lam * inv_hb1 * inv_s[i] * inv_s[j];
     }
     __syncthreads();
+    // squared distance of the centre's move from the reference, under the previous fit
+    double a2 = 0.0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        double a = 0.0;
+        for (int j = 0; j <= i; ++j) a = fma(Mo[i * LD + j], dmu[j], a);
+        a2 = fma(a, a, a2);
+    }
+    a2 = cta_sum(a2);
     if (threadIdx.x == 0) {
-        // squared distance of the centre's move from the reference, under
-        // the previous fit
-        double m2 = 0.0;
-        for (int i = 0; i < p; ++i) {
-            double a = 0.0;
-            for (int j = 0; j <= i; ++j) a += C.rp.M[i * PMAX + j] * dmu[j];
-            m2 += a * a;
-        }
-        s_m2 = m2;
+        s_m2 = a2;
         int sw = swaps[c];
         C.swaps = sw;
         atomicAdd(&st->gram_rows, (unsigned long long)(full ? cs->hb : sw));
         C.steps += 1;
         C.full_count += full;
+        s_cont = 0;
         if (C.steps >= 2 && sw == 0) {
             C.active = 0;
             C.status = CH_OK;
@@ -465,6 +532,13 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
             set_warning(st, RTD_WARN_MAXITER);
         } else {
             C.full = ((C.steps >= 2 && 4.0 * sw > hb) || s_m2 > 1.0) ? 1 : 0;
+            s_cont = 1;
+        }
+        if (!s_cont) clear_rule(rule[c]);
+    }
+    __syncthreads();
+    if (s_cont && chain_prep(C, rule[c], cs, swaps + c, st, sm)) {
+        if (threadIdx.x == 0) {
             atomicAdd(&st->active, 1);
             atomicAdd(&blk[l], 1);
         }
@@ -474,7 +548,10 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
 
 void launch_cstep_finalize(const Plan& P, cudaStream_t s) {
     launch_reduce_slots(P, 0, s);
-    k_cstep_finalize<<<2 * P.q, CT, 0, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles, P.swaps, P.blk_active, P.st);
+    size_t sm = 3 * MAT * sizeof(double);
+    auto k = k_cstep_finalize;
+    big_smem(k, sm);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles, P.swaps, P.blk_active, P.rule, P.st);
 }
 
 // =====================================================================

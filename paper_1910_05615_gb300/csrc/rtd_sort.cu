@@ -660,7 +660,8 @@ __global__ void __launch_bounds__(1024) k_select_bucket(unsigned* __restrict__ h
     __shared__ unsigned cnt[1024];
     __shared__ int s_bin;
     const int c = blockIdx.x;
-    if (!ch[c].active) return;
+    if (!ch[c].active || rule[c].fast) return;
+    if (threadIdx.x == 0 && rule[c].win) rule[c].acc_miss += 1;
     unsigned* h = hist + (size_t)c * HIST_BINS;
     const int per = HIST_BINS / 1024;
     unsigned loc[HIST_BINS / 1024];
@@ -708,31 +709,64 @@ void launch_select_bucket(const Plan& P, cudaStream_t s) {
 
 // =====================================================================
 // Radix select, step 2 (one CTA per chain): the r-th smallest (key, pos)
-// of a candidate list, by 8-bit radix narrowing on the composite
-// (key, position) until at most SEL_SMALL entries share the prefix, then
-// direct ranking in shared memory.  Positions make every entry unique, so
-// ties between equal distances go to the lower position.
+// of a candidate list.  Long lists are narrowed by 8-bit radix passes on
+// the composite (key, position) until at most SEL_SMALL entries share the
+// prefix; those are sorted in shared memory (bitonic network).  Positions
+// make every entry unique, so ties between equal distances go to the lower
+// position.
 // =====================================================================
 constexpr int SEL_T = 1024;
-constexpr int SEL_SMALL = 1024;
+constexpr int SEL_SMALL = 2048;
 typedef unsigned __int128 u128;
 
 __device__ inline u128 comp(const Cand& e) { return ((u128)e.key << 32) | (u128)e.pos; }
 
-__device__ Cand cta_select_rank(const Cand* list, int C, int r, int key_bits, Cand* buf, Status* st) {
-    __shared__ unsigned hcnt[256];
-    __shared__ unsigned long long s_and, s_or;
-    __shared__ int s_digit, s_r, s_cnt, s_n;
-    __shared__ Cand s_out;
-    (void)key_bits;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        s_out.key = ~0ull; s_out.pos = 0xffffffffu; s_out.pad = 1;
-        s_and = ~0ull; s_or = 0ull; s_n = 0;
+// Ascending sort of a[0, n) (n <= SEL_SMALL) in shared memory; a must hold
+// the next power of two of entries.
+__device__ inline void cta_bitonic(Cand* a, int n) {
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
+        a[i].key = ~0ull; a[i].pos = 0xffffffffu; a[i].pad = 1;
     }
     __syncthreads();
-    // key bits shared by every entry need no pass
-    {
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const Cand x = a[i], y = a[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((comp(x) > comp(y)) == up) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// buf: SEL_SMALL entries of shared memory.
+__device__ Cand cta_select_rank(const Cand* list, int C, int r, int key_bits, Cand* buf, Status* st) {
+    __shared__ unsigned hcnt[256];
+    __shared__ unsigned wtot[8];
+    __shared__ unsigned long long s_and, s_or;
+    __shared__ int s_digit, s_r, s_cnt, s_n;
+    (void)key_bits;
+    const int lane = threadIdx.x & 31;
+    Cand bad;
+    bad.key = ~0ull; bad.pos = 0xffffffffu; bad.pad = 1;
+    if (r < 1 || r > C) {
+        if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
+        return bad;
+    }
+    if (threadIdx.x == 0) { s_and = ~0ull; s_or = 0ull; s_n = 0; }
+    __syncthreads();
+    const int total = 96;                 // composite value: key (64) : position (32)
+    int pbits = 0;
+    u128 prefix = 0;
+    int cnt = C, rr = r;
+    if (C > SEL_SMALL) {
+        // key bits shared by every entry need no pass
         unsigned long long a = ~0ull, o = 0ull;
         for (int i = threadIdx.x; i < C; i += blockDim.x) { unsigned long long k = list[i].key; a &= k; o |= k; }
         for (int d = 16; d > 0; d >>= 1) {
@@ -740,111 +774,103 @@ __device__ Cand cta_select_rank(const Cand* list, int C, int r, int key_bits, Ca
             o |= __shfl_xor_sync(0xffffffffu, o, d);
         }
         if (lane == 0) { atomicAnd(&s_and, a); atomicOr(&s_or, o); }
-    }
-    __syncthreads();
-    const unsigned long long diff = s_and ^ s_or;
-    // composite value: 96 bits = key (64) : position (32)
-    const int total = 96;
-    int top = diff ? 32 + 63 - __clzll((long long)diff) : 31;   // highest differing bit
-    int pbits = total - 1 - top;
-    u128 prefix = (((u128)s_and << 32) >> (top + 1));
-    int cnt = C, rr = r;
-    while (cnt > SEL_SMALL && pbits < total) {
-        const int width = (total - pbits) < 8 ? (total - pbits) : 8;
-        const int shift = total - pbits - width;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hcnt[i] = 0u;
         __syncthreads();
-        for (int base = 0; base < C; base += blockDim.x) {
-            int i = base + threadIdx.x;
-            unsigned tag = 0x1000u + lane;
-            unsigned dg = 0;
-            if (i < C) {
-                u128 v = comp(list[i]);
-                if (pbits == 0 || (v >> (total - pbits)) == prefix) {
-                    dg = (unsigned)(v >> shift) & ((1u << width) - 1u);
-                    tag = dg;
+        const unsigned long long diff = s_and ^ s_or;
+        const int top = diff ? 32 + 63 - __clzll((long long)diff) : 31;   // highest differing bit
+        pbits = total - 1 - top;
+        prefix = (((u128)s_and << 32) >> (top + 1));
+        while (cnt > SEL_SMALL && pbits < total) {
+            const int width = (total - pbits) < 8 ? (total - pbits) : 8;
+            const int shift = total - pbits - width;
+            for (int i = threadIdx.x; i < 256; i += blockDim.x) hcnt[i] = 0u;
+            __syncthreads();
+            for (int base = 0; base < C; base += blockDim.x) {
+                const int i = base + threadIdx.x;
+                unsigned tag = 0x1000u + lane;
+                unsigned dg = 0;
+                if (i < C) {
+                    const u128 v = comp(list[i]);
+                    if (pbits == 0 || (v >> (total - pbits)) == prefix) {
+                        dg = (unsigned)(v >> shift) & ((1u << width) - 1u);
+                        tag = dg;
+                    }
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, tag);
+                if (tag < 0x1000u && (__ffs(peers) - 1) == lane) atomicAdd(&hcnt[dg], (unsigned)__popc(peers));
+            }
+            if (threadIdx.x == 0) s_digit = -1;
+            __syncthreads();
+            // digit of rank rr: parallel inclusive scan of the 256 counts
+            unsigned v = 0, x = 0;
+            if (threadIdx.x < 256) {
+                v = hcnt[threadIdx.x];
+                x = v;
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    unsigned y = __shfl_up_sync(0xffffffffu, x, o2);
+                    if (lane >= o2) x += y;
+                }
+                if (lane == 31) wtot[threadIdx.x >> 5] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x < 256) {
+                unsigned off = 0;
+                for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) off += wtot[w];
+                const unsigned incl = off + x, excl = incl - v;
+                if (v && excl < (unsigned)rr && (unsigned)rr <= incl) {
+                    s_digit = threadIdx.x; s_r = rr - (int)excl; s_cnt = (int)v;
                 }
             }
-            unsigned peers = __match_any_sync(0xffffffffu, tag);
-            if (tag < 0x1000u && (__ffs(peers) - 1) == lane) atomicAdd(&hcnt[dg], (unsigned)__popc(peers));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int cum = 0;
-            s_digit = -1;
-            for (int d = 0; d < (1 << width); ++d) {
-                int hd = (int)hcnt[d];
-                if (cum + hd >= rr) { s_digit = d; s_r = rr - cum; s_cnt = hd; break; }
-                cum += hd;
+            __syncthreads();
+            if (s_digit < 0) {
+                if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
+                __syncthreads();
+                return bad;
             }
+            prefix = (prefix << width) | (u128)(unsigned)s_digit;
+            pbits += width;
+            rr = s_r;
+            cnt = s_cnt;
+            __syncthreads();
         }
-        __syncthreads();
-        if (s_digit < 0) { if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL); __syncthreads(); return s_out; }
-        prefix = (prefix << width) | (u128)(unsigned)s_digit;
-        pbits += width;
-        rr = s_r;
-        cnt = s_cnt;
-        __syncthreads();
     }
     for (int base = 0; base < C; base += blockDim.x) {
-        int i = base + threadIdx.x;
+        const int i = base + threadIdx.x;
         bool m = false;
         Cand e;
         if (i < C) {
             e = list[i];
-            u128 v = comp(e);
+            const u128 v = comp(e);
             m = (pbits == 0 || (v >> (total - pbits)) == prefix);
         }
-        unsigned bal = __ballot_sync(0xffffffffu, m);
+        const unsigned bal = __ballot_sync(0xffffffffu, m);
         int wb = 0;
         if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
         wb = __shfl_sync(0xffffffffu, wb, 0);
         if (m) {
-            int slot = wb + __popc(bal & ((1u << lane) - 1u));
+            const int slot = wb + __popc(bal & ((1u << lane) - 1u));
             if (slot < SEL_SMALL) buf[slot] = e;
         }
     }
     __syncthreads();
-    int n = s_n < SEL_SMALL ? s_n : SEL_SMALL;
-    if (s_n > SEL_SMALL || rr < 1 || rr > n) {
+    const int n = s_n;
+    if (n > SEL_SMALL || rr < 1 || rr > n) {
         if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
         __syncthreads();
-        return s_out;
+        return bad;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        u128 v = comp(buf[i]);
-        int rank = 0;
-        for (int j = 0; j < n; ++j) rank += comp(buf[j]) < v ? 1 : 0;
-        if (rank == rr - 1) s_out = buf[i];
-    }
-    __syncthreads();
-    Cand res = s_out;
+    cta_bitonic(buf, n);
+    const Cand res = buf[rr - 1];
     __syncthreads();
     return res;
 }
 
-// FP64 distance of one row of Xp under a chain's current fit.
-__device__ inline double row_d2_fp64(const float* __restrict__ x, const RowParams& rp, int p) {
-    double cc[PMAX];
-    for (int j = 0; j < p; ++j) cc[j] = (double)x[j] - rp.mu[j];
-    double d2 = 0.0;
-    for (int i = 0; i < p; ++i) {
-        double a = 0.0;
-        for (int j = 0; j <= i; ++j) a += rp.M[i * PMAX + j] * cc[j];
-        d2 += a * a;
-    }
-    return d2;
-}
-
 __global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
                                                           const Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
-                                                          uint8_t* __restrict__ memb_all, const float* __restrict__ Xp,
-                                                          int m, int p, int pb, int hb, int fp32, Status* st) {
+                                                          int m, int hb, int fp32, Status* st) {
     __shared__ Cand buf[SEL_SMALL];
     __shared__ int s_nlo, s_nb;
     const int c = blockIdx.x;
-    if (!ch[c].active) return;
-    const int l = c / 2;
+    if (!ch[c].active || rule[c].fast) return;
     SelRule& R = rule[c];
     const int C = R.cand < m ? R.cand : m;
     const int r = hb - R.below;
@@ -859,15 +885,14 @@ __global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict
         if (threadIdx.x == 0) { R.t_key = t.key; R.t_pos = t.pos; }
         return;
     }
-    // FP32 form: FP64 decision inside [t (1 - eps), t (1 + eps)]
+    // FP32 form: rows inside [t (1 - eps), t (1 + eps)] are decided in FP64
+    // (band distances: k_band64; their ranking: k_select_band)
     const float tf = __uint_as_float((unsigned)t.key);
     const unsigned long long t_lo = __float_as_uint(tf * (float)(1.0 - BAND_EPS));
     const unsigned long long t_hi = __float_as_uint(tf * (float)(1.0 + BAND_EPS));
     if (threadIdx.x == 0) { s_nlo = 0; s_nb = 0; }
     __syncthreads();
     Cand* band = band_all + (size_t)c * m;
-    const RowParams& rp = ch[c].rp;
-    // collect the band rows first, so that the FP64 distances run on full warps
     int nlo = 0;
     const int lane = threadIdx.x & 31;
     for (int base = 0; base < C; base += blockDim.x) {
@@ -887,37 +912,192 @@ __global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict
     }
     nlo = warp_sum_int(nlo);
     if (lane == 0 && nlo) atomicAdd(&s_nlo, nlo);
-    __threadfence_block();
     __syncthreads();
-    const int nb = s_nb;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        Cand e = band[i];
-        const float* x = Xp + ((size_t)l * m + e.pos) * pb;
-        e.key = (unsigned long long)__double_as_longlong(row_d2_fp64(x, rp, p));  // d2 >= 0: bits order as values
-        band[i] = e;
+    if (threadIdx.x == 0) {
+        R.t_lo = t_lo;
+        R.t_hi = t_hi;
+        R.band = s_nb;
+        R.nlo = R.below + s_nlo;
+        R.band_off = 0;
+        R.bandsel = 1;
+        R.t_prev2 = R.have_t ? R.t_prev : 0.f;
+        R.t_prev = tf;
+        R.have_t = 1;
     }
-    __threadfence_block();
+}
+
+void launch_select_finish(const Plan& P, cudaStream_t s) {
+    k_select_finish<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.m, P.hb,
+                                              P.precision == RTD_FP32, P.st);
+}
+
+// =====================================================================
+// Window path of the FP32 form (from the second C-step on).  The distance
+// pass has counted the rows below the window, listed the rows inside it and
+// binned them in WIN_BINS bins.  The bin of rank h_b gives a key range that
+// holds the threshold t; the candidates within the FP64 band of that range
+// (a few hundred rows) are the only ones the selection has to order.  The
+// rule is the histogram path's: rows below [t (1 - eps), t (1 + eps)] are
+// in, band rows are ranked by their FP64 distance (ties to the lower
+// position).  The band list goes to the upper half of the chain's band
+// buffer (the lower half holds the rows of the bin's range).  A chain whose
+// rank or band falls outside the window is marked need_hist and left to the
+// histogram path.
+// =====================================================================
+__global__ void __launch_bounds__(SEL_T) k_select_win(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
+                                                       const Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
+                                                       unsigned* __restrict__ hist, int m, int hb, Status* st) {
+    static_assert(WIN_BINS == SEL_T, "one window bin per thread");
+    __shared__ Cand buf[SEL_SMALL];
+    __shared__ unsigned cnt[WIN_BINS];
+    __shared__ int s_bin, s_ns, s_nslo, s_nb, s_nlo;
+    const int c = blockIdx.x;
+    if (!ch[c].active) return;
+    SelRule& R = rule[c];
+    if (!R.win) return;
+    const int lane = threadIdx.x & 31;
+    // window histogram: inclusive scan, bins reset for the next use
+    unsigned* h = hist + (size_t)c * HIST_BINS;
+    const unsigned own = h[threadIdx.x];
+    h[threadIdx.x] = 0u;
+    cnt[threadIdx.x] = own;
+    if (threadIdx.x == 0) { s_bin = -1; s_ns = 0; s_nslo = 0; s_nb = 0; s_nlo = 0; }
     __syncthreads();
-    const int r2 = hb - R.below - s_nlo;
+    for (int o = 1; o < WIN_BINS; o <<= 1) {
+        unsigned v = threadIdx.x >= o ? cnt[threadIdx.x - o] : 0u;
+        __syncthreads();
+        cnt[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int C = R.cand < m ? R.cand : m;
+    const int r = hb - R.below;
+    if (threadIdx.x == 0) { R.acc_win += 1; R.acc_cand += C; }
+    if (r < 1 || r > C) {
+        if (threadIdx.x == 0) R.need_hist = 1;
+        return;
+    }
+    {
+        const unsigned incl = cnt[threadIdx.x], excl = incl - own;
+        if (excl < (unsigned)r && (unsigned)r <= incl) s_bin = threadIdx.x;
+    }
+    __syncthreads();
+    const int b = s_bin;
+    if (b < 0) {   // the counts disagree with the list: take the histogram path
+        if (threadIdx.x == 0) R.need_hist = 1;
+        return;
+    }
+    // key range of bin b and its FP64 band
+    const unsigned lo_key = R.w_lo + ((unsigned)b << R.w_sh);
+    unsigned hi_key = lo_key + ((1u << R.w_sh) - 1u);
+    if (hi_key > R.w_hi || hi_key < lo_key) hi_key = R.w_hi;
+    const unsigned long long kb_lo = __float_as_uint(__uint_as_float(lo_key) * (float)(1.0 - BAND_EPS));
+    const unsigned long long kb_hi = __float_as_uint(__uint_as_float(hi_key) * (float)(1.0 + BAND_EPS));
+    // candidates inside [kb_lo, kb_hi] -> lower half of the band buffer
+    const Cand* cand = cand_all + (size_t)c * m;
+    Cand* sub = band_all + (size_t)c * m;
+    const int cap = m / 2;
+    int nlo = 0;
+    for (int base = 0; base < C; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        bool in = false;
+        Cand e;
+        if (i < C) {
+            e = cand[i];
+            if (e.key < kb_lo) ++nlo;
+            else in = e.key <= kb_hi;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        int wb = 0;
+        if (lane == 0 && bal) wb = atomicAdd(&s_ns, __popc(bal));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (in) {
+            const int idx = wb + __popc(bal & ((1u << lane) - 1u));
+            if (idx < cap) sub[idx] = e;
+        }
+    }
+    nlo = warp_sum_int(nlo);
+    if (lane == 0 && nlo) atomicAdd(&s_nslo, nlo);
+    __syncthreads();
+    const int ns = s_ns, r1 = r - s_nslo;
+    if (ns > cap || r1 < 1 || r1 > ns) {
+        if (threadIdx.x == 0) R.need_hist = 1;
+        return;
+    }
+    Cand t = cta_select_rank(sub, ns, r1, 32, buf, st);
+    if (t.pad) return;
+    const float tf = __uint_as_float((unsigned)t.key);
+    const unsigned long long t_lo = __float_as_uint(tf * (float)(1.0 - BAND_EPS));
+    const unsigned long long t_hi = __float_as_uint(tf * (float)(1.0 + BAND_EPS));
+    if (t_lo < (unsigned long long)R.w_lo || t_hi > (unsigned long long)R.w_hi) {
+        if (threadIdx.x == 0) R.need_hist = 1;
+        return;
+    }
+    // band rows -> upper half; rows of the range below the band
+    Cand* band = band_all + (size_t)c * m + cap;
+    int blo = 0;
+    for (int base = 0; base < ns; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        bool inb = false;
+        Cand e;
+        if (i < ns) {
+            e = sub[i];
+            if (e.key < t_lo) ++blo;
+            else inb = e.key <= t_hi;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, inb);
+        int wb = 0;
+        if (lane == 0 && bal) wb = atomicAdd(&s_nb, __popc(bal));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (inb) band[wb + __popc(bal & ((1u << lane) - 1u))] = e;
+    }
+    blo = warp_sum_int(blo);
+    if (lane == 0 && blo) atomicAdd(&s_nlo, blo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R.t_lo = t_lo;
+        R.t_hi = t_hi;
+        R.band = s_nb;
+        R.nlo = R.below + s_nslo + s_nlo;
+        R.band_off = cap;
+        R.t_prev2 = R.t_prev;
+        R.t_prev = tf;
+        R.fast = 1;
+    }
+}
+
+// Band ranking of the FP32 form (both paths): the band rows whose FP64
+// (d2, position) is at most that of rank h_b - (rows below the band) get the
+// decision bit (bit 1) the membership pass reads.
+__global__ void __launch_bounds__(SEL_T) k_select_band(const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
+                                                        const Cand* __restrict__ band_all,
+                                                        uint8_t* __restrict__ memb_all, int m, int hb, Status* st) {
+    __shared__ Cand buf[SEL_SMALL];
+    const int c = blockIdx.x;
+    if (!ch[c].active) return;
+    const SelRule& R = rule[c];
+    if (!(R.fast || R.bandsel)) return;
+    const int nb = R.band, r2 = hb - R.nlo;
+    if (threadIdx.x == 0) const_cast<SelRule&>(R).acc_band += nb;
     if (r2 < 1 || r2 > nb) {
         if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
         return;
     }
+    const Cand* band = band_all + (size_t)c * m + R.band_off;
     Cand tb = cta_select_rank(band, nb, r2, 64, buf, st);
     if (tb.pad) return;
     const u128 tv = comp(tb);
     uint8_t* mb = memb_all + (size_t)c * m;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        Cand e = band[i];
-        bool in = comp(e) <= tv;
-        mb[e.pos] = (uint8_t)((mb[e.pos] & 1) | (in ? 2 : 0));
+        const Cand e = band[i];
+        mb[e.pos] = (uint8_t)((mb[e.pos] & 1) | (comp(e) <= tv ? 2 : 0));
     }
-    if (threadIdx.x == 0) { R.t_lo = t_lo; R.t_hi = t_hi; R.band = nb; }
 }
 
-void launch_select_finish(const Plan& P, cudaStream_t s) {
-    k_select_finish<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.memb, P.Xp, P.m, P.p, P.pb,
-                                              P.hb, P.precision == RTD_FP32, P.st);
+void launch_select_win(const Plan& P, cudaStream_t s) {
+    k_select_win<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.hist, P.m, P.hb, P.st);
+}
+void launch_select_band(const Plan& P, cudaStream_t s) {
+    k_select_band<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.band, P.memb, P.m, P.hb, P.st);
 }
 
 }  // namespace rtd
