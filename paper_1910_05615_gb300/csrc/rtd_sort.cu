@@ -207,6 +207,57 @@ __device__ inline double uval(const K* s, long long i) { return kval(s[i]); }
 
 struct D2 { double a, b; };
 
+// ---- compensated FP32 pairs ("float-float", value hi + lo, about 48
+// significant bits): TwoSum (Knuth), FastTwoSum and TwoProduct through FMA
+// (Dekker).  Sums of 32-bit keys use them instead of FP64, whose rate is a
+// small fraction of the FP32 rate on this GPU; every pair converts exactly
+// to a double.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return FF{s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    FF s = ff_two_sum(a.hi, b.hi);
+    const FF t = ff_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = ff_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_sq(FF a) {          // a^2, dropping lo^2
+    const float p = a.hi * a.hi;
+    float e = fmaf(a.hi, a.hi, -p);
+    e = fmaf(2.f * a.hi, a.lo, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ double ff_d(FF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+    return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ FF ff_shfl_up(FF a, int o) {
+    return FF{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
+}
+
+// Shifted value d = s_i - c and d^2 of one sorted element: exact pair for
+// 32-bit keys (float values), double otherwise.
+struct FF2 { FF a, b; };
+__device__ __forceinline__ FF2 ff_elem(uint32_t k, float c) {
+    const float v = key2f(k);
+    const FF d = ff_two_sum(v, -c);
+    return FF2{d, ff_sq(d)};
+}
+__device__ __forceinline__ FF2 ff_zero2() { return FF2{FF{0.f, 0.f}, FF{0.f, 0.f}}; }
+__device__ __forceinline__ FF2 ff_add2(FF2 x, FF2 y) { return FF2{ff_add(x.a, y.a), ff_add(x.b, y.b)}; }
+__device__ __forceinline__ FF2 ff_warp_sum2(FF2 v) {
+    for (int o = 16; o > 0; o >>= 1) v = ff_add2(v, FF2{ff_shfl_xor(v.a, o), ff_shfl_xor(v.b, o)});
+    return v;
+}
+
 __device__ inline D2 warp_sum2(D2 v) {
     for (int o = 16; o > 0; o >>= 1) {
         v.a += __shfl_xor_sync(0xffffffffu, v.a, o);
@@ -227,26 +278,41 @@ __device__ inline D2 cta_sum2(D2 v) {
     return t;
 }
 
-// Sum of (s_i - c, (s_i - c)^2) over [a, b) by one warp / by the CTA.
-template <typename K>
-__device__ inline D2 warp_range_sum(const K* s, double c, long long a, long long b) {
+// Middle order statistic c of a segment, in the arithmetic of the sums.
+__device__ inline float ucenter(const uint32_t* s, long long L) { return key2f(s[L / 2]); }
+__device__ inline double ucenter(const unsigned long long* s, long long L) { return key2d(s[L / 2]); }
+
+// Sum of (s_i - c, (s_i - c)^2) over [a, b) by one warp / by the CTA
+// (pairs for 32-bit keys, FP64 for 64-bit keys), returned as doubles.
+__device__ inline D2 warp_range_sum(const uint32_t* s, float c, long long a, long long b) {
+    FF2 acc = ff_zero2();
+    for (long long i = a + (threadIdx.x & 31); i < b; i += 32) acc = ff_add2(acc, ff_elem(s[i], c));
+    acc = ff_warp_sum2(acc);
+    return D2{ff_d(acc.a), ff_d(acc.b)};
+}
+__device__ inline D2 warp_range_sum(const unsigned long long* s, double c, long long a, long long b) {
     D2 acc{0.0, 0.0};
     for (long long i = a + (threadIdx.x & 31); i < b; i += 32) {
-        double d = uval(s, i) - c;
+        double d = key2d(s[i]) - c;
         acc.a += d;
         acc.b = fma(d, d, acc.b);
     }
     return warp_sum2(acc);
 }
-template <typename K>
-__device__ inline D2 cta_range_sum(const K* s, double c, long long a, long long b) {
-    D2 acc{0.0, 0.0};
-    for (long long i = a + threadIdx.x; i < b; i += UT) {
-        double d = uval(s, i) - c;
-        acc.a += d;
-        acc.b = fma(d, d, acc.b);
-    }
-    return cta_sum2(acc);
+template <typename K, typename C>
+__device__ inline D2 cta_range_sum(const K* s, C c, long long a, long long b) {
+    __shared__ double wa[UT / 32], wb[UT / 32];
+    // each warp sums a contiguous share, then the warp totals in fixed order
+    const long long n = b - a, per = (n + (UT / 32) - 1) / (UT / 32);
+    const int w = threadIdx.x >> 5;
+    const long long wa0 = a + w * per, wb0 = (wa0 + per < b) ? wa0 + per : b;
+    D2 t = (wa0 < wb0) ? warp_range_sum(s, c, wa0, wb0) : D2{0.0, 0.0};
+    if ((threadIdx.x & 31) == 0) { wa[w] = t.a; wb[w] = t.b; }
+    __syncthreads();
+    D2 r{0.0, 0.0};
+    for (int k = 0; k < UT / 32; ++k) { r.a += wa[k]; r.b += wb[k]; }
+    __syncthreads();
+    return r;
 }
 
 // U1: warp per chunk.
@@ -257,7 +323,7 @@ __global__ void __launch_bounds__(UT) k_uni_chunks(const K* __restrict__ sorted,
     const int ch = blockIdx.x * (UT / 32) + (threadIdx.x >> 5);
     if (ch >= nch) return;
     const K* s = sorted + (long long)seg * L;
-    const double c = uval(s, L / 2);
+    const auto c = ucenter(s, L);
     long long a = (long long)ch * UC, b = a + UC < L ? a + UC : L;
     D2 t = warp_range_sum(s, c, a, b);
     if ((threadIdx.x & 31) == 0) {
@@ -267,49 +333,55 @@ __global__ void __launch_bounds__(UT) k_uni_chunks(const K* __restrict__ sorted,
     }
 }
 
-// U2: cpre[seg][k] = sum of chunks < k, k = 0..nch (one CTA per segment).
+// U2: cpre[seg][k] = sum of chunks < k, k = 0..nch (one CTA per segment):
+// per-thread runs, then a shuffle scan of the run totals (fixed order).
 __global__ void __launch_bounds__(1024) k_uni_prefix(const double* __restrict__ csum, int nch,
                                                      double* __restrict__ cpre) {
-    __shared__ double pa[1024], pb[1024];
+    __shared__ double wa[32], wb[32];
     const int seg = blockIdx.x;
     const double* c = csum + (size_t)seg * nch * 2;
     double* o = cpre + (size_t)seg * (nch + 1) * 2;
     const int per = (nch + 1023) / 1024;
     const int b0 = threadIdx.x * per, b1 = b0 + per < nch ? b0 + per : nch;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double sa = 0.0, sb = 0.0;
     for (int k = b0; k < b1; ++k) { sa += c[2 * k]; sb += c[2 * k + 1]; }
-    pa[threadIdx.x] = sa;
-    pb[threadIdx.x] = sb;
+    double xa = sa, xb = sb;
+    for (int off = 1; off < 32; off <<= 1) {
+        const double ya = __shfl_up_sync(0xffffffffu, xa, off), yb = __shfl_up_sync(0xffffffffu, xb, off);
+        if (lane >= off) { xa += ya; xb += yb; }
+    }
+    if (lane == 31) { wa[w] = xa; wb[w] = xb; }
     __syncthreads();
-    if (threadIdx.x == 0) {   // fixed order
-        double ra = 0.0, rb = 0.0;
-        for (int t = 0; t < 1024; ++t) {
-            double va = pa[t], vb = pb[t];
-            pa[t] = ra; pb[t] = rb;
-            ra += va; rb += vb;
+    if (w == 0) {
+        double ya = wa[lane], yb = wb[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const double za = __shfl_up_sync(0xffffffffu, ya, off), zb = __shfl_up_sync(0xffffffffu, yb, off);
+            if (lane >= off) { ya += za; yb += zb; }
         }
-        o[2 * nch] = ra;
-        o[2 * nch + 1] = rb;
+        wa[lane] = ya;   // inclusive warp totals
+        wb[lane] = yb;
     }
     __syncthreads();
-    double ra = pa[threadIdx.x], rb = pb[threadIdx.x];
+    double ra = (w ? wa[w - 1] : 0.0) + xa - sa, rb = (w ? wb[w - 1] : 0.0) + xb - sb;
     for (int k = b0; k < b1; ++k) {
         o[2 * k] = ra;
         o[2 * k + 1] = rb;
         ra += c[2 * k];
         rb += c[2 * k + 1];
     }
+    if (threadIdx.x == 1023) { o[2 * nch] = wa[31]; o[2 * nch + 1] = wb[31]; }
 }
 
-// Running sums up to position x (exact FP64): anchor plus a partial chunk.
-template <typename K>
-__device__ inline D2 warp_prefix(const K* s, double c, const double* cpre, long long x) {
+// Running sums up to position x: anchor plus a partial chunk.
+template <typename K, typename C>
+__device__ inline D2 warp_prefix(const K* s, C c, const double* cpre, long long x) {
     long long k = x / UC;
     D2 t = warp_range_sum(s, c, k * UC, x);
     return D2{cpre[2 * k] + t.a, cpre[2 * k + 1] + t.b};
 }
-template <typename K>
-__device__ inline D2 cta_prefix(const K* s, double c, const double* cpre, long long x) {
+template <typename K, typename C>
+__device__ inline D2 cta_prefix(const K* s, C c, const double* cpre, long long x) {
     long long k = x / UC;
     D2 t = cta_range_sum(s, c, k * UC, x);
     return D2{cpre[2 * k] + t.a, cpre[2 * k + 1] + t.b};
@@ -325,7 +397,8 @@ __global__ void __launch_bounds__(UT) k_uni_bound(const K* __restrict__ sorted, 
     const K* s = sorted + (long long)seg * L;
     const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
     const long long h = L / 2 + 1, nwin = L - h + 1;
-    const double hd = (double)h, c = uval(s, L / 2);
+    const double hd = (double)h;
+    const auto c = ucenter(s, L);
     const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
     // aligned core [lo, hi) inside [b - 1, a + h)
     const long long lo = ((b - 1 + UC - 1) / UC) * UC, hi = ((a + h) / UC) * UC;
@@ -362,7 +435,111 @@ __global__ void __launch_bounds__(UT) k_uni_ub(const double* __restrict__ wb, in
     }
 }
 
-// U5: exact windows of the ranges the bound does not exclude.
+// U5: exact windows of the ranges the bound does not exclude.  For the
+// window at j of a range starting at a,
+//   S_k(j) = S_k(a) + sum_{a <= i < j} (d_{i+h}^k - d_i^k),  k = 1, 2,
+// so one exclusive scan over the range gives every window.  32-bit keys:
+// compensated FP32 pairs throughout.
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_from_d(double d) {
+    const float hi = (float)d;
+    return FF{hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ bool ff_less(FF a, FF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+__global__ void __launch_bounds__(UT) k_uni_eval_ff(const uint32_t* __restrict__ sorted, long long L, int nch,
+                                                    int nwr, const double* __restrict__ cpre_all,
+                                                    const double* __restrict__ wb, const double* __restrict__ ub,
+                                                    double* __restrict__ wres) {
+    __shared__ FF sw[UT / 32][2];
+    __shared__ FF sbase[2];
+    __shared__ FF sq[UT / 32], ss[UT / 32];
+    __shared__ long long sj[UT / 32];
+    const int seg = blockIdx.y, r = blockIdx.x;
+    double* o = wres + ((size_t)seg * nwr + r) * 3;
+    const double lb = wb[((size_t)seg * nwr + r) * 2];
+    if (lb > ub[seg] * (1.0 + 1e-12)) {
+        if (threadIdx.x == 0) { o[0] = INFINITY; o[1] = -1.0; o[2] = 0.0; }
+        return;
+    }
+    const uint32_t* s = sorted + (long long)seg * L;
+    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    const float hf = (float)h;                       // exact: h < 2^24
+    const float c = ucenter(s, L);
+    const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {   // sums of the range's first window (a is on the chunk grid)
+        D2 pb = warp_prefix(s, c, cpre, a + h);
+        if (lane == 0) {
+            sbase[0] = ff_from_d(pb.a - cpre[2 * (a / UC)]);
+            sbase[1] = ff_from_d(pb.b - cpre[2 * (a / UC) + 1]);
+        }
+    }
+    const long long j = a + threadIdx.x;
+    FF e1{0.f, 0.f}, e2{0.f, 0.f};
+    if (j < b && j + h < L) {
+        const FF2 A = ff_elem(s[j], c), B = ff_elem(s[j + h], c);
+        e1 = ff_add(B.a, ff_neg(A.a));
+        e2 = ff_add(B.b, ff_neg(A.b));
+    }
+    // inclusive warp scan, then exclusive within the CTA
+    FF x1 = e1, x2 = e2;
+    for (int off = 1; off < 32; off <<= 1) {
+        const FF y1 = ff_shfl_up(x1, off), y2 = ff_shfl_up(x2, off);
+        if (lane >= off) { x1 = ff_add(x1, y1); x2 = ff_add(x2, y2); }
+    }
+    if (lane == 31) { sw[w][0] = x1; sw[w][1] = x2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // exclusive prefix of the 8 warp totals, base folded in (fixed order)
+        FF p1 = sbase[0], p2 = sbase[1];
+        for (int k = 0; k < UT / 32; ++k) {
+            const FF q1 = sw[k][0], q2 = sw[k][1];
+            sw[k][0] = p1;
+            sw[k][1] = p2;
+            p1 = ff_add(p1, q1);
+            p2 = ff_add(p2, q2);
+        }
+    }
+    __syncthreads();
+    // S_k(j) = warp prefix + exclusive lane prefix
+    const FF S1 = ff_add(sw[w][0], ff_add(x1, ff_neg(e1)));
+    const FF S2 = ff_add(sw[w][1], ff_add(x2, ff_neg(e2)));
+    FF q{INFINITY, 0.f}, s1{0.f, 0.f};
+    long long bj = -1;
+    if (j < b) {
+        q = ff_add(ff_mul_f(S2, hf), ff_neg(ff_sq(S1)));
+        s1 = S1;
+        bj = j;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const FF oq = ff_shfl_xor(q, off), os = ff_shfl_xor(s1, off);
+        const long long oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        if (oj >= 0 && (bj < 0 || ff_less(oq, q) || (oq.hi == q.hi && oq.lo == q.lo && oj < bj))) {
+            q = oq; bj = oj; s1 = os;
+        }
+    }
+    if (lane == 0) { sq[w] = q; sj[w] = bj; ss[w] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        FF bq{INFINITY, 0.f}, bs{0.f, 0.f};
+        long long jj = -1;
+        for (int k = 0; k < UT / 32; ++k)
+            if (sj[k] >= 0 && (jj < 0 || ff_less(sq[k], bq) || (sq[k].hi == bq.hi && sq[k].lo == bq.lo && sj[k] < jj))) {
+                bq = sq[k]; jj = sj[k]; bs = ss[k];
+            }
+        o[0] = jj >= 0 ? ff_d(bq) : INFINITY;
+        o[1] = (double)jj;
+        o[2] = ff_d(bs);
+    }
+}
+
 template <typename K>
 __global__ void __launch_bounds__(UT) k_uni_eval(const K* __restrict__ sorted, long long L, int nch, int nwr,
                                                  const double* __restrict__ cpre_all, const double* __restrict__ wb,
@@ -381,7 +558,8 @@ __global__ void __launch_bounds__(UT) k_uni_eval(const K* __restrict__ sorted, l
     const K* s = sorted + (long long)seg * L;
     const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
     const long long h = L / 2 + 1, nwin = L - h + 1;
-    const double hd = (double)h, c = uval(s, L / 2);
+    const double hd = (double)h;
+    const auto c = ucenter(s, L);
     const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w == 0) {
@@ -483,7 +661,8 @@ __global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sor
     const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
     const long long h = L / 2 + 1;
     const double hd = (double)h;
-    const double c = uval(s, L / 2);
+    const auto cc = ucenter(s, L);
+    const double c = (double)cc;
     double best = INFINITY, bs1 = 0.0;
     long long bj = -1;
     for (int r = threadIdx.x; r < nwr; r += UT) {
@@ -522,8 +701,8 @@ __global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sor
         if (threadIdx.x == 0) { o[0] = NAN; o[1] = NAN; o[2] = mu0; o[3] = s20; }
         return;
     }
-    D2 Pa = cta_prefix(s, c, cpre, wlo);
-    D2 Pb = cta_prefix(s, c, cpre, whi);
+    D2 Pa = cta_prefix(s, cc, cpre, wlo);
+    D2 Pb = cta_prefix(s, cc, cpre, whi);
     if (threadIdx.x == 0) {
         double T1 = Pb.a - Pa.a, T2 = Pb.b - Pa.b;
         o[0] = c + T1 / (double)nw;
@@ -553,7 +732,10 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, cpre);
     k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
     k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub);
-    k_uni_eval<K><<<dim3(D.nwr, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
+    if (sizeof(K) == 4)
+        k_uni_eval_ff<<<dim3(D.nwr, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
+    else
+        k_uni_eval<K><<<dim3(D.nwr, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
     k_uni_finish_seg<K><<<nseg, UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wres, P.cs, which_c1, out);
 }
 
