@@ -10,39 +10,58 @@ constexpr int LD = PMAX + 1;   // padded leading dimension of shared matrices
 // In-place Cholesky A = L L^T (lower triangle overwritten by L; the strict
 // upper triangle is zeroed).  Returns false (uniformly) if A is not
 // numerically positive definite.  Right-looking, one barrier per column:
-// step k updates the trailing block from the unscaled column k, and column
-// k - 1 is scaled in step k (no thread reads it any more).
+// step k updates the trailing block from the unscaled column k and scales
+// column k - 1 (no thread reads it any more).  The pivot's reciprocal square
+// root is taken once, by the thread that updates the next diagonal entry,
+// and passed on in shared memory (FP64 square roots are long dependent
+// sequences on this GPU; every thread repeating them would occupy the FP64
+// pipe for the whole factorisation).
 __device__ inline bool cta_cholesky(double* A, int p) {
+    __shared__ double piv[2][2];    // (d_k, 1/d_k) by column parity
+    __shared__ int bad;
     __syncthreads();
-    bool ok = true;
-    double d_prev = 0.0, r_prev = 0.0;
+    if (threadIdx.x == 0) {
+        const double a = A[0];
+        bad = !(a > 0.0) || !isfinite(a);
+        if (!bad) { const double r = rsqrt(a); piv[0][0] = a * r; piv[0][1] = r; }
+    }
+    __syncthreads();
+    if (bad) return false;
+    double dprev = 0.0, rprev = 0.0;   // pivot of column k - 1, kept in registers
     for (int k = 0; k < p; ++k) {
-        const double akk = A[k * LD + k];
-        if (!(akk > 0.0) || !isfinite(akk)) { ok = false; break; }   // same value in every thread
-        const double dk = sqrt(akk), rk = 1.0 / dk, rk2 = rk * rk;
+        // piv[k & 1] was written before the last barrier; piv[(k + 1) & 1] is written below
+        const double dk = piv[k & 1][0], rk = piv[k & 1][1];
         if (k > 0) {
-            for (int i = k + threadIdx.x; i < p; i += blockDim.x) A[i * LD + (k - 1)] *= r_prev;
-            if (threadIdx.x == 0) A[(k - 1) * LD + (k - 1)] = d_prev;
+            for (int i = k + threadIdx.x; i < p; i += blockDim.x) A[i * LD + (k - 1)] *= rprev;
+            if (threadIdx.x == 0) A[(k - 1) * LD + (k - 1)] = dprev;
         }
         const int rem = p - k - 1;
+        const double rk2 = rk * rk;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
             const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-            if (j <= i) A[i * LD + j] -= A[i * LD + k] * A[j * LD + k] * rk2;
+            if (j <= i) {
+                const double v = A[i * LD + j] - A[i * LD + k] * A[j * LD + k] * rk2;
+                A[i * LD + j] = v;
+                if (e == 0) {   // (k+1, k+1): the next pivot
+                    const bool b = !(v > 0.0) || !isfinite(v);
+                    if (b) bad = 1;
+                    else { const double r = rsqrt(v); piv[(k + 1) & 1][0] = v * r; piv[(k + 1) & 1][1] = r; }
+                }
+            }
         }
-        d_prev = dk;
-        r_prev = rk;
+        dprev = dk;
+        rprev = rk;
         __syncthreads();
+        if (bad) return false;
     }
-    if (ok && p > 0) {
-        if (threadIdx.x == 0) A[(p - 1) * LD + (p - 1)] = d_prev;
-    }
+    if (threadIdx.x == 0) A[(p - 1) * LD + (p - 1)] = dprev;
     __syncthreads();
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         if (j > i) A[i * LD + j] = 0.0;
     }
     __syncthreads();
-    return ok;
+    return true;
 }
 
 // Li = L^-1 for lower-triangular L (column-parallel forward substitution

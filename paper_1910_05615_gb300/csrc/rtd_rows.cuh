@@ -113,10 +113,41 @@ struct GramShape {
     static constexpr int FLUSH = 64;
 };
 
+// Running sums that leave the T chunks: FP64 for T = double; for T = float
+// a compensated FP32 pair (TwoSum error terms collected in lo), which keeps
+// the FP64 pipe free.
+template <typename T> struct GramHi;
+template <> struct GramHi<double> {
+    double v[16];
+    __device__ void zero() {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = 0.0;
+    }
+    __device__ void add(const double (&a)[16]) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] += a[e];
+    }
+};
+template <> struct GramHi<float> {
+    float hi[16], lo[16];
+    __device__ void zero() {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { hi[e] = 0.f; lo[e] = 0.f; }
+    }
+    __device__ void add(const float (&a)[16]) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const FF t = ff_two_sum(hi[e], a[e]);
+            hi[e] = t.hi;
+            lo[e] += t.lo;
+        }
+    }
+};
+
 template <int PB, typename T>
 struct GramAcc {
     typedef GramShape<PB, T> S;
-    double a64[16];
+    GramHi<T> big;
     T a32[16];
     int since, bi, bj, g, ng;
     bool on;
@@ -131,13 +162,15 @@ struct GramAcc {
         bi = 0;
         while (b >= S::NB - bi) { b -= S::NB - bi; ++bi; }
         bj = bi + b;
+        big.zero();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) { a64[e] = 0.0; a32[e] = (T)0; }
+        for (int e = 0; e < 16; ++e) a32[e] = (T)0;
         since = 0;
     }
     __device__ void flush() {
+        big.add(a32);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) { a64[e] += (double)a32[e]; a32[e] = (T)0; }
+        for (int e = 0; e < 16; ++e) a32[e] = (T)0;
         since = 0;
     }
     // tile: k rows of PE values, weights wt
@@ -157,19 +190,35 @@ struct GramAcc {
         }
     }
     // Reduce over groups in fixed order and write one slot (NBLK*16 doubles).
+    // red: shared scratch of G*NBLK*16 doubles.
     __device__ void store(double* red, double* slot) {
         flush();
         __syncthreads();
-        if (on) {
-            int blk = threadIdx.x % S::NBLK;
+        if constexpr (sizeof(T) == 8) {
+            if (on) {
+                int blk = threadIdx.x % S::NBLK;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) red[(g * S::NBLK + blk) * 16 + e] = a64[e];
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < S::NBLK * 16; e += NT) {
-            double s = 0.0;
-            for (int gg = 0; gg < ng; ++gg) s += red[gg * S::NBLK * 16 + e];
-            slot[e] = s;
+                for (int e = 0; e < 16; ++e) red[(g * S::NBLK + blk) * 16 + e] = big.v[e];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < S::NBLK * 16; e += NT) {
+                double s = 0.0;
+                for (int gg = 0; gg < ng; ++gg) s += red[gg * S::NBLK * 16 + e];
+                slot[e] = s;
+            }
+        } else {
+            FF* rf = reinterpret_cast<FF*>(red);
+            if (on) {
+                int blk = threadIdx.x % S::NBLK;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) rf[(g * S::NBLK + blk) * 16 + e] = ff_two_sum(big.hi[e], big.lo[e]);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < S::NBLK * 16; e += NT) {
+                FF s{0.f, 0.f};
+                for (int gg = 0; gg < ng; ++gg) s = ff_add(s, rf[gg * S::NBLK * 16 + e]);
+                slot[e] = ff_d(s);
+            }
         }
         __syncthreads();
     }
@@ -633,75 +682,84 @@ void dist_t(const Plan& P, cudaStream_t s) {
 // back to.
 // =====================================================================
 template <int PB> struct DistWin {
-    static constexpr int R = 2;                      // rows per thread
-    static constexpr int NTW = PB <= 24 ? 256 : 128; // threads
-    static constexpr int TR = NTW * R;               // rows per tile
-    static constexpr int STAGES = 2;
+    static constexpr int R = 2;                      // rows per lane
+    static constexpr int NTW = PB <= 40 ? 256 : 128; // threads
+    static constexpr int NW = NTW / 32;              // warps
+    static constexpr int WT = 32 * R;                // rows per warp tile
+    static constexpr int STAGES = 2;                 // tiles in flight per warp
     static constexpr int PH = PB / 2;                // column pairs per row
-    static constexpr size_t TILE = (size_t)TR * PB * sizeof(float);
-    static constexpr size_t SMEM = STAGES * TILE + 2 * (size_t)PB * PB * sizeof(float) +
+    static constexpr size_t WTILE = (size_t)WT * PB * sizeof(float);
+    static constexpr int CTAS_PER_SM = (2 * (NW * STAGES * WTILE + 2 * (size_t)PB * PB * sizeof(float) +
+                                             2 * (size_t)WIN_BINS * sizeof(unsigned)) <= 220 * 1024) ? 2 : 1;
+    static constexpr size_t SMEM = NW * STAGES * WTILE + 2 * (size_t)PB * PB * sizeof(float) +
                                    2 * (size_t)WIN_BINS * sizeof(unsigned);
 };
 
 // d2 of R rows for lower-triangular M stored as column pairs (row stride
-// PB / 2 pairs, zero above the diagonal); b the folded centre.  Column pairs
-// alternate between two accumulators per row to shorten dependence chains.
+// PB / 2 pairs, zero above the diagonal and beyond p); b the folded centre.
+// Two rows of M at a time (they share their column pairs), and column pairs
+// alternating between two accumulators, give 8 independent chains.
 template <int PB, int R>
 __device__ __forceinline__ void tri_d2_pk(const float2* __restrict__ sM, int p, const float2 (&c)[R][PB / 2],
                                           const float* __restrict__ b, float (&d2)[R]) {
 #pragma unroll
     for (int r = 0; r < R; ++r) d2[r] = 0.f;
 #pragma unroll
-    for (int i = 0; i < PB; ++i) {
+    for (int i = 0; i < PB; i += 2) {
         if (i < p) {
-            const int npair = i / 2 + 1;                    // pairs holding columns 0..i
-            const float2 binit = make_float2(-b[i], 0.f);
-            float2 a0[R], a1[R];
+            const int npair = i / 2 + 1;                    // pairs holding columns 0..i+1
+            const float2 bi = make_float2(-b[i], 0.f), bj = make_float2(-b[i + 1], 0.f);
+            float2 a0[R], a1[R], c0[R], c1[R];             // rows i (a) and i + 1 (c)
 #pragma unroll
-            for (int g = 0; 4 * g <= i; ++g) {
-                const float4 mv = *reinterpret_cast<const float4*>(sM + i * (PB / 2) + 2 * g);
-                const float2 m0 = make_float2(mv.x, mv.y);
-                const float2 m1 = make_float2(mv.z, mv.w);
+            for (int g = 0; 2 * g < npair; ++g) {
+                const float4 mi = *reinterpret_cast<const float4*>(sM + i * (PB / 2) + 2 * g);
+                const float4 mj = *reinterpret_cast<const float4*>(sM + (i + 1) * (PB / 2) + 2 * g);
 #pragma unroll
-                for (int r = 0; r < R; ++r) a0[r] = __ffma2_rn(m0, c[r][2 * g], g == 0 ? binit : a0[r]);
+                for (int r = 0; r < R; ++r) {
+                    a0[r] = __ffma2_rn(make_float2(mi.x, mi.y), c[r][2 * g], g == 0 ? bi : a0[r]);
+                    c0[r] = __ffma2_rn(make_float2(mj.x, mj.y), c[r][2 * g], g == 0 ? bj : c0[r]);
+                }
                 if (2 * g + 1 < npair) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        a1[r] = (g == 0) ? __fmul2_rn(m1, c[r][1]) : __ffma2_rn(m1, c[r][2 * g + 1], a1[r]);
+                    for (int r = 0; r < R; ++r) {
+                        const float2 mi1 = make_float2(mi.z, mi.w), mj1 = make_float2(mj.z, mj.w);
+                        a1[r] = (g == 0) ? __fmul2_rn(mi1, c[r][1]) : __ffma2_rn(mi1, c[r][2 * g + 1], a1[r]);
+                        c1[r] = (g == 0) ? __fmul2_rn(mj1, c[r][1]) : __ffma2_rn(mj1, c[r][2 * g + 1], c1[r]);
+                    }
                 }
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float2 a = a0[r];
-                if (npair > 1) a = __fadd2_rn(a, a1[r]);
-                const float y = a.x + a.y;
-                d2[r] = fmaf(y, y, d2[r]);
+                float2 a = a0[r], cc = c0[r];
+                if (npair > 1) { a = __fadd2_rn(a, a1[r]); cc = __fadd2_rn(cc, c1[r]); }
+                const float ya = a.x + a.y, yc = cc.x + cc.y;
+                d2[r] = fmaf(ya, ya, d2[r]);
+                d2[r] = fmaf(yc, yc, d2[r]);
             }
         }
     }
 }
 
 template <int PB>
-__global__ void __launch_bounds__(DistWin<PB>::NTW, 2)
+__global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
     k_dist_win(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
                const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys,
                long long qm, Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st) {
     typedef DistWin<PB> D;
-    constexpr int R = D::R, PH = D::PH, NTW = D::NTW;
+    constexpr int R = D::R, PH = D::PH, NTW = D::NTW, NW = D::NW, WT = D::WT;
     extern __shared__ __align__(128) unsigned char smem[];
-    float* tiles = reinterpret_cast<float*>(smem);
-    float2* sM = reinterpret_cast<float2*>(smem + D::STAGES * D::TILE);   // [2][PB][PH]
-    unsigned* sh = reinterpret_cast<unsigned*>(smem + D::STAGES * D::TILE + 2 * (size_t)PB * PB * sizeof(float));
-    __shared__ __align__(8) uint64_t bar[D::STAGES];
+    float2* sM = reinterpret_cast<float2*>(smem + NW * D::STAGES * D::WTILE);   // [2][PB][PH]
+    unsigned* sh = reinterpret_cast<unsigned*>(smem + NW * D::STAGES * D::WTILE + 2 * (size_t)PB * PB * sizeof(float));
+    __shared__ __align__(8) uint64_t bar[NW][D::STAGES];
     __shared__ float2 s_nu[PH];
     __shared__ float s_b[2][PB];
     __shared__ unsigned s_wlo[2], s_whi[2];
     __shared__ int s_wsh[2], s_on[2], s_below[2], s_fail;
     const int l = blockIdx.y;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int r0, r1;
     block_rows(m, cpb, r0, r1);
-    const int ntiles = (r1 - r0 + D::TR - 1) / D::TR;
+    const int ntiles = (r1 - r0 + WT - 1) / WT;      // warp tiles of the CTA
     if (threadIdx.x < 2) {
         const int c = 2 * l + threadIdx.x;
         s_on[threadIdx.x] = ch[c].active && rule[c].win;
@@ -710,12 +768,12 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, 2)
         s_wsh[threadIdx.x] = rule[c].w_sh;
         s_below[threadIdx.x] = 0;
     }
-    for (int e = threadIdx.x; e < 2 * WIN_BINS; e += NTW) sh[e] = 0u;
-    if (threadIdx.x == 0) {
-        s_fail = 0;
-        for (int s = 0; s < D::STAGES; ++s) mbar_init(&bar[s], 1);
+    if (threadIdx.x == 0) s_fail = 0;
+    if (lane == 0) {
+        for (int s = 0; s < D::STAGES; ++s) mbar_init(&bar[w][s], 1);
         mbar_init_fence();
     }
+    for (int e = threadIdx.x; e < 2 * WIN_BINS; e += NTW) sh[e] = 0u;
     for (int e = threadIdx.x; e < 2 * PB * PH; e += NTW) {
         const int k = e / (PB * PH), i = (e / PH) % PB, h = e % PH;
         const float* Mf = ch[2 * l + k].rp.Mf;
@@ -732,104 +790,106 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, 2)
         s_nu[h] = make_float2(a, b);
     }
     __syncthreads();
-    if ((!s_on[0] && !s_on[1]) || ntiles <= 0) return;   // uniform; nothing issued yet
+    if (!s_on[0] && !s_on[1]) return;   // uniform; nothing issued yet
 
-    auto issue = [&](int t, int s) {
-        const int row0 = r0 + t * D::TR;
-        const int rows = min(D::TR, r1 - row0);
+    // warp w takes the CTA's warp tiles w, w + NW, ...; its k-th tile sits in stage k % STAGES
+    float* wst = reinterpret_cast<float*>(smem) + (size_t)w * D::STAGES * WT * PB;
+    auto issue = [&](int k) {   // lane 0 only
+        const int t = w + k * NW;
+        const int row0 = r0 + t * WT;
+        const int rows = min(WT, r1 - row0);
         const unsigned bytes = (unsigned)rows * PB * (unsigned)sizeof(float);
-        mbar_expect_tx(&bar[s], bytes);
-        bulk_load(tiles + (size_t)s * D::TR * PB, Xp + (size_t)row0 * PB, bytes, &bar[s]);
+        uint64_t* br = &bar[w][k % D::STAGES];
+        mbar_expect_tx(br, bytes);
+        bulk_load(wst + (size_t)(k % D::STAGES) * WT * PB, Xp + (size_t)row0 * PB, bytes, br);
     };
-    if (threadIdx.x == 0)
-        for (int s = 0; s < D::STAGES && s < ntiles; ++s) issue(s, s);
+    const int nmine = (ntiles > w) ? (ntiles - w + NW - 1) / NW : 0;
+    if (lane == 0)
+        for (int k = 0; k < D::STAGES && k < nmine; ++k) issue(k);
+    __syncwarp();
 
     int below0 = 0, below1 = 0;
-    int t = 0;
-    for (; t < ntiles; ++t) {
-        const int s = t % D::STAGES;
-        const int row0 = r0 + t * D::TR;
-        const int rows = min(D::TR, r1 - row0);
-        const bool ok = mbar_wait(&bar[s], (unsigned)(t / D::STAGES) & 1u);
-        if (!ok) s_fail = 1;
-        if (ok) {
-            const float* T = tiles + (size_t)s * D::TR * PB;
-            float2 c[R][PH];
+    bool failed = false;
+    int k = 0;
+    for (; k < nmine; ++k) {
+        const int t = w + k * NW;
+        const int row0 = r0 + t * WT;
+        const int rows = min(WT, r1 - row0);
+        const bool ok = mbar_wait(&bar[w][k % D::STAGES], (unsigned)(k / D::STAGES) & 1u);
+        if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+        const float* T = wst + (size_t)(k % D::STAGES) * WT * PB;
+        float2 c[R][PH];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = r * 32 + lane;
+            if (j < rows) {
+                const float4* src = reinterpret_cast<const float4*>(T + (size_t)j * PB);
+#pragma unroll
+                for (int q4 = 0; q4 < PB / 4; ++q4) {
+                    const float4 v = src[q4];
+                    c[r][2 * q4] = __fadd2_rn(make_float2(v.x, v.y), s_nu[2 * q4]);
+                    c[r][2 * q4 + 1] = __fadd2_rn(make_float2(v.z, v.w), s_nu[2 * q4 + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < PH; ++h) c[r][h] = make_float2(0.f, 0.f);
+            }
+        }
+        __syncwarp();   // the stage is read: lane 0 may refill it
+        if (lane == 0 && k + D::STAGES < nmine) {
+            async_proxy_fence();
+            issue(k + D::STAGES);
+        }
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+            if (!s_on[kc]) continue;
+            float d2[R];
+            tri_d2_pk<PB, R>(sM + kc * PB * PH, p, c, s_b[kc], d2);
+            const int cidx = 2 * l + kc;
+            const unsigned wlo = s_wlo[kc], whi = s_whi[kc];
+            const int wsh = s_wsh[kc];
+            float* out = dkeys + (size_t)kc * qm;
+            int nb = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int j = r * NTW + threadIdx.x;
+                const int j = r * 32 + lane;
+                const int row = row0 + j;
+                const unsigned key = __float_as_uint(d2[r]);
+                bool cnd = false;
                 if (j < rows) {
-                    const float4* src = reinterpret_cast<const float4*>(T + (size_t)j * PB);
-#pragma unroll
-                    for (int q4 = 0; q4 < PB / 4; ++q4) {
-                        const float4 v = src[q4];
-                        c[r][2 * q4] = __fadd2_rn(make_float2(v.x, v.y), s_nu[2 * q4]);
-                        c[r][2 * q4 + 1] = __fadd2_rn(make_float2(v.z, v.w), s_nu[2 * q4 + 1]);
-                    }
-                } else {
-#pragma unroll
-                    for (int h = 0; h < PH; ++h) c[r][h] = make_float2(0.f, 0.f);
+                    const bool in = key < wlo;
+                    cnd = !in && key <= whi;
+                    nb += in ? 1 : 0;
+                    out[row] = d2[r];
+                    if (cnd) atomicAdd(&sh[kc * WIN_BINS + ((key - wlo) >> wsh)], 1u);
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (!s_on[k]) continue;
-                float d2[R];
-                tri_d2_pk<PB, R>(sM + k * PB * PH, p, c, s_b[k], d2);
-                const int cidx = 2 * l + k;
-                const unsigned wlo = s_wlo[k], whi = s_whi[k];
-                const int wsh = s_wsh[k];
-                float* out = dkeys + (size_t)k * qm;
-                int nb = 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int j = r * NTW + threadIdx.x;
-                    const int row = row0 + j;
-                    const unsigned key = __float_as_uint(d2[r]);
-                    bool cnd = false;
-                    if (j < rows) {
-                        const bool in = key < wlo;
-                        cnd = !in && key <= whi;
-                        nb += in ? 1 : 0;
-                        out[row] = d2[r];
-                        if (cnd) atomicAdd(&sh[k * WIN_BINS + ((key - wlo) >> wsh)], 1u);
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, cnd);
-                    if (bal) {
-                        const int lead = __ffs(bal) - 1;
-                        int b0 = 0;
-                        if (lane == lead) b0 = atomicAdd(&rule[cidx].cand, __popc(bal));
-                        b0 = __shfl_sync(0xffffffffu, b0, lead);
-                        if (cnd) {
-                            const int idx = b0 + __popc(bal & ((1u << lane) - 1u));
-                            if (idx < m) {
-                                Cand e;
-                                e.key = key;
-                                e.pos = (unsigned)(row - l * m);
-                                e.pad = 0;
-                                cand[(size_t)cidx * m + idx] = e;
-                            }
+                const unsigned bal = __ballot_sync(0xffffffffu, cnd);
+                if (bal) {
+                    const int lead = __ffs(bal) - 1;
+                    int b0 = 0;
+                    if (lane == lead) b0 = atomicAdd(&rule[cidx].cand, __popc(bal));
+                    b0 = __shfl_sync(0xffffffffu, b0, lead);
+                    if (cnd) {
+                        const int idx = b0 + __popc(bal & ((1u << lane) - 1u));
+                        if (idx < m) {
+                            Cand e;
+                            e.key = key;
+                            e.pos = (unsigned)(row - l * m);
+                            e.pad = 0;
+                            cand[(size_t)cidx * m + idx] = e;
                         }
                     }
                 }
-                if (k == 0) below0 += nb; else below1 += nb;
             }
-        }
-        __syncthreads();                 // stage s read by every thread
-        if (s_fail) break;               // uniform after the barrier
-        if (threadIdx.x == 0 && t + D::STAGES < ntiles) {
-            async_proxy_fence();
-            issue(t + D::STAGES, s);
+            if (kc == 0) below0 += nb; else below1 += nb;
         }
     }
-    if (s_fail) {
-        // let the copies still in flight land before the CTA's shared memory is released
-        if (threadIdx.x == 0) {
-            for (int u = t; u < ntiles && u < t + D::STAGES; ++u)
-                (void)mbar_wait(&bar[u % D::STAGES], (unsigned)(u / D::STAGES) & 1u);
-            set_error(st, RTD_EINTERNAL);
-        }
-        return;
+    if (failed) {
+        // let this warp's copies still in flight land before the CTA's shared memory is released
+        if (lane == 0)
+            for (int u = k; u < nmine && u < k + D::STAGES; ++u)
+                (void)mbar_wait(&bar[w][u % D::STAGES], (unsigned)(u / D::STAGES) & 1u);
+        if (lane == 0) s_fail = 1;
     }
     below0 = warp_sum_int(below0);
     below1 = warp_sum_int(below1);
@@ -838,13 +898,17 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, 2)
         if (below1) atomicAdd(&s_below[1], below1);
     }
     __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
+        return;
+    }
     if (threadIdx.x < 2 && s_on[threadIdx.x] && s_below[threadIdx.x])
         atomicAdd(&rule[2 * l + threadIdx.x].below, s_below[threadIdx.x]);
-    for (int k = 0; k < 2; ++k) {
-        if (!s_on[k]) continue;
-        unsigned* gh = hist + (size_t)(2 * l + k) * HIST_BINS;
+    for (int kc = 0; kc < 2; ++kc) {
+        if (!s_on[kc]) continue;
+        unsigned* gh = hist + (size_t)(2 * l + kc) * HIST_BINS;
         for (int b = threadIdx.x; b < WIN_BINS; b += NTW) {
-            const unsigned v = sh[k * WIN_BINS + b];
+            const unsigned v = sh[kc * WIN_BINS + b];
             if (v) atomicAdd(gh + b, v);
         }
     }
@@ -874,50 +938,48 @@ void dist_win_t(const Plan& P, cudaStream_t s) {
 // are staged in shared memory in FP64.
 // =====================================================================
 constexpr int BAND_CTAS = 16;    // CTAs per chain
-constexpr int BAND_T = 128;      // threads per CTA: one warp per band row, one lane per component
+// One warp per CTA and one band row per lane: an FP64 warp instruction costs
+// the FP64 pipe the same whether 1 or 32 lanes are active, so full warps of
+// rows use it best.
+constexpr int BAND_T = 32;
 
 template <int PB>
 __global__ void __launch_bounds__(BAND_T) k_band64(const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
                                                    Cand* __restrict__ band_all, const float* __restrict__ Xp,
                                                    int m, int p) {
-    constexpr int LDM = PB + 1;                  // padded row stride of M in shared memory
-    __shared__ double sM[PB * LDM];
+    __shared__ double sM[PB * PB];
     __shared__ double smu[PB];
-    __shared__ double scc[BAND_T / 32][PB];
     const int c = blockIdx.x;
     if (!ch[c].active) return;
     const SelRule& R = rule[c];
     if (!(R.fast || R.bandsel)) return;
     const int nb = R.band, l = c / 2;
-    if (nb <= (int)blockIdx.y) return;
+    if (nb <= (int)blockIdx.y * BAND_T) return;
     const RowParams& rp = ch[c].rp;
     for (int e = threadIdx.x; e < PB * PB; e += BAND_T) {
         const int i = e / PB, j = e % PB;
-        sM[i * LDM + j] = (i < p && j <= i) ? rp.M[i * PMAX + j] : 0.0;
+        sM[e] = (i < p && j <= i) ? rp.M[i * PMAX + j] : 0.0;
     }
     for (int j = threadIdx.x; j < PB; j += BAND_T) smu[j] = (j < p) ? rp.mu[j] : 0.0;
     __syncthreads();
     Cand* band = band_all + (size_t)c * m + R.band_off;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    constexpr int NW = BAND_T / 32;
-    // rows dealt round-robin over the chain's CTAs and their warps
-    for (int i = blockIdx.y + gridDim.y * w; i < nb; i += gridDim.y * NW) {
+    for (int i = blockIdx.y * BAND_T + threadIdx.x; i < nb; i += gridDim.y * BAND_T) {
         Cand e = band[i];
-        const float* x = Xp + ((size_t)l * m + e.pos) * PB;
-        for (int j = lane; j < PB; j += 32) scc[w][j] = (double)x[j] - smu[j];
-        __syncwarp();
+        float x[PB];
+        load_row_padded<PB>(Xp + ((size_t)l * m + e.pos) * PB, x);
+        double cc[PB];
+#pragma unroll
+        for (int j = 0; j < PB; ++j) cc[j] = (double)x[j] - smu[j];
         double d2 = 0.0;
-        for (int ii = lane; ii < p; ii += 32) {
+#pragma unroll
+        for (int ii = 0; ii < PB; ++ii) {
             double a = 0.0;
-            for (int jj = 0; jj <= ii; ++jj) a = fma(sM[ii * LDM + jj], scc[w][jj], a);
+#pragma unroll
+            for (int jj = 0; jj <= ii; ++jj) a = fma(sM[ii * PB + jj], cc[jj], a);
             d2 = fma(a, a, d2);
         }
-        d2 = warp_sum_d(d2);
-        __syncwarp();
-        if (lane == 0) {
-            e.key = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bits order as values
-            band[i] = e;
-        }
+        e.key = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bits order as values
+        band[i] = e;
     }
 }
 

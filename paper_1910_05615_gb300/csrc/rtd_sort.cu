@@ -207,42 +207,6 @@ __device__ inline double uval(const K* s, long long i) { return kval(s[i]); }
 
 struct D2 { double a, b; };
 
-// ---- compensated FP32 pairs ("float-float", value hi + lo, about 48
-// significant bits): TwoSum (Knuth), FastTwoSum and TwoProduct through FMA
-// (Dekker).  Sums of 32-bit keys use them instead of FP64, whose rate is a
-// small fraction of the FP32 rate on this GPU; every pair converts exactly
-// to a double.
-struct FF { float hi, lo; };
-__device__ __forceinline__ FF ff_two_sum(float a, float b) {
-    const float s = a + b, bb = s - a;
-    return FF{s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {   // |a| >= |b|
-    const float s = a + b;
-    return FF{s, b - (s - a)};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-    FF s = ff_two_sum(a.hi, b.hi);
-    const FF t = ff_two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = ff_fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
-    return ff_fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ FF ff_sq(FF a) {          // a^2, dropping lo^2
-    const float p = a.hi * a.hi;
-    float e = fmaf(a.hi, a.hi, -p);
-    e = fmaf(2.f * a.hi, a.lo, e);
-    return ff_fast_two_sum(p, e);
-}
-__device__ __forceinline__ double ff_d(FF a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
-    return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
-__device__ __forceinline__ FF ff_shfl_up(FF a, int o) {
-    return FF{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
-}
-
 // Shifted value d = s_i - c and d^2 of one sorted element: exact pair for
 // 32-bit keys (float values), double otherwise.
 struct FF2 { FF a, b; };
