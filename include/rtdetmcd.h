@@ -68,7 +68,12 @@ typedef struct {
     int32_t  reweight_consistency; /* 0: plain covariance of the reweighted set;
                                       1 (default): times 0.975 / F_{chi2_{p+2}}(chi2_{p,0.975});
                                       2: times c(|W|/n) at the kept fraction */
-    int32_t  reserved;
+    int32_t  select_path;          /* FP32 form, C-step selection from the second step on:
+                                      0 (default) rows classified against a threshold window
+                                      predicted from the last steps, histogram path when it misses;
+                                      1 histogram path at every step;
+                                      2 window of the smallest half-width (misses exercise the
+                                      histogram path).  All three select the same h-subset. */
     /* optional per-row output (nullable, device or host, n bytes, original row
        order): bit0 = row is in the final h-subset of its block's chosen start,
        bit1 = row is in the reweighting set W. */

@@ -43,7 +43,7 @@ class _Options(ctypes.Structure):
                 ("q_override", ctypes.c_int32), ("max_csteps", ctypes.c_int32),
                 ("cutoff_q", ctypes.c_double), ("kappa_max", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("reweight_consistency", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
+                ("select_path", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
                 ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p)]
 
 
@@ -185,8 +185,9 @@ def rtdetmcd_status_string(code):
 
 
 def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100,
-                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, d2=True, flags=True,
-                 subset=False, diag=False, profile=False, stream=None, workspace=None, check=True):
+                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, select_path=0, d2=True,
+                 flags=True, subset=False, diag=False, profile=False, stream=None, workspace=None,
+                 check=True):
     """RT-DetMCD fit of the rows of X (float32, row-major) with coverage h.
 
     X on a CUDA device: outputs are CUDA tensors on the same device.  X in
@@ -202,6 +203,7 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     o.precision, o.omega, o.q_override, o.seed = precision, omega, q, seed
     o.max_csteps, o.cutoff_q, o.kappa_max = max_csteps, cutoff_q, kappa_max
     o.reweight_consistency = reweight_consistency
+    o.select_path = select_path
     ws_need = lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o))
     if ws_need == 0:
         raise RtdError(1, "invalid n, p or options")

@@ -69,6 +69,7 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (o.omega < 1 || o.max_csteps < 1 || o.q_override < 0) return RTD_EINVAL;
     if (!(o.cutoff_q > 0.0 && o.cutoff_q < 1.0) || !(o.kappa_max > 1.0)) return RTD_EINVAL;
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
+    if (o.select_path < 0 || o.select_path > 2) return RTD_EINVAL;
     S.n = n; S.h = h; S.ld = ld; S.p = p; S.pb = pad_p(p);
     S.precision = o.precision;
     S.max_steps = o.max_csteps;
@@ -366,7 +367,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
             // FP32 form from the second step on: classification against the
             // predicted window, selection from the window's rows; chains whose
             // window missed take the histogram path below
-            const bool win = S.precision == RTD_FP32 && it > 0;
+            const bool win = S.precision == RTD_FP32 && it > 0 && o.select_path != 1;
             pf.begin(RTD_STAGE_CDIST);
             if (win) launch_dist_win(P, s);
             else launch_dist(P, s);
@@ -374,17 +375,17 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
             pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_ + (win ? 2 * mch : 0));
             pf.begin(RTD_STAGE_CSELECT);
             if (win) {
-                launch_select_win(P, s);
-                launch_hist_keys(P, s);
+                launch_select_win(P, s);   // a chain whose window missed takes the histogram path there
+            } else {
+                launch_select_bucket(P, s);
+                launch_compact(P, s);
+                launch_select_finish(P, s);
             }
-            launch_select_bucket(P, s);
-            launch_compact(P, s);
-            launch_select_finish(P, s);
             if (S.precision == RTD_FP32) {
                 launch_band64(P, s);
                 launch_select_band(P, s);
             }
-            pf.end(3 + (win ? 2 : 0) + (S.precision == RTD_FP32 ? 2 : 0), win ? 0.0 : mch * K_);
+            pf.end((win ? 1 : 3) + (S.precision == RTD_FP32 ? 2 : 0), win ? 0.0 : mch * K_);
             pf.begin(RTD_STAGE_CUPDATE);
             RTD_CUDA(cudaMemsetAsync(&P.st->active, 0, 3 * sizeof(int), s));
             RTD_CUDA(cudaMemsetAsync(&P.st->gram_rows, 0, sizeof(unsigned long long), s));

@@ -37,7 +37,7 @@ struct Status {
 struct Consts {
     int n, p, pb, q, m, hb;
     long long h;
-    int precision, max_steps, rew_mode, pad0;
+    int precision, max_steps, rew_mode, select_path;
     double alpha, c_alpha, c_rew, cutoff_d2, kappa_max;
     double uni_cut2;          // chi2_{1,cutoff_q}
     double c1_n, c1_m;        // univariate raw consistency factors at h~/n, h~/m

@@ -16,7 +16,7 @@ constexpr int LD = PMAX + 1;   // padded leading dimension of shared matrices
 // and passed on in shared memory (FP64 square roots are long dependent
 // sequences on this GPU; every thread repeating them would occupy the FP64
 // pipe for the whole factorisation).
-__device__ inline bool cta_cholesky(double* A, int p) {
+__device__ inline bool cta_cholesky(double* A, int p, double* rdiag = nullptr) {
     __shared__ double piv[2][2];    // (d_k, 1/d_k) by column parity
     __shared__ int bad;
     __syncthreads();
@@ -49,6 +49,7 @@ __device__ inline bool cta_cholesky(double* A, int p) {
                 }
             }
         }
+        if (rdiag && threadIdx.x == 0) rdiag[k] = rk;
         dprev = dk;
         rprev = rk;
         __syncthreads();
@@ -66,10 +67,14 @@ __device__ inline bool cta_cholesky(double* A, int p) {
 
 // Li = L^-1 for lower-triangular L (column-parallel forward substitution
 // with the reciprocal diagonal).
-__device__ inline void cta_tri_inverse(const double* L, double* Li, int p) {
-    __shared__ double rd[PMAX];
-    for (int j = threadIdx.x; j < p; j += blockDim.x) rd[j] = 1.0 / L[j * LD + j];
-    __syncthreads();
+__device__ inline void cta_tri_inverse(const double* L, double* Li, int p, const double* rdiag = nullptr) {
+    __shared__ double rdl[PMAX];
+    const double* rd = rdiag;
+    if (!rd) {
+        for (int j = threadIdx.x; j < p; j += blockDim.x) rdl[j] = 1.0 / L[j * LD + j];
+        __syncthreads();
+        rd = rdl;
+    }
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         for (int i = 0; i < j; ++i) Li[i * LD + j] = 0.0;
         Li[j * LD + j] = rd[j];
@@ -127,27 +132,43 @@ __device__ inline double cta_max(double v) {
     return r;
 }
 
-// kappa_1 = ||S||_1 ||S^-1||_1 with S^-1 = Li^T Li (Section 3.4; exact).
-// W is a p x p shared scratch matrix.
-__device__ inline double cta_kappa1(const double* S, const double* Li, double* W, int p) {
+// kappa_1 = ||S||_1 ||S^-1||_1 with S^-1 = Li^T Li (Section 3.4), from the
+// FP64 factors but summed in FP32: the monitor only compares kappa_1 with
+// kappa_max, and FP32 keeps the dependent sums off the (slow) FP64 pipe.
+// W is a p x p shared scratch matrix (as floats).
+__device__ inline float cta_max_f(float v) {
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    float r = 0.f;
+    for (int k = 0; k < nw; ++k) r = fmaxf(r, red[k]);
+    __syncthreads();
+    return r;
+}
+__device__ inline double cta_kappa1(const double* S, const double* Li, double* Wd, int p) {
+    float* W = reinterpret_cast<float*>(Wd);
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         int k0 = i > j ? i : j;
-        double v = 0.0;
-        for (int k = k0; k < p; ++k) v += Li[k * LD + i] * Li[k * LD + j];
+        float v = 0.f;
+        for (int k = k0; k < p; ++k) v = fmaf((float)Li[k * LD + i], (float)Li[k * LD + j], v);
         W[i * LD + j] = v;
     }
     __syncthreads();
-    double n1 = 0.0, n1i = 0.0;
+    float n1 = 0.f, n1i = 0.f;
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        double cs = 0.0, csi = 0.0;
-        for (int i = 0; i < p; ++i) { cs += fabs(S[i * LD + j]); csi += fabs(W[i * LD + j]); }
-        n1 = fmax(n1, cs);
-        n1i = fmax(n1i, csi);
+        float cs = 0.f, csi = 0.f;
+        for (int i = 0; i < p; ++i) { cs += fabsf((float)S[i * LD + j]); csi += fabsf(W[i * LD + j]); }
+        n1 = fmaxf(n1, cs);
+        n1i = fmaxf(n1i, csi);
     }
-    n1 = cta_max(n1);
-    n1i = cta_max(n1i);
-    return n1 * n1i;
+    n1 = cta_max_f(n1);
+    n1i = cta_max_f(n1i);
+    return (double)n1 * (double)n1i;
 }
 
 // Symmetric eigen-decomposition by cyclic Jacobi rotations in the
@@ -188,12 +209,34 @@ __device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, doub
                 if (j < p) {
                     double aij = A[i * LD + j];
                     if (aij != 0.0) {
-                        double th = (A[j * LD + j] - A[i * LD + i]) / (2.0 * aij);
-                        double t;
-                        if (fabs(th) > 1e150) t = 0.5 / th;
-                        else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        s = t * c;
+                        // t = tan(theta) solves t^2 + 2 tau t - 1 = 0, tau = (a_jj - a_ii) / (2 a_ij),
+                        // smaller root: t = sgn(d) 2 a_ij / (|d| + sqrt(d^2 + 4 a_ij^2)), d = a_jj - a_ii.
+                        // The angle is taken in FP32 (FP64 square roots and divisions are
+                        // long on this GPU); (c, s) is then normalised in FP64 by two
+                        // first-order steps, so the rotation is orthogonal to FP64 precision
+                        // and whatever the FP32 angle leaves of a_ij goes in the next sweep.
+                        const double d = A[j * LD + j] - A[i * LD + i];
+                        const float df = (float)d, cf = (float)aij;
+                        const float q = sqrtf(fmaf(df, df, 4.f * cf * cf));
+                        float tf = 2.f * cf / (fabsf(df) + q);
+                        if (df < 0.f) tf = -tf;
+                        if (isfinite(tf) && q > 0.f) {
+                            const float cr = rsqrtf(fmaf(tf, tf, 1.f));
+                            c = (double)cr;
+                            s = (double)(tf * cr);
+                            for (int it = 0; it < 2; ++it) {   // c^2 + s^2 - 1: 1e-7 -> 1e-14 -> rounding
+                                const double f = fma(-0.5, fma(c, c, s * s), 1.5);
+                                c *= f;
+                                s *= f;
+                            }
+                        } else {   // out of FP32 range: FP64 formula
+                            double th = d / (2.0 * aij);
+                            double t;
+                            if (fabs(th) > 1e150) t = 0.5 / th;
+                            else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                            c = 1.0 / sqrt(t * t + 1.0);
+                            s = t * c;
+                        }
                     }
                 }
                 rc[k] = c; rs[k] = s; ri[k] = i; rj[k] = (j < p) ? j : -1;
@@ -224,13 +267,11 @@ __device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, doub
                 A[j * LD + r] = s * a + c * b;
             }
             __syncthreads();
-            // exact zero of the annihilated pair, symmetric copy
+            // the rotated pair keeps what the FP32 angle left of it (removed by
+            // the next sweep); its two copies are made equal
             if (threadIdx.x < half) {
                 int k = threadIdx.x;
-                if (rj[k] >= 0 && rs[k] != 0.0) {
-                    A[ri[k] * LD + rj[k]] = 0.0;
-                    A[rj[k] * LD + ri[k]] = 0.0;
-                }
+                if (rj[k] >= 0 && rs[k] != 0.0) A[rj[k] * LD + ri[k]] = A[ri[k] * LD + rj[k]];
             }
             __syncthreads();
         }

@@ -967,17 +967,25 @@ __global__ void __launch_bounds__(BAND_T) k_band64(const Chain* __restrict__ ch,
         Cand e = band[i];
         float x[PB];
         load_row_padded<PB>(Xp + ((size_t)l * m + e.pos) * PB, x);
-        double cc[PB];
+        // y = M (x - mu) column by column: every FMA of a column step feeds a
+        // different accumulator, so the FP64 latency is overlapped
+        double y[PB];
 #pragma unroll
-        for (int j = 0; j < PB; ++j) cc[j] = (double)x[j] - smu[j];
-        double d2 = 0.0;
+        for (int ii = 0; ii < PB; ++ii) y[ii] = 0.0;
 #pragma unroll
-        for (int ii = 0; ii < PB; ++ii) {
-            double a = 0.0;
+        for (int jj = 0; jj < PB; ++jj) {
+            const double cj = (double)x[jj] - smu[jj];
 #pragma unroll
-            for (int jj = 0; jj <= ii; ++jj) a = fma(sM[ii * PB + jj], cc[jj], a);
-            d2 = fma(a, a, d2);
+            for (int ii = jj; ii < PB; ++ii) y[ii] = fma(sM[ii * PB + jj], cj, y[ii]);
         }
+        // d2 = sum of y^2 as a pairwise tree
+#pragma unroll
+        for (int ii = 0; ii < PB; ++ii) y[ii] *= y[ii];
+#pragma unroll
+        for (int w2 = 1; w2 < PB; w2 <<= 1)
+#pragma unroll
+            for (int ii = 0; ii + w2 < PB; ii += 2 * w2) y[ii] += y[ii + w2];
+        const double d2 = y[0];
         e.key = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bits order as values
         band[i] = e;
     }
@@ -1038,12 +1046,12 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
     const int l = blockIdx.y;
     int r0, r1;
     block_rows(m, cpb, r0, r1);
-    for (int k = 0; k < 2; ++k) {
+    {   // one start per CTA (blockIdx.z)
+        const int k = blockIdx.z;
         const int c = 2 * l + k;
-        if (!ch[c].active) continue;     // uniform over the CTA
+        if (!ch[c].active) return;       // uniform over the CTA
         const int full = ch[c].full;
         const SelRule R = rule[c];
-        __syncthreads();
         for (int j = threadIdx.x; j < PB; j += NT) {
             if (j < p) {
                 if (fp32) { s_hi[j] = (T)ch[c].rp.ref_hi[j]; s_lo[j] = (T)ch[c].rp.ref_lo[j]; }
@@ -1122,7 +1130,7 @@ void memb_t(const Plan& P, cudaStream_t s) {
     size_t sm = memb_smem_bytes<PB, T>();
     auto k = k_memb<PB, T>;
     set_smem(k, sm);
-    dim3 grid(P.cpb, P.q);
+    dim3 grid(P.cpb, P.q, 2);
     k<<<grid, NT, sm, s>>>(P.Xp, (const T*)P.dkeys, P.p, P.m, P.cpb, (long long)P.q * P.m,
                            P.precision == RTD_FP32, P.ch, P.rule, P.memb, P.swaps, P.partial,
                            P.slot_doubles);

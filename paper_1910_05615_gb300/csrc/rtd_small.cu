@@ -65,10 +65,11 @@ struct SetupScalars {
 };
 
 __global__ void k_setup(Consts* cs, long long n, int p, int pb, int q, int m, int hb, long long h,
-                        int precision, int max_steps, int rew_mode, SetupScalars sc) {
+                        int precision, int max_steps, int rew_mode, int select_path, SetupScalars sc) {
     if (threadIdx.x != 0) return;
     cs->n = (int)n; cs->p = p; cs->pb = pb; cs->q = q; cs->m = m; cs->hb = hb; cs->h = h;
     cs->precision = precision; cs->max_steps = max_steps; cs->rew_mode = rew_mode;
+    cs->select_path = select_path;
     cs->alpha = sc.alpha;
     cs->c_alpha = sc.c_alpha;
     cs->cutoff_d2 = sc.cutoff_d2;
@@ -96,7 +97,7 @@ void launch_setup(const Plan& P, const rtd_options& o, cudaStream_t s) {
     sc.c1_n = consistency((double)(P.n / 2 + 1) / (double)P.n, 1);
     sc.c1_m = consistency((double)(P.m / 2 + 1) / (double)P.m, 1);
     k_setup<<<1, 32, 0, s>>>(P.cs, P.n, P.p, P.pb, P.q, P.m, P.hb, P.h, P.precision, P.max_steps,
-                             o.reweight_consistency, sc);
+                             o.reweight_consistency, o.select_path, sc);
 }
 
 __global__ void k_uni_finish(Consts* cs, const double* __restrict__ uni, int p, Status* st) {
@@ -300,16 +301,23 @@ void launch_refine_end(const Plan& P, cudaStream_t s) {
 __device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __restrict__ S_z,
                                const double* __restrict__ mu_uni, const double* __restrict__ s_uni,
                                int p, double* A, double* Li, RowParams& rp, double* logdet) {
-    __shared__ double inv_s[PMAX], dm[PMAX];
+    __shared__ double inv_s[PMAX], dm[PMAX], rdg[PMAX];
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         A[i * LD + j] = S_z[i * PMAX + j];
     }
     for (int j = threadIdx.x; j < p; j += blockDim.x) inv_s[j] = 1.0 / s_uni[j];
-    if (!cta_cholesky(A, p)) return false;
-    cta_tri_inverse(A, Li, p);
+    if (!cta_cholesky(A, p, rdg)) return false;
+    // log det = 2 sum log L_jj, taken by the last warp while the others invert L
     double ld = 0.0;
-    for (int j = threadIdx.x; j < p; j += blockDim.x) ld += log(A[j * LD + j]);
+    const int lw = (int)(blockDim.x >> 5) - 1;
+    if (lw > 0) {
+        if ((int)(threadIdx.x >> 5) == lw)
+            for (int j = threadIdx.x & 31; j < p; j += 32) ld += log(A[j * LD + j]);
+    } else {
+        for (int j = threadIdx.x; j < p; j += blockDim.x) ld += log(A[j * LD + j]);
+    }
+    cta_tri_inverse(A, Li, p, rdg);
     ld = 2.0 * cta_sum(ld);
     *logdet = ld;
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -341,16 +349,20 @@ __device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __
 // FP32 form: the window of keys the distance pass classifies against,
 // predicted from the chain's last two thresholds (none before the first
 // selection: the histogram path runs).
-__device__ inline void set_window(SelRule& R, int fp32) {
+__device__ inline void set_window(SelRule& R, int fp32, int path) {
     R.below = 0; R.cand = 0; R.band = 0; R.nlo = 0;
     R.fast = 0; R.need_hist = 0; R.bandsel = 0; R.band_off = 0;
     R.win = 0;
-    if (!fp32 || !R.have_t || !(R.t_prev >= 0.f) || !isfinite(R.t_prev)) return;
-    // half-width: twice the last relative change, within [4 eps, 1/2]; the
-    // first window (one threshold known) takes 1/2
-    float t = R.t_prev, d = 0.5f;
+    if (!fp32 || path == 1 || !R.have_t || !(R.t_prev >= 0.f) || !isfinite(R.t_prev)) return;
+    // centre: the last threshold.  Half-width: twice the last relative
+    // change, within [4 eps, 1/2]; 1/2 for the first window (one threshold
+    // known), whose step moves from the refined start to the first h-subset
+    // scatter and shifts the threshold by tens of percent.
+    const float t = R.t_prev;
+    float d = 0.5f;
     if (R.t_prev2 > 0.f && t > 0.f) d = 2.f * fabsf(t - R.t_prev2) / t;
     d = fminf(fmaxf(d, 4.f * (float)BAND_EPS), 0.5f);
+    if (path == 2) d = 4.f * (float)BAND_EPS;
     R.w_lo = __float_as_uint(t * (1.f - d));
     R.w_hi = __float_as_uint(t * (1.f + d));
     int sh = 0;
@@ -379,7 +391,7 @@ __device__ bool chain_prep(Chain& C, SelRule& R, const Consts* __restrict__ cs, 
     }
     if (threadIdx.x == 0) {
         *swap_slot = 0;
-        set_window(R, cs->precision == RTD_FP32);
+        set_window(R, cs->precision == RTD_FP32, cs->select_path);
     }
     __syncthreads();
     bool ok = make_rowparams(C.mu, C.Sigma, cs->mu_uni, cs->s_uni, p, A, Li, C.rp, &s_ld);

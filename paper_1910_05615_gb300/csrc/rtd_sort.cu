@@ -1010,35 +1010,25 @@ __device__ Cand cta_select_rank(const Cand* list, int C, int r, int key_bits, Ca
     return res;
 }
 
-__global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
-                                                          const Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
-                                                          int m, int hb, int fp32, Status* st) {
-    __shared__ Cand buf[SEL_SMALL];
+// FP32 form, histogram path: threshold t = the r-th smallest candidate; the
+// band rows [t (1 - eps), t (1 + eps)] go to the chain's band list (their
+// FP64 distances: k_band64; their ranking: k_select_band).  `below` rows
+// lie under the candidate range.
+__device__ void hist_path_band(SelRule& R, const Cand* cand, int C, int below, int hb, Cand* band_all_c,
+                               Cand* buf, Status* st) {
     __shared__ int s_nlo, s_nb;
-    const int c = blockIdx.x;
-    if (!ch[c].active || rule[c].fast) return;
-    SelRule& R = rule[c];
-    const int C = R.cand < m ? R.cand : m;
-    const int r = hb - R.below;
+    const int r = hb - below;
     if (r < 1 || r > C) {
         if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
         return;
     }
-    const Cand* cand = cand_all + (size_t)c * m;
-    Cand t = cta_select_rank(cand, C, r, fp32 ? 32 : 64, buf, st);
+    Cand t = cta_select_rank(cand, C, r, 32, buf, st);
     if (t.pad) return;     // error already recorded
-    if (!fp32) {
-        if (threadIdx.x == 0) { R.t_key = t.key; R.t_pos = t.pos; }
-        return;
-    }
-    // FP32 form: rows inside [t (1 - eps), t (1 + eps)] are decided in FP64
-    // (band distances: k_band64; their ranking: k_select_band)
     const float tf = __uint_as_float((unsigned)t.key);
     const unsigned long long t_lo = __float_as_uint(tf * (float)(1.0 - BAND_EPS));
     const unsigned long long t_hi = __float_as_uint(tf * (float)(1.0 + BAND_EPS));
     if (threadIdx.x == 0) { s_nlo = 0; s_nb = 0; }
     __syncthreads();
-    Cand* band = band_all + (size_t)c * m;
     int nlo = 0;
     const int lane = threadIdx.x & 31;
     for (int base = 0; base < C; base += blockDim.x) {
@@ -1054,7 +1044,7 @@ __global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict
         int wb = 0;
         if (lane == 0 && bal) wb = atomicAdd(&s_nb, __popc(bal));
         wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (inb) band[wb + __popc(bal & ((1u << lane) - 1u))] = e;
+        if (inb) band_all_c[wb + __popc(bal & ((1u << lane) - 1u))] = e;
     }
     nlo = warp_sum_int(nlo);
     if (lane == 0 && nlo) atomicAdd(&s_nlo, nlo);
@@ -1063,13 +1053,118 @@ __global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict
         R.t_lo = t_lo;
         R.t_hi = t_hi;
         R.band = s_nb;
-        R.nlo = R.below + s_nlo;
+        R.nlo = below + s_nlo;
         R.band_off = 0;
         R.bandsel = 1;
         R.t_prev2 = R.have_t ? R.t_prev : 0.f;
         R.t_prev = tf;
         R.have_t = 1;
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SEL_T) k_select_finish(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
+                                                          const Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
+                                                          int m, int hb, int fp32, Status* st) {
+    __shared__ Cand buf[SEL_SMALL];
+    const int c = blockIdx.x;
+    if (!ch[c].active || rule[c].fast) return;
+    SelRule& R = rule[c];
+    const int C = R.cand < m ? R.cand : m;
+    const Cand* cand = cand_all + (size_t)c * m;
+    if (fp32) {
+        hist_path_band(R, cand, C, R.below, hb, band_all + (size_t)c * m, buf, st);
+        return;
+    }
+    const int r = hb - R.below;
+    if (r < 1 || r > C) {
+        if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
+        return;
+    }
+    Cand t = cta_select_rank(cand, C, r, 64, buf, st);
+    if (t.pad) return;     // error already recorded
+    if (threadIdx.x == 0) { R.t_key = t.key; R.t_pos = t.pos; }
+}
+
+// The histogram path run by one CTA over one chain's FP32 keys (a window
+// that missed): top-digit histogram, bucket of rank h_b, compaction of the
+// bucket widened by the band, then the band as above.
+__device__ void cta_hist_path(SelRule& R, const float* keys, int m, int hb, Cand* cand, Cand* band_all_c,
+                              Cand* buf, unsigned* h, Status* st) {
+    __shared__ int s_bin, s_below, s_cand;
+    __shared__ unsigned wt[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = threadIdx.x; b < HIST_BINS; b += blockDim.x) h[b] = 0u;
+    if (threadIdx.x == 0) { s_bin = -1; s_below = 0; s_cand = 0; }
+    __syncthreads();
+    for (int base = 0; base < m; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const bool v = i < m;
+        const float d = v ? keys[i] : 0.f;
+        const unsigned bin = coarse_key(d) >> (32 - HIST_BITS);
+        const unsigned tag = v ? bin : (0x80000000u | lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, tag);
+        if (v && (__ffs(peers) - 1) == lane) atomicAdd(h + bin, (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    // bin of rank hb: per-thread runs of HIST_BINS / blockDim bins, then a scan of the run totals
+    const int per = HIST_BINS / blockDim.x;
+    unsigned run = 0;
+    for (int k = 0; k < per; ++k) run += h[threadIdx.x * per + k];
+    unsigned x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    unsigned off = 0;
+    for (int k = 0; k < w; ++k) off += wt[k];
+    unsigned cum = off + x - run;
+    for (int k = 0; k < per; ++k) {
+        const unsigned v = h[threadIdx.x * per + k];
+        if (cum < (unsigned)hb && (unsigned)hb <= cum + v) s_bin = threadIdx.x * per + k;
+        cum += v;
+    }
+    (void)nw;
+    __syncthreads();
+    const int b = s_bin;
+    if (b < 0) {
+        if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
+        return;
+    }
+    const unsigned lo_bits = (unsigned)b << (32 - HIST_BITS);
+    const unsigned hi_bits = lo_bits | ((1u << (32 - HIST_BITS)) - 1u);
+    const unsigned lo = __float_as_uint(__uint_as_float(lo_bits) * (float)(1.0 - BAND_EPS));
+    const unsigned hi = __float_as_uint(__uint_as_float(hi_bits) * (float)(1.0 + BAND_EPS));
+    int below = 0;
+    for (int base = 0; base < m; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const bool v = i < m;
+        const float d = v ? keys[i] : 0.f;
+        const unsigned ck = coarse_key(d);
+        below += (v && ck < lo) ? 1 : 0;
+        const bool take = v && ck >= lo && ck <= hi;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (bal) {
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&s_cand, __popc(bal));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (take) {
+                Cand e;
+                e.key = (unsigned long long)__float_as_uint(d);
+                e.pos = (unsigned)i;
+                e.pad = 0;
+                cand[b0 + __popc(bal & ((1u << lane) - 1u))] = e;
+            }
+        }
+    }
+    below = warp_sum_int(below);
+    if (lane == 0 && below) atomicAdd(&s_below, below);
+    __syncthreads();
+    const int C = s_cand < m ? s_cand : m;
+    if (threadIdx.x == 0) { R.cand = C; R.below = s_below; R.lo = lo; R.hi = hi; R.acc_miss += 1; }
+    hist_path_band(R, cand, C, s_below, hb, band_all_c, buf, st);
 }
 
 void launch_select_finish(const Plan& P, cudaStream_t s) {
@@ -1090,20 +1185,37 @@ void launch_select_finish(const Plan& P, cudaStream_t s) {
 // rank or band falls outside the window is marked need_hist and left to the
 // histogram path.
 // =====================================================================
+__device__ void select_win_body(SelRule& R, Cand* cand, Cand* band_all_c, unsigned* h, int m, int hb,
+                                Cand* buf, unsigned* cnt, Status* st);
+
 __global__ void __launch_bounds__(SEL_T) k_select_win(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
-                                                       const Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
-                                                       unsigned* __restrict__ hist, int m, int hb, Status* st) {
+                                                       Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
+                                                       unsigned* __restrict__ hist, const float* __restrict__ dkeys,
+                                                       long long qm, int m, int hb, Status* st) {
     static_assert(WIN_BINS == SEL_T, "one window bin per thread");
     __shared__ Cand buf[SEL_SMALL];
-    __shared__ unsigned cnt[WIN_BINS];
-    __shared__ int s_bin, s_ns, s_nslo, s_nb, s_nlo;
+    static_assert(SEL_SMALL * sizeof(Cand) >= HIST_BINS * sizeof(unsigned), "histogram aliases buf");
+    // the bin counts are dead before the ranking reuses buf
+    unsigned* cnt = reinterpret_cast<unsigned*>(buf);
     const int c = blockIdx.x;
     if (!ch[c].active) return;
     SelRule& R = rule[c];
     if (!R.win) return;
+    select_win_body(R, cand_all + (size_t)c * m, band_all + (size_t)c * m, hist + (size_t)c * HIST_BINS, m, hb,
+                    buf, cnt, st);
+    __syncthreads();
+    if (R.need_hist) {   // the window missed: the histogram path, in this CTA
+        const int l = c / 2, k = c % 2;
+        cta_hist_path(R, dkeys + (size_t)k * qm + (size_t)l * m, m, hb, cand_all + (size_t)c * m,
+                      band_all + (size_t)c * m, buf, cnt, st);
+    }
+}
+
+__device__ void select_win_body(SelRule& R, Cand* cand_w, Cand* band_all_c, unsigned* h, int m, int hb,
+                                Cand* buf, unsigned* cnt, Status* st) {
+    __shared__ int s_bin, s_ns, s_nslo, s_nb, s_nlo;
     const int lane = threadIdx.x & 31;
     // window histogram: inclusive scan, bins reset for the next use
-    unsigned* h = hist + (size_t)c * HIST_BINS;
     const unsigned own = h[threadIdx.x];
     h[threadIdx.x] = 0u;
     cnt[threadIdx.x] = own;
@@ -1139,8 +1251,8 @@ __global__ void __launch_bounds__(SEL_T) k_select_win(const Chain* __restrict__ 
     const unsigned long long kb_lo = __float_as_uint(__uint_as_float(lo_key) * (float)(1.0 - BAND_EPS));
     const unsigned long long kb_hi = __float_as_uint(__uint_as_float(hi_key) * (float)(1.0 + BAND_EPS));
     // candidates inside [kb_lo, kb_hi] -> lower half of the band buffer
-    const Cand* cand = cand_all + (size_t)c * m;
-    Cand* sub = band_all + (size_t)c * m;
+    const Cand* cand = cand_w;
+    Cand* sub = band_all_c;
     const int cap = m / 2;
     int nlo = 0;
     for (int base = 0; base < C; base += blockDim.x) {
@@ -1179,7 +1291,7 @@ __global__ void __launch_bounds__(SEL_T) k_select_win(const Chain* __restrict__ 
         return;
     }
     // band rows -> upper half; rows of the range below the band
-    Cand* band = band_all + (size_t)c * m + cap;
+    Cand* band = band_all_c + cap;
     int blo = 0;
     for (int base = 0; base < ns; base += blockDim.x) {
         const int i = base + threadIdx.x;
@@ -1214,7 +1326,9 @@ __global__ void __launch_bounds__(SEL_T) k_select_win(const Chain* __restrict__ 
 // Band ranking of the FP32 form (both paths): the band rows whose FP64
 // (d2, position) is at most that of rank h_b - (rows below the band) get the
 // decision bit (bit 1) the membership pass reads.
-__global__ void __launch_bounds__(SEL_T) k_select_band(const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
+constexpr int BANDSEL_T = 256;   // band lists are short: fewer threads, cheaper barriers
+
+__global__ void __launch_bounds__(BANDSEL_T) k_select_band(const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
                                                         const Cand* __restrict__ band_all,
                                                         uint8_t* __restrict__ memb_all, int m, int hb, Status* st) {
     __shared__ Cand buf[SEL_SMALL];
@@ -1229,10 +1343,24 @@ __global__ void __launch_bounds__(SEL_T) k_select_band(const Chain* __restrict__
         return;
     }
     const Cand* band = band_all + (size_t)c * m + R.band_off;
+    uint8_t* mb = memb_all + (size_t)c * m;
+    if (nb <= 2 * BANDSEL_T) {
+        // short band: each row counts the rows ordered before it and takes
+        // its own decision (rank < r2), no sort
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) buf[i] = band[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const u128 v = comp(buf[i]);
+            int rank = 0;
+            for (int j = 0; j < nb; ++j) rank += comp(buf[j]) < v ? 1 : 0;
+            const unsigned pos = buf[i].pos;
+            mb[pos] = (uint8_t)((mb[pos] & 1) | (rank < r2 ? 2 : 0));
+        }
+        return;
+    }
     Cand tb = cta_select_rank(band, nb, r2, 64, buf, st);
     if (tb.pad) return;
     const u128 tv = comp(tb);
-    uint8_t* mb = memb_all + (size_t)c * m;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const Cand e = band[i];
         mb[e.pos] = (uint8_t)((mb[e.pos] & 1) | (comp(e) <= tv ? 2 : 0));
@@ -1240,10 +1368,11 @@ __global__ void __launch_bounds__(SEL_T) k_select_band(const Chain* __restrict__
 }
 
 void launch_select_win(const Plan& P, cudaStream_t s) {
-    k_select_win<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.hist, P.m, P.hb, P.st);
+    k_select_win<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.hist, (const float*)P.dkeys,
+                                           (long long)P.q * P.m, P.m, P.hb, P.st);
 }
 void launch_select_band(const Plan& P, cudaStream_t s) {
-    k_select_band<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.band, P.memb, P.m, P.hb, P.st);
+    k_select_band<<<2 * P.q, BANDSEL_T, 0, s>>>(P.ch, P.rule, P.band, P.memb, P.m, P.hb, P.st);
 }
 
 }  // namespace rtd

@@ -202,3 +202,33 @@ def test_fit_deterministic(rtd):
     b = rtd.rtdetmcd_fit(X, fr.h, subset=True)
     assert np.array_equal(a["mu"], b["mu"]) and np.array_equal(a["Sigma"], b["Sigma"])
     assert torch.equal(a["flags"], b["flags"]) and torch.equal(a["subset"], b["subset"])
+
+
+# ------------------------------------------- selection paths of the C-step
+@pytest.mark.parametrize("case", ["main", "point"])
+def test_select_paths_agree(rtd, main_case, case):
+    """The FP32 form's window selection (default), the histogram path at every
+    step, and windows of the smallest width (whose misses fall back to the
+    histogram path) all take the FP64-exact h_b smallest at every step, so
+    they give the same subsets and bitwise the same fits."""
+    if case == "main":
+        fr = main_case[0]
+    else:
+        fr = datagen.contaminated_gaussian(120_000, 5, eps=0.1, kind="point", shift=10.0, seed=3)
+    X = torch.from_numpy(fr.X).cuda()
+    res = {sp: rtd.rtdetmcd_fit(X, fr.h, select_path=sp, subset=True, profile=True) for sp in (0, 1, 2)}
+    for sp in (1, 2):
+        assert torch.equal(res[sp]["subset"], res[0]["subset"]), sp
+        assert np.array_equal(res[sp]["mu"], res[0]["mu"]) and np.array_equal(res[sp]["Sigma"], res[0]["Sigma"])
+        assert np.array_equal(res[sp]["mu_raw"], res[0]["mu_raw"])
+        assert torch.equal(res[sp]["flags"], res[0]["flags"])
+    p0, p1, p2 = (res[sp]["profile"] for sp in (0, 1, 2))
+    assert p0["win_steps"] > 0 and p1["win_steps"] == 0
+    assert p2["win_steps"] > 0
+    assert p0["sel_band"] > 0
+
+
+def test_select_path_rejects_bad_value(rtd):
+    fr = datagen.small_fp64_case()
+    with pytest.raises(rtd.RtdError):
+        rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, select_path=3)
