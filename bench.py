@@ -35,9 +35,10 @@ CPU_SAMPLE_ROWS = 250_000
 REF_SAMPLE_ROWS = 200_000
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_dist launch at n=1e6,
-# p=20 with both chains of every block active (80.14 MB + 2.74 MB)
-K_DIST_TRAFFIC = 82.88e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_dist_win launch at
+# n=1e6, p=20 with both chains of every block active (None until captured on
+# the current kernel)
+K_DIST_TRAFFIC = None
 
 
 def selection_stats(pp):
@@ -314,12 +315,12 @@ def main():
     # kernel changed after its capture); the summaries live under profiles/
     roof["traffic_note"] = ("k_sort_scatter alone: 282.4 MB DRAM per refinement pass of 40 M keys "
                             "(320 MB algorithmic), profiles/k_sort_scatter_refine_n1e6_p20.md")
-    roof_c = stage_roof("cstep_dist", "k_dist (C-step distances + fused top-digit histogram; "
+    roof_c = stage_roof("cstep_dist", "k_dist_win (C-step distances from step 2 on, k_dist at step 1; "
                         "per row 4p B read + 4 B per active chain written)")
     s_ms = sum(pp["stages"][k]["ms"] for pp in prof32 for k in ("cstep_dist", "cstep_select"))
     s_by = sum(pp["stages"][k]["bytes"] for pp in prof32 for k in ("cstep_dist", "cstep_select"))
     roof_c["traffic"] = K_DIST_TRAFFIC
-    roof_c["traffic_note"] = "second C-step launch, both chains active: profiles/k_dist_cstep_n1e6_p20.md"
+    roof_c["traffic_note"] = "one k_dist_win launch with both chains active: profiles/k_dist_win_cstep_n1e6_p20.md"
     roof_c["dist_plus_select_frac"] = (s_by / (s_ms / 1e3) / 1e9) / peak
     launches = int(sum(sum(st["launches"] for st in pp["stages"].values()) for pp in prof32))
     cpu = None

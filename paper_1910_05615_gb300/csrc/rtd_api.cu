@@ -371,8 +371,8 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
             pf.begin(RTD_STAGE_CDIST);
             if (win) launch_dist_win(P, s);
             else launch_dist(P, s);
-            // rows read, keys written (+ membership bytes read and written)
-            pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_ + (win ? 2 * mch : 0));
+            // rows read, keys written
+            pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_);
             pf.begin(RTD_STAGE_CSELECT);
             if (win) {
                 launch_select_win(P, s);   // a chain whose window missed takes the histogram path there

@@ -42,14 +42,17 @@ __device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uin
         : "memory");
 }
 
+// One bounded probe of the phase: the thread may be suspended until the
+// phase completes or about 1 ms passes (suspend-time hint, in ns), so a
+// waiting warp issues few instructions.
 __device__ inline bool mbar_test(uint64_t* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(1000000u)
         : "memory");
     return ok != 0;
 }

@@ -8,58 +8,62 @@ namespace rtd {
 constexpr int LD = PMAX + 1;   // padded leading dimension of shared matrices
 
 // In-place Cholesky A = L L^T (lower triangle overwritten by L; the strict
-// upper triangle is zeroed).  Returns false (uniformly) if A is not
-// numerically positive definite.  Right-looking, one barrier per column:
-// step k updates the trailing block from the unscaled column k and scales
-// column k - 1 (no thread reads it any more).  The pivot's reciprocal square
-// root is taken once, by the thread that updates the next diagonal entry,
-// and passed on in shared memory (FP64 square roots are long dependent
-// sequences on this GPU; every thread repeating them would occupy the FP64
-// pipe for the whole factorisation).
+// upper triangle is zeroed); rdiag (optional) receives 1 / L_kk.  Returns
+// false (uniformly) if A is not numerically positive definite.
+// Computed as A = U D U^T (U unit lower) and scaled to L = U D^{1/2} at the
+// end, so the column-to-column chain holds one FP64 reciprocal per pivot and
+// no square root (FP64 square roots are long dependent sequences on this
+// GPU; the p square roots of the final scaling run in parallel).
+// Right-looking, one barrier per column: step k updates the trailing block
+// from the unscaled column k and scales column k - 1 (no thread reads it any
+// more); the next pivot's reciprocal is taken once, by the thread that
+// updates that diagonal entry, and passed on in shared memory.
 __device__ inline bool cta_cholesky(double* A, int p, double* rdiag = nullptr) {
-    __shared__ double piv[2][2];    // (d_k, 1/d_k) by column parity
+    __shared__ double piv[2];       // 1 / D_k by column parity
+    __shared__ double sd[PMAX];
     __shared__ int bad;
     __syncthreads();
     if (threadIdx.x == 0) {
         const double a = A[0];
         bad = !(a > 0.0) || !isfinite(a);
-        if (!bad) { const double r = rsqrt(a); piv[0][0] = a * r; piv[0][1] = r; }
+        if (!bad) piv[0] = 1.0 / a;
     }
     __syncthreads();
     if (bad) return false;
-    double dprev = 0.0, rprev = 0.0;   // pivot of column k - 1, kept in registers
+    double rprev = 0.0;   // 1 / D_{k-1}, kept in registers
     for (int k = 0; k < p; ++k) {
         // piv[k & 1] was written before the last barrier; piv[(k + 1) & 1] is written below
-        const double dk = piv[k & 1][0], rk = piv[k & 1][1];
-        if (k > 0) {
+        const double rk = piv[k & 1];
+        if (k > 0)
             for (int i = k + threadIdx.x; i < p; i += blockDim.x) A[i * LD + (k - 1)] *= rprev;
-            if (threadIdx.x == 0) A[(k - 1) * LD + (k - 1)] = dprev;
-        }
         const int rem = p - k - 1;
-        const double rk2 = rk * rk;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
             const int i = k + 1 + e / rem, j = k + 1 + e % rem;
             if (j <= i) {
-                const double v = A[i * LD + j] - A[i * LD + k] * A[j * LD + k] * rk2;
+                const double v = A[i * LD + j] - A[i * LD + k] * A[j * LD + k] * rk;
                 A[i * LD + j] = v;
-                if (e == 0) {   // (k+1, k+1): the next pivot
-                    const bool b = !(v > 0.0) || !isfinite(v);
-                    if (b) bad = 1;
-                    else { const double r = rsqrt(v); piv[(k + 1) & 1][0] = v * r; piv[(k + 1) & 1][1] = r; }
+                if (e == 0) {   // (k+1, k+1): the next pivot D_{k+1}
+                    if (!(v > 0.0) || !isfinite(v)) bad = 1;
+                    else piv[(k + 1) & 1] = 1.0 / v;
                 }
             }
         }
-        if (rdiag && threadIdx.x == 0) rdiag[k] = rk;
-        dprev = dk;
         rprev = rk;
         __syncthreads();
         if (bad) return false;
     }
-    if (threadIdx.x == 0) A[(p - 1) * LD + (p - 1)] = dprev;
+    // L = U D^{1/2}
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        const double d = sqrt(A[j * LD + j]);
+        sd[j] = d;
+        if (rdiag) rdiag[j] = 1.0 / d;
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        int i = e / p, j = e % p;
-        if (j > i) A[i * LD + j] = 0.0;
+        const int i = e / p, j = e % p;
+        if (j < i) A[i * LD + j] *= sd[j];
+        else if (j == i) A[i * LD + j] = sd[j];
+        else A[i * LD + j] = 0.0;
     }
     __syncthreads();
     return true;
@@ -150,12 +154,18 @@ __device__ inline float cta_max_f(float v) {
     return r;
 }
 __device__ inline double cta_kappa1(const double* S, const double* Li, double* Wd, int p) {
-    float* W = reinterpret_cast<float*>(Wd);
+    float* W = reinterpret_cast<float*>(Wd);        // p x LD floats
+    float* Lf = W + PMAX * LD;                      // FP32 copy of Li (same shared block)
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        Lf[i * LD + j] = (float)Li[i * LD + j];
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         int k0 = i > j ? i : j;
         float v = 0.f;
-        for (int k = k0; k < p; ++k) v = fmaf((float)Li[k * LD + i], (float)Li[k * LD + j], v);
+        for (int k = k0; k < p; ++k) v = fmaf(Lf[k * LD + i], Lf[k * LD + j], v);
         W[i * LD + j] = v;
     }
     __syncthreads();

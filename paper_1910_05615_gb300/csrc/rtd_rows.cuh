@@ -689,10 +689,12 @@ template <int PB> struct DistWin {
     static constexpr int STAGES = 2;                 // tiles in flight per warp
     static constexpr int PH = PB / 2;                // column pairs per row
     static constexpr size_t WTILE = (size_t)WT * PB * sizeof(float);
-    static constexpr int CTAS_PER_SM = (2 * (NW * STAGES * WTILE + 2 * (size_t)PB * PB * sizeof(float) +
-                                             2 * (size_t)WIN_BINS * sizeof(unsigned)) <= 220 * 1024) ? 2 : 1;
     static constexpr size_t SMEM = NW * STAGES * WTILE + 2 * (size_t)PB * PB * sizeof(float) +
                                    2 * (size_t)WIN_BINS * sizeof(unsigned);
+    // resident CTAs per SM by shared memory (1 KB reserved per CTA), at most 2
+    static constexpr int BY_SMEM = (int)((227 * 1024) / (SMEM + 1024));
+    static constexpr int CTAS_PER_SM = BY_SMEM > 2 ? 2 : (BY_SMEM < 1 ? 1 : BY_SMEM);
+    static_assert(SMEM + 1024 <= 227 * 1024, "row stages exceed shared memory");
 };
 
 // d2 of R rows for lower-triangular M stored as column pairs (row stride
@@ -917,10 +919,15 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
 template <int PB>
 void dist_win_t(const Plan& P, cudaStream_t s) {
     typedef DistWin<PB> D;
-    dim3 grid(P.cpb_win, P.q);
+    // one resident wave, at least 256 rows per CTA
+    long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
+    const long long lim = ((long long)P.m + 255) / 256;
+    if (cw > lim) cw = lim;
+    const int cpb = (int)(cw > 0 ? cw : 1);
+    dim3 grid(cpb, P.q);
     auto k = k_dist_win<PB>;
     set_smem(k, D::SMEM);
-    k<<<grid, D::NTW, D::SMEM, s>>>(P.Xp, P.p, P.m, P.cpb_win, P.cs, P.ch, P.rule, (float*)P.dkeys,
+    k<<<grid, D::NTW, D::SMEM, s>>>(P.Xp, P.p, P.m, cpb, P.cs, P.ch, P.rule, (float*)P.dkeys,
                                     (long long)P.q * P.m, P.cand, P.hist, P.st);
 }
 

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
                                                        const double* __restrict__ gsum, size_t slot_d,
                                                        int* swaps, int* blk, SelRule* rule, Status* st) {
     extern __shared__ double sm[];
-    __shared__ double dmu[PMAX], inv_s[PMAX];
+    __shared__ double dmu[PMAX], inv_s[PMAX], Ss[PMAX];
     __shared__ double s_m2;
     __shared__ int s_cont;
     const int c = blockIdx.x, l = c / 2;
@@ -491,15 +491,21 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
         double expect = full ? hb : 0.0;
         if (fabs(cnt - expect) > 0.5) set_error(st, RTD_EINTERNAL);
     }
+    // new S and G, kept in shared memory for the centre and scatter below
+    double* Gs = sm + MAT;
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         double v = gram_get(ext, j, p, nb);
-        C.S[j] = full ? v : C.S[j] + v;
+        v = full ? v : C.S[j] + v;
+        C.S[j] = v;
+        Ss[j] = v;
         inv_s[j] = 1.0 / cs->s_uni[j];
     }
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         double v = gram_get(ext, i, j, nb);
-        C.G[i * PMAX + j] = full ? v : C.G[i * PMAX + j] + v;
+        v = full ? v : C.G[i * PMAX + j] + v;
+        C.G[i * PMAX + j] = v;
+        Gs[i * LD + j] = v;
     }
     // the previous M, for the centre's move below
     double* Mo = sm;
@@ -509,13 +515,13 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
     }
     __syncthreads();
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        double mx = C.rp.ref[j] + C.S[j] * inv_hb;
+        double mx = C.rp.ref[j] + Ss[j] * inv_hb;
         C.mu[j] = (mx - cs->mu_uni[j]) * inv_s[j];
         dmu[j] = mx - C.rp.ref[j];
     }
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
-        double lam = C.G[i * PMAX + j] - C.S[i] * C.S[j] * inv_hb;
+        double lam = Gs[i * LD + j] - Ss[i] * Ss[j] * inv_hb;
         C.Sigma[i * PMAX + j] = lam * inv_hb1 * inv_s[i] * inv_s[j];
     }
     __syncthreads();
