@@ -36,9 +36,8 @@ REF_SAMPLE_ROWS = 200_000
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_dist_win launch at
-# n=1e6, p=20 with both chains of every block active (None until captured on
-# the current kernel)
-K_DIST_TRAFFIC = None
+# n=1e6, p=20 with both chains of every block active (80.22 MB + 3.35 MB)
+K_DIST_TRAFFIC = 83.57e6
 
 
 def selection_stats(pp):
@@ -48,6 +47,61 @@ def selection_stats(pp):
     return {"window_chain_steps": ws, "window_misses": pp.get("win_miss", 0),
             "candidates_per_window_step": pp.get("sel_cand", 0) / steps,
             "band_rows_total": pp.get("sel_band", 0)}
+
+
+SCORE_N, SCORE_P = 2048 * 4096, 4       # one test image of the paper's almond line (Section 6)
+
+
+def scoring_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind, reps=20):
+    """Scoring of new rows against an existing fit (Section 6, step 10):
+    rtdetmcd_distances then rtdetmcd_flag on device buffers.  Whole calls are
+    timed; the streaming kernels' HBM fraction uses the call time minus the
+    fixed cost of a 1,024-row call (fit preparation, status read)."""
+    import numpy as np
+    n, p = SCORE_N, SCORE_P
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    R, _ = datagen.random_correlation(p, 100.0, np.random.default_rng(7))
+    L = torch.linalg.cholesky(torch.from_numpy(R)).to(dev, torch.float32)
+    X = torch.randn(n, p, generator=g, device=dev) @ L.T
+    X[: n // 10] += 6.0                      # 10% shifted rows
+    mu, Sigma = np.zeros(p), R
+    cut = rtd.rtdetmcd_chi2_quantile(p, 0.975)
+    wsd = torch.empty(rtd.rtdetmcd_distances_workspace_size(n, p), dtype=torch.uint8, device=dev)
+    wsf = torch.empty(n * 5 + 1024, dtype=torch.uint8, device=dev)
+
+    def call(Xin):
+        d2 = rtd.rtdetmcd_distances(Xin, mu, Sigma, workspace=wsd, stream=stream.cuda_stream)
+        return rtd.rtdetmcd_flag(d2, cut, workspace=wsf, stream=stream.cuda_stream)
+
+    def time_calls(Xin, k):
+        ts = []
+        for i in range(k):
+            flush.fill_(i & 255)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl, nf = call(Xin)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), nf
+
+    for _ in range(3):
+        call(X)
+        call(X[:1024])
+    t_full, nflag = time_calls(X, reps)
+    t_small, _ = time_calls(X[:1024], reps)
+    bytes_ = n * (4 * p + 4) + n * (4 + 1)       # rows + d2 written; d2 read + flags written
+    t_stream = max(t_full - t_small, 1e-6)
+    a = bytes_ / (t_stream / 1e3) / 1e9
+    return {"workload": f"scoring {n:,} x {p} float32 rows (one {2048}x{4096} image), distances + flags",
+            "rows_per_s": n / (t_full / 1e3), "ms_per_call": t_full, "fixed_ms": t_small,
+            "n_flagged": int(nflag),
+            "roofline": {"kernel": "k_final (distances, no decision) + k_flag", "bound": "hbm",
+                         "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                         "peak_kind": peak_kind, "bytes_per_call": bytes_,
+                         "stream_ms": t_stream}}
 
 
 def peaks():
@@ -189,6 +243,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-score", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -332,6 +387,9 @@ def main():
                              f"one fit, one host thread", "seconds": d["times"][0]}
         except Exception as ex:  # report, do not hide
             cpu = {"error": str(ex)[-300:]}
+    scoring = None
+    if not args.no_score:
+        scoring = scoring_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind)
     line = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws_n, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
@@ -345,7 +403,7 @@ def main():
         "roofline": roof, "roofline_cstep": roof_c, "stages": stages, "csteps": prof32[-1]["csteps"],
         "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "scoring": scoring,
         "n_flagged": r32["n_flagged"], "step_ms": t32,
     }
     print(json.dumps(line), flush=True)

@@ -83,6 +83,15 @@ typedef struct {
     double*  diag_out;
     /* optional stage profile (nullable, host), filled on return */
     struct rtd_profile* profile;
+    /* optional warm start (both or neither; host, X units): the final mu (p)
+       and Sigma (p x p, row-major) of an earlier fit, used as the input to
+       step 3 of Section 4 (end of Section 4).  Every block then runs one
+       C-step chain from it; the univariate standardisation, the initial
+       estimators and their refinement (Sections 3.1-3.3) are skipped, and Z
+       is standardised by the warm fit's centre and diagonal.  Rejected with
+       RTD_EINVAL unless finite with a positive diagonal. */
+    const double* init_mu;
+    const double* init_sigma;
 } rtd_options;
 
 /* Stages of a fit, for rtd_profile. */

@@ -31,6 +31,10 @@ project's design notes):
       (reweight_consistency=1, default).  0 gives the literal plain covariance;
       2 uses c(|W|/n) at the fraction of rows kept.
   R9  KL of Section 4 step 6 uses log|det(A B^-1)| (A may be indefinite).
+  R13 warm start (end of Section 4): a run's final (mu, Sigma) as the input
+      to step 3 of the next; blocks kept, steps 1-2 and the univariate
+      standardisation skipped, Z standardised by the warm fit's centre and
+      diagonal, one chain per block.
 """
 from __future__ import annotations
 
@@ -505,14 +509,27 @@ def validate(n: int, p: int, h: int):
 def fit(X, h: int, *, omega: int = OMEGA, seed: int = 0,
         kappa_max: float = KAPPA_MAX, cutoff_q: float = CUTOFF_Q,
         max_steps: int = MAX_CSTEPS, q: int | None = None,
-        reweight_consistency: int = 1) -> Fit:
+        reweight_consistency: int = 1, init=None) -> Fit:
+    """init = (mu, Sigma) in X units: warm start (end of Section 4: the final
+    estimate of a run as the input to step 3 of the next).  Reading R13:
+    the blocks are kept (step 3 runs per block), steps 1-2 and the
+    univariate standardisation are skipped; Z is standardised by the warm
+    fit's own centre and diagonal, and each block runs one chain, from the
+    warm fit."""
     X = np.asarray(X, dtype=np.float64)
     n, p = X.shape
     validate(n, p, h)
-    # Section 3.1 and Section 4 (eq. standardization): whole-X univariate MCD.
-    uni = [univariate_mcd(X[:, j], cutoff_q) for j in range(p)]
-    mu_uni = np.array([u.mu for u in uni])
-    s_uni = np.sqrt(np.array([u.s2 for u in uni]))
+    if init is not None:
+        mu_uni = np.asarray(init[0], dtype=np.float64).reshape(p)
+        S_init = np.asarray(init[1], dtype=np.float64).reshape(p, p)
+        if not (np.all(np.isfinite(mu_uni)) and np.all(np.isfinite(S_init)) and np.all(np.diag(S_init) > 0)):
+            raise OracleError("warm start needs a finite centre and a positive diagonal")
+        s_uni = np.sqrt(np.diag(S_init))
+    else:
+        # Section 3.1 and Section 4 (eq. standardization): whole-X univariate MCD.
+        uni = [univariate_mcd(X[:, j], cutoff_q) for j in range(p)]
+        mu_uni = np.array([u.mu for u in uni])
+        s_uni = np.sqrt(np.array([u.s2 for u in uni]))
     Z = (X - mu_uni) / s_uni
     # Section 4: random partition into q blocks of m rows (eq. partitionsize).
     if q is None:
@@ -528,16 +545,23 @@ def fit(X, h: int, *, omega: int = OMEGA, seed: int = 0,
     for l in range(q):
         rows = perm[l * m:(l + 1) * m]
         Zl = Z[rows]
-        # Step 1: the two initial scatters; step 2: refinement; step 3: C-steps.
-        S = [start_wrap(Zl), start_gsscm(Zl)]
-        starts, chains = [], []
-        for Sk in S:
-            st = refine(Zl, Sk, kappa_max)
-            starts.append(st)
-            if st is None:
-                chains.append(None)
-                continue
-            chains.append(csteps(Zl, st.mu, st.Sigma, h_b, kappa_max, max_steps))
+        if init is not None:
+            # warm start: step 3 only, from the warm fit (Z units)
+            S = [None, None]
+            starts = [None, None]
+            Sz = S_init / np.outer(s_uni, s_uni)
+            chains = [csteps(Zl, np.zeros(p), Sz, h_b, kappa_max, max_steps), None]
+        else:
+            # Step 1: the two initial scatters; step 2: refinement; step 3: C-steps.
+            S = [start_wrap(Zl), start_gsscm(Zl)]
+            starts, chains = [], []
+            for Sk in S:
+                st = refine(Zl, Sk, kappa_max)
+                starts.append(st)
+                if st is None:
+                    chains.append(None)
+                    continue
+                chains.append(csteps(Zl, st.mu, st.Sigma, h_b, kappa_max, max_steps))
         # Step 4: the start with the lower determinant (start 1 on ties).
         b = Block(rows, S, starts, chains)
         ok = [k for k in range(2) if chains[k] is not None and chains[k].ok]

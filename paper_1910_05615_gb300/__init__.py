@@ -21,7 +21,7 @@ from . import build as _build_mod
 __all__ = [
     "RTD_FP32", "RTD_FP64", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
     "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
-    "rtdetmcd_diag_size", "parse_diag",
+    "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag",
 ]
 
 RTD_FP64 = 0
@@ -44,7 +44,8 @@ class _Options(ctypes.Structure):
                 ("cutoff_q", ctypes.c_double), ("kappa_max", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("reweight_consistency", ctypes.c_int32),
                 ("select_path", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
-                ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p)]
+                ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p),
+                ("init_mu", ctypes.c_void_p), ("init_sigma", ctypes.c_void_p)]
 
 
 STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_dist",
@@ -176,6 +177,10 @@ def rtdetmcd_diag_size(p, q):
     return _load().rtdetmcd_diag_size(p, q)
 
 
+def rtdetmcd_distances_workspace_size(n, p):
+    return _load().rtdetmcd_distances_workspace_size(n, p)
+
+
 def rtdetmcd_chi2_quantile(p, q=0.975):
     return _load().rtdetmcd_chi2_quantile(p, q)
 
@@ -185,8 +190,8 @@ def rtdetmcd_status_string(code):
 
 
 def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100,
-                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, select_path=0, d2=True,
-                 flags=True, subset=False, diag=False, profile=False, stream=None, workspace=None,
+                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, select_path=0, init=None,
+                 d2=True, flags=True, subset=False, diag=False, profile=False, stream=None, workspace=None,
                  check=True):
     """RT-DetMCD fit of the rows of X (float32, row-major) with coverage h.
 
@@ -204,6 +209,12 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     o.max_csteps, o.cutoff_q, o.kappa_max = max_csteps, cutoff_q, kappa_max
     o.reweight_consistency = reweight_consistency
     o.select_path = select_path
+    if init is not None:   # warm start: (mu, Sigma) of an earlier fit, X units
+        init_mu = np.ascontiguousarray(init[0], dtype=np.float64).reshape(-1)
+        init_sigma = np.ascontiguousarray(init[1], dtype=np.float64).reshape(-1)
+        if init_mu.size != p or init_sigma.size != p * p:
+            raise ValueError("init must be (mu of length p, Sigma of shape p x p)")
+        o.init_mu, o.init_sigma = init_mu.ctypes.data, init_sigma.ctypes.data
     ws_need = lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o))
     if ws_need == 0:
         raise RtdError(1, "invalid n, p or options")

@@ -1,4 +1,5 @@
 #include <vector>
+#include <cmath>
 // rtd_api.cu - C ABI entry points and host orchestration of RT-DetMCD.
 //
 // The host validates arguments, lays out the caller's workspace, and issues
@@ -70,6 +71,14 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (!(o.cutoff_q > 0.0 && o.cutoff_q < 1.0) || !(o.kappa_max > 1.0)) return RTD_EINVAL;
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
     if (o.select_path < 0 || o.select_path > 2) return RTD_EINVAL;
+    if ((o.init_mu == nullptr) != (o.init_sigma == nullptr)) return RTD_EINVAL;
+    if (o.init_mu) {   // warm start: finite, positive diagonal (host memory)
+        for (int j = 0; j < p; ++j) {
+            if (!std::isfinite(o.init_mu[j]) || !(o.init_sigma[(size_t)j * p + j] > 0.0)) return RTD_EINVAL;
+            for (int i = 0; i < p; ++i)
+                if (!std::isfinite(o.init_sigma[(size_t)i * p + j])) return RTD_EINVAL;
+        }
+    }
     S.n = n; S.h = h; S.ld = ld; S.p = p; S.pb = pad_p(p);
     S.precision = o.precision;
     S.max_steps = o.max_csteps;
@@ -127,7 +136,9 @@ size_t layout(const Shape& S, Regions& R) {
     R.uni = L.add(4 * ((2 * p * q > p) ? 2 * p * q : p) * sizeof(double));
     {
         size_t a = unimcd_scratch_doubles((int)p, S.n), b = unimcd_scratch_doubles(2 * (int)(p * q), S.m);
-        R.uscratch = L.add((a > b ? a : b) * sizeof(double));
+        size_t c = (size_t)p + (size_t)p * p;   // a warm start's (mu, Sigma)
+        size_t u = a > b ? a : b;
+        R.uscratch = L.add((u > c ? u : c) * sizeof(double));
     }
     R.gss = L.add(2 * q * sizeof(double));
     R.dkeys = L.add(2 * qm * K);
@@ -310,6 +321,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     Status hs;
     Prof pf;
     pf.init(o.profile, s);
+    const bool warm = o.init_mu != nullptr;
     const double n_ = (double)S.n, p_ = (double)S.p, qm_ = (double)qm, K_ = (double)S.key_bytes;
     // Section 4: random partition copy
     pf.begin(RTD_STAGE_PARTITION);
@@ -327,15 +339,26 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     // Sections 3.1 and 4: setup, univariate MCD of every column
     pf.begin(RTD_STAGE_UNIVARIATE);
     launch_setup(P, o, s);
-    launch_col_keys(P, (uint32_t*)P.arenaA, s);
-    sorted_(P.arenaA, 4, S.p, S.n, RTD_STAGE_UNIVARIATE);
-    launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
-    launch_uni_finish(P, s);
-    // rows read, keys written, window search (chunk sums read the keys once)
-    pf.end(9, n_ * p_ * (4 + 4 + 4 + 4));
+    launch_col_keys(P, (uint32_t*)P.arenaA, s);   // also the non-finite check
+    if (warm) {
+        // warm start (end of Section 4): standardisation and one chain per
+        // block from the given fit; steps 1-2 are skipped
+        RTD_CUDA(cudaMemcpyAsync(P.uscratch, o.init_mu, (size_t)S.p * sizeof(double), cudaMemcpyHostToDevice, s));
+        RTD_CUDA(cudaMemcpyAsync(P.uscratch + S.p, o.init_sigma, (size_t)S.p * S.p * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+        launch_warm_start(P, P.uscratch, s);
+        pf.end(3, n_ * p_ * (4 + 4));
+    } else {
+        sorted_(P.arenaA, 4, S.p, S.n, RTD_STAGE_UNIVARIATE);
+        launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
+        launch_uni_finish(P, s);
+        // rows read, keys written, window search (chunk sums read the keys once)
+        pf.end(9, n_ * p_ * (4 + 4 + 4 + 4));
+    }
     { int e = fetch_status(P.st, s, hs); if (e) return e; }
     pf.collect();
     if (hs.code) goto finish;
+    if (warm) goto csteps;
     // Section 3.2: initial estimators per block
     pf.begin(RTD_STAGE_STARTS);
     launch_start1(P, s);
@@ -357,6 +380,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     launch_refine_end(P, s);
     pf.end(17, 2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * 2));
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
+csteps:
     {
         int act_chains = 2 * S.q, act_blocks = S.q;
         pf.begin(RTD_STAGE_CPREP);

@@ -103,6 +103,7 @@ void launch_start_reduce(const Plan& P, cudaStream_t s);
 void launch_refine_eigen(const Plan& P, cudaStream_t s);
 void launch_refine_mid(const Plan& P, cudaStream_t s);
 void launch_refine_end(const Plan& P, cudaStream_t s);
+void launch_warm_start(const Plan& P, const double* init, cudaStream_t s);
 void launch_chol_prep(const Plan& P, cudaStream_t s);
 void launch_cstep_finalize(const Plan& P, cudaStream_t s);
 void launch_block_choose(const Plan& P, cudaStream_t s);

@@ -318,13 +318,13 @@ void member_gram_t(const Plan& P, cudaStream_t s) {
 }
 
 // FP64 distance of one row (band recomputation).
+// FP64 distance of one row (global memory, read through L1) under rp; used
+// only for rows inside an FP64 band, so the centred row is not kept.
 __device__ inline double d2_fp64(const float* __restrict__ x, const RowParams& rp, int p) {
-    double c[PMAX];
-    for (int j = 0; j < p; ++j) c[j] = (double)x[j] - rp.mu[j];
     double d2 = 0.0;
     for (int i = 0; i < p; ++i) {
         double a = 0.0;
-        for (int j = 0; j <= i; ++j) a += rp.M[i * PMAX + j] * c[j];
+        for (int j = 0; j <= i; ++j) a += rp.M[i * PMAX + j] * ((double)__ldg(x + j) - rp.mu[j]);
         d2 += a * a;
     }
     return d2;
@@ -543,6 +543,7 @@ template <> struct Vec4<double> {
     }
 };
 
+// rows per thread of the plain distance passes
 template <int PB, typename T> struct DistRows { static constexpr int R = (PB <= 24 && sizeof(T) == 4) ? 2 : 1; };
 
 // y = M c row by row (lower triangular M, row stride PB, zero above the
@@ -1189,7 +1190,7 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
             if (!fp32) in = (double)d2[0] <= cut;
             else if (d2[0] < cut_lo) in = true;
             else if (d2[0] > cut_hi) in = false;
-            else in = d2_fp64(x, *rp, p) <= cut;
+            else in = d2_fp64(Xp + (size_t)row * PB, *rp, p) <= cut;   // row re-read: x stays in registers
             wset[row] = in ? 2 : 0;
         }
         int tot;
@@ -1245,28 +1246,34 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
     const double cut = cutp ? *cutp : INFINITY;
     const T cut_lo = (T)(cut * (1.0 - BAND_EPS)), cut_hi = (T)(cut * (1.0 + BAND_EPS));
     int nflag = 0;
+    // a CTA takes tiles of NT * R rows; thread t holds rows t, t + NT, ...
+    // (each load instruction of a warp reads consecutive rows)
     const long long stride = (long long)gridDim.x * NT * R;
-    for (long long base = ((long long)blockIdx.x * NT + threadIdx.x) * R; base < n; base += stride) {
+    for (long long tb = (long long)blockIdx.x * NT * R; tb < n; tb += stride) {
         T c[R][PB];
         float xs[R][PB];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (base + r < n) load_row_user<PB>(X + (base + r) * ld, p, vec4 != 0, xs[r]);
+            const long long i = tb + (long long)r * NT + threadIdx.x;
+            if (i < n) load_row_user<PB>(X + i * ld, p, vec4 != 0, xs[r]);
             else {
 #pragma unroll
                 for (int j = 0; j < PB; ++j) xs[r][j] = 0.f;
             }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int j = 0; j < PB; ++j) c[r][j] = ((T)xs[r][j] - s_hi[j]) - s_lo[j];
-        }
         T d2[R];
         tri_d2<PB, T, R>(sM, p, c, d2);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const long long i = base + r;
+            const long long i = tb + (long long)r * NT + threadIdx.x;
             if (i >= n) continue;
             double d = (double)d2[r];
-            if (fp32 && decide && d2[r] >= cut_lo && d2[r] <= cut_hi) d = d2_fp64(xs[r], *rp, p);
+            if (fp32 && decide && d2[r] >= cut_lo && d2[r] <= cut_hi)
+                d = d2_fp64(X + i * ld, *rp, p);   // row re-read: xs stays in registers
             const bool out = d > cut;
             if (d2_out) d2_out[i] = (float)d;
             if (flags) flags[i] = out ? 1 : 0;

@@ -293,6 +293,43 @@ void launch_refine_end(const Plan& P, cudaStream_t s) {
 }
 
 // =====================================================================
+// Warm start (end of Section 4): the given fit (X units, init = mu then
+// Sigma row-major) standardises Z by its centre and diagonal, and starts
+// the one chain of every block (mu_z = 0, Sigma_z = D^-1 Sigma D^-1); the
+// block's second chain has no start.
+// =====================================================================
+__global__ void __launch_bounds__(CT) k_warm_start(Chain* ch, Consts* cs, const double* __restrict__ init) {
+    __shared__ double rs[PMAX];
+    const int c = blockIdx.x;
+    const int p = cs->p;
+    const double* mu = init;
+    const double* S = init + p;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        const double d = sqrt(S[(size_t)j * p + j]);
+        rs[j] = 1.0 / d;
+        if (c == 0) { cs->mu_uni[j] = mu[j]; cs->s_uni[j] = d; }
+    }
+    __syncthreads();
+    Chain& C = ch[c];
+    if (c & 1) {
+        if (threadIdx.x == 0) { C.active = 0; C.status = CH_DROPPED; }
+        return;
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        const double v = S[(size_t)i * p + j] * rs[i] * rs[j];
+        C.Sigma[i * PMAX + j] = v;
+        C.Sigma0[i * PMAX + j] = v;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) { C.mu[j] = 0.0; C.mu0[j] = 0.0; }
+    if (threadIdx.x == 0) { C.status = CH_OK; C.active = 1; C.full = 1; C.steps = 0; C.started = 1; }
+}
+
+void launch_warm_start(const Plan& P, const double* init, cudaStream_t s) {
+    k_warm_start<<<2 * P.q, CT, 0, s>>>(P.ch, P.cs, init);
+}
+
+// =====================================================================
 // Row parameters of a fit (mu, Sigma in Z units): Cholesky Sigma = L L^T
 // (Section 3.4), M = L^-1 D^-1, mu_x = mu_uni + D mu, FP32 copies with the
 // centre split into hi + lo.  Returns false if Sigma is not positive

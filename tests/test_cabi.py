@@ -88,3 +88,26 @@ def test_distances_rejects_bad_arguments(lib):
     st = lib.rtdetmcd_distances(X.ctypes.data, 10, 3, 3, mu.ctypes.data, S.ctypes.data, 7,
                                 out.ctypes.data, None, 0, None)
     assert st == 1
+
+
+@pytest.mark.parametrize("case", ["mu_only", "zero_diag", "nan_sigma", "nan_mu"])
+def test_fit_rejects_bad_warm_start(lib, case):
+    """A warm start needs both mu and Sigma, finite, with a positive diagonal;
+    anything else is RTD_EINVAL before any device work."""
+    import paper_1910_05615_gb300 as m
+    n, p, h = 1000, 3, 700
+    X = np.zeros((n, p), np.float32)
+    mu, S = np.zeros(p), np.eye(p)
+    if case == "zero_diag":
+        S[1, 1] = 0.0
+    elif case == "nan_sigma":
+        S[0, 2] = np.nan
+    elif case == "nan_mu":
+        mu[0] = np.nan
+    o = m._Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.init_mu = mu.ctypes.data
+    o.init_sigma = None if case == "mu_only" else S.ctypes.data
+    res = m._Result()
+    st = lib.rtdetmcd_fit(X.ctypes.data, n, p, p, h, ctypes.byref(o), None, 0, None, ctypes.byref(res), None, None)
+    assert st == 1 and res.status == 1

@@ -232,3 +232,27 @@ def test_select_path_rejects_bad_value(rtd):
     fr = datagen.small_fp64_case()
     with pytest.raises(rtd.RtdError):
         rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, select_path=3)
+
+
+# ------------------------------------------------ warm start (end of Section 4)
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
+def test_warm_start_parity(rtd, form):
+    """C-steps of every block from an earlier fit (reading R13), against the
+    oracle's warm start from its own full fit."""
+    fr = datagen.contaminated_gaussian(60_000, 6, eps=0.15, kind="cluster", shift=6.0, seed=21)
+    base = O.fit(fr.X, fr.h)
+    ref = O.fit(fr.X, fr.h, init=(base.mu, base.Sigma))
+    got = rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, init=(base.mu, base.Sigma),
+                           precision=rtd.RTD_FP32 if form == "fp32" else rtd.RTD_FP64, subset=True)
+    assert got["q"] == ref.q
+    ok, rep = compare_fit(got, ref, fr.X, form)
+    if not ok:
+        pytest.fail(str(rep))
+
+
+def test_warm_start_rejects_non_positive_diagonal(rtd):
+    fr = datagen.small_fp64_case()
+    S = np.eye(fr.X.shape[1])
+    S[0, 0] = -1.0
+    with pytest.raises(rtd.RtdError):
+        rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, init=(np.zeros(fr.X.shape[1]), S))

@@ -319,3 +319,32 @@ def test_outliers_detected_small_case():
     assert np.all(f.flags[fr.outlier])
     assert not np.any(f.subset_mask()[fr.outlier])
     assert O.kl_cov(f.Sigma, fr.R) < 0.02
+
+
+# ------------------------------------------------ warm start (end of Section 4)
+def test_warm_start_scale_free_and_runs_one_chain():
+    """R13: C-steps rank distances, which a positive factor on the warm
+    scatter does not change; the standardisation by the warm diagonal
+    absorbs it.  So the fit from (mu, 4 Sigma) equals the fit from
+    (mu, Sigma), and each block runs exactly one chain."""
+    fr = datagen.contaminated_gaussian(6000, 4, eps=0.15, kind="cluster", shift=6.0, seed=11)
+    base = O.fit(fr.X, fr.h, q=3)
+    a = O.fit(fr.X, fr.h, q=3, init=(base.mu, base.Sigma))
+    b = O.fit(fr.X, fr.h, q=3, init=(base.mu, 4.0 * base.Sigma))
+    np.testing.assert_allclose(a.mu, b.mu, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(a.Sigma, b.Sigma, rtol=1e-10, atol=1e-12)
+    assert np.array_equal(a.flags, b.flags)
+    for blk in a.blocks:
+        assert blk.chains[1] is None and blk.chains[0] is not None and blk.chosen == 0
+
+
+def test_warm_start_from_separated_optimum_keeps_it():
+    """On well-separated data the exact MCD optimum is a C-step fixed point
+    (A7 theorem); a warm start at the optimum's (mean, covariance) with q=1
+    stays on the optimal h-subset."""
+    rng = np.random.default_rng(5)
+    X = np.vstack([rng.standard_normal((12, 2)), rng.standard_normal((4, 2)) * 0.3 + 40.0])
+    h = 9
+    mu_e, S_e, H_e = O.exact_mcd(X, h)[:3]
+    f = O.fit(X, h, q=1, init=(mu_e, S_e))
+    assert np.array_equal(f.blocks[0].chains[0].H, H_e)
