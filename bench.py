@@ -104,6 +104,42 @@ def scoring_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind, reps=2
                          "stream_ms": t_stream}}
 
 
+def adjoint_leg(rtd, torch, X, h, dev, stream, flush, peak, peak_kind, reps=20):
+    """Value and gradient of log det Sigma + sum_i RD_i in X with the
+    reweighting set W of the fit held fixed (steps 8-10): rtdetmcd_grad on
+    the bench's own rows.  Algorithmic bytes per call: the rows twice (the
+    Gram pass and the gradient pass), the subset bytes twice, the gradient
+    written once."""
+    fit = rtd.rtdetmcd_fit(X, h, subset=True, d2=False, flags=False, stream=stream.cuda_stream)
+    n, p = X.shape
+    sub, mu, S, c = fit["subset"], fit["mu"], fit["Sigma"], fit["c_rew"]
+    ws = torch.empty(rtd.rtdetmcd_grad_workspace_size(n, p), dtype=torch.uint8, device=dev)
+
+    def call():
+        return rtd.rtdetmcd_grad(X, sub, mu, S, c, workspace=ws, stream=stream.cuda_stream)
+
+    for _ in range(3):
+        call()
+    ts = []
+    for i in range(reps):
+        flush.fill_(i & 255)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        val, g = call()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    t = statistics.median(ts)
+    bytes_ = n * (4 * p * 3 + 2)
+    a = bytes_ / (t / 1e3) / 1e9
+    return {"workload": f"adjoint of steps 8-10 on the fit of the bench rows ({n:,} x {p}), W fixed",
+            "rows_per_s": n / (t / 1e3), "ms_per_call": t, "value": val, "n_reweight": fit["n_reweight"],
+            "roofline": {"kernel": "k_grad_gram + k_sum_slots + k_grad_rows (whole call)", "bound": "hbm",
+                         "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                         "peak_kind": peak_kind, "bytes_per_call": bytes_}}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -244,6 +280,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-score", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -390,6 +427,9 @@ def main():
     scoring = None
     if not args.no_score:
         scoring = scoring_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_leg(rtd, torch, X, h, dev, stream, flush, peak, peak_kind)
     line = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws_n, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
@@ -404,6 +444,7 @@ def main():
         "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "scoring": scoring,
+        "adjoint": adjoint,
         "n_flagged": r32["n_flagged"], "step_ms": t32,
     }
     print(json.dumps(line), flush=True)

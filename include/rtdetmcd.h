@@ -140,6 +140,7 @@ typedef struct {
     int64_t n_reweight;    /* |W| */
     int32_t csteps_max;    /* largest number of C-steps over all chains */
     int32_t chains_ok;     /* chains that produced a fit */
+    double  c_rew;         /* factor of the reweighted scatter: sigma = c_rew * (sample covariance of W) */
 } rtd_result;
 
 /* Fill *opt with the defaults listed above. */
@@ -231,6 +232,38 @@ int rtdetmcd_distances_noalloc(const float* X, int64_t n, int32_t p, int64_t ld,
  */
 int rtdetmcd_flag(const float* d2, int64_t n, double cutoff_d2,
                   uint8_t* flags_out, int64_t* n_flagged,
+                  void* workspace, size_t ws_bytes, void* stream);
+
+/* Bytes of workspace rtdetmcd_grad needs. */
+size_t rtdetmcd_grad_workspace_size(int64_t n, int32_t p);
+
+/*
+ * Adjoint of the reweighting and final-distance steps (Section 4 steps 8-10)
+ * with the reweighting set W held fixed.  The paper has no counterpart: the
+ * set W is a discrete choice, and with it fixed the fit is a smooth function
+ * of the rows, so that a caller can differentiate a loss through it.
+ *   f(X) = w_logdet * log det Sigma + w_rd * sum_i RD_i
+ *   mu = mean of the rows in W, Sigma = c * S_W (sample covariance of W,
+ *   denominator |W| - 1), RD_i = sqrt((x_i - mu)^T Sigma^-1 (x_i - mu)) over
+ *   all n rows.
+ *   X           device, n rows of stride ld floats
+ *   wset        device, n bytes; row i is in W when bit `wbit` of wset[i] is
+ *               set (bit 1 of rtd_options.subset_out marks the fit's W)
+ *   mu_host     p doubles (host): the mean of W
+ *   sigma_host  p x p doubles, row-major (host): c * S_W, as rtdetmcd_fit
+ *               returns it in rtd_result.mu / .sigma with c = rtd_result.c_rew;
+ *               positive definite (RTD_EDEGENERATE otherwise)
+ *   value_out   nullable, host: f
+ *   grad_out    nullable, device, n x p floats (row-major, stride p): df/dX.
+ *               Rows with RD_i = 0 take the zero subgradient of their own
+ *               distance term.
+ * Returns RTD_EINVAL for host X, wset or grad_out, RTD_EDEGENERATE when
+ * |W| < p + 1.  Row arithmetic in FP32, sums across rows in FP64.
+ */
+int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld,
+                  const uint8_t* wset, int32_t wbit,
+                  const double* mu_host, const double* sigma_host, double c,
+                  double w_logdet, double w_rd, double* value_out, float* grad_out,
                   void* workspace, size_t ws_bytes, void* stream);
 
 /* chi2_{p, q} quantile as used for the cutoff (computed by the library's own

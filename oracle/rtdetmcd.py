@@ -623,4 +623,50 @@ def logdet(S) -> float:
     return float(2.0 * np.sum(np.log(np.diag(np.linalg.cholesky(S)))))
 
 
+
+
+# ----------------------------------------------------------------------------
+# Adjoint of Section 4 steps 8-10 with the reweighting set W fixed
+# ----------------------------------------------------------------------------
+def fixed_set_objective(X, W, c, w_logdet=1.0, w_rd=1.0):
+    """f(X) = w_logdet log det Sigma + w_rd sum_j RD_j, with mu = mean of the
+    rows in W, Sigma = c * (sample covariance of W, denominator |W|-1) and
+    RD_j = sqrt((x_j - mu)^T Sigma^-1 (x_j - mu)) over all rows (steps 8-10
+    with W held fixed)."""
+    X = np.asarray(X, dtype=np.float64)
+    Xw = X[W]
+    mu = Xw.mean(axis=0)
+    S = c * np.cov(Xw, rowvar=False, ddof=1).reshape(X.shape[1], X.shape[1])
+    L = np.linalg.cholesky(S)
+    Y = solve_triangular(L, (X - mu).T, lower=True)
+    rd = np.sqrt(np.sum(Y * Y, axis=0))
+    return w_logdet * float(2.0 * np.sum(np.log(np.diag(L)))) + w_rd * float(rd.sum())
+
+
+def fixed_set_gradient(X, W, c, w_logdet=1.0, w_rd=1.0):
+    """Gradient of fixed_set_objective with respect to X, from the closed
+    forms: with r_i = x_i - mu, u_i = Sigma^-1 r_i, N = |W|,
+      d log det Sigma / d x_i = [i in W] 2 c/(N-1) u_i   (Sigma^-1 = S_W^-1 / c),
+      d sum RD / d x_i = u_i/RD_i + [i in W] (g/N + 2 c/(N-1) G r_i),
+      g = -sum_j u_j/RD_j,   G = -1/2 sum_j u_j u_j^T / RD_j.
+    Rows with RD_i = 0 take the zero subgradient of their own term."""
+    X = np.asarray(X, dtype=np.float64)
+    W = np.asarray(W, dtype=bool)
+    N = int(W.sum())
+    Xw = X[W]
+    mu = Xw.mean(axis=0)
+    S = c * np.cov(Xw, rowvar=False, ddof=1).reshape(X.shape[1], X.shape[1])
+    Sinv = np.linalg.inv(S)
+    R = X - mu
+    U = R @ Sinv
+    rd = np.sqrt(np.einsum("ij,ij->i", R, U))
+    inv = np.where(rd > 0, 1.0 / np.where(rd > 0, rd, 1.0), 0.0)
+    g = -(U * inv[:, None]).sum(axis=0)
+    G = -0.5 * (U * inv[:, None]).T @ U
+    grad = w_rd * U * inv[:, None]
+    grad[W] += w_rd * (g / N + (2.0 * c / (N - 1)) * (R[W] @ G))
+    grad[W] += w_logdet * (2.0 * c / (N - 1)) * U[W]
+    return grad
+
+
 __all__ = [name for name in dir() if not name.startswith("_")]

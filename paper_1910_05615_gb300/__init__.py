@@ -21,7 +21,8 @@ from . import build as _build_mod
 __all__ = [
     "RTD_FP32", "RTD_FP64", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
     "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
-    "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag",
+    "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
+    "rtdetmcd_grad_workspace_size", "rtdetmcd_objective",
 ]
 
 RTD_FP64 = 0
@@ -69,7 +70,7 @@ class _Result(ctypes.Structure):
                 ("logdet", ctypes.c_double), ("logdet_raw", ctypes.c_double),
                 ("cutoff_d2", ctypes.c_double), ("n_flagged", ctypes.c_int64),
                 ("n_reweight", ctypes.c_int64), ("csteps_max", ctypes.c_int32),
-                ("chains_ok", ctypes.c_int32)]
+                ("chains_ok", ctypes.c_int32), ("c_rew", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -103,6 +104,11 @@ def _load():
     lib.rtdetmcd_distances.restype = i32
     lib.rtdetmcd_distances_noalloc.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp]
     lib.rtdetmcd_distances_noalloc.restype = i32
+    lib.rtdetmcd_grad_workspace_size.argtypes = [i64, i32]
+    lib.rtdetmcd_grad_workspace_size.restype = sz
+    lib.rtdetmcd_grad.argtypes = [vp, i64, i32, i64, vp, i32, vp, vp, dbl, dbl, dbl, ctypes.POINTER(dbl), vp,
+                                  vp, sz, vp]
+    lib.rtdetmcd_grad.restype = i32
     lib.rtdetmcd_flag.argtypes = [vp, i64, dbl, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.rtdetmcd_flag.restype = i32
     lib.rtdetmcd_chi2_quantile.argtypes = [i32, dbl]
@@ -243,7 +249,7 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
         "Sigma_raw": np.array(res.sigma_raw[:pp * pp]).reshape(pp, pp),
         "logdet": res.logdet, "logdet_raw": res.logdet_raw, "cutoff_d2": res.cutoff_d2,
         "n_flagged": res.n_flagged, "n_reweight": res.n_reweight, "csteps_max": res.csteps_max,
-        "chains_ok": res.chains_ok, "d2": d2_out, "flags": fl_out, "subset": sub_out,
+        "chains_ok": res.chains_ok, "c_rew": res.c_rew, "d2": d2_out, "flags": fl_out, "subset": sub_out,
     }
     if diag:
         a = dg.cpu().numpy() if not isinstance(dg, np.ndarray) else dg
@@ -308,6 +314,72 @@ def rtdetmcd_distances_noalloc(X, mu, Sigma, *, precision=RTD_FP32, out=None, st
     if st != 0:
         raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
     return d2
+
+
+def rtdetmcd_grad_workspace_size(n, p):
+    return _load().rtdetmcd_grad_workspace_size(n, p)
+
+
+def rtdetmcd_grad(X, wset, mu, Sigma, c, *, wbit=1, w_logdet=1.0, w_rd=1.0, grad=True, stream=None,
+                  workspace=None):
+    """Value and gradient in X of w_logdet log det Sigma + w_rd sum_i RD_i with
+    the reweighting set W (bit `wbit` of wset) held fixed (Section 4 steps
+    8-10).  X and wset are CUDA tensors; mu, Sigma = c S_W the fit of W.
+    Returns (value, grad) with grad an n x p CUDA tensor, or None."""
+    lib = _load()
+    torch = _torch()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    if dev is None or not (isinstance(wset, torch.Tensor) and wset.is_cuda):
+        raise ValueError("rtdetmcd_grad needs X and wset on a CUDA device")
+    if wset.dtype != torch.uint8 or wset.numel() != n or not wset.is_contiguous():
+        raise ValueError("wset must be a contiguous uint8 tensor of n bytes")
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    S = np.ascontiguousarray(Sigma, dtype=np.float64)
+    if mu.size != p or S.size != p * p:
+        raise ValueError("mu must have p entries and Sigma p x p")
+    ws = workspace if workspace is not None else _workspace(lib.rtdetmcd_grad_workspace_size(n, p), dev)
+    g = torch.empty((n, p), dtype=torch.float32, device=dev) if grad else None
+    val = ctypes.c_double(0.0)
+    st = lib.rtdetmcd_grad(ptr, n, p, ld, wset.data_ptr(), wbit, mu.ctypes.data, S.ctypes.data, float(c),
+                           float(w_logdet), float(w_rd), ctypes.byref(val), _ptr(g), ws.data_ptr(), ws.numel(),
+                           _stream_ptr(dev, stream))
+    del keep
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return val.value, g
+
+
+_objective_fn = None
+
+
+def rtdetmcd_objective(X, h, *, w_logdet=1.0, w_rd=1.0, **fit_kwargs):
+    """Differentiable scalar w_logdet log det Sigma + w_rd sum_i RD_i of the
+    reweighted fit of the rows of X (a CUDA float32 tensor).  The forward
+    pass runs rtdetmcd_fit; the backward pass holds its reweighting set W
+    fixed (the set is a discrete choice) and applies rtdetmcd_grad.  Returns
+    a 0-d float64 tensor on X's device."""
+    global _objective_fn
+    torch = _torch()
+    if _objective_fn is None:
+        class _Objective(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Xt, hh, wl, wr, kw):
+                fit = rtdetmcd_fit(Xt.detach(), hh, d2=False, flags=False, subset=True, **kw)
+                val, _ = rtdetmcd_grad(Xt.detach(), fit["subset"], fit["mu"], fit["Sigma"], fit["c_rew"],
+                                       w_logdet=wl, w_rd=wr, grad=False)
+                ctx.save_for_backward(Xt, fit["subset"])
+                ctx.fit = (fit["mu"], fit["Sigma"], fit["c_rew"], wl, wr)
+                return torch.tensor(val, dtype=torch.float64, device=Xt.device)
+
+            @staticmethod
+            def backward(ctx, gout):
+                Xt, sub = ctx.saved_tensors
+                mu, S, c, wl, wr = ctx.fit
+                _, g = rtdetmcd_grad(Xt.detach(), sub, mu, S, c, w_logdet=wl, w_rd=wr, grad=True)
+                return g * gout.to(torch.float32), None, None, None, None
+
+        _objective_fn = _Objective
+    return _objective_fn.apply(X, h, float(w_logdet), float(w_rd), fit_kwargs)
 
 
 def rtdetmcd_flag(d2, cutoff_d2, *, stream=None, workspace=None):

@@ -602,6 +602,65 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld, const d
     return hs.code;
 }
 
+size_t rtdetmcd_grad_workspace_size(int64_t n, int32_t p) {
+    if (n < 1 || p < 1 || p > RTD_MAX_P) return 0;
+    const size_t slot_d = (size_t)gram_nblk(pad_p(p)) * 16 + 2;
+    Layout L;
+    L.add(sizeof(Status));
+    L.add(sizeof(RowParams));
+    L.add((size_t)RTD_MAX_P * (RTD_MAX_P + 1) * sizeof(double));
+    L.add((size_t)GRAD_SLOTS * slot_d * sizeof(double));
+    L.add(slot_d * sizeof(double));
+    L.add(sizeof(double));
+    return (L.total + 255) & ~(size_t)255;
+}
+
+int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t* wset, int32_t wbit,
+                  const double* mu_host, const double* sigma_host, double c, double w_logdet, double w_rd,
+                  double* value_out, float* grad_out, void* workspace, size_t ws_bytes, void* stream) {
+    if (!X || !wset || !mu_host || !sigma_host || n < 2 || p < 1 || p > RTD_MAX_P || ld < p || wbit < 0 ||
+        wbit > 7 || !(c > 0.0) || !std::isfinite(c) || !std::isfinite(w_logdet) || !std::isfinite(w_rd) ||
+        !is_device_ptr(X) || !is_device_ptr(wset) || (grad_out && !is_device_ptr(grad_out)))
+        return RTD_EINVAL;
+    size_t need = rtdetmcd_grad_workspace_size(n, p);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t slot_d = (size_t)gram_nblk(pad_p(p)) * 16 + 2;
+    Layout L;
+    Region rst = L.add(sizeof(Status));
+    Region rrp = L.add(sizeof(RowParams));
+    Region rms = L.add((size_t)RTD_MAX_P * (RTD_MAX_P + 1) * sizeof(double));
+    Region rpa = L.add((size_t)GRAD_SLOTS * slot_d * sizeof(double));
+    Region rto = L.add(slot_d * sizeof(double));
+    Region rld = L.add(sizeof(double));
+    Status* st = at<Status>(workspace, rst);
+    RowParams* rp = at<RowParams>(workspace, rrp);
+    double* ms = at<double>(workspace, rms);
+    double* tot = at<double>(workspace, rto);
+    double* ldv = at<double>(workspace, rld);
+    int dev = 0, nsm = 0;
+    RTD_CUDA(cudaGetDevice(&dev));
+    RTD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RTD_CUDA(cudaMemsetAsync(st, 0, sizeof(Status), s));
+    RTD_CUDA(cudaMemcpyAsync(ms, mu_host, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, s));
+    RTD_CUDA(cudaMemcpyAsync(ms + RTD_MAX_P, sigma_host, (size_t)p * p * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_score_prep(ms, ms + RTD_MAX_P, p, rp, st, s, ldv);
+    launch_grad(X, n, p, ld, wset, (int)wbit, rp, at<double>(workspace, rpa), slot_d, tot, c, w_logdet, w_rd,
+                grad_out, nsm, s);
+    RTD_CUDA(cudaGetLastError());
+    double h[3];
+    RTD_CUDA(cudaMemcpyAsync(h, tot + slot_d - 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RTD_CUDA(cudaMemcpyAsync(h + 2, ldv, sizeof(double), cudaMemcpyDeviceToHost, s));
+    Status hs;
+    int e = fetch_status(st, s, hs);
+    if (e) return e;
+    if (hs.code) return hs.code;
+    // |W| must allow a non-singular covariance
+    if (h[1] < (double)p + 1.0) return RTD_EDEGENERATE;
+    if (value_out) *value_out = w_logdet * h[2] + w_rd * h[0];
+    return RTD_OK;
+}
+
 int rtdetmcd_flag(const float* d2, int64_t n, double cutoff_d2, uint8_t* flags_out, int64_t* n_flagged,
                   void* workspace, size_t ws_bytes, void* stream) {
     if (!d2 || n < 1 || !(cutoff_d2 == cutoff_d2)) return RTD_EINVAL;

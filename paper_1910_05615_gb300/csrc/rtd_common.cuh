@@ -47,6 +47,7 @@ struct Consts {
     double mu_raw[PMAX], Sigma_raw[PMAX * PMAX];
     double mu_rew[PMAX], Sigma_rew[PMAX * PMAX];
     double logdet_raw, logdet_rew;
+    double f_rew;             // factor applied to the reweighted scatter
     long long n_rew;
     int chains_ok, csteps_max;
 };

@@ -113,7 +113,12 @@ void launch_fit_prep(const Plan& P, int which, cudaStream_t s);
 void launch_rew_finalize(const Plan& P, cudaStream_t s);
 void launch_result(const Plan& P, rtd_result* dev_out, double* diag, cudaStream_t s);
 void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* rp,
-                       Status* st, cudaStream_t s);
+                       Status* st, cudaStream_t s, double* logdet_out = nullptr);
+// adjoint of steps 8-10 (rtd_rows.cu): slot count of the reduction pass
+constexpr int GRAD_SLOTS = 1024;
+void launch_grad(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
+                 const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,
+                 double w_rd, float* grad, int nsm, cudaStream_t s);
 
 // Gram partial layout: blocks (bi <= bj) of 4 x 4 over the extended vector
 // e = (v_0 .. v_{p-1}, 1, 0 ...) of length pe = pb + 4.

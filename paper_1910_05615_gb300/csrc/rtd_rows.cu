@@ -235,6 +235,11 @@ void launch_transform(const Plan& P, int which, cudaStream_t s) { (void)which; R
 void launch_dist(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist, P, s); }
 void launch_dist_win(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist_win, P, s); }
 void launch_band64(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, band64, P, s); }
+void launch_grad(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
+                 const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,
+                 double w_rd, float* grad, int nsm, cudaStream_t s) {
+    RTD_PB_CALL(pad_p(p), grad, X, n, p, ld, wset, wbit, rp, partial, slot_d, tot, c, w_ld, w_rd, grad, nsm, s);
+}
 void launch_memb(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, memb, P, s); }
 void launch_rew(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, rew, P, s); }
 void launch_member_gram(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, member_gram, P, s); }

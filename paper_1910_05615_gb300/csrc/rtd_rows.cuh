@@ -224,6 +224,16 @@ struct GramAcc {
     }
 };
 
+// out[e] = sum over slots s (in order) of partial[s * slot_d + e], e < nv.
+__global__ inline void k_sum_slots(const double* __restrict__ partial, int nslots, size_t slot_d, int nv,
+                                   double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nv) return;
+    double t = 0.0;
+    for (int s = 0; s < nslots; ++s) t += partial[(size_t)s * slot_d + e];
+    out[e] = t;
+}
+
 template <int PB, typename T>
 constexpr size_t gram_smem_bytes() {
     typedef GramShape<PB, T> S;
@@ -1220,6 +1230,174 @@ void rew_t(const Plan& P, cudaStream_t s) {
     k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb, P.precision == RTD_FP32, P.cs, P.fitrp + 0,
                            P.wset, P.partial, P.slot_doubles);
 }
+// =====================================================================
+// Adjoint of Section 4 steps 8-10 with the reweighting set W fixed:
+// f = w_ld log det Sigma + w_rd sum_j RD_j, mu = mean of W, Sigma = c S_W.
+// With r = x - mu, y = M r (M = L^-1, Sigma = L L^T), RD = |y| and
+// u = M^T y = Sigma^-1 r:
+//   pass 1: sum over all rows of (u, 1)(u, 1)^T / RD (so that
+//           G = -1/2 sum u u^T / RD and g = -sum u / RD), sum RD and |W|;
+//   pass 2: grad = w_rd (u / RD + [W] (g / N + a G r)) + w_ld [W] a u,
+//           a = 2 c / (N - 1).
+// Rows with RD = 0 take the zero subgradient of their own term.  FP32 row
+// arithmetic, FP64 cross-CTA sums.
+// =====================================================================
+template <int PB>
+__device__ __forceinline__ void grad_row(const float* __restrict__ sM, const float (&c)[PB], float (&u)[PB],
+                                         float& rd) {
+    // row i of M gives y_i = M_i. c and then its share M_ij y_i of u_j
+    float d2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < PB; ++j) u[j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+        float m[PB];
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            m[j] = sM[i * PB + j];
+            a = fmaf(m[j], c[j], a);
+        }
+        d2 = fmaf(a, a, d2);
+#pragma unroll
+        for (int j = 0; j <= i; ++j) u[j] = fmaf(m[j], a, u[j]);
+    }
+    rd = sqrtf(d2);
+}
+
+template <int PB>
+__device__ inline void grad_load_m(const RowParams& rp, int p, float* sM, float* s_hi, float* s_lo) {
+    for (int e = threadIdx.x; e < PB * PB; e += NT) {
+        const int i = e / PB, j = e % PB;
+        sM[e] = (i < p && j <= i) ? rp.Mf[i * PMAX + j] : 0.f;
+    }
+    for (int j = threadIdx.x; j < PB; j += NT) {
+        s_hi[j] = (j < p) ? rp.mu_hi[j] : 0.f;
+        s_lo[j] = (j < p) ? rp.mu_lo[j] : 0.f;
+    }
+}
+
+template <int PB>
+__global__ void __launch_bounds__(NT) k_grad_gram(const float* __restrict__ X, long long n, int p, long long ld,
+                                                  int vec4, const uint8_t* __restrict__ wset, int wbit,
+                                                  const RowParams* __restrict__ rp, double* __restrict__ partial,
+                                                  size_t slot_d) {
+    typedef GramShape<PB, float> S;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* tile = reinterpret_cast<float*>(smem);
+    float* wt = tile + S::TR * S::PE;
+    __shared__ float sM[PB * PB], s_hi[PB], s_lo[PB];
+    grad_load_m<PB>(*rp, p, sM, s_hi, s_lo);
+    __syncthreads();
+    GramAcc<PB, float> acc;
+    acc.init();
+    double rdsum = 0.0;
+    int nw = 0;
+    for (long long tb = (long long)blockIdx.x * S::TR; tb < n; tb += (long long)gridDim.x * S::TR) {
+        const long long row = tb + threadIdx.x;
+        const int k = (int)((n - tb) < S::TR ? (n - tb) : S::TR);
+        asm volatile("" ::: "memory");   // keep M in shared memory, not hoisted into registers
+        if (threadIdx.x < k) {
+            float x[PB], c[PB], u[PB], rd;
+            load_row_user<PB>(X + row * ld, p, vec4 != 0, x);
+#pragma unroll
+            for (int j = 0; j < PB; ++j) c[j] = (x[j] - s_hi[j]) - s_lo[j];
+            grad_row<PB>(sM, c, u, rd);
+            rdsum += (double)rd;
+            nw += (wset[row] >> wbit) & 1;
+            float* dst = tile + threadIdx.x * S::PE;
+#pragma unroll
+            for (int j = 0; j < PB; ++j) dst[j] = u[j];
+            dst[PB] = 0.f; dst[PB + 1] = 0.f; dst[PB + 2] = 0.f; dst[PB + 3] = 0.f;
+            dst[p] = 1.f;
+            wt[threadIdx.x] = rd > 0.f ? 1.f / rd : 0.f;
+        }
+        __syncthreads();
+        acc.rows(tile, wt, k);
+        __syncthreads();
+    }
+    double* slot = partial + (size_t)blockIdx.x * slot_d;
+    acc.store(reinterpret_cast<double*>(smem), slot);
+    // sum RD and |W|, fixed-order within the CTA
+    __shared__ double srd[NT / 32];
+    double v = warp_sum_d(rdsum);
+    const int nws = cta_sum_int(nw);
+    if ((threadIdx.x & 31) == 0) srd[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += srd[w];
+        slot[S::NBLK * 16] = t;
+        slot[S::NBLK * 16 + 1] = (double)nws;
+    }
+}
+
+template <int PB>
+__global__ void __launch_bounds__(NT) k_grad_rows(const float* __restrict__ X, long long n, int p, long long ld,
+                                                  int vec4, const uint8_t* __restrict__ wset, int wbit,
+                                                  const RowParams* __restrict__ rp, const double* __restrict__ tot,
+                                                  double c, double w_ld, double w_rd, float* __restrict__ grad) {
+    typedef GramShape<PB, float> S;
+    __shared__ float sM[PB * PB], sG[PB * PB], sg[PB], s_hi[PB], s_lo[PB];
+    grad_load_m<PB>(*rp, p, sM, s_hi, s_lo);
+    const int nb = S::NB;
+    for (int e = threadIdx.x; e < PB * PB; e += NT) {
+        const int i = e / PB, j = e % PB;
+        sG[e] = (i < p && j < p) ? (float)(-0.5 * gram_get(tot, i, j, nb)) : 0.f;
+    }
+    const double N = tot[S::NBLK * 16 + 1];
+    for (int j = threadIdx.x; j < PB; j += NT) sg[j] = (j < p) ? (float)(-gram_get(tot, j, p, nb) / N) : 0.f;
+    __syncthreads();
+    const float a = (float)(2.0 * c / (N - 1.0)), wl = (float)w_ld, wr = (float)w_rd;
+    for (long long row = (long long)blockIdx.x * NT + threadIdx.x; row < n; row += (long long)gridDim.x * NT) {
+        asm volatile("" ::: "memory");   // keep M and G in shared memory, not hoisted into registers
+        float x[PB], cc[PB], u[PB], rd;
+        load_row_user<PB>(X + row * ld, p, vec4 != 0, x);
+#pragma unroll
+        for (int j = 0; j < PB; ++j) cc[j] = (x[j] - s_hi[j]) - s_lo[j];
+        grad_row<PB>(sM, cc, u, rd);
+        const float inv = rd > 0.f ? 1.f / rd : 0.f;
+        const bool inW = (wset[row] >> wbit) & 1;
+        float* out = grad + row * p;
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+            if (k >= p) break;
+            float gk = wr * u[k] * inv;
+            if (inW) {
+                float gr = 0.f;
+#pragma unroll
+                for (int j = 0; j < PB; ++j) gr = fmaf(sG[k * PB + j], cc[j], gr);
+                gk += wr * (sg[k] + a * gr) + wl * a * u[k];
+            }
+            out[k] = gk;
+        }
+    }
+}
+
+template <int PB>
+void grad_t(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit, const RowParams* rp,
+            double* partial, size_t slot_d, double* tot, double c, double w_ld, double w_rd, float* grad, int nsm,
+            cudaStream_t s) {
+    typedef GramShape<PB, float> S;
+    const int vec4 = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    long long tiles = (n + S::TR - 1) / S::TR;
+    int g1 = (int)(tiles < 2LL * nsm ? tiles : 2LL * nsm);
+    if (g1 > GRAD_SLOTS) g1 = GRAD_SLOTS;
+    if (g1 < 1) g1 = 1;
+    const size_t sm = gram_smem_bytes<PB, float>();
+    auto k1 = k_grad_gram<PB>;
+    // static M (up to 16 KB) plus the dynamic tile can pass 48 KB: always opt in
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k1<<<g1, NT, sm, s>>>(X, n, p, ld, vec4, wset, wbit, rp, partial, slot_d);
+    const int nv = S::NBLK * 16 + 2;
+    k_sum_slots<<<(nv + 255) / 256, 256, 0, s>>>(partial, g1, slot_d, nv, tot);
+    if (grad) {
+        long long blocks = (n + NT - 1) / NT;
+        int g2 = (int)(blocks < 8LL * nsm ? blocks : 8LL * nsm);
+        k_grad_rows<PB><<<g2, NT, 0, s>>>(X, n, p, ld, vec4, wset, wbit, rp, tot, c, w_ld, w_rd, grad);
+    }
+}
+
 // =====================================================================
 // Final distances and flags (Section 4 step 10) for every row, original
 // order; also the scoring call (Section 6).

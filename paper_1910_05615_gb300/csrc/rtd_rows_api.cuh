@@ -11,6 +11,9 @@ namespace rtd {
     void dist_pb##N(const Plan& P, cudaStream_t s);                                                 \
     void dist_win_pb##N(const Plan& P, cudaStream_t s);                                             \
     void band64_pb##N(const Plan& P, cudaStream_t s);                                               \
+    void grad_pb##N(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,   \
+                    const RowParams* rp, double* partial, size_t slot_d, double* tot, double c,       \
+                    double w_ld, double w_rd, float* grad, int nsm, cudaStream_t s);                   \
     void memb_pb##N(const Plan& P, cudaStream_t s);                                                 \
     void rew_pb##N(const Plan& P, cudaStream_t s);                                                  \
     void member_gram_pb##N(const Plan& P, cudaStream_t s);                                          \

@@ -995,7 +995,7 @@ __global__ void __launch_bounds__(256) k_rew_finalize(Consts* cs, const RowParam
         double lam = gram_get(ext, i, j, nb) - si * sj / nw;
         cs->Sigma_rew[i * PMAX + j] = f * lam / (nw - 1.0) / (su[i] * su[j]);
     }
-    if (threadIdx.x == 0) cs->n_rew = (long long)(nw + 0.5);
+    if (threadIdx.x == 0) { cs->n_rew = (long long)(nw + 0.5); cs->f_rew = f; }
 }
 
 void launch_rew_finalize(const Plan& P, cudaStream_t s) {
@@ -1036,6 +1036,7 @@ __global__ void k_result(const Consts* __restrict__ cs, const Status* __restrict
         out->n_reweight = cs->n_rew;
         out->csteps_max = cs->csteps_max;
         out->chains_ok = cs->chains_ok;
+        out->c_rew = cs->f_rew;
     }
     if (!diag) return;
     for (int j = threadIdx.x; j < p; j += blockDim.x) { diag[j] = cs->mu_uni[j]; diag[p + j] = su[j]; }
@@ -1080,7 +1081,7 @@ void launch_result(const Plan& P, rtd_result* dev_out, double* diag, cudaStream_
 
 // Scoring: row parameters of a caller fit (X units, D = I).
 __global__ void __launch_bounds__(CT) k_score_prep(const double* __restrict__ mu, const double* __restrict__ S,
-                                                   int p, RowParams* rp, Status* st) {
+                                                   int p, RowParams* rp, Status* st, double* logdet_out) {
     extern __shared__ double sm[];
     double* A = sm;
     double* Li = sm + MAT;
@@ -1095,13 +1096,15 @@ __global__ void __launch_bounds__(CT) k_score_prep(const double* __restrict__ mu
     // mu_x = 0 + 1 * mu
     bool ok = make_rowparams(mu, Sp, zero, one, p, A, Li, *rp, &s_ld);
     if (!ok && threadIdx.x == 0) set_error(st, RTD_EDEGENERATE);
+    if (ok && logdet_out && threadIdx.x == 0) *logdet_out = s_ld;
 }
 
-void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* rp, Status* st, cudaStream_t s) {
+void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* rp, Status* st, cudaStream_t s,
+                       double* logdet_out) {
     size_t sm = 2 * MAT * sizeof(double);
     auto k = k_score_prep;
     big_smem(k, sm);
-    k<<<1, CT, sm, s>>>(mu, Sigma, p, rp, st);
+    k<<<1, CT, sm, s>>>(mu, Sigma, p, rp, st, logdet_out);
 }
 
 }  // namespace rtd

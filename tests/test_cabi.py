@@ -111,3 +111,27 @@ def test_fit_rejects_bad_warm_start(lib, case):
     res = m._Result()
     st = lib.rtdetmcd_fit(X.ctypes.data, n, p, p, h, ctypes.byref(o), None, 0, None, ctypes.byref(res), None, None)
     assert st == 1 and res.status == 1
+
+
+@pytest.mark.parametrize("case", ["host_x", "bad_c", "bad_wbit", "p_too_big", "one_row"])
+def test_grad_rejects_bad_arguments(lib, case):
+    """rtdetmcd_grad wants device rows and subset bytes, c > 0, a bit index
+    0..7, 1 <= p <= 64 and n >= 2; anything else is RTD_EINVAL."""
+    n, p, c, wbit = 100, 3, 1.2, 1
+    if case == "bad_c":
+        c = 0.0
+    elif case == "bad_wbit":
+        wbit = 8
+    elif case == "p_too_big":
+        p = 65
+    elif case == "one_row":
+        n = 1
+    X = np.zeros((n, p), np.float32)
+    w = np.full(n, 2, np.uint8)
+    mu, S = np.zeros(p), np.eye(p)
+    val = ctypes.c_double(0.0)
+    st = lib.rtdetmcd_grad(X.ctypes.data, n, p, p, w.ctypes.data, wbit, mu.ctypes.data, S.ctypes.data, c,
+                           1.0, 1.0, ctypes.byref(val), None, None, 0, None)
+    assert st == 1
+    ws = lib.rtdetmcd_grad_workspace_size(n, p)
+    assert (ws == 0) if case == "p_too_big" else (ws > 0 and ws % 256 == 0)
