@@ -56,9 +56,13 @@ extern "C" {
 /* arithmetic of the row passes (distances, Grams, sort keys) */
 #define RTD_FP64 0   /* plain FP64 form */
 #define RTD_FP32 1   /* FP32 row passes, FP64 p x p algebra, FP64 recompute near every threshold */
+#define RTD_BF16 2   /* the FP32 form with every Gram (starts, C-steps, reweighting) on the tensor
+                        cores: rows centred in FP32 and split into BF16 high and low parts, all four
+                        partial products with FP32 accumulation, FP64 sums every 4,096 rows;
+                        25 <= p <= 48 (RTD_EINVAL otherwise) */
 
 typedef struct {
-    int32_t  precision;            /* RTD_FP32 (default) or RTD_FP64 */
+    int32_t  precision;            /* RTD_FP32 (default), RTD_FP64 or RTD_BF16 */
     int32_t  omega;                /* eq. partitionsize, default 4096 */
     int32_t  q_override;           /* number of blocks; 0 = q = max(floor(n/(p omega)), 1) */
     int32_t  max_csteps;           /* C-step cap per start, default 100 */

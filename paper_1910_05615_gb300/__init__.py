@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = [
-    "RTD_FP32", "RTD_FP64", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
+    "RTD_FP32", "RTD_FP64", "RTD_BF16", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
     "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
     "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
     "rtdetmcd_grad_workspace_size", "rtdetmcd_objective",
@@ -27,6 +27,7 @@ __all__ = [
 
 RTD_FP64 = 0
 RTD_FP32 = 1
+RTD_BF16 = 2     # FP32 form with the Grams on the tensor cores (25 <= p <= 48)
 RTD_MAX_P = 64
 
 STATUS = {0: "RTD_OK", 1: "RTD_EINVAL", 2: "RTD_ENONFINITE", 3: "RTD_EILLCOND", 4: "RTD_EDEGENERATE",

@@ -35,7 +35,7 @@ struct Layout {
 
 struct Shape {
     long long n, h, ld;
-    int p, pb, q, m, hb, precision, cpb, key_bytes, max_steps;
+    int p, pb, q, m, hb, precision, cpb, key_bytes, max_steps, tc;
     size_t slot_doubles;
 };
 
@@ -66,7 +66,8 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (p < 1 || p > RTD_MAX_P) return RTD_EINVAL;
     if (n <= 2LL * p || n >= (1LL << 31)) return RTD_EINVAL;
     if (ld < p) return RTD_EINVAL;
-    if (o.precision != RTD_FP32 && o.precision != RTD_FP64) return RTD_EINVAL;
+    if (o.precision != RTD_FP32 && o.precision != RTD_FP64 && o.precision != RTD_BF16) return RTD_EINVAL;
+    if (o.precision == RTD_BF16 && (p < 25 || p > 48)) return RTD_EINVAL;
     if (o.omega < 1 || o.max_csteps < 1 || o.q_override < 0) return RTD_EINVAL;
     if (!(o.cutoff_q > 0.0 && o.cutoff_q < 1.0) || !(o.kappa_max > 1.0)) return RTD_EINVAL;
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
@@ -80,7 +81,9 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
         }
     }
     S.n = n; S.h = h; S.ld = ld; S.p = p; S.pb = pad_p(p);
-    S.precision = o.precision;
+    // the split-BF16 form is the FP32 form with its Grams on the tensor cores
+    S.precision = (o.precision == RTD_BF16) ? RTD_FP32 : o.precision;
+    S.tc = o.precision == RTD_BF16;
     S.max_steps = o.max_csteps;
     long long q = o.q_override ? o.q_override : n / ((long long)p * o.omega);
     if (q < 1) q = 1;
@@ -248,7 +251,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     Plan P;
     memset(&P, 0, sizeof(P));
     P.n = S.n; P.h = S.h; P.ld = S.ld; P.p = S.p; P.pb = S.pb; P.q = S.q; P.m = S.m; P.hb = S.hb;
-    P.precision = S.precision; P.cpb = S.cpb; P.max_steps = S.max_steps; P.key_bytes = S.key_bytes;
+    P.precision = S.precision; P.tc = S.tc; P.cpb = S.cpb; P.max_steps = S.max_steps; P.key_bytes = S.key_bytes;
     int dev = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     RTD_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -28,6 +28,7 @@ struct Plan {
     int p, pb, q, m, hb, precision, cpb, nsm, max_steps;
     int cpb_dist;           // CTAs per block of the distance and compaction passes
     int cpb_win;            // CTAs per block of the window-path distance pass
+    int tc;                 // Grams on the tensor cores (split-BF16 form)
     int key_bytes;          // 4 (FP32 form) or 8 (FP64 form) for refinement sorts
     Feistel F;
     // device buffers

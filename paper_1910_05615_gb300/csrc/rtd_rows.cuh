@@ -7,6 +7,7 @@
 #pragma once
 #include "rtd_internal.cuh"
 #include "rtd_async.cuh"
+#include "rtd_tc.cuh"
 
 namespace rtd {
 
@@ -249,6 +250,32 @@ inline void set_smem(K kernel, size_t bytes) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 __host__ __device__ constexpr inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ constexpr inline size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
+
+// Gram accumulator of a row kernel: CUDA-core GramAcc, or with TC the
+// tensor-core GramTC (FP32 rows, split-BF16 products) and the extra dynamic
+// shared memory it takes after the kernel's own.
+template <int PB, typename T, bool TC>
+struct GramPick {
+    typedef GramAcc<PB, T> type;
+    static constexpr size_t extra = 0;
+};
+template <int PB>
+struct GramPick<PB, float, true> {
+    typedef GramTC<PB, NT, GramShape<PB, float>::TR> type;
+    static constexpr size_t extra = 128 + (size_t)type::SMEM;
+};
+template <typename A>
+__device__ inline void gram_setup(A&, unsigned char*) {}
+template <int PB, int NTH, int TR>
+__device__ inline void gram_setup(GramTC<PB, NTH, TR>& a, unsigned char* region) {
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_err;
+    a.setup(region, &s_taddr, &s_bar, &s_err);
+}
+// widths whose tensor-core Gram variants are built (25 <= p <= 48)
+template <int PB> constexpr bool tc_width() { return PB == 32 || PB == 40 || PB == 48; }
 
 // row range of CTA b of block l
 __device__ inline void block_rows(int m, int cpb, int& r0, int& r1) {
@@ -354,7 +381,7 @@ __device__ inline T wrap_g(T z) {
     return (T)0;
 }
 
-template <int PB, typename T, typename K>
+template <int PB, typename T, typename K, bool TC = false>
 __global__ void __launch_bounds__(NT) k_start1(const float* __restrict__ Xp, int p, int m, int cpb,
                                                const Consts* __restrict__ cs, K* __restrict__ rkeys,
                                                double* __restrict__ partial, size_t slot_d) {
@@ -370,7 +397,8 @@ __global__ void __launch_bounds__(NT) k_start1(const float* __restrict__ Xp, int
     __syncthreads();
     int r0, r1;
     block_rows(m, cpb, r0, r1);
-    GramAcc<PB, T> acc;
+    typename GramPick<PB, T, TC>::type acc;
+    gram_setup(acc, smem + align128(gram_smem_bytes<PB, T>()));
     acc.init();
     for (int base = r0; base < r1; base += S::TR) {
         int row = base + threadIdx.x;
@@ -406,7 +434,7 @@ __global__ void __launch_bounds__(NT) k_start1(const float* __restrict__ Xp, int
     acc.store(reinterpret_cast<double*>(smem), partial + sl * slot_d);
 }
 
-template <int PB, typename T, typename K>
+template <int PB, typename T, typename K, bool TC = false>
 __global__ void __launch_bounds__(NT) k_start2(const float* __restrict__ Xp, int p, int m, int cpb,
                                                const Consts* __restrict__ cs, const double* __restrict__ gss,
                                                double* __restrict__ partial, size_t slot_d) {
@@ -423,7 +451,8 @@ __global__ void __launch_bounds__(NT) k_start2(const float* __restrict__ Xp, int
     const double A = gss[2 * blockIdx.y], B = gss[2 * blockIdx.y + 1];
     int r0, r1;
     block_rows(m, cpb, r0, r1);
-    GramAcc<PB, T> acc;
+    typename GramPick<PB, T, TC>::type acc;
+    gram_setup(acc, smem + align128(gram_smem_bytes<PB, T>()));
     acc.init();
     for (int base = r0; base < r1; base += S::TR) {
         int row = base + threadIdx.x;
@@ -463,19 +492,27 @@ __global__ void __launch_bounds__(NT) k_start2(const float* __restrict__ Xp, int
     acc.store(reinterpret_cast<double*>(smem), partial + sl * slot_d);
 }
 
-template <int PB, typename T, typename K>
+template <int PB, typename T, typename K, bool TC = false>
 void start1_t(const Plan& P, cudaStream_t s) {
-    size_t sm = gram_smem_bytes<PB, T>();
-    auto k = k_start1<PB, T, K>;
-    set_smem(k, sm);
+    if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
+        if (P.tc) { start1_t<PB, T, K, true>(P, s); return; }
+    }
+    size_t sm = TC ? align128(gram_smem_bytes<PB, T>()) + GramPick<PB, T, TC>::extra : gram_smem_bytes<PB, T>();
+    auto k = k_start1<PB, T, K, TC>;
+    if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else set_smem(k, sm);
     dim3 grid(P.cpb, P.q);
     k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb, P.cs, (K*)P.arenaA, P.partial, P.slot_doubles);
 }
-template <int PB, typename T, typename K>
+template <int PB, typename T, typename K, bool TC = false>
 void start2_t(const Plan& P, cudaStream_t s) {
-    size_t sm = gram_smem_bytes<PB, T>();
-    auto k = k_start2<PB, T, K>;
-    set_smem(k, sm);
+    if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
+        if (P.tc) { start2_t<PB, T, K, true>(P, s); return; }
+    }
+    size_t sm = TC ? align128(gram_smem_bytes<PB, T>()) + GramPick<PB, T, TC>::extra : gram_smem_bytes<PB, T>();
+    auto k = k_start2<PB, T, K, TC>;
+    if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else set_smem(k, sm);
     dim3 grid(P.cpb, P.q);
     k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb, P.cs, P.gss, P.partial, P.slot_doubles);
 }
@@ -1049,7 +1086,7 @@ constexpr size_t memb_smem_bytes() { return align16(gram_smem_bytes<PB, T>()) + 
 // is scanned first (membership from the key and, inside the FP32 band, from
 // the FP64 decision bit), the rows to add are listed in a fixed order, then
 // staged in tiles for the Gram.
-template <int PB, typename T>
+template <int PB, typename T, bool TC = false>
 __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const T* __restrict__ dkeys,
                                              int p, int m, int cpb, long long qm, int fp32,
                                              const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
@@ -1079,7 +1116,8 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
         __syncthreads();
         const T* keys = dkeys + (size_t)k * qm;
         uint8_t* mb = memb + (size_t)c * m;
-        GramAcc<PB, T> acc;
+        typename GramPick<PB, T, TC>::type acc;
+        gram_setup(acc, smem + align128(memb_smem_bytes<PB, T>()));
         acc.init(full ? S::G : 1);     // few swapped rows: one group, little FP64 reduction
         int nswap = 0;
         for (int c0 = r0; c0 < r1; c0 += MEMB_CHUNK) {
@@ -1143,11 +1181,15 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
     }
 }
 
-template <int PB, typename T>
+template <int PB, typename T, bool TC = false>
 void memb_t(const Plan& P, cudaStream_t s) {
-    size_t sm = memb_smem_bytes<PB, T>();
-    auto k = k_memb<PB, T>;
-    set_smem(k, sm);
+    if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
+        if (P.tc) { memb_t<PB, T, true>(P, s); return; }
+    }
+    size_t sm = TC ? align128(memb_smem_bytes<PB, T>()) + GramPick<PB, T, TC>::extra : memb_smem_bytes<PB, T>();
+    auto k = k_memb<PB, T, TC>;
+    if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else set_smem(k, sm);
     dim3 grid(P.cpb, P.q, 2);
     k<<<grid, NT, sm, s>>>(P.Xp, (const T*)P.dkeys, P.p, P.m, P.cpb, (long long)P.q * P.m,
                            P.precision == RTD_FP32, P.ch, P.rule, P.memb, P.swaps, P.partial,
@@ -1157,7 +1199,7 @@ void memb_t(const Plan& P, cudaStream_t s) {
 // Reweighting (Section 4 steps 8-9): rows of all blocks with
 // d2(raw) <= chi2_{p,q} enter the Gram of the reweighted estimate.
 // =====================================================================
-template <int PB, typename T>
+template <int PB, typename T, bool TC = false>
 __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p, int m, int cpb, int fp32,
                                             const Consts* __restrict__ cs, const RowParams* __restrict__ rp,
                                             uint8_t* __restrict__ wset, double* __restrict__ partial,
@@ -1183,7 +1225,8 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
     const T cut_lo = (T)(cut * (1.0 - BAND_EPS)), cut_hi = (T)(cut * (1.0 + BAND_EPS));
     int r0, r1;
     block_rows(m, cpb, r0, r1);
-    GramAcc<PB, T> acc;
+    typename GramPick<PB, T, TC>::type acc;
+    gram_setup(acc, smem + align128(align16(gram_smem_bytes<PB, T>()) + PB * PB * sizeof(T)));
     acc.init();
     for (int base = r0; base < r1; base += S::TR) {
         int row = base + threadIdx.x;
@@ -1221,11 +1264,16 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
     acc.store(reinterpret_cast<double*>(smem), partial + sl * slot_d);
 }
 
-template <int PB, typename T>
+template <int PB, typename T, bool TC = false>
 void rew_t(const Plan& P, cudaStream_t s) {
+    if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
+        if (P.tc) { rew_t<PB, T, true>(P, s); return; }
+    }
     size_t sm = align16(gram_smem_bytes<PB, T>()) + PB * PB * sizeof(T);
-    auto k = k_rew<PB, T>;
-    set_smem(k, sm);
+    if (TC) sm = align128(sm) + GramPick<PB, T, TC>::extra;
+    auto k = k_rew<PB, T, TC>;
+    if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else set_smem(k, sm);
     dim3 grid(P.cpb, P.q);
     k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb, P.precision == RTD_FP32, P.cs, P.fitrp + 0,
                            P.wset, P.partial, P.slot_doubles);

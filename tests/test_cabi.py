@@ -77,6 +77,24 @@ def test_fit_rejects_before_device_work(lib, n, p, ld, h, code):
     assert st == code and res.status == code
 
 
+@pytest.mark.parametrize("p", [24, 49])
+def test_bf16_form_width_range(lib, p):
+    """The tensor-core Gram form covers 25 <= p <= 48 only."""
+    import paper_1910_05615_gb300 as m
+    n = 20_000
+    X = np.zeros((n, p), np.float32)
+    o = m._Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision = m.RTD_BF16
+    res = m._Result()
+    st = lib.rtdetmcd_fit(X.ctypes.data, n, p, p, (3 * n) // 4, ctypes.byref(o), None, 0, None,
+                          ctypes.byref(res), None, None)
+    assert st == 1
+    assert lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o)) == 0
+    o.precision = m.RTD_FP32
+    assert lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o)) > 0
+
+
 def test_distances_rejects_bad_arguments(lib):
     X = np.zeros((10, 3), np.float32)
     mu = np.zeros(3)

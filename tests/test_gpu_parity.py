@@ -339,3 +339,52 @@ def test_grad_rejects_small_set(rtd):
     sub[:4] = 2                                   # |W| = p: singular covariance
     with pytest.raises(rtd.RtdError):
         rtd.rtdetmcd_grad(X, sub, fit["mu"], fit["Sigma"], fit["c_rew"])
+
+
+# --------------------------- split-BF16 form: Grams on the tensor cores
+BF16_TOL = 1e-3
+
+
+@pytest.mark.parametrize("n,p", [(400_000, 40), (200_003, 25), (200_003, 48)])
+def test_bf16_form_parity(rtd, n, p):
+    """Every Gram on tcgen05 (split-BF16 products, FP32 accumulation in
+    tensor memory, FP64 sums every 4,096 rows): mu and Sigma (raw and
+    reweighted) within 1e-3 relative of the FP64 oracle, and the same flags
+    outside a 1e-3 band around the cutoff (the distances inherit the scatter's
+    error)."""
+    fr = datagen.large_case(n=n, p=p, seed=5)
+    ref = O.fit(fr.X, fr.h)
+    got = rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, precision=rtd.RTD_BF16, subset=True)
+    assert got["q"] == ref.q
+    rep = {
+        "mu": rel_center(got["mu"], ref.mu, ref.Sigma),
+        "Sigma": rel_mat(got["Sigma"], ref.Sigma),
+        "mu_raw": rel_center(got["mu_raw"], ref.mu_raw, ref.Sigma_raw),
+        "Sigma_raw": rel_mat(got["Sigma_raw"], ref.Sigma_raw),
+        "logdet": abs(got["logdet"] - np.linalg.slogdet(ref.Sigma)[1]),
+    }
+    fl = to_np(got["flags"]).astype(bool)
+    band = np.abs(ref.d2 - ref.cutoff_d2) <= BF16_TOL * ref.cutoff_d2
+    rep["flag_mismatch"] = int(np.sum((fl != ref.flags) & ~band))
+    d2 = to_np(got["d2"]).astype(np.float64)
+    rep["d2"] = float(np.max(np.abs(d2 - ref.d2) / np.maximum(ref.d2, 1e-3)))
+    print(rep)
+    for k in ("mu", "Sigma", "mu_raw", "Sigma_raw"):
+        assert rep[k] <= BF16_TOL, rep
+    assert rep["flag_mismatch"] == 0, rep
+
+
+def test_bf16_form_matches_fp32_gram(rtd):
+    """The tensor-core Gram against the CUDA-core one on the same rows: with
+    both forms on the same fixed point, the raw fits differ by the Gram's
+    rounding only (split-BF16 products carry about 2^-16 relative error)."""
+    fr = datagen.large_case(n=300_000, p=32, seed=9)
+    X = torch.from_numpy(fr.X).cuda()
+    a = rtd.rtdetmcd_fit(X, fr.h, precision=rtd.RTD_FP32, subset=True)
+    b = rtd.rtdetmcd_fit(X, fr.h, precision=rtd.RTD_BF16, subset=True)
+    sa, sb = to_np(a["subset"]), to_np(b["subset"])
+    same = np.mean((sa & 1) == (sb & 1))
+    print({"same_subset_fraction": same, "Sigma_raw": rel_mat(b["Sigma_raw"], a["Sigma_raw"]),
+           "Sigma": rel_mat(b["Sigma"], a["Sigma"])})
+    assert same > 0.999
+    assert rel_mat(b["Sigma_raw"], a["Sigma_raw"]) <= 1e-4
