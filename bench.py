@@ -140,6 +140,70 @@ def adjoint_leg(rtd, torch, X, h, dev, stream, flush, peak, peak_kind, reps=20):
                          "peak_kind": peak_kind, "bytes_per_call": bytes_}}
 
 
+LARGE_N, LARGE_P = 10_000_000, 40
+
+
+def large_p_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind, reps=3):
+    """The large-p workload (n = 10,000,000, p = 40, 15% mixed contamination):
+    the split-BF16 form (every Gram on tcgen05) beside the FP32 and FP64
+    forms, with the BF16 and FP32 forms' errors against the FP64 form (which
+    holds 1e-9 against the FP64 oracle in the parity tests)."""
+    import numpy as np
+    fr = datagen.large_case(seed=0, n=LARGE_N, p=LARGE_P)
+    n, p, h = fr.X.shape[0], fr.X.shape[1], fr.h
+    X = torch.from_numpy(fr.X).to(dev)
+    del fr
+    out = {"workload": f"n={n:,} x p={p} float32 rows, h=floor(0.75n), 7.5% point outliers at 8 v_min "
+                       f"+ 7.5% cluster N(5 v_min, 0.1^2 I), cond(R)=100, seed 0"}
+    fits = {}
+    for name, prec in (("bf16", rtd.RTD_BF16), ("fp32", rtd.RTD_FP32), ("fp64", rtd.RTD_FP64)):
+        ws = torch.empty(rtd.rtdetmcd_workspace_size(n, p, precision=prec), dtype=torch.uint8, device=dev)
+        r = rtd.rtdetmcd_fit(X, h, precision=prec, workspace=ws, stream=stream.cuda_stream)   # warm-up
+        ts = []
+        for i in range(reps if name != "fp64" else 1):
+            flush.fill_(i & 255)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = rtd.rtdetmcd_fit(X, h, precision=prec, workspace=ws, stream=stream.cuda_stream,
+                                 profile=(name == "bf16" and i == 0))
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            if "profile" in r:
+                prof = r["profile"]
+        t = statistics.median(ts)
+        fits[name] = r
+        out[name] = {"ms_per_fit": t, "rows_per_s": n / (t / 1e3), "q": r["q"], "csteps": r["csteps_max"]}
+        del ws
+    ref = fits["fp64"]
+    d2ref = ref["d2"].double()
+    for name in ("bf16", "fp32"):
+        g = fits[name]
+        sc = np.sqrt(np.max(np.diag(ref["Sigma"])))
+        out[name]["err_vs_fp64"] = {
+            "mu": float(np.max(np.abs(g["mu"] - ref["mu"])) / sc),
+            "Sigma": float(np.max(np.abs(g["Sigma"] - ref["Sigma"])) / np.max(np.abs(ref["Sigma"]))),
+            "Sigma_raw": float(np.max(np.abs(g["Sigma_raw"] - ref["Sigma_raw"])) / np.max(np.abs(ref["Sigma_raw"]))),
+            "logdet_abs": abs(g["logdet"] - ref["logdet"]),
+            "d2_max_rel": float(((g["d2"].double() - d2ref).abs() / d2ref.clamp_min(1e-3)).max()),
+            "flags_differ": int((g["flags"] != ref["flags"]).sum()),
+        }
+    st = prof["stages"]
+    gram_ms = sum(st[k]["ms"] for k in ("starts", "cstep_update", "reweight"))
+    gram_by = sum(st[k]["bytes"] for k in ("starts", "cstep_update", "reweight"))
+    a = gram_by / (gram_ms / 1e3) / 1e9
+    out["bf16"]["gram_stages"] = {
+        "stages": "starts + cstep_update + reweight (the kernels holding the tcgen05 Gram)",
+        "ms_per_fit": gram_ms, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s",
+        "frac": a / peak, "peak_kind": peak_kind}
+    out["bf16_speedup_vs_fp32"] = out["fp32"]["ms_per_fit"] / out["bf16"]["ms_per_fit"]
+    out["bf16_speedup_vs_fp64"] = out["fp64"]["ms_per_fit"] / out["bf16"]["ms_per_fit"]
+    del X, fits, ref, d2ref
+    torch.cuda.empty_cache()
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -281,6 +345,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-score", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--form", default="fp32", choices=["fp32", "bf16"],
+                    help="form of the timed fits (the headline is fp32; bf16 needs 25 <= p <= 48)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -312,7 +379,8 @@ def main():
     X = torch.from_numpy(fr.X).to(dev)
     Xh = torch.from_numpy(fr.X).pin_memory()
     stream = torch.cuda.current_stream(dev)
-    ws32 = torch.empty(rtd.rtdetmcd_workspace_size(n, p), dtype=torch.uint8, device=dev)
+    FORM = rtd.RTD_BF16 if args.form == "bf16" else rtd.RTD_FP32
+    ws32 = torch.empty(rtd.rtdetmcd_workspace_size(n, p, precision=FORM), dtype=torch.uint8, device=dev)
     ws64 = (torch.empty(rtd.rtdetmcd_workspace_size(n, p, precision=rtd.RTD_FP64), dtype=torch.uint8,
                         device=dev) if args.fp64_steps > 0 else None)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -339,16 +407,16 @@ def main():
         return out, profs, last
 
     for _ in range(args.warmup):
-        fit(X, rtd.RTD_FP32, ws32)
+        fit(X, FORM, ws32)
     barrier()
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or str(local)
     clk = Clocks(gpu_index if gpu_index.isdigit() else local)
     time.sleep(0.3)
-    t32, _, r32 = timed(X, rtd.RTD_FP32, ws32, args.steps)
+    t32, _, r32 = timed(X, FORM, ws32, args.steps)
     barrier()
     clocks = clk.stop()
     # the same steps again with per-stage CUDA events on the fit's stream
-    tprof, prof32, _ = timed(X, rtd.RTD_FP32, ws32, args.steps, profile=True)
+    tprof, prof32, _ = timed(X, FORM, ws32, args.steps, profile=True)
     # plain FP64 form beside it
     t64 = []
     if args.fp64_steps > 0:
@@ -357,7 +425,7 @@ def main():
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        fit(Xh, rtd.RTD_FP32, ws32)
+        fit(Xh, FORM, ws32)
         te = []
         for i in range(max(3, args.steps // 2)):
             flush.fill_(i & 255)
@@ -365,7 +433,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rh = fit(Xh, rtd.RTD_FP32, ws32)
+            rh = fit(Xh, FORM, ws32)
             e1.record(stream)
             e1.synchronize()
             te.append(e0.elapsed_time(e1))
@@ -427,14 +495,17 @@ def main():
     scoring = None
     if not args.no_score:
         scoring = scoring_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind)
+    large = None
+    if not args.no_large:
+        large = large_p_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind)
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_leg(rtd, torch, X, h, dev, stream, flush, peak, peak_kind)
     line = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws_n, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "p": p, "h": h, "q": r32["q"], "form": "fp32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "bf16x2 products, f32 rows", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "p": p, "h": h, "q": r32["q"], "form": args.form,
                    "l2": "512 MiB write between timed steps (input 80 MB < L2)",
                    "parallelism": f"{ws_n} independent replica(s)"},
         "fp64_form": ({"value": n / (statistics.mean(t64) / 1e3), "unit": "rows/s",
@@ -444,7 +515,7 @@ def main():
         "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "scoring": scoring,
-        "adjoint": adjoint,
+        "adjoint": adjoint, "large_p": large,
         "n_flagged": r32["n_flagged"], "step_ms": t32,
     }
     print(json.dumps(line), flush=True)

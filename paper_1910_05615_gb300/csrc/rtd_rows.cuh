@@ -153,7 +153,7 @@ struct GramAcc {
     int since, bi, bj, g, ng;
     bool on;
     // ng groups of NBLK threads take interleaved rows (ng <= G)
-    __device__ void init(int groups = S::G) {
+    __device__ void init(int groups = S::G, bool = false) {
         int t = threadIdx.x;
         ng = groups;
         g = t / S::NBLK;
@@ -167,6 +167,18 @@ struct GramAcc {
 #pragma unroll
         for (int e = 0; e < 16; ++e) a32[e] = (T)0;
         since = 0;
+    }
+    // before the put() calls of a batch (the tensor-core variant waits there)
+    __device__ void begin() {}
+    // row `slot` of the batch tile: values v (zero beyond p), then the
+    // constant 1 at index p, weight w
+    __device__ void put(T* tile, T* wt, int slot, const T (&v)[PB], int p, T w) {
+        T* dst = tile + slot * S::PE;
+#pragma unroll
+        for (int j = 0; j < PB; ++j) dst[j] = v[j];
+        dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
+        dst[p] = (T)1;
+        wt[slot] = w;
     }
     __device__ void flush() {
         big.add(a32);
@@ -418,14 +430,8 @@ __global__ void __launch_bounds__(NT) k_start1(const float* __restrict__ Xp, int
         }
         int tot;
         int slot = cta_compact(pred, tot);
-        if (slot >= 0) {
-            T* dst = tile + slot * S::PE;
-#pragma unroll
-            for (int j = 0; j < PB; ++j) dst[j] = w[j];
-            dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
-            dst[p] = (T)1;
-            wt[slot] = (T)1;
-        }
+        acc.begin();
+        if (slot >= 0) acc.put(tile, wt, slot, w, p, (T)1);
         __syncthreads();
         acc.rows(tile, wt, tot);
         __syncthreads();
@@ -476,14 +482,8 @@ __global__ void __launch_bounds__(NT) k_start2(const float* __restrict__ Xp, int
         }
         int tot;
         int slot = cta_compact(pred, tot);
-        if (slot >= 0) {
-            T* dst = tile + slot * S::PE;
-#pragma unroll
-            for (int j = 0; j < PB; ++j) dst[j] = z[j];
-            dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
-            dst[p] = (T)1;
-            wt[slot] = xi2;
-        }
+        acc.begin();
+        if (slot >= 0) acc.put(tile, wt, slot, z, p, xi2);
         __syncthreads();
         acc.rows(tile, wt, tot);
         __syncthreads();
@@ -1118,7 +1118,7 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
         uint8_t* mb = memb + (size_t)c * m;
         typename GramPick<PB, T, TC>::type acc;
         gram_setup(acc, smem + align128(memb_smem_bytes<PB, T>()));
-        acc.init(full ? S::G : 1);     // few swapped rows: one group, little FP64 reduction
+        acc.init(full ? S::G : 1, !full);   // few swapped rows: one group; swapped-out rows subtract
         int nswap = 0;
         for (int c0 = r0; c0 < r1; c0 += MEMB_CHUNK) {
             uint8_t bb[MEMB_U];
@@ -1157,17 +1157,16 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
             __syncthreads();
             for (int b0 = 0; b0 < total; b0 += S::TR) {
                 const int nbat = min(S::TR, total - b0);
+                acc.begin();
                 if (threadIdx.x < nbat) {
                     const int e = lst[b0 + threadIdx.x];
                     const int row = e & 0x7fffffff;
                     float x[PB];
                     load_row_padded<PB>(Xp + (size_t)row * PB, x);
-                    T* dst = tile + threadIdx.x * S::PE;
+                    T v[PB];
 #pragma unroll
-                    for (int j = 0; j < PB; ++j) dst[j] = ((T)x[j] - s_hi[j]) - s_lo[j];
-                    dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
-                    dst[p] = (T)1;
-                    wt[threadIdx.x] = (e < 0) ? (T)-1 : (T)1;
+                    for (int j = 0; j < PB; ++j) v[j] = ((T)x[j] - s_hi[j]) - s_lo[j];
+                    acc.put(tile, wt, threadIdx.x, v, p, (e < 0) ? (T)-1 : (T)1);
                 }
                 __syncthreads();
                 acc.rows(tile, wt, nbat);
@@ -1248,14 +1247,8 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
         }
         int tot;
         int slot = cta_compact(in, tot);
-        if (slot >= 0) {
-            T* dst = tile + slot * S::PE;
-#pragma unroll
-            for (int j = 0; j < PB; ++j) dst[j] = c[0][j];
-            dst[PB] = (T)0; dst[PB + 1] = (T)0; dst[PB + 2] = (T)0; dst[PB + 3] = (T)0;
-            dst[p] = (T)1;
-            wt[slot] = (T)1;
-        }
+        acc.begin();
+        if (slot >= 0) acc.put(tile, wt, slot, c[0], p, (T)1);
         __syncthreads();
         if (tot) acc.rows(tile, wt, tot);
         __syncthreads();

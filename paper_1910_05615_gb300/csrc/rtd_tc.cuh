@@ -1,16 +1,15 @@
 // rtd_tc.cuh - fifth-generation tensor-core (tcgen05) Gram accumulation for
-// the split-BF16 form (Section 3.4's mean and scatter of a subset, with the
-// rows' products taken on the tensor cores).
+// the split-BF16 form (the mean and scatter of a subset, Section 3.4, with
+// the rows' products taken on the tensor cores).
 //
-// Every row e (centred in FP32) is split as e = e_hi + e_lo with
-// e_hi = bf16(e) and e_lo = bf16(e - e_hi) (16 significant bits together);
-// the weighted row a = w e is split the same way.  One 16-row step issues
-//   D1 += [a_hi]^T [e_hi | e_lo]      D2 += [a_lo]^T [e_hi | e_lo]
-// (M = 128 lanes, features on the lanes; N = 2H columns, K = 16 rows), so
-// that D1 + D2 holds all four products hi*hi, hi*lo, lo*hi, lo*lo with FP32
-// accumulation in tensor memory.  Every FLUSH_ROWS rows the accumulators are
-// read back and added to an FP64 copy in shared memory, which bounds the FP32
-// accumulation error to that many rows.
+// Every weighted row a = sqrt(w) e (centred in FP32) is split as
+// a = a_hi + a_lo, a_hi = bf16(a), a_lo = bf16(a - a_hi) (16 significant
+// bits together).  One 16-row step issues D += [a_hi | a_lo]^T [a_hi | a_lo]
+// (M = 128 lanes, features on the lanes; N = 2H columns, K = 16 rows), whose
+// four H x H quadrants are the products hi*hi, hi*lo, lo*hi and lo*lo, with
+// FP32 accumulation in tensor memory.  Every FLUSH_ROWS rows the accumulators
+// are read back and summed into an FP64 copy in shared memory, which bounds
+// the FP32 accumulation error to that many rows.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -38,9 +37,11 @@ __device__ inline void tmem_dealloc(uint32_t taddr, unsigned ncols) {
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, K-major, no swizzle: 8-row x 16-byte core
-// matrices; `lbo` = byte distance between the two core matrices of a row
-// group along K, `sbo` = byte distance between successive 8-row groups.
+// Shared-memory matrix descriptor without swizzle; core matrices are 8 rows
+// of 16 bytes.  K-major operands: `lbo` = byte distance between core
+// matrices along K, `sbo` = between successive 8-row groups along M/N.
+// MN-major operands: `lbo` = byte distance between successive 8-row groups
+// along K, `sbo` = between core matrices along M/N.
 __device__ inline uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
@@ -56,6 +57,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
            | (1u << 7) | (1u << 10)       // A, B format: BF16
            | ((uint32_t)(N >> 3) << 17)   // N / 8
            | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+// the same with both operands MN-major (transpose bits of A and B)
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ inline void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool acc) {
@@ -97,45 +103,55 @@ __device__ inline void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& 
 }
 
 // ---------------------------------------------------------------- GramTC
-// Drop-in for GramAcc<PB, float> (same rows()/store() contract, same slot
-// layout) for 25 <= p <= 48.  Needs SMEM bytes of dynamic shared memory
-// (16-byte aligned) handed over by setup(), and 256 tensor-memory columns.
+// Drop-in for GramAcc<PB, float> (same put()/rows()/store() contract, same
+// slot layout) for 25 <= p <= 48.  Rows are put by the threads that hold
+// them: a = sqrt(|w|) (v, 1, 0 ...) is split into BF16 high and low parts
+// and written as the MN-major operand [a_hi | a_lo] (2H features) of one
+// 16-row step.  The same buffer serves as A (M = 128 lanes: a_hi on lanes
+// 0 .. H-1, a_lo on lanes H .. 2H-1, the rest unused) and as B (N = 2H), so
+// one MMA per step accumulates all four partial products.  Rows of negative
+// weight (signed mode) go to a second buffer and accumulator, subtracted at
+// the flush.  Needs SMEM bytes of dynamic shared memory (16-byte aligned)
+// handed over by setup(), and 128 (256 signed) tensor-memory columns.
 template <int PB, int NTH, int TROWS>
 struct GramTC {
     static constexpr int PE = PB + 4;
-    static constexpr int H = ((PB + 1) + 15) / 16 * 16;     // features on lanes (>= p + 1)
-    static constexpr int N = 2 * H;                         // [e_hi | e_lo]
+    static constexpr int H = ((PB + 1) + 7) / 8 * 8;        // features incl. the constant (>= p + 1)
+    static constexpr int N = 2 * H;                         // [a_hi | a_lo]
     static constexpr int TR = TROWS;                        // rows per rows() call, at most
-    static constexpr int KS = TR / 16;                      // 16-row MMA steps per call
-    static constexpr int KSTEP = 128 * H;                   // bytes per step: A_hi, A_lo (H rows), B (2H rows)
-    static constexpr int OPS = KS * KSTEP;
+    static constexpr int GROUP = 32 * H;                    // bytes per 8 rows: 2H/8 chunks of 8 rows x 16 B
+    static constexpr int OPS1 = TR / 8 * GROUP;             // one operand buffer
+    static constexpr int PAD = 2048;                        // A reads 16 chunks past each group start
     static constexpr int ACC_LD = H + 1;                    // FP64 row stride (bank spread)
-    static constexpr int SMEM = OPS + H * ACC_LD * 8;
-    static constexpr unsigned TCOLS = 256;
+    static constexpr int SMEM = 2 * OPS1 + PAD + H * ACC_LD * 8;
     static constexpr int FLUSH_ROWS = 4096;
-    static_assert(H >= 48 && H <= 64, "tensor-core Gram covers 25 <= p <= 63");
+    static_assert(N <= 128 && N % 16 == 0, "features on at most 128 lanes, N a multiple of 16");
     static_assert(TR % 16 == 0, "tile rows must be a multiple of 16");
-    static_assert(4 * H <= (int)TCOLS, "tensor memory columns");
 
     unsigned char* ops;
     double* acc;
     uint32_t* s_taddr;
     uint64_t* bar;
+    int* err;           // shared failure flag
     unsigned phase;
-    int pending;       // a commit not yet waited for
-    int since;         // rows in the tensor-memory accumulators
-    int fresh;         // next MMA starts the accumulators
-    int* err;          // shared failure flag
+    unsigned tcols;
+    int pending;        // a commit not yet waited for
+    int since;          // rows in the tensor-memory accumulators
+    int fresh;          // next MMA starts the accumulators
+    int sgn;            // signed mode: negative weights allowed
 
     __device__ void setup(unsigned char* region, uint32_t* taddr_slot, uint64_t* mbar, int* err_flag) {
         ops = region;
-        acc = reinterpret_cast<double*>(region + OPS);
+        acc = reinterpret_cast<double*>(region + 2 * OPS1 + PAD);
         s_taddr = taddr_slot;
         bar = mbar;
         err = err_flag;
     }
 
-    __device__ void init(int = 0) {
+    // all threads; signed_rows: some rows may carry negative weights
+    __device__ void init(int = 0, bool signed_rows = false) {
+        sgn = signed_rows ? 1 : 0;
+        tcols = sgn ? 256u : 128u;
         for (int e = threadIdx.x; e < H * ACC_LD; e += NTH) acc[e] = 0.0;
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
@@ -143,7 +159,7 @@ struct GramTC {
             *err = 0;
         }
         if (threadIdx.x < 32) {
-            tmem_alloc(s_taddr, TCOLS);
+            tmem_alloc(s_taddr, tcols);
             tmem_relinquish();
         }
         tc_fence_before();
@@ -165,27 +181,36 @@ struct GramTC {
         tc_fence_after();
     }
 
-    // tensor memory -> FP64 accumulators (rows owned by lanes 0 .. H-1)
+    // tensor memory -> FP64 accumulators: lanes L < H hold a_hi rows, lanes
+    // H <= L < 2H the a_lo rows of the same features; both add into row L % H
+    // (in two phases, so that each FP64 row has one writer at a time)
     __device__ void flush() {
         wait_mma();
         if (!fresh) {
             const int w = threadIdx.x >> 5;
-            if (w < 2) {
-                const uint32_t base = *s_taddr + ((uint32_t)(w * 32) << 16);
-                const int i = threadIdx.x;       // lane = feature row
-                double* arow = acc + i * ACC_LD;
+            const int L = threadIdx.x;
+            for (int ph = 0; ph < 2; ++ph) {
+                if (w < 4) {
+                    const uint32_t base = *s_taddr + ((uint32_t)(w * 32) << 16);
+                    const bool mine = (ph == 0) ? (L < H) : (L >= H && L < 2 * H);
+                    double* arow = acc + (L % H) * ACC_LD;
 #pragma unroll 1
-                for (int c0 = 0; c0 < 4 * H; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(base + (uint32_t)c0, v);
-                    if (i < H) {
+                    for (int c0 = 0; c0 < N; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(base + (uint32_t)c0, v);
+                        if (sgn) {
+                            float vn[16];
+                            tmem_ld16(base + (uint32_t)(N + c0), vn);
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int j = (c0 + u) % H;
-                            arow[j] += (double)v[u];
+                            for (int u = 0; u < 16; ++u) v[u] -= vn[u];
+                        }
+                        if (mine) {
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) arow[(c0 + u) % H] += (double)v[u];
                         }
                     }
                 }
+                __syncthreads();
             }
             tc_fence_before();
         }
@@ -195,47 +220,67 @@ struct GramTC {
         fresh = 1;
     }
 
-    // k rows of PE floats at tile (k <= TR), weights wt
-    __device__ void rows(const float* tile, const float* wt, int k) {
-        if (k <= 0) return;
-        if (since + k > FLUSH_ROWS) flush();
-        else wait_mma();                 // operand buffers free again
-        const int nks = (k + 15) >> 4;
-        const int items = H * nks * 2;   // (feature, 8-row chunk)
-        for (int it = threadIdx.x; it < items; it += NTH) {
-            const int j = it % H, c = it / H;
-            uint32_t ah[4], al[4], bh[4], bl[4];
+    // all threads, before the put() calls of a batch: operand buffers free
+    __device__ void begin() {
+        if (since + TR > FLUSH_ROWS) flush();
+        else wait_mma();
+    }
+
+    // one thread: row `slot` (< TR) of the batch, centred values v (zero
+    // beyond p), weight w
+    __device__ void put(float*, float*, int slot, const float (&v)[PB], int p, float w) {
+        const float sw = sqrtf(fabsf(w));
+        unsigned char* dst = ops + ((sgn && w < 0.f) ? OPS1 : 0) + (slot >> 3) * GROUP + (slot & 7) * 16;
+#pragma unroll
+        for (int g = 0; g < H / 8; ++g) {
+            uint32_t hi[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int r0 = 8 * c + 2 * q, r1 = r0 + 1;
-                float e0 = 0.f, e1 = 0.f, w0 = 0.f, w1 = 0.f;
-                if (j < PE) {
-                    if (r0 < k) { e0 = tile[r0 * PE + j]; w0 = wt[r0]; }
-                    if (r1 < k) { e1 = tile[r1 * PE + j]; w1 = wt[r1]; }
-                }
-                split_bf16x2(w0 * e0, w1 * e1, ah[q], al[q]);
-                split_bf16x2(e0, e1, bh[q], bl[q]);
+                const int j0 = 8 * g + 2 * q, j1 = j0 + 1;
+                const float a0 = (j0 < PB ? v[j0 < PB ? j0 : 0] : 0.f) * sw + (j0 == p ? sw : 0.f);
+                const float a1 = (j1 < PB ? v[j1 < PB ? j1 : 0] : 0.f) * sw + (j1 == p ? sw : 0.f);
+                split_bf16x2(a0, a1, hi[q], lo[q]);
             }
-            unsigned char* step = ops + (c >> 1) * KSTEP;
-            const int off = (j >> 3) * 256 + (c & 1) * 128 + (j & 7) * 16;
-            *reinterpret_cast<uint4*>(step + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-            *reinterpret_cast<uint4*>(step + 32 * H + off) = make_uint4(al[0], al[1], al[2], al[3]);
-            *reinterpret_cast<uint4*>(step + 64 * H + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
-            *reinterpret_cast<uint4*>(step + 96 * H + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+            *reinterpret_cast<uint4*>(dst + g * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(dst + (H / 8 + g) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        if (sgn) {   // the other buffer's copy of this slot is zero
+            unsigned char* z = ops + ((w < 0.f) ? 0 : OPS1) + (slot >> 3) * GROUP + (slot & 7) * 16;
+#pragma unroll
+            for (int g = 0; g < 2 * H / 8; ++g) *reinterpret_cast<uint4*>(z + g * 128) = make_uint4(0, 0, 0, 0);
+        }
+    }
+
+    // all threads, after the put() calls: k rows were put (slots 0 .. k-1)
+    __device__ void rows(const float*, const float*, int k) {
+        if (k <= 0) return;
+        const int nks = (k + 15) >> 4;
+        const int kpad = nks * 16;
+        const int nbuf = sgn ? 2 : 1;
+        // zero rows k .. kpad-1 of the last step
+        for (int e = threadIdx.x; e < (kpad - k) * (2 * H / 8) * nbuf; e += NTH) {
+            const int per = (kpad - k) * (2 * H / 8);
+            const int b = e / per, r = e % per;
+            const int slot = k + r / (2 * H / 8), g = r % (2 * H / 8);
+            *reinterpret_cast<uint4*>(ops + b * OPS1 + (slot >> 3) * GROUP + (slot & 7) * 16 + g * 128) =
+                make_uint4(0, 0, 0, 0);
         }
         async_proxy_fence();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc_fence_after();
             const uint32_t t = *s_taddr;
-            const uint32_t id = idesc_bf16(128, N);
+            const uint32_t id = idesc_bf16_mn(128, N);
             const uint32_t base = smem_addr(ops);
             for (int s = 0; s < nks; ++s) {
-                const uint32_t a = base + (uint32_t)(s * KSTEP);
-                const uint64_t bd = smem_desc(a + 64 * H, 128, 256);
                 const bool accum = !(fresh && s == 0);
-                mma_bf16(t, smem_desc(a, 128, 256), bd, id, accum);
-                mma_bf16(t + (uint32_t)N, smem_desc(a + 32 * H, 128, 256), bd, id, accum);
+                const uint32_t a = base + (uint32_t)(s * 2 * GROUP);
+                const uint64_t d = smem_desc(a, GROUP, 128);
+                mma_bf16(t, d, d, id, accum);
+                if (sgn) {
+                    const uint64_t dn = smem_desc(a + OPS1, GROUP, 128);
+                    mma_bf16(t + (uint32_t)N, dn, dn, id, accum);
+                }
             }
             mma_commit(bar);
         }
@@ -261,7 +306,7 @@ struct GramTC {
             slot[e] = ((i < H && j < H) ? acc[i * ACC_LD + j] : 0.0) + bad;
         }
         __syncthreads();
-        if (threadIdx.x < 32) tmem_dealloc(*s_taddr, TCOLS);
+        if (threadIdx.x < 32) tmem_dealloc(*s_taddr, tcols);
     }
 };
 
