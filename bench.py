@@ -140,6 +140,56 @@ def adjoint_leg(rtd, torch, X, h, dev, stream, flush, peak, peak_kind, reps=20):
                          "peak_kind": peak_kind, "bytes_per_call": bytes_}}
 
 
+BATCH_FRAMES = 4096
+
+
+def batched_leg(rtd, torch, datagen, dev, stream, nstreams=16, reps=2):
+    """Many independent frames (n ~ U[2000, 50000], p ~ U{8, 16, 24, 32, 40},
+    0-25% point outliers at 10 v_min, each fitted with q = 1) through
+    rtdetmcd_fit_batch.  Frames are drawn on the device: N(0, R) rows with R
+    the frame's seeded random correlation matrix (condition 100), outlier
+    rows at seeded random positions set to 10 v_min."""
+    import numpy as np
+    g = torch.Generator(device=dev)
+    frames, hs = [], []
+    for f in range(BATCH_FRAMES):
+        rng = np.random.default_rng(10_000 + f)
+        n = int(rng.integers(2000, 50001))
+        p = int(rng.choice([8, 16, 24, 32, 40]))
+        eps = float(rng.uniform(0.0, 0.25))
+        R, v = datagen.random_correlation(p, 100.0, rng)
+        C = torch.linalg.cholesky(torch.from_numpy(R)).to(dev, torch.float32)
+        g.manual_seed(f)
+        X = torch.randn(n, p, generator=g, device=dev) @ C.T
+        k = int(np.floor(eps * n))
+        if k:
+            pos = torch.randperm(n, generator=g, device=dev)[:k]
+            X[pos] = (10.0 * torch.from_numpy(v)).to(dev, torch.float32)
+        frames.append(X.contiguous())
+        hs.append(int(np.floor(0.75 * n)))
+    rows = sum(int(X.shape[0]) for X in frames)
+    ws = torch.empty(rtd.rtdetmcd_fit_batch_workspace_size(frames, nstreams), dtype=torch.uint8, device=dev)
+    rtd.rtdetmcd_fit_batch(frames, hs, nstreams=nstreams, workspace=ws, stream=stream.cuda_stream)   # warm-up
+    ts = []
+    for i in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = rtd.rtdetmcd_fit_batch(frames, hs, nstreams=nstreams, workspace=ws, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    t = statistics.median(ts)
+    res = {"workload": f"{BATCH_FRAMES} frames, n ~ U[2000, 50000], p ~ U{{8,16,24,32,40}}, 0-25% point "
+                       f"outliers at 10 v_min, FP32 form, q = 1 per frame ({rows:,} rows, inputs larger than L2)",
+           "frames_per_s": BATCH_FRAMES / (t / 1e3), "rows_per_s": rows / (t / 1e3), "ms_per_batch": t,
+           "nstreams": nstreams, "flagged_total": int(sum(o["n_flagged"] for o in out)),
+           "form": "concurrent single fits on streams (host worker threads), not yet one persistent launch"}
+    del frames, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 LARGE_N, LARGE_P = 10_000_000, 40
 
 
@@ -346,6 +396,7 @@ def main():
     ap.add_argument("--no-score", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16"],
                     help="form of the timed fits (the headline is fp32; bf16 needs 25 <= p <= 48)")
     args = ap.parse_args()
@@ -495,6 +546,9 @@ def main():
     scoring = None
     if not args.no_score:
         scoring = scoring_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind)
+    batched = None
+    if not args.no_batch:
+        batched = batched_leg(rtd, torch, datagen, dev, stream)
     large = None
     if not args.no_large:
         large = large_p_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind)
@@ -515,7 +569,7 @@ def main():
         "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "scoring": scoring,
-        "adjoint": adjoint, "large_p": large,
+        "adjoint": adjoint, "large_p": large, "batched": batched,
         "n_flagged": r32["n_flagged"], "step_ms": t32,
     }
     print(json.dumps(line), flush=True)

@@ -186,6 +186,37 @@ int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h,
                  const rtd_options* opt, void* workspace, size_t ws_bytes,
                  void* stream, rtd_result* out, float* d2_out, uint8_t* flags_out);
 
+/* Largest number of concurrent streams of rtdetmcd_fit_batch. */
+#define RTD_BATCH_MAX_STREAMS 64
+
+/* Bytes of workspace rtdetmcd_fit_batch needs: one slice per stream, each
+   sized for the largest frame (h taken at its lower bound does not change the
+   size). */
+size_t rtdetmcd_fit_batch_workspace_size(int32_t nframes, const int64_t* n, const int32_t* p,
+                                         const rtd_options* opt, int32_t nstreams);
+
+/*
+ * Many independent fits (Section 4 steps 1-10 each), as in a sorting line
+ * that scores frames of uneven size: frame f has n[f] rows of p[f] columns,
+ * row stride ld[f], coverage h[f].  The frames run concurrently on nstreams
+ * streams (1 .. RTD_BATCH_MAX_STREAMS), each with its own workspace slice;
+ * host threads take the frames in order from a shared counter.  The work
+ * starts after everything earlier on `stream` and the call returns when every
+ * frame is done.
+ *   X[f]        device or host rows of frame f
+ *   opt         shared by all frames; its subset_out, diag_out and profile
+ *               are ignored
+ *   out         nframes results (host)
+ *   d2_out, flags_out  nullable arrays of nframes nullable per-frame outputs
+ * Every frame is validated before any device work: RTD_EINVAL (with the
+ * offending frames' out[f].status set) if any is invalid.  Otherwise returns
+ * RTD_OK or the first nonzero frame status in frame order.
+ */
+int rtdetmcd_fit_batch(int32_t nframes, const float* const* X, const int64_t* n, const int32_t* p,
+                       const int64_t* ld, const int64_t* h, const rtd_options* opt,
+                       void* workspace, size_t ws_bytes, void* stream, int32_t nstreams,
+                       rtd_result* out, float* const* d2_out, uint8_t* const* flags_out);
+
 /* Bytes of workspace rtdetmcd_distances needs. */
 size_t rtdetmcd_distances_workspace_size(int64_t n, int32_t p);
 

@@ -22,7 +22,8 @@ __all__ = [
     "RTD_FP32", "RTD_FP64", "RTD_BF16", "RtdError", "library_path", "rtdetmcd_fit", "rtdetmcd_distances",
     "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
     "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
-    "rtdetmcd_grad_workspace_size", "rtdetmcd_objective",
+    "rtdetmcd_grad_workspace_size", "rtdetmcd_objective", "rtdetmcd_fit_batch",
+    "rtdetmcd_fit_batch_workspace_size",
 ]
 
 RTD_FP64 = 0
@@ -105,6 +106,12 @@ def _load():
     lib.rtdetmcd_distances.restype = i32
     lib.rtdetmcd_distances_noalloc.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp]
     lib.rtdetmcd_distances_noalloc.restype = i32
+    P64, P32 = ctypes.POINTER(i64), ctypes.POINTER(i32)
+    lib.rtdetmcd_fit_batch_workspace_size.argtypes = [i32, P64, P32, vp, i32]
+    lib.rtdetmcd_fit_batch_workspace_size.restype = sz
+    lib.rtdetmcd_fit_batch.argtypes = [i32, ctypes.POINTER(vp), P64, P32, P64, P64, vp, vp, sz, vp, i32,
+                                       vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.rtdetmcd_fit_batch.restype = i32
     lib.rtdetmcd_grad_workspace_size.argtypes = [i64, i32]
     lib.rtdetmcd_grad_workspace_size.restype = sz
     lib.rtdetmcd_grad.argtypes = [vp, i64, i32, i64, vp, i32, vp, vp, dbl, dbl, dbl, ctypes.POINTER(dbl), vp,
@@ -260,6 +267,71 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
                           "sel_cand": prof.sel_cand, "sel_band": prof.sel_band, "stages": {
             name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i]}
             for i, name in enumerate(STAGES)}}
+    return out
+
+
+def rtdetmcd_fit_batch_workspace_size(frames, nstreams=8, precision=RTD_FP32):
+    """Workspace bytes of rtdetmcd_fit_batch for these frames (2-D arrays or
+    tensors, only their shapes are used)."""
+    lib = _load()
+    F = len(frames)
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision = precision
+    n = (ctypes.c_int64 * F)(*[int(X.shape[0]) for X in frames])
+    p = (ctypes.c_int32 * F)(*[int(X.shape[1]) for X in frames])
+    return lib.rtdetmcd_fit_batch_workspace_size(F, n, p, ctypes.byref(o), nstreams)
+
+
+def rtdetmcd_fit_batch(frames, hs, *, precision=RTD_FP32, nstreams=8, d2=True, flags=True, stream=None,
+                       workspace=None, check=True, **opts):
+    """Independent fits of many frames of uneven n and p (each frame a 2-D
+    float32 array or tensor, all on the same CUDA device or all in host
+    memory), run concurrently on `nstreams` streams.  Returns a list of
+    per-frame dicts (reweighted and raw fits, counts, status, d2 and flags)."""
+    lib = _load()
+    F = len(frames)
+    if F < 1 or len(hs) != F:
+        raise ValueError("need one h per frame")
+    rows = [_rows(Xf) for Xf in frames]
+    devs = {r[4] for r in rows}
+    if len(devs) != 1:
+        raise ValueError("frames must all be on one CUDA device or all in host memory")
+    dev = rows[0][4]
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision = precision
+    for k, v in opts.items():
+        setattr(o, k, v)
+    Xp = (ctypes.c_void_p * F)(*[r[0] for r in rows])
+    n = (ctypes.c_int64 * F)(*[r[1] for r in rows])
+    p = (ctypes.c_int32 * F)(*[r[2] for r in rows])
+    ld = (ctypes.c_int64 * F)(*[r[3] for r in rows])
+    h = (ctypes.c_int64 * F)(*[int(x) for x in hs])
+    need = lib.rtdetmcd_fit_batch_workspace_size(F, n, p, ctypes.byref(o), nstreams)
+    if need == 0:
+        raise RtdError(1, "invalid frame shape, options or stream count")
+    ws = workspace if workspace is not None else _workspace(need, dev)
+    d2s = [_out(r[1], np.float32, dev) for r in rows] if d2 else None
+    fls = [_out(r[1], np.uint8, dev) for r in rows] if flags else None
+    d2p = (ctypes.c_void_p * F)(*[_ptr(a) for a in d2s]) if d2 else None
+    flp = (ctypes.c_void_p * F)(*[_ptr(a) for a in fls]) if flags else None
+    res = (_Result * F)()
+    st = lib.rtdetmcd_fit_batch(F, Xp, n, p, ld, h, ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                                _stream_ptr(dev, stream), nstreams, res, d2p, flp)
+    del rows
+    if st != 0 and check:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    out = []
+    for f in range(F):
+        r, pp = res[f], p[f]
+        out.append({
+            "status": r.status, "n": r.n, "p": r.p, "q": r.q, "h": r.h,
+            "mu": np.array(r.mu[:pp]), "Sigma": np.array(r.sigma[:pp * pp]).reshape(pp, pp),
+            "mu_raw": np.array(r.mu_raw[:pp]), "Sigma_raw": np.array(r.sigma_raw[:pp * pp]).reshape(pp, pp),
+            "logdet": r.logdet, "cutoff_d2": r.cutoff_d2, "n_flagged": r.n_flagged, "n_reweight": r.n_reweight,
+            "csteps_max": r.csteps_max, "c_rew": r.c_rew,
+            "d2": d2s[f] if d2 else None, "flags": fls[f] if flags else None})
     return out
 
 

@@ -1,5 +1,7 @@
 #include <vector>
 #include <cmath>
+#include <atomic>
+#include <thread>
 // rtd_api.cu - C ABI entry points and host orchestration of RT-DetMCD.
 //
 // The host validates arguments, lays out the caller's workspace, and issues
@@ -548,6 +550,91 @@ int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, co
     int r = run_fit(X, S, o, workspace, s, out, d2_out, flags_out);
     out->status = r;
     return r;
+}
+
+size_t rtdetmcd_fit_batch_workspace_size(int32_t nframes, const int64_t* n, const int32_t* p,
+                                         const rtd_options* opt, int32_t nstreams) {
+    if (nframes < 1 || !n || !p || nstreams < 1 || nstreams > RTD_BATCH_MAX_STREAMS) return 0;
+    rtd_options o = opt ? *opt : defaults();
+    size_t slice = 0;
+    for (int f = 0; f < nframes; ++f) {
+        Shape S;
+        if (make_shape(n[f], p[f], p[f], (n[f] + p[f] + 1) / 2, o, S) != RTD_OK) return 0;
+        Regions R;
+        size_t b = layout(S, R);
+        if (b > slice) slice = b;
+    }
+    slice = (slice + 255) & ~(size_t)255;
+    return slice * (size_t)(nstreams < nframes ? nstreams : nframes);
+}
+
+int rtdetmcd_fit_batch(int32_t nframes, const float* const* X, const int64_t* n, const int32_t* p,
+                       const int64_t* ld, const int64_t* h, const rtd_options* opt, void* workspace,
+                       size_t ws_bytes, void* stream, int32_t nstreams, rtd_result* out, float* const* d2_out,
+                       uint8_t* const* flags_out) {
+    if (nframes < 1 || !X || !n || !p || !ld || !h || !out || nstreams < 1 || nstreams > RTD_BATCH_MAX_STREAMS)
+        return RTD_EINVAL;
+    rtd_options o = opt ? *opt : defaults();
+    o.subset_out = nullptr;    // per-frame outputs of the single-fit options do not apply
+    o.diag_out = nullptr;
+    o.profile = nullptr;
+    // every frame is checked before any device work
+    std::vector<Shape> shapes((size_t)nframes);
+    int bad = RTD_OK;
+    for (int f = 0; f < nframes; ++f) {
+        memset(&out[f], 0, sizeof(rtd_result));
+        int e = make_shape(n[f], p[f], ld[f], h[f], o, shapes[f]);
+        if (!e) e = check_h(shapes[f]);
+        if (!X[f]) e = RTD_EINVAL;
+        out[f].status = e;
+        if (e && !bad) bad = e;
+    }
+    if (bad) return bad;
+    const int nw = nstreams < nframes ? nstreams : nframes;
+    const size_t need = rtdetmcd_fit_batch_workspace_size(nframes, n, p, &o, nstreams);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    const size_t slice = need / (size_t)nw;
+    int dev = 0;
+    RTD_CUDA(cudaGetDevice(&dev));
+    cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    // the workers' streams start after the caller's earlier work
+    cudaEvent_t ready;
+    RTD_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    RTD_CUDA(cudaEventRecord(ready, caller));
+    std::vector<cudaStream_t> ss((size_t)nw, nullptr);
+    int serr = RTD_OK;
+    for (int w = 0; w < nw; ++w) {
+        if (cudaStreamCreateWithFlags(&ss[w], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamWaitEvent(ss[w], ready, 0) != cudaSuccess) {
+            serr = RTD_ECUDA;
+            break;
+        }
+    }
+    if (!serr) {
+        // frames are taken in order from a shared counter, so that workers
+        // stay busy whatever the mix of frame sizes
+        std::atomic<int> next(0);
+        auto worker = [&](int w) {
+            cudaSetDevice(dev);
+            void* wsw = static_cast<unsigned char*>(workspace) + slice * (size_t)w;
+            for (int f = next.fetch_add(1); f < nframes; f = next.fetch_add(1)) {
+                int r = run_fit(X[f], shapes[f], o, wsw, ss[w], &out[f], d2_out ? d2_out[f] : nullptr,
+                                flags_out ? flags_out[f] : nullptr);
+                out[f].status = r;
+            }
+        };
+        std::vector<std::thread> th;
+        for (int w = 1; w < nw; ++w) th.emplace_back(worker, w);
+        worker(0);
+        for (auto& t : th) t.join();
+    }
+    for (int w = 0; w < nw; ++w)
+        if (ss[w]) cudaStreamDestroy(ss[w]);
+    cudaEventDestroy(ready);
+    if (serr) return serr;
+    for (int f = 0; f < nframes; ++f)
+        if (out[f].status) return out[f].status;
+    return RTD_OK;
 }
 
 size_t rtdetmcd_distances_workspace_size(int64_t n, int32_t p) {

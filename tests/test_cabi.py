@@ -153,3 +153,24 @@ def test_grad_rejects_bad_arguments(lib, case):
     assert st == 1
     ws = lib.rtdetmcd_grad_workspace_size(n, p)
     assert (ws == 0) if case == "p_too_big" else (ws > 0 and ws % 256 == 0)
+
+
+def test_fit_batch_rejects_before_device_work(lib):
+    """An invalid frame (here h below [(n+p+1)/2]) stops the whole batch with
+    RTD_EINVAL before any device work, and only that frame carries the code."""
+    import paper_1910_05615_gb300 as m
+    F = 3
+    frames = [np.zeros((1000, 5), np.float32) for _ in range(F)]
+    Xp = (ctypes.c_void_p * F)(*[a.ctypes.data for a in frames])
+    n = (ctypes.c_int64 * F)(1000, 1000, 1000)
+    p = (ctypes.c_int32 * F)(5, 5, 5)
+    ld = (ctypes.c_int64 * F)(5, 5, 5)
+    h = (ctypes.c_int64 * F)(700, 400, 700)
+    res = (m._Result * F)()
+    st = lib.rtdetmcd_fit_batch(F, Xp, n, p, ld, h, None, None, 0, None, 2, res, None, None)
+    assert st == 1
+    assert [res[f].status for f in range(F)] == [0, 1, 0]
+    one = lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 1)
+    assert one > 0 and lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 2) == 2 * one
+    assert lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 8) == 3 * one   # at most one slice per frame
+    assert lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 0) == 0

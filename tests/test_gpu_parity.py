@@ -388,3 +388,34 @@ def test_bf16_form_matches_fp32_gram(rtd):
            "Sigma": rel_mat(b["Sigma"], a["Sigma"])})
     assert same > 0.999
     assert rel_mat(b["Sigma_raw"], a["Sigma_raw"]) <= 1e-4
+
+
+# -------------------- many frames of uneven n and p (batched form)
+def test_fit_batch_matches_single_fits_and_oracle(rtd):
+    """Frames of the many-frames workload (n in [2000, 50000], p in
+    {8, 16, 24, 32, 40}, 0-25% point outliers): each batched result equals
+    the single-fit result bit for bit, and matches the oracle (FP32 form
+    tolerances, q = 1 per frame)."""
+    frames = [datagen.batched_frame(f) for f in range(12)]
+    Xs = [torch.from_numpy(fr.X).cuda() for fr in frames]
+    got = rtd.rtdetmcd_fit_batch(Xs, [fr.h for fr in frames], nstreams=4)
+    for f, fr in enumerate(frames):
+        one = rtd.rtdetmcd_fit(Xs[f], fr.h)
+        g = got[f]
+        assert g["status"] == 0 and g["q"] == 1
+        assert np.array_equal(g["mu"], one["mu"]) and np.array_equal(g["Sigma"], one["Sigma"])
+        assert torch.equal(g["d2"], one["d2"]) and torch.equal(g["flags"], one["flags"])
+    for f in (0, 5, 11):
+        fr = frames[f]
+        ref = O.fit(fr.X, fr.h)
+        ok, rep = compare_fit(got[f], ref, fr.X, "fp32", check_subsets=False)
+        assert ok, (f, rep)
+
+
+def test_fit_batch_host_frames(rtd):
+    frames = [datagen.batched_frame(f) for f in range(20, 26)]
+    got = rtd.rtdetmcd_fit_batch([fr.X for fr in frames], [fr.h for fr in frames], nstreams=3)
+    for f, fr in enumerate(frames):
+        one = rtd.rtdetmcd_fit(fr.X, fr.h)
+        assert np.array_equal(got[f]["Sigma"], one["Sigma"])
+        assert np.array_equal(got[f]["flags"], one["flags"])
