@@ -85,8 +85,15 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
         int idx = w * SKPW + r * 32 + lane;
         bool valid = idx < cnt;
         unsigned d = (unsigned)(key[r] >> shift) & 255u;
-        unsigned tag = valid ? d : 256u + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, tag);
+        // lanes holding the same digit: the intersection over the digit's 8
+        // bits of the ballots that agree with this lane's bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = 1u << lane;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
         unsigned base = valid ? wcnt[w][d] : 0u;
         rank[r] = base + __popc(peers & lt);
         __syncwarp();
@@ -118,13 +125,21 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
         for (int k = 0; k < 8; ++k) { tstart[threadIdx.x * 8 + k] = ex; ex += v[k]; }
     }
     __syncthreads();
+    {   // fold the digit starts into the per-warp bases and the global offsets,
+        // so that staging and writing each read one digit-indexed word per key
+        const unsigned ts = tstart[threadIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < SW; ++ww) wcnt[ww][threadIdx.x] += ts;
+        goff[threadIdx.x] -= ts;
+    }
+    __syncthreads();
     // tile-local sorted order in shared memory
 #pragma unroll
     for (int r = 0; r < SITEMS; ++r) {
         int idx = w * SKPW + r * 32 + lane;
         if (idx < cnt) {
             unsigned d = (unsigned)(key[r] >> shift) & 255u;
-            stage[tstart[d] + wcnt[w][d] + rank[r]] = key[r];
+            stage[wcnt[w][d] + rank[r]] = key[r];
         }
     }
     __syncthreads();
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
     for (int i = threadIdx.x; i < cnt; i += ST) {
         K k = stage[i];
         unsigned d = (unsigned)(k >> shift) & 255u;
-        unsigned pos = goff[d] + (unsigned)i - tstart[d];
+        unsigned pos = goff[d] + (unsigned)i;
         if (pos < (unsigned)L) dst[pos] = k;
     }
 }
