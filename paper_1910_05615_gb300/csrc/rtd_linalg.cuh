@@ -186,13 +186,147 @@ __device__ inline double cta_kappa1(const double* S, const double* Li, double* W
 // on disjoint index pairs and are applied in parallel.  On return A's
 // diagonal holds the eigenvalues, V (columns) the eigenvectors; lam/Vs hold
 // them sorted by decreasing eigenvalue.
-__device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, double* Vs) {
+// The same round-robin sweeps entirely in FP32 (A and V of p x LD floats),
+// until the off-diagonal norm is below 1e-6 of the diagonal's or `sweeps`
+// run out: the cheap first stage of cta_jacobi.
+__device__ inline void jacobi_sweeps_f32(float* A, float* V, int p, int sweeps) {
+    __shared__ float fc[PMAX / 2 + 1], fs[PMAX / 2 + 1];
+    __shared__ int fi[PMAX / 2 + 1], fj[PMAX / 2 + 1];
+    const int P = p + (p & 1);
+    const int half = P / 2;
+    for (int sweep = 0; sweep < sweeps && p > 1; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            double a = (double)A[i * LD + j];
+            if (i != j) off += a * a; else dg += a * a;
+        }
+        off = cta_sum(off);
+        dg = cta_sum(dg);
+        if (off <= 1e-12 * dg || off == 0.0) break;
+        for (int round = 0; round < P - 1; ++round) {
+            if (threadIdx.x < half) {
+                int k = threadIdx.x;
+                int a = (k == 0) ? 0 : 1 + (k - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - k + round) % (P - 1);
+                int i = a < b ? a : b, j = a < b ? b : a;
+                float c = 1.f, sn = 0.f;
+                if (j < p) {
+                    const float aij = A[i * LD + j];
+                    if (aij != 0.f) {
+                        const float d = A[j * LD + j] - A[i * LD + i];
+                        const float q = sqrtf(fmaf(d, d, 4.f * aij * aij));
+                        float t = 2.f * aij / (fabsf(d) + q);
+                        if (d < 0.f) t = -t;
+                        if (isfinite(t) && q > 0.f) {
+                            c = rsqrtf(fmaf(t, t, 1.f));
+                            sn = t * c;
+                        }
+                    }
+                }
+                fc[k] = c; fs[k] = sn; fi[k] = i; fj[k] = (j < p) ? j : -1;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+                int k = e / p, r = e % p;
+                int i = fi[k], j = fj[k];
+                if (j < 0 || fs[k] == 0.f) continue;
+                float c = fc[k], sn = fs[k];
+                float a = A[r * LD + i], b = A[r * LD + j];
+                A[r * LD + i] = c * a - sn * b;
+                A[r * LD + j] = sn * a + c * b;
+                a = V[r * LD + i]; b = V[r * LD + j];
+                V[r * LD + i] = c * a - sn * b;
+                V[r * LD + j] = sn * a + c * b;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+                int k = e / p, r = e % p;
+                int i = fi[k], j = fj[k];
+                if (j < 0 || fs[k] == 0.f) continue;
+                float c = fc[k], sn = fs[k];
+                float a = A[i * LD + r], b = A[j * LD + r];
+                A[i * LD + r] = c * a - sn * b;
+                A[j * LD + r] = sn * a + c * b;
+            }
+            __syncthreads();
+            if (threadIdx.x < half) {
+                int k = threadIdx.x;
+                if (fj[k] >= 0 && fs[k] != 0.f) A[fj[k] * LD + fi[k]] = A[fi[k] * LD + fj[k]];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// C = op(X) Y for p x p shared matrices (leading dimension LD), op = X^T when tx
+__device__ inline void cta_matmul(const double* X, const double* Y, double* C, int p, bool tx) {
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        double v = 0.0;
+        for (int k = 0; k < p; ++k) v = fma(tx ? X[k * LD + i] : X[i * LD + k], Y[k * LD + j], v);
+        C[i * LD + j] = v;
+    }
+    __syncthreads();
+}
+
+// Symmetric eigen-decomposition in two stages.  FP32 sweeps bring A close to
+// diagonal; their rotations V32 are made orthogonal to FP64 precision by two
+// Newton-Schulz steps V <- V (3 I - V^T V) / 2, A is replaced by V^T A V in
+// FP64, and the FP64 sweeps of cta_jacobi finish (one or two sweeps, as the
+// convergence is quadratic).  T is a fourth p x LD double scratch matrix.
+__device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, double* Vs, double* T);
+
+__device__ inline void cta_jacobi_mixed(double* A, double* V, int p, double* lam, double* Vs, double* T) {
+    float* A32 = reinterpret_cast<float*>(T);
+    float* V32 = A32 + PMAX * LD;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        A32[i * LD + j] = (float)A[i * LD + j];
+        V32[i * LD + j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_sweeps_f32(A32, V32, p, 30);
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        V[i * LD + j] = (double)V32[i * LD + j];
+    }
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+        cta_matmul(V, V, Vs, p, true);                       // G = V^T V
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            Vs[i * LD + j] = ((i == j) ? 1.5 : 0.0) - 0.5 * Vs[i * LD + j];
+        }
+        __syncthreads();
+        cta_matmul(V, Vs, T, p, false);                      // V (3 I - G) / 2
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            V[i * LD + j] = T[i * LD + j];
+        }
+        __syncthreads();
+    }
+    cta_matmul(A, V, T, p, false);                           // A V
+    cta_matmul(V, T, A, p, true);                            // V^T A V
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {  // exact symmetry
+        int i = e / p, j = e % p;
+        if (i < j) A[j * LD + i] = A[i * LD + j];
+    }
+    __syncthreads();
+    cta_jacobi(A, V, p, lam, Vs, nullptr);
+}
+
+// T == nullptr: V already holds the rotations so far (cta_jacobi_mixed);
+// otherwise V starts as the identity.
+__device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, double* Vs, double* T) {
     __shared__ double rc[PMAX / 2 + 1], rs[PMAX / 2 + 1];
     __shared__ int ri[PMAX / 2 + 1], rj[PMAX / 2 + 1];
     __shared__ int order[PMAX];
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        int i = e / p, j = e % p;
-        V[i * LD + j] = (i == j) ? 1.0 : 0.0;
+    if (T) {
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            V[i * LD + j] = (i == j) ? 1.0 : 0.0;
+        }
     }
     __syncthreads();
     const int P = p + (p & 1);

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(CT) k_refine_eigen(Chain* ch, const Consts* __
         if (threadIdx.x == 0) { C.status = CH_DROPPED; set_warning(st, RTD_WARN_DROPPED_START); }
         return;
     }
-    cta_jacobi(A, V, p, lam, Vs);
+    cta_jacobi_mixed(A, V, p, lam, Vs, sm + 3 * MAT);
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         int i = e / p, j = e % p;
         C.V[i * PMAX + j] = Vs[i * LD + j];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(CT) k_refine_eigen(Chain* ch, const Consts* __
 }
 
 void launch_refine_eigen(const Plan& P, cudaStream_t s) {
-    size_t sm = 3 * MAT * sizeof(double);
+    size_t sm = 4 * MAT * sizeof(double);
     auto k = k_refine_eigen;
     big_smem(k, sm);
     k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.st);

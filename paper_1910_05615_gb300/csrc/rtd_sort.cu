@@ -31,25 +31,38 @@ __global__ void __launch_bounds__(ST) k_sort_hist(const K* __restrict__ keys, lo
     hist[((size_t)seg * 256 + threadIdx.x) * tiles + tile] = h[threadIdx.x];
 }
 
-// Exclusive scan of one segment's 256 * tiles counters (one CTA per segment).
+// Exclusive scan of one segment's 256 * tiles counters (one CTA per segment):
+// per-thread runs, then warp-shuffle scans of the run totals.
 __global__ void __launch_bounds__(1024) k_sort_scan(unsigned* __restrict__ hist, int tiles) {
-    __shared__ unsigned part[1024];
+    __shared__ unsigned wsum[32];
     const long long N = 256LL * tiles;
     unsigned* a = hist + (size_t)blockIdx.x * N;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     long long per = (N + blockDim.x - 1) / blockDim.x;
     long long b = threadIdx.x * per, e = b + per < N ? b + per : N;
     unsigned s = 0;
     for (long long i = b; i < e; ++i) s += a[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partials
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    unsigned x = s;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {     // exclusive scan of the warp totals
+        const int nw = blockDim.x >> 5;
+        const unsigned t = lane < nw ? wsum[lane] : 0u;
+        unsigned z = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < nw) wsum[lane] = z - t;
+    }
+    __syncthreads();
+    unsigned run = wsum[w] + x - s;
     for (long long i = b; i < e; ++i) {
         unsigned v = a[i];
         a[i] = run;
