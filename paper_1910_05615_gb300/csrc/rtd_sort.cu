@@ -107,10 +107,12 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
             const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bb : ~bb;
         }
-        unsigned base = valid ? wcnt[w][d] : 0u;
+        // the group's first lane reads and advances the warp's digit count
+        const int leader = __ffs(peers) - 1;
+        unsigned base = (valid && lane == leader) ? wcnt[w][d] : 0u;
+        base = __shfl_sync(0xffffffffu, base, leader);
         rank[r] = base + __popc(peers & lt);
-        __syncwarp();
-        if (valid && (__ffs(peers) - 1) == lane) wcnt[w][d] = base + __popc(peers);
+        if (valid && lane == leader) wcnt[w][d] = base + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
