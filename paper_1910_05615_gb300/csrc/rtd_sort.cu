@@ -278,10 +278,13 @@ __device__ inline double ucenter(const unsigned long long* s, long long L) { ret
 
 // Sum of (s_i - c, (s_i - c)^2) over [a, b) by one warp / by the CTA
 // (pairs for 32-bit keys, FP64 for 64-bit keys), returned as doubles.
-__device__ inline D2 warp_range_sum(const uint32_t* s, float c, long long a, long long b) {
+__device__ inline FF2 ff_range_sum(const uint32_t* s, float c, long long a, long long b) {
     FF2 acc = ff_zero2();
     for (long long i = a + (threadIdx.x & 31); i < b; i += 32) acc = ff_add2(acc, ff_elem(s[i], c));
-    acc = ff_warp_sum2(acc);
+    return ff_warp_sum2(acc);
+}
+__device__ inline D2 warp_range_sum(const uint32_t* s, float c, long long a, long long b) {
+    const FF2 acc = ff_range_sum(s, c, a, b);
     return D2{ff_d(acc.a), ff_d(acc.b)};
 }
 __device__ inline D2 warp_range_sum(const unsigned long long* s, double c, long long a, long long b) {
@@ -319,25 +322,41 @@ __global__ void __launch_bounds__(UT) k_uni_chunks(const K* __restrict__ sorted,
     const K* s = sorted + (long long)seg * L;
     const auto c = ucenter(s, L);
     long long a = (long long)ch * UC, b = a + UC < L ? a + UC : L;
-    D2 t = warp_range_sum(s, c, a, b);
-    if ((threadIdx.x & 31) == 0) {
-        double* o = csum + ((size_t)seg * nch + ch) * 2;
-        o[0] = t.a;
-        o[1] = t.b;
+    double* o = csum + ((size_t)seg * nch + ch) * 2;
+    if constexpr (sizeof(K) == 4) {
+        // the pair components as they are; k_uni_prefix converts them with one
+        // thread per chunk (an FP64 instruction costs the pipe the same for
+        // one lane as for 32, so a warp per chunk should not convert)
+        const FF2 t = ff_range_sum(s, c, a, b);
+        if ((threadIdx.x & 31) == 0)
+            *reinterpret_cast<float4*>(o) = make_float4(t.a.hi, t.a.lo, t.b.hi, t.b.lo);
+    } else {
+        D2 t = warp_range_sum(s, c, a, b);
+        if ((threadIdx.x & 31) == 0) {
+            o[0] = t.a;
+            o[1] = t.b;
+        }
     }
 }
 
 // U2: cpre[seg][k] = sum of chunks < k, k = 0..nch (one CTA per segment):
 // per-thread runs, then a shuffle scan of the run totals (fixed order).
-__global__ void __launch_bounds__(1024) k_uni_prefix(const double* __restrict__ csum, int nch,
+__global__ void __launch_bounds__(1024) k_uni_prefix(double* __restrict__ csum, int nch, int pairs,
                                                      double* __restrict__ cpre) {
     __shared__ double wa[32], wb[32];
     const int seg = blockIdx.x;
-    const double* c = csum + (size_t)seg * nch * 2;
+    double* c = csum + (size_t)seg * nch * 2;
     double* o = cpre + (size_t)seg * (nch + 1) * 2;
     const int per = (nch + 1023) / 1024;
     const int b0 = threadIdx.x * per, b1 = b0 + per < nch ? b0 + per : nch;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (pairs) {   // chunk sums stored as compensated pairs: to doubles, in place
+        for (int k = b0; k < b1; ++k) {
+            const float4 v = *reinterpret_cast<const float4*>(c + 2 * k);
+            c[2 * k] = ff_d(FF{v.x, v.y});
+            c[2 * k + 1] = ff_d(FF{v.z, v.w});
+        }
+    }
     double sa = 0.0, sb = 0.0;
     for (int k = b0; k < b1; ++k) { sa += c[2 * k]; sb += c[2 * k + 1]; }
     double xa = sa, xb = sb;
@@ -381,7 +400,56 @@ __device__ inline D2 cta_prefix(const K* s, C c, const double* cpre, long long x
     return D2{cpre[2 * k] + t.a, cpre[2 * k + 1] + t.b};
 }
 
-// U3: warp per range: lower bound over the range and q at its first window.
+// U3 body for range r (warp-uniform inputs, the partial sums pb at a + h).
+__device__ inline void uni_bound_out(const double* cpre, long long L, int r, int nwr, D2 pb, double* o) {
+    const long long h = L / 2 + 1, nwin = L - h + 1;
+    const double hd = (double)h;
+    const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
+    const long long lo = ((b - 1 + UC - 1) / UC) * UC, hi = ((a + h) / UC) * UC;
+    double lb = -INFINITY;
+    if (hi - lo >= 2) {
+        double n = (double)(hi - lo);
+        double s1 = cpre[2 * (hi / UC)] - cpre[2 * (lo / UC)];
+        double s2 = cpre[2 * (hi / UC) + 1] - cpre[2 * (lo / UC) + 1];
+        lb = hd * (n * s2 - s1 * s1) / n;
+    }
+    double S1 = pb.a - cpre[2 * (a / UC)], S2 = pb.b - cpre[2 * (a / UC) + 1];
+    o[0] = lb;
+    o[1] = hd * S2 - S1 * S1;
+}
+
+// U3, 32-bit keys: a warp takes 32 consecutive ranges; it sums each range's
+// partial chunk at a + h in turn (compensated pairs), and then every lane
+// does the FP64 arithmetic of its own range, so that the FP64 pipe sees one
+// instruction per 32 ranges.
+__global__ void __launch_bounds__(UT) k_uni_bound32(const uint32_t* __restrict__ sorted, long long L, int nch,
+                                                    int nwr, const double* __restrict__ cpre_all,
+                                                    double* __restrict__ wb) {
+    const int seg = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int r0 = (blockIdx.x * (UT / 32) + (threadIdx.x >> 5)) * 32;
+    if (r0 >= nwr) return;
+    const uint32_t* s = sorted + (long long)seg * L;
+    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
+    const long long h = L / 2 + 1;
+    const float c = ucenter(s, L);
+    FF2 mine = ff_zero2();
+    const int nr = nwr - r0 < 32 ? nwr - r0 : 32;
+    for (int rr = 0; rr < nr; ++rr) {
+        const long long x = (long long)(r0 + rr) * UW + h;
+        const long long k = x / UC;
+        const FF2 t = ff_range_sum(s, c, k * UC, x);
+        if (lane == rr) mine = t;
+    }
+    if (lane < nr) {
+        const int r = r0 + lane;
+        const long long k = ((long long)r * UW + h) / UC;
+        const D2 pb{cpre[2 * k] + ff_d(mine.a), cpre[2 * k + 1] + ff_d(mine.b)};
+        uni_bound_out(cpre, L, r, nwr, pb, wb + ((size_t)seg * nwr + r) * 2);
+    }
+}
+
+// U3, warp per range: lower bound over the range and q at its first window.
 template <typename K>
 __global__ void __launch_bounds__(UT) k_uni_bound(const K* __restrict__ sorted, long long L, int nch, int nwr,
                                                   const double* __restrict__ cpre_all, double* __restrict__ wb) {
@@ -723,8 +791,14 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     double* wres = ub + nseg;
     const int wpb = UT / 32;
     k_uni_chunks<K><<<dim3((D.nch + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, csum);
-    k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, cpre);
-    k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
+    k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, sizeof(K) == 4 ? 1 : 0, cpre);
+    if (sizeof(K) == 4) {
+        const int warps = (D.nwr + 31) / 32;
+        k_uni_bound32<<<dim3((warps + wpb - 1) / wpb, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr,
+                                                                         cpre, wb);
+    } else {
+        k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
+    }
     k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub);
     if (sizeof(K) == 4)
         k_uni_eval_ff<<<dim3(D.nwr, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
