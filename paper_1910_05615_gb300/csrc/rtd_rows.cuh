@@ -1222,15 +1222,49 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
     __syncthreads();
     const double cut = cs->cutoff_d2;
     const T cut_lo = (T)(cut * (1.0 - BAND_EPS)), cut_hi = (T)(cut * (1.0 + BAND_EPS));
+    // rows inside the FP64 band: listed, then decided one row per thread
+    // (see k_final) and added to the Gram after the pass
+    __shared__ int s_band[2 * NT];
+    __shared__ int s_nb;
+    if (threadIdx.x == 0) s_nb = 0;
     int r0, r1;
     block_rows(m, cpb, r0, r1);
     typename GramPick<PB, T, TC>::type acc;
     gram_setup(acc, smem + align128(align16(gram_smem_bytes<PB, T>()) + PB * PB * sizeof(T)));
     acc.init();
+    auto band_pass = [&]() {   // all threads; s_nb <= 2 NT
+        const int nb = s_nb;
+        for (int k0 = 0; k0 < nb; k0 += NT) {
+            const int k = k0 + threadIdx.x;
+            bool in = false;
+            int row = 0;
+            if (k < nb) {
+                row = s_band[k];
+                in = d2_fp64(Xp + (size_t)row * PB, *rp, p) <= cut;
+                wset[row] = in ? 2 : 0;
+            }
+            int tot;
+            const int slot = cta_compact(in, tot);
+            acc.begin();
+            if (slot >= 0) {
+                float x[PB];
+                load_row_padded<PB>(Xp + (size_t)row * PB, x);
+                T v[PB];
+#pragma unroll
+                for (int j = 0; j < PB; ++j) v[j] = ((T)x[j] - s_hi[j]) - s_lo[j];
+                acc.put(tile, wt, slot, v, p, (T)1);
+            }
+            __syncthreads();
+            if (tot) acc.rows(tile, wt, tot);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_nb = 0;
+        __syncthreads();
+    };
     for (int base = r0; base < r1; base += S::TR) {
         int row = base + threadIdx.x;
         bool valid = threadIdx.x < S::TR && row < r1;
-        bool in = false;
+        bool in = false, inband = false;
         T c[R][PB];
         if (valid) {
             float x[PB];
@@ -1242,8 +1276,15 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
             if (!fp32) in = (double)d2[0] <= cut;
             else if (d2[0] < cut_lo) in = true;
             else if (d2[0] > cut_hi) in = false;
-            else in = d2_fp64(Xp + (size_t)row * PB, *rp, p) <= cut;   // row re-read: x stays in registers
-            wset[row] = in ? 2 : 0;
+            else inband = true;                       // decided in band_pass
+            if (!inband) wset[row] = in ? 2 : 0;
+        }
+        {   // band rows listed in thread order, so that the Gram's order is fixed
+            int btot;
+            const int bs = cta_compact(inband, btot);
+            if (bs >= 0) s_band[s_nb + bs] = row;
+            __syncthreads();
+            if (threadIdx.x == 0) s_nb += btot;
         }
         int tot;
         int slot = cta_compact(in, tot);
@@ -1252,7 +1293,9 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
         __syncthreads();
         if (tot) acc.rows(tile, wt, tot);
         __syncthreads();
+        if (s_nb >= NT) band_pass();   // at most NT - 1 + TR entries before the next tile
     }
+    if (s_nb) band_pass();
     size_t sl = ((size_t)blockIdx.y * cpb + blockIdx.x) * 2 + 0;
     acc.store(reinterpret_cast<double*>(smem), partial + sl * slot_d);
 }
@@ -1465,6 +1508,27 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
     const double cut = cutp ? *cutp : INFINITY;
     const T cut_lo = (T)(cut * (1.0 - BAND_EPS)), cut_hi = (T)(cut * (1.0 + BAND_EPS));
     int nflag = 0;
+    // Rows inside the FP64 band are listed and recomputed together, one row
+    // per thread: an FP64 instruction costs the pipe as much for one active
+    // lane as for 32, so a warp must not recompute a lone band row.
+    __shared__ int s_band[NT * (R + 1)];
+    __shared__ int s_nb;
+    if (threadIdx.x == 0) s_nb = 0;
+    __syncthreads();
+    auto band_pass = [&]() {
+        const int nb = s_nb;
+        for (int k = threadIdx.x; k < nb; k += NT) {
+            const long long i = s_band[k];
+            const double d = d2_fp64(X + i * ld, *rp, p);
+            const bool out = d > cut;
+            if (d2_out) d2_out[i] = (float)d;
+            if (flags) flags[i] = out ? 1 : 0;
+            nflag += out ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nb = 0;
+        __syncthreads();
+    };
     // a CTA takes tiles of NT * R rows; thread t holds rows t, t + NT, ...
     // (each load instruction of a warp reads consecutive rows)
     const long long stride = (long long)gridDim.x * NT * R;
@@ -1490,15 +1554,21 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
         for (int r = 0; r < R; ++r) {
             const long long i = tb + (long long)r * NT + threadIdx.x;
             if (i >= n) continue;
-            double d = (double)d2[r];
-            if (fp32 && decide && d2[r] >= cut_lo && d2[r] <= cut_hi)
-                d = d2_fp64(X + i * ld, *rp, p);   // row re-read: xs stays in registers
+            if (fp32 && decide && d2[r] >= cut_lo && d2[r] <= cut_hi) {
+                s_band[atomicAdd(&s_nb, 1)] = (int)i;   // decided in band_pass
+                continue;
+            }
+            const double d = (double)d2[r];
             const bool out = d > cut;
             if (d2_out) d2_out[i] = (float)d;
             if (flags) flags[i] = out ? 1 : 0;
             nflag += out ? 1 : 0;
         }
+        __syncthreads();
+        if (s_nb >= NT) band_pass();   // at most NT - 1 + NT * R entries before the next tile
     }
+    __syncthreads();
+    if (s_nb) band_pass();
     if (count) {
         nflag = cta_sum_int(nflag);
         if (threadIdx.x == 0 && nflag) atomicAdd(count, (unsigned long long)nflag);
