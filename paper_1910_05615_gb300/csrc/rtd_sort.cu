@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(UT) k_uni_chunks(const K* __restrict__ sorted,
 // U2: cpre[seg][k] = sum of chunks < k, k = 0..nch (one CTA per segment):
 // per-thread runs, then a shuffle scan of the run totals (fixed order).
 __global__ void __launch_bounds__(1024) k_uni_prefix(double* __restrict__ csum, int nch, int pairs,
-                                                     double* __restrict__ cpre) {
+                                                     double* __restrict__ cpre, int* __restrict__ count) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = 0;   // candidate list of k_uni_ub
     __shared__ double wa[32], wb[32];
     const int seg = blockIdx.x;
     double* c = csum + (size_t)seg * nch * 2;
@@ -482,8 +483,14 @@ __global__ void __launch_bounds__(UT) k_uni_bound(const K* __restrict__ sorted, 
 }
 
 // U4: least first-window q of each segment.
-__global__ void __launch_bounds__(UT) k_uni_ub(const double* __restrict__ wb, int nwr, double* __restrict__ ub) {
+// Also lists the ranges the bound does not exclude (any order: each range's
+// result has its own slot) and marks the excluded ones in wres, so that the
+// exact pass runs over the list only.
+__global__ void __launch_bounds__(UT) k_uni_ub(const double* __restrict__ wb, int nwr, double* __restrict__ ub,
+                                               double* __restrict__ wres, int2* __restrict__ list,
+                                               int* __restrict__ count) {
     __shared__ double red[UT / 32];
+    __shared__ double s_ub;
     const int seg = blockIdx.x;
     double m = INFINITY;
     for (int r = threadIdx.x; r < nwr; r += UT) m = fmin(m, wb[((size_t)seg * nwr + r) * 2 + 1]);
@@ -494,6 +501,25 @@ __global__ void __launch_bounds__(UT) k_uni_ub(const double* __restrict__ wb, in
         double v = INFINITY;
         for (int k = 0; k < UT / 32; ++k) v = fmin(v, red[k]);
         ub[seg] = v;
+        s_ub = v;
+    }
+    __syncthreads();
+    const double lim = s_ub * (1.0 + 1e-12);
+    for (int r0 = 0; r0 < nwr; r0 += UT) {
+        const int r = r0 + threadIdx.x;
+        const bool live = r < nwr && !(wb[((size_t)seg * nwr + r) * 2] > lim);
+        if (r < nwr && !live) {
+            double* o = wres + ((size_t)seg * nwr + r) * 3;
+            o[0] = INFINITY; o[1] = -1.0; o[2] = 0.0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, live);
+        if (bal) {
+            const int lane = threadIdx.x & 31;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(count, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (live) list[base + __popc(bal & ((1u << lane) - 1u))] = make_int2(seg, r);
+        }
     }
 }
 
@@ -517,88 +543,87 @@ __device__ __forceinline__ bool ff_less(FF a, FF b) { return a.hi < b.hi || (a.h
 
 __global__ void __launch_bounds__(UT) k_uni_eval_ff(const uint32_t* __restrict__ sorted, long long L, int nch,
                                                     int nwr, const double* __restrict__ cpre_all,
-                                                    const double* __restrict__ wb, const double* __restrict__ ub,
+                                                    const int2* __restrict__ list, const int* __restrict__ count,
                                                     double* __restrict__ wres) {
     __shared__ FF sw[UT / 32][2];
     __shared__ FF sbase[2];
     __shared__ FF sq[UT / 32], ss[UT / 32];
     __shared__ long long sj[UT / 32];
-    const int seg = blockIdx.y, r = blockIdx.x;
-    double* o = wres + ((size_t)seg * nwr + r) * 3;
-    const double lb = wb[((size_t)seg * nwr + r) * 2];
-    if (lb > ub[seg] * (1.0 + 1e-12)) {
-        if (threadIdx.x == 0) { o[0] = INFINITY; o[1] = -1.0; o[2] = 0.0; }
-        return;
-    }
-    const uint32_t* s = sorted + (long long)seg * L;
-    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
-    const long long h = L / 2 + 1, nwin = L - h + 1;
-    const float hf = (float)h;                       // exact: h < 2^24
-    const float c = ucenter(s, L);
-    const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w == 0) {   // sums of the range's first window (a is on the chunk grid)
-        D2 pb = warp_prefix(s, c, cpre, a + h);
-        if (lane == 0) {
-            sbase[0] = ff_from_d(pb.a - cpre[2 * (a / UC)]);
-            sbase[1] = ff_from_d(pb.b - cpre[2 * (a / UC) + 1]);
-        }
-    }
-    const long long j = a + threadIdx.x;
-    FF e1{0.f, 0.f}, e2{0.f, 0.f};
-    if (j < b && j + h < L) {
-        const FF2 A = ff_elem(s[j], c), B = ff_elem(s[j + h], c);
-        e1 = ff_add(B.a, ff_neg(A.a));
-        e2 = ff_add(B.b, ff_neg(A.b));
-    }
-    // inclusive warp scan, then exclusive within the CTA
-    FF x1 = e1, x2 = e2;
-    for (int off = 1; off < 32; off <<= 1) {
-        const FF y1 = ff_shfl_up(x1, off), y2 = ff_shfl_up(x2, off);
-        if (lane >= off) { x1 = ff_add(x1, y1); x2 = ff_add(x2, y2); }
-    }
-    if (lane == 31) { sw[w][0] = x1; sw[w][1] = x2; }
-    __syncthreads();
-    if (threadIdx.x == 0) {   // exclusive prefix of the 8 warp totals, base folded in (fixed order)
-        FF p1 = sbase[0], p2 = sbase[1];
-        for (int k = 0; k < UT / 32; ++k) {
-            const FF q1 = sw[k][0], q2 = sw[k][1];
-            sw[k][0] = p1;
-            sw[k][1] = p2;
-            p1 = ff_add(p1, q1);
-            p2 = ff_add(p2, q2);
-        }
-    }
-    __syncthreads();
-    // S_k(j) = warp prefix + exclusive lane prefix
-    const FF S1 = ff_add(sw[w][0], ff_add(x1, ff_neg(e1)));
-    const FF S2 = ff_add(sw[w][1], ff_add(x2, ff_neg(e2)));
-    FF q{INFINITY, 0.f}, s1{0.f, 0.f};
-    long long bj = -1;
-    if (j < b) {
-        q = ff_add(ff_mul_f(S2, hf), ff_neg(ff_sq(S1)));
-        s1 = S1;
-        bj = j;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        const FF oq = ff_shfl_xor(q, off), os = ff_shfl_xor(s1, off);
-        const long long oj = __shfl_xor_sync(0xffffffffu, bj, off);
-        if (oj >= 0 && (bj < 0 || ff_less(oq, q) || (oq.hi == q.hi && oq.lo == q.lo && oj < bj))) {
-            q = oq; bj = oj; s1 = os;
-        }
-    }
-    if (lane == 0) { sq[w] = q; sj[w] = bj; ss[w] = s1; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        FF bq{INFINITY, 0.f}, bs{0.f, 0.f};
-        long long jj = -1;
-        for (int k = 0; k < UT / 32; ++k)
-            if (sj[k] >= 0 && (jj < 0 || ff_less(sq[k], bq) || (sq[k].hi == bq.hi && sq[k].lo == bq.lo && sj[k] < jj))) {
-                bq = sq[k]; jj = sj[k]; bs = ss[k];
+    const int nlist = *count;
+    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {   // uniform over the CTA
+        const int seg = list[it].x, r = list[it].y;
+        double* o = wres + ((size_t)seg * nwr + r) * 3;
+        const uint32_t* s = sorted + (long long)seg * L;
+        const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
+        const long long h = L / 2 + 1, nwin = L - h + 1;
+        const float hf = (float)h;                       // exact: h < 2^24
+        const float c = ucenter(s, L);
+        const long long a = (long long)r * UW, b = a + UW < nwin ? a + UW : nwin;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (w == 0) {   // sums of the range's first window (a is on the chunk grid)
+            D2 pb = warp_prefix(s, c, cpre, a + h);
+            if (lane == 0) {
+                sbase[0] = ff_from_d(pb.a - cpre[2 * (a / UC)]);
+                sbase[1] = ff_from_d(pb.b - cpre[2 * (a / UC) + 1]);
             }
-        o[0] = jj >= 0 ? ff_d(bq) : INFINITY;
-        o[1] = (double)jj;
-        o[2] = ff_d(bs);
+        }
+        const long long j = a + threadIdx.x;
+        FF e1{0.f, 0.f}, e2{0.f, 0.f};
+        if (j < b && j + h < L) {
+            const FF2 A = ff_elem(s[j], c), B = ff_elem(s[j + h], c);
+            e1 = ff_add(B.a, ff_neg(A.a));
+            e2 = ff_add(B.b, ff_neg(A.b));
+        }
+        // inclusive warp scan, then exclusive within the CTA
+        FF x1 = e1, x2 = e2;
+        for (int off = 1; off < 32; off <<= 1) {
+            const FF y1 = ff_shfl_up(x1, off), y2 = ff_shfl_up(x2, off);
+            if (lane >= off) { x1 = ff_add(x1, y1); x2 = ff_add(x2, y2); }
+        }
+        if (lane == 31) { sw[w][0] = x1; sw[w][1] = x2; }
+        __syncthreads();
+        if (threadIdx.x == 0) {   // exclusive prefix of the 8 warp totals, base folded in (fixed order)
+            FF p1 = sbase[0], p2 = sbase[1];
+            for (int k = 0; k < UT / 32; ++k) {
+                const FF q1 = sw[k][0], q2 = sw[k][1];
+                sw[k][0] = p1;
+                sw[k][1] = p2;
+                p1 = ff_add(p1, q1);
+                p2 = ff_add(p2, q2);
+            }
+        }
+        __syncthreads();
+        // S_k(j) = warp prefix + exclusive lane prefix
+        const FF S1 = ff_add(sw[w][0], ff_add(x1, ff_neg(e1)));
+        const FF S2 = ff_add(sw[w][1], ff_add(x2, ff_neg(e2)));
+        FF q{INFINITY, 0.f}, s1{0.f, 0.f};
+        long long bj = -1;
+        if (j < b) {
+            q = ff_add(ff_mul_f(S2, hf), ff_neg(ff_sq(S1)));
+            s1 = S1;
+            bj = j;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const FF oq = ff_shfl_xor(q, off), os = ff_shfl_xor(s1, off);
+            const long long oj = __shfl_xor_sync(0xffffffffu, bj, off);
+            if (oj >= 0 && (bj < 0 || ff_less(oq, q) || (oq.hi == q.hi && oq.lo == q.lo && oj < bj))) {
+                q = oq; bj = oj; s1 = os;
+            }
+        }
+        if (lane == 0) { sq[w] = q; sj[w] = bj; ss[w] = s1; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            FF bq{INFINITY, 0.f}, bs{0.f, 0.f};
+            long long jj = -1;
+            for (int k = 0; k < UT / 32; ++k)
+                if (sj[k] >= 0 && (jj < 0 || ff_less(sq[k], bq) || (sq[k].hi == bq.hi && sq[k].lo == bq.lo && sj[k] < jj))) {
+                    bq = sq[k]; jj = sj[k]; bs = ss[k];
+                }
+            o[0] = jj >= 0 ? ff_d(bq) : INFINITY;
+            o[1] = (double)jj;
+            o[2] = ff_d(bs);
+        }
+        __syncthreads();   // shared state is reused by the next listed range
     }
 }
 
@@ -789,9 +814,11 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     double* wb = cpre + (size_t)nseg * (D.nch + 1) * 2;
     double* ub = wb + (size_t)nseg * D.nwr * 2;
     double* wres = ub + nseg;
+    int* count = reinterpret_cast<int*>(wres + (size_t)nseg * D.nwr * 3);
+    int2* list = reinterpret_cast<int2*>(wres + (size_t)nseg * D.nwr * 3 + 1);
     const int wpb = UT / 32;
     k_uni_chunks<K><<<dim3((D.nch + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, csum);
-    k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, sizeof(K) == 4 ? 1 : 0, cpre);
+    k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, sizeof(K) == 4 ? 1 : 0, cpre, count);
     if (sizeof(K) == 4) {
         const int warps = (D.nwr + 31) / 32;
         k_uni_bound32<<<dim3((warps + wpb - 1) / wpb, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr,
@@ -799,10 +826,12 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     } else {
         k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
     }
-    k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub);
-    if (sizeof(K) == 4)
-        k_uni_eval_ff<<<dim3(D.nwr, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
-    else
+    k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub, wres, list, count);
+    if (sizeof(K) == 4) {
+        long long g = (long long)nseg * D.nwr;
+        if (g > 4LL * P.nsm) g = 4LL * P.nsm;
+        k_uni_eval_ff<<<(int)g, UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr, cpre, list, count, wres);
+    } else
         k_uni_eval<K><<<dim3(D.nwr, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
     k_uni_finish_seg<K><<<nseg, UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wres, P.cs, which_c1, out);
 }
@@ -815,7 +844,8 @@ void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, lon
 
 size_t unimcd_scratch_doubles(int nseg, long long L) {
     const UniDims D = uni_dims(L);
-    return (size_t)nseg * (2 * (size_t)D.nch + 2 * ((size_t)D.nch + 1) + 2 * (size_t)D.nwr + 1 + 3 * (size_t)D.nwr);
+    return (size_t)nseg * (2 * (size_t)D.nch + 2 * ((size_t)D.nch + 1) + 2 * (size_t)D.nwr + 1 + 3 * (size_t)D.nwr +
+                           (size_t)D.nwr) + 1;   // + candidate list (int2) and its count
 }
 
 // =====================================================================
