@@ -419,35 +419,20 @@ __device__ inline void uni_bound_out(const double* cpre, long long L, int r, int
     o[1] = hd * S2 - S1 * S1;
 }
 
-// U3, 32-bit keys: a warp takes 32 consecutive ranges; it sums each range's
-// partial chunk at a + h in turn (compensated pairs), and then every lane
-// does the FP64 arithmetic of its own range, so that the FP64 pipe sees one
-// instruction per 32 ranges.
-__global__ void __launch_bounds__(UT) k_uni_bound32(const uint32_t* __restrict__ sorted, long long L, int nch,
-                                                    int nwr, const double* __restrict__ cpre_all,
-                                                    double* __restrict__ wb) {
+// U3, 32-bit keys: warp per range, the compensated sums of the partial chunk
+// at a + h only (stored as pairs); k_uni_ub finishes the range with one
+// thread per range, so that the FP64 arithmetic takes one instruction per 32
+// ranges (an FP64 instruction costs the pipe the same for one lane as for 32).
+__global__ void __launch_bounds__(UT) k_uni_part32(const uint32_t* __restrict__ sorted, long long L, int nwr,
+                                                   float4* __restrict__ part) {
     const int seg = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const int r0 = (blockIdx.x * (UT / 32) + (threadIdx.x >> 5)) * 32;
-    if (r0 >= nwr) return;
+    const int r = blockIdx.x * (UT / 32) + (threadIdx.x >> 5);
+    if (r >= nwr) return;
     const uint32_t* s = sorted + (long long)seg * L;
-    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
-    const long long h = L / 2 + 1;
-    const float c = ucenter(s, L);
-    FF2 mine = ff_zero2();
-    const int nr = nwr - r0 < 32 ? nwr - r0 : 32;
-    for (int rr = 0; rr < nr; ++rr) {
-        const long long x = (long long)(r0 + rr) * UW + h;
-        const long long k = x / UC;
-        const FF2 t = ff_range_sum(s, c, k * UC, x);
-        if (lane == rr) mine = t;
-    }
-    if (lane < nr) {
-        const int r = r0 + lane;
-        const long long k = ((long long)r * UW + h) / UC;
-        const D2 pb{cpre[2 * k] + ff_d(mine.a), cpre[2 * k + 1] + ff_d(mine.b)};
-        uni_bound_out(cpre, L, r, nwr, pb, wb + ((size_t)seg * nwr + r) * 2);
-    }
+    const long long x = (long long)r * UW + L / 2 + 1;
+    const long long k = x / UC;
+    const FF2 t = ff_range_sum(s, ucenter(s, L), k * UC, x);
+    if ((threadIdx.x & 31) == 0) part[(size_t)seg * nwr + r] = make_float4(t.a.hi, t.a.lo, t.b.hi, t.b.lo);
 }
 
 // U3, warp per range: lower bound over the range and q at its first window.
@@ -486,12 +471,25 @@ __global__ void __launch_bounds__(UT) k_uni_bound(const K* __restrict__ sorted, 
 // Also lists the ranges the bound does not exclude (any order: each range's
 // result has its own slot) and marks the excluded ones in wres, so that the
 // exact pass runs over the list only.
-__global__ void __launch_bounds__(UT) k_uni_ub(const double* __restrict__ wb, int nwr, double* __restrict__ ub,
+// With part (32-bit keys) the range bounds are first finished here from the
+// partial-chunk pairs, one thread per range.
+__global__ void __launch_bounds__(UT) k_uni_ub(double* __restrict__ wb, int nwr, double* __restrict__ ub,
                                                double* __restrict__ wres, int2* __restrict__ list,
-                                               int* __restrict__ count) {
+                                               int* __restrict__ count, const float4* __restrict__ part,
+                                               const double* __restrict__ cpre_all, long long L, int nch) {
     __shared__ double red[UT / 32];
     __shared__ double s_ub;
     const int seg = blockIdx.x;
+    if (part) {
+        const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
+        for (int r = threadIdx.x; r < nwr; r += UT) {
+            const float4 v = part[(size_t)seg * nwr + r];
+            const long long k = ((long long)r * UW + L / 2 + 1) / UC;
+            const D2 pb{cpre[2 * k] + ff_d(FF{v.x, v.y}), cpre[2 * k + 1] + ff_d(FF{v.z, v.w})};
+            uni_bound_out(cpre, L, r, nwr, pb, wb + ((size_t)seg * nwr + r) * 2);
+        }
+        __syncthreads();
+    }
     double m = INFINITY;
     for (int r = threadIdx.x; r < nwr; r += UT) m = fmin(m, wb[((size_t)seg * nwr + r) * 2 + 1]);
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -819,14 +817,16 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     const int wpb = UT / 32;
     k_uni_chunks<K><<<dim3((D.nch + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, csum);
     k_uni_prefix<<<nseg, 1024, 0, s>>>(csum, D.nch, sizeof(K) == 4 ? 1 : 0, cpre, count);
+    float4* part = nullptr;
     if (sizeof(K) == 4) {
-        const int warps = (D.nwr + 31) / 32;
-        k_uni_bound32<<<dim3((warps + wpb - 1) / wpb, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nch, D.nwr,
-                                                                         cpre, wb);
+        // 16-byte aligned after the list (one spare double in the scratch size)
+        const uintptr_t pa = reinterpret_cast<uintptr_t>(list + (size_t)nseg * D.nwr);
+        part = reinterpret_cast<float4*>((pa + 15) & ~(uintptr_t)15);
+        k_uni_part32<<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>((const uint32_t*)keys, L, D.nwr, part);
     } else {
         k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
     }
-    k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub, wres, list, count);
+    k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub, wres, list, count, part, cpre, L, D.nch);
     if (sizeof(K) == 4) {
         long long g = (long long)nseg * D.nwr;
         if (g > 4LL * P.nsm) g = 4LL * P.nsm;
@@ -845,7 +845,8 @@ void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, lon
 size_t unimcd_scratch_doubles(int nseg, long long L) {
     const UniDims D = uni_dims(L);
     return (size_t)nseg * (2 * (size_t)D.nch + 2 * ((size_t)D.nch + 1) + 2 * (size_t)D.nwr + 1 + 3 * (size_t)D.nwr +
-                           (size_t)D.nwr) + 1;   // + candidate list (int2) and its count
+                           (size_t)D.nwr + 2 * (size_t)D.nwr) + 2;   // + candidate list (int2), its count,
+                                                                     // partial-chunk pairs (float4)
 }
 
 // =====================================================================
