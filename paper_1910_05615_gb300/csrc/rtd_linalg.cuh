@@ -442,8 +442,9 @@ __device__ inline void cta_jacobi(double* A, double* V, int p, double* lam, doub
 // log|det A| by LU with partial pivoting (A overwritten).  -inf if singular.
 __device__ inline double cta_logabsdet(double* A, int p) {
     __shared__ int piv;
-    __shared__ double acc;
-    if (threadIdx.x == 0) acc = 0.0;
+    __shared__ int zero;
+    __shared__ double pv[PMAX];
+    if (threadIdx.x == 0) zero = 0;
     __syncthreads();
     for (int k = 0; k < p; ++k) {
         if (threadIdx.x == 0) {
@@ -454,11 +455,11 @@ __device__ inline double cta_logabsdet(double* A, int p) {
                 if (v > bv) { bv = v; best = i; }
             }
             piv = best;
-            if (bv == 0.0) acc = -INFINITY;
-            else acc += log(bv);
+            pv[k] = bv;
+            if (bv == 0.0) zero = 1;
         }
         __syncthreads();
-        if (acc == -INFINITY) break;
+        if (zero) break;
         int pr = piv;
         if (pr != k) {
             for (int j = threadIdx.x; j < p; j += blockDim.x) {
@@ -468,17 +469,26 @@ __device__ inline double cta_logabsdet(double* A, int p) {
             }
         }
         __syncthreads();
-        double d = A[k * LD + k];
+        // multipliers once per row (one division each), then the update
+        const double d = A[k * LD + k];
+        for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) A[i * LD + k] = A[i * LD + k] / d;
+        __syncthreads();
         int rem = p - k - 1;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
             int i = k + 1 + e / rem, j = k + 1 + e % rem;
-            A[i * LD + j] -= A[i * LD + k] / d * A[k * LD + j];
+            A[i * LD + j] -= A[i * LD + k] * A[k * LD + j];
         }
         __syncthreads();
     }
-    double r = acc;
+    // log|det| = sum of the pivots' logs, taken in parallel (a log is long
+    // on this GPU, so not one after another on the pivot thread)
+    double r = 0.0;
+    if (!zero)
+        for (int k = threadIdx.x; k < p; k += blockDim.x) r += log(pv[k]);
+    r = cta_sum(r);
+    const double out = zero ? -INFINITY : r;
     __syncthreads();
-    return r;
+    return out;
 }
 
 }  // namespace rtd
