@@ -1390,22 +1390,30 @@ __device__ void select_win_body(SelRule& R, Cand* cand_w, Cand* band_all_c, unsi
     Cand* sub = band_all_c;
     const int cap = m / 2;
     int nlo = 0;
-    for (int base = 0; base < C; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        bool in = false;
-        Cand e;
-        if (i < C) {
-            e = cand[i];
-            if (e.key < kb_lo) ++nlo;
-            else in = e.key <= kb_hi;
+    constexpr int CU = 4;   // candidates per thread and round, loaded before they are used
+    for (int base = 0; base < C; base += CU * blockDim.x) {
+        Cand e[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            if (i < C) e[u] = cand[i];
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, in);
-        int wb = 0;
-        if (lane == 0 && bal) wb = atomicAdd(&s_ns, __popc(bal));
-        wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (in) {
-            const int idx = wb + __popc(bal & ((1u << lane) - 1u));
-            if (idx < cap) sub[idx] = e;
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            bool in = false;
+            if (i < C) {
+                if (e[u].key < kb_lo) ++nlo;
+                else in = e[u].key <= kb_hi;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            int wb = 0;
+            if (lane == 0 && bal) wb = atomicAdd(&s_ns, __popc(bal));
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (in) {
+                const int idx = wb + __popc(bal & ((1u << lane) - 1u));
+                if (idx < cap) sub[idx] = e[u];
+            }
         }
     }
     nlo = warp_sum_int(nlo);
