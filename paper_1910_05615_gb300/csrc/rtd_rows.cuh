@@ -1362,7 +1362,7 @@ __device__ inline void grad_load_m(const RowParams& rp, int p, float* sM, float*
 }
 
 template <int PB>
-__global__ void __launch_bounds__(NT) k_grad_gram(const float* __restrict__ X, long long n, int p, long long ld,
+__global__ void __launch_bounds__(NT, 2) k_grad_gram(const float* __restrict__ X, long long n, int p, long long ld,
                                                   int vec4, const uint8_t* __restrict__ wset, int wbit,
                                                   const RowParams* __restrict__ rp, double* __restrict__ partial,
                                                   size_t slot_d) {
@@ -1465,7 +1465,7 @@ void grad_t(const float* X, long long n, int p, long long ld, const uint8_t* wse
     typedef GramShape<PB, float> S;
     const int vec4 = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     long long tiles = (n + S::TR - 1) / S::TR;
-    int g1 = (int)(tiles < 2LL * nsm ? tiles : 2LL * nsm);
+    int g1 = (int)(tiles < 4LL * nsm ? tiles : 4LL * nsm);   // two resident CTAs per SM, two waves
     if (g1 > GRAD_SLOTS) g1 = GRAD_SLOTS;
     if (g1 < 1) g1 = 1;
     const size_t sm = gram_smem_bytes<PB, float>();
