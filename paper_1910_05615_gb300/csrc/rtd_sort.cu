@@ -755,12 +755,19 @@ __global__ void __launch_bounds__(UT) k_uni_finish_seg(const K* __restrict__ sor
         long long jj = (long long)x[1];
         if (jj >= 0 && (bj < 0 || x[0] < best || (x[0] == best && jj < bj))) { best = x[0]; bj = jj; bs1 = x[2]; }
     }
-    sv[threadIdx.x] = best; ss[threadIdx.x] = bs1; sj[threadIdx.x] = bj;
+    // least (q, j) over the CTA: warp butterflies, then the warp results in
+    // order (the same total order as one pass over all threads)
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off), os = __shfl_xor_sync(0xffffffffu, bs1, off);
+        const long long oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; bs1 = os; }
+    }
+    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; ss[threadIdx.x >> 5] = bs1; sj[threadIdx.x >> 5] = bj; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double b = INFINITY, bsum = 0.0;
         long long jj = -1;
-        for (int t = 0; t < UT; ++t)
+        for (int t = 0; t < UT / 32; ++t)
             if (sj[t] >= 0 && (jj < 0 || sv[t] < b || (sv[t] == b && sj[t] < jj))) { b = sv[t]; jj = sj[t]; bsum = ss[t]; }
         s_q = b; s_j = jj; s_s1 = bsum;
     }
