@@ -110,7 +110,7 @@ int check_h(const Shape& S) {
     return RTD_OK;
 }
 
-size_t tiles_of(long long L) { return (size_t)((L + 4095) / 4096); }
+size_t tiles_of(long long L) { return (size_t)((L + SORT_TILE_KEYS - 1) / SORT_TILE_KEYS); }
 
 size_t layout(const Shape& S, Regions& R) {
     Layout L;

@@ -117,6 +117,8 @@ void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* 
                        Status* st, cudaStream_t s, double* logdet_out = nullptr);
 // adjoint of steps 8-10 (rtd_rows.cu): slot count of the reduction pass
 constexpr int GRAD_SLOTS = 1024;
+// keys per tile of the segmented radix sort (threads x keys per thread)
+constexpr int SORT_TILE_KEYS = 4096;
 void launch_grad(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
                  const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,
                  double w_rd, float* grad, int nsm, cudaStream_t s);

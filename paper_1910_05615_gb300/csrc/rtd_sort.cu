@@ -7,12 +7,12 @@ namespace rtd {
 // =====================================================================
 // Segmented LSD radix sort of equal-length segments (keys only, 8-bit
 // digits, stable).  Per pass: tile histograms, per-segment exclusive scan
-// in (digit, tile) order, stable scatter.  A tile is 4096 keys: 8 warps of
-// 512 keys, ranked with warp match in 16 rounds of 32.
+// in (digit, tile) order, stable scatter.  A tile is SORT_TILE_KEYS keys:
+// 8 warps, ranked with warp ballots in rounds of 32.
 // =====================================================================
 constexpr int ST = 256;                 // threads
 constexpr int SW = ST / 32;             // warps
-constexpr int SITEMS = 16;              // rounds per warp
+constexpr int SITEMS = SORT_TILE_KEYS / ST;   // rounds per warp
 constexpr int STILE = ST * SITEMS;      // keys per tile
 constexpr int SKPW = STILE / SW;        // keys per warp
 
