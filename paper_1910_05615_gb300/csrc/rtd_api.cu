@@ -261,13 +261,6 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         long long cd = (2LL * P.nsm + S.q - 1) / S.q;
         long long lim = (S.m + 511) / 512;
         P.cpb_dist = (int)(cd < lim ? (cd > 0 ? cd : 1) : lim);
-        // window-path distance pass: exactly one resident wave, at least 256
-        // rows per CTA
-        long long per_sm = S.pb <= 24 ? 2 : 1;   // shared memory of the row stages
-        long long cw = per_sm * P.nsm / S.q;
-        long long limw = (S.m + 255) / 256;
-        if (cw > limw) cw = limw;
-        P.cpb_win = (int)(cw > 0 ? cw : 1);
     }
     feistel_setup(P.F, S.n, o.seed, S.q == 1);
     P.st = at<Status>(ws, R.st);

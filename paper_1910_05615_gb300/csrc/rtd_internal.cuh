@@ -27,7 +27,6 @@ struct Plan {
     long long n, h, ld;
     int p, pb, q, m, hb, precision, cpb, nsm, max_steps;
     int cpb_dist;           // CTAs per block of the distance and compaction passes
-    int cpb_win;            // CTAs per block of the window-path distance pass
     int tc;                 // Grams on the tensor cores (split-BF16 form)
     int key_bytes;          // 4 (FP32 form) or 8 (FP64 form) for refinement sorts
     Feistel F;
@@ -72,7 +71,6 @@ void launch_start2(const Plan& P, cudaStream_t s);
 void launch_transform(const Plan& P, int which, cudaStream_t s);
 void launch_dist(const Plan& P, cudaStream_t s);
 void launch_dist_win(const Plan& P, cudaStream_t s);
-void launch_hist_keys(const Plan& P, cudaStream_t s);
 void launch_band64(const Plan& P, cudaStream_t s);
 void launch_compact(const Plan& P, cudaStream_t s);
 void launch_memb(const Plan& P, cudaStream_t s);

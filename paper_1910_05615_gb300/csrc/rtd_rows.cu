@@ -135,43 +135,6 @@ void launch_compact(const Plan& P, cudaStream_t s) {
 
 
 
-// Top-digit histogram of the keys of chains whose window missed (the
-// distance pass of the window path does not build it).
-__global__ void __launch_bounds__(NT) k_hist_keys(const float* __restrict__ dkeys, int m, int cpb, long long qm,
-                                                  const Chain* __restrict__ ch, const SelRule* __restrict__ rule,
-                                                  unsigned* __restrict__ hist) {
-    __shared__ unsigned sh[HIST_BINS];
-    const int l = blockIdx.y;
-    int r0, r1;
-    block_rows(m, cpb, r0, r1);
-    for (int k = 0; k < 2; ++k) {
-        const int c = 2 * l + k;
-        if (!ch[c].active || !rule[c].need_hist) continue;   // uniform
-        __syncthreads();
-        for (int b = threadIdx.x; b < HIST_BINS; b += NT) sh[b] = 0u;
-        __syncthreads();
-        const float* in = dkeys + (size_t)k * qm;
-        for (int base = r0; base < r1; base += NT) {
-            const int row = base + threadIdx.x;
-            const bool v = row < r1;
-            const float d = v ? in[row] : 0.f;
-            hist_add(sh, coarse_key(d) >> (32 - HIST_BITS), v);
-        }
-        __syncthreads();
-        unsigned* gh = hist + (size_t)c * HIST_BINS;
-        for (int b = threadIdx.x; b < HIST_BINS; b += NT) {
-            const unsigned v = sh[b];
-            if (v) atomicAdd(gh + b, v);
-        }
-    }
-}
-
-void launch_hist_keys(const Plan& P, cudaStream_t s) {
-    dim3 grid(P.cpb_dist, P.q);
-    k_hist_keys<<<grid, NT, 0, s>>>((const float*)P.dkeys, P.m, P.cpb_dist, (long long)P.q * P.m, P.ch, P.rule,
-                                    P.hist);
-}
-
 // ---------------------------------------------------------------- flags
 // Four distances per thread and step (one 16-byte load, one 4-byte store)
 // when d2 and flags are 16- and 4-byte aligned; one otherwise.
