@@ -31,8 +31,9 @@ if ROOT not in sys.path:
 METRIC = "rows/s per full RT-DetMCD fit (n=1e6,p=20) vs plain FP64 GPU; HBM roofline %"
 WORKLOAD = ("RT-DetMCD fit, n=1,000,000 x p=20 float32 rows, h=floor(0.75n), q=12 blocks; "
             "N(0,R) cond(R)=100 + 20% cluster outliers N(5 v_min, 0.1^2 I), seed=rank")
-CPU_SAMPLE_ROWS = 250_000
-REF_SAMPLE_ROWS = 200_000
+# oracle sample: the first 655,360 rows of the workload (q = 8 blocks, so 16
+# independent (block, start) units for the host cores)
+CPU_SAMPLE_ROWS = 655_360
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_dist_win launch at
@@ -254,6 +255,24 @@ def large_p_leg(rtd, torch, datagen, dev, stream, flush, peak, peak_kind, reps=3
     return out
 
 
+# FP64 FMA pipe of this GPU: 152 SMs x 2 FP64 FMA per clock (measured with
+# dependent-chain microbenchmarks: about 1 TFLOP/s at the median clock) x 2
+# flops x the 2,070 MHz maximum SM clock.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+
+def fp64_roofline(pp):
+    """The plain FP64 form's C-step distance stage against the FP64 ALU: p (p + 3)
+    flops per row and active chain (triangular product and squares), over the
+    stage's CUDA-event time."""
+    st = pp["stages"]["cstep_dist"]
+    a = st["flops"] / (st["ms"] / 1e3) / 1e9
+    return {"kernel": "k_dist<FP64> (C-step distances, both starts)", "bound": "alu", "achieved": a,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": a / FP64_PEAK_GFLOPS,
+            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
+            "stage_ms_per_fit": st["ms"], "share_of_fit": st["ms"] / sum(v["ms"] for v in pp["stages"].values())}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -309,34 +328,58 @@ class Clocks:
 
 
 # ------------------------------------------------------------- CPU oracle
+# The oracle as it stands, in a process of its own (no CUDA): `workers` = 1
+# runs it on one thread; more map its independent units (the column
+# univariate MCDs and the (block, start) units of steps 1-3, the paper's
+# one-thread-per-block topology) over a pool of spawned processes, one
+# single-threaded worker per core.
 CPU_CODE = r"""
-import json, os, sys, time
+import concurrent.futures as cf, json, multiprocessing as mp, os, sys, time
 sys.path.insert(0, os.environ["RTD_ROOT"])
 import datagen, oracle
-n = int(sys.argv[1]); seed = int(sys.argv[2]); reps = int(sys.argv[3])
+n = int(sys.argv[1]); seed = int(sys.argv[2]); reps = int(sys.argv[3]); workers = int(sys.argv[4])
 fr = datagen.main_case(seed=seed)
 X = fr.X[:n]
 h = int(0.75 * n)
+ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) if workers > 1 else None
+mf = ex.map if ex else map
+if ex:
+    list(ex.map(abs, range(4 * workers)))       # workers started before the clock
 ts = []
 for _ in range(reps):
     t = time.perf_counter()
-    f = oracle.fit(X, h)
+    f = oracle.fit(X, h, map_fn=mf)
     ts.append(time.perf_counter() - t)
-print(json.dumps({"n": n, "times": ts, "q": f.q}))
+if ex:
+    ex.shutdown()
+print(json.dumps({"n": n, "times": ts, "q": f.q, "workers": workers}))
 """
 
 
-def run_oracle(n_rows, seed=0, reps=1):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_oracle(n_rows, seed=0, reps=1, workers=1):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
     env["RTD_ROOT"] = ROOT
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, "-c", CPU_CODE, str(n_rows), str(seed), str(reps)],
+    r = subprocess.run([sys.executable, "-c", CPU_CODE, str(n_rows), str(seed), str(reps), str(workers)],
                        capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_text(q, workers):
+    how = "one host thread" if workers == 1 else (
+        f"{workers} single-threaded worker processes over the column MCDs and the 2q (block, start) units")
+    return f"first {CPU_SAMPLE_ROWS:,} rows of the seed-0 workload (q={q}), one fit per step, {how}"
 
 
 # ---------------------------------------------------------------- helpers
@@ -363,20 +406,17 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    steps = []
-    for i in range(args.warmup + args.steps):
-        d = run_oracle(REF_SAMPLE_ROWS, seed=0, reps=1)
-        if i >= args.warmup:
-            steps.append(d["times"][0])
+    cores = host_cores()
+    d = run_oracle(CPU_SAMPLE_ROWS, seed=0, reps=args.warmup + args.steps, workers=cores)
+    steps = d["times"][args.warmup:]
     t = statistics.mean(steps)
-    v = REF_SAMPLE_ROWS / t
-    sample = (f"first {REF_SAMPLE_ROWS} rows of the seed-0 workload per step "
-              f"(q={d['q']}), one host thread")
+    v = CPU_SAMPLE_ROWS / t
+    sample = oracle_sample_text(d["q"], cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": REF_SAMPLE_ROWS, "p": 20, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "n": CPU_SAMPLE_ROWS, "p": 20, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -469,10 +509,11 @@ def main():
     # the same steps again with per-stage CUDA events on the fit's stream
     tprof, prof32, _ = timed(X, FORM, ws32, args.steps, profile=True)
     # plain FP64 form beside it
-    t64 = []
+    t64, prof64 = [], []
     if args.fp64_steps > 0:
         fit(X, rtd.RTD_FP64, ws64)
         t64, _, r64 = timed(X, rtd.RTD_FP64, ws64, args.fp64_steps)
+        _, prof64, _ = timed(X, rtd.RTD_FP64, ws64, 1, profile=True)
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -520,7 +561,7 @@ def main():
                 "bytes_per_launch": by / la, "launch_ms": ms / la}
     dominant = max(stages, key=lambda k: stages[k]["ms_per_fit"])
     roof = stage_roof("sort", "k_sort_hist/scan/scatter (segmented LSD radix sort, 8-bit digits; "
-                      "per pass 4 B read for the histogram + 4 B read + 4 B written per key)")
+                      "algorithmic bytes per key and pass: 4 B read + 4 B written)")
     roof["dominant_stage"] = dominant
     # ncu DRAM bytes of one launch, taken on the current kernels (null when a
     # kernel changed after its capture); the summaries live under profiles/
@@ -537,10 +578,14 @@ def main():
     cpu = None
     if not args.no_cpu:
         try:
-            d = run_oracle(CPU_SAMPLE_ROWS, seed=0, reps=1)
-            cpu = {"value": CPU_SAMPLE_ROWS / d["times"][0], "unit": "rows/s", "cores": 1, "kind": "oracle",
-                   "sample": f"first {CPU_SAMPLE_ROWS} rows of the seed-0 workload (q={d['q']}), "
-                             f"one fit, one host thread", "seconds": d["times"][0]}
+            cores = host_cores()
+            dm = run_oracle(CPU_SAMPLE_ROWS, seed=0, reps=2, workers=cores)
+            d1 = run_oracle(CPU_SAMPLE_ROWS, seed=0, reps=1, workers=1)
+            tm = dm["times"][-1]
+            cpu = {"value": CPU_SAMPLE_ROWS / tm, "unit": "rows/s", "cores": cores, "kind": "oracle",
+                   "sample": oracle_sample_text(dm["q"], cores), "seconds": tm,
+                   "single_thread": {"value": CPU_SAMPLE_ROWS / d1["times"][0], "unit": "rows/s", "cores": 1,
+                                     "seconds": d1["times"][0], "sample": oracle_sample_text(d1["q"], 1)}}
         except Exception as ex:  # report, do not hide
             cpu = {"error": str(ex)[-300:]}
     scoring = None
@@ -564,7 +609,8 @@ def main():
                    "parallelism": f"{ws_n} independent replica(s)"},
         "fp64_form": ({"value": n / (statistics.mean(t64) / 1e3), "unit": "rows/s",
                        "ms_per_step": statistics.mean(t64),
-                       "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps)} if t64 else None),
+                       "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps),
+                       "roofline": fp64_roofline(prof64[0])} if t64 else None),
         "roofline": roof, "roofline_cstep": roof_c, "stages": stages, "csteps": prof32[-1]["csteps"],
         "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),

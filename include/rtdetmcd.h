@@ -13,6 +13,8 @@
  *   - Row data are float32, row-major, row stride `ld` floats (ld >= p).
  *     Every data / output pointer may be device memory or host memory
  *     (pageable or pinned); host buffers are staged through the workspace.
+ *     Device memory must belong to the current device (RTD_EINVAL for
+ *     another device's memory).
  *   - `workspace` is device memory owned by the caller, at least the size
  *     returned by the matching *_workspace_size call, 256-byte aligned.  No
  *     entry point allocates device memory.
@@ -36,6 +38,7 @@ extern "C" {
 #endif
 
 #define RTD_MAX_P 64
+#define RTD_MAX_BLOCKS 1024   /* largest number of blocks q of Section 4 */
 
 /* status codes */
 #define RTD_OK            0
@@ -64,7 +67,8 @@ extern "C" {
 typedef struct {
     int32_t  precision;            /* RTD_FP32 (default), RTD_FP64 or RTD_BF16 */
     int32_t  omega;                /* eq. partitionsize, default 4096 */
-    int32_t  q_override;           /* number of blocks; 0 = q = max(floor(n/(p omega)), 1) */
+    int32_t  q_override;           /* number of blocks, at most RTD_MAX_BLOCKS (RTD_EINVAL above);
+                                      0 = q = min(max(floor(n/(p omega)), 1), RTD_MAX_BLOCKS) */
     int32_t  max_csteps;           /* C-step cap per start, default 100 */
     double   cutoff_q;             /* chi-square quantile of the cutoff, default 0.975 */
     double   kappa_max;            /* condition threshold, default 1000 (Sections 3.3, 3.4) */
@@ -126,6 +130,10 @@ typedef struct rtd_profile {
     int32_t reserved;
     int64_t sel_cand;      /* selection candidates listed, summed over chain steps */
     int64_t sel_band;      /* rows decided in FP64 inside the band, summed over chain steps */
+    /* algorithmic floating-point operations per stage (an FMA counts 2);
+       filled for the C-step distances: p (p + 3) per row and active chain
+       (the triangular product and the squares), in the form's precision */
+    double  flops[RTD_NSTAGES];
 } rtd_profile;
 
 typedef struct {
@@ -245,8 +253,9 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld,
  * a fixed memory budget, or a process whose device memory is owned by
  * another component).  The paper has no counterpart; this is an interface
  * convenience.
- *   X, d2_out  device pointers (RTD_EINVAL for host memory: staging host rows
- *              would need memory proportional to n)
+ *   X, d2_out  device pointers on the current device (RTD_EINVAL for host
+ *              memory, whose staging would need memory proportional to n, and
+ *              for another device's memory)
  *   p          <= RTD_MAX_P, the largest fit the array holds (RTD_EINVAL above)
  * The working state (factorised fit, status word) lives in one file-scope
  * device array of RTD_NOALLOC_SCRATCH_BYTES that every GPU using the library
@@ -255,7 +264,10 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld,
  * into a CUDA graph.  All calls on a device share the array and it keeps the
  * last call's contents: calls whose device work overlaps (several threads or
  * streams at the same time) race on it and must be serialised by the caller.
- * No cudaMalloc, cudaFree or other allocation is made.
+ * The looked-up address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, so do not reset a device that
+ * this entry point has used.  No cudaMalloc, cudaFree or other allocation is
+ * made.
  */
 int rtdetmcd_distances_noalloc(const float* X, int64_t n, int32_t p, int64_t ld,
                                const double* mu_host, const double* sigma_host,

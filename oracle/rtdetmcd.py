@@ -31,6 +31,11 @@ project's design notes):
       (reweight_consistency=1, default).  0 gives the literal plain covariance;
       2 uses c(|W|/n) at the fraction of rows kept.
   R9  KL of Section 4 step 6 uses log|det(A B^-1)| (A may be indefinite).
+  R10 block count q = max(floor(n/(p omega)), 1) capped at QMAX = 1024 blocks
+      (the paper caps q by the number of CPU cores instead); an explicit q
+      above QMAX is refused.
+  R11 step 4 keeps start 1 when the two determinants tie ("<="); two starts
+      that reach the same h-subset tie exactly.
   R13 warm start (end of Section 4): a run's final (mu, Sigma) as the input
       to step 3 of the next; blocks kept, steps 1-2 and the univariate
       standardisation skipped, Z standardised by the warm fit's centre and
@@ -48,6 +53,7 @@ from scipy.linalg import solve_triangular
 
 KAPPA_MAX = 1000.0          # Section 3.3 step 2 and Section 3.4
 OMEGA = 4096                # Section 5, default omega = 2^12
+QMAX = 1024                 # largest number of blocks (reading R10)
 WRAP_B, WRAP_C = 1.5, 4.0   # Section 3.2, eq. wrapping
 WRAP_Q1, WRAP_Q2 = 1.541, 0.862
 CUTOFF_Q = 0.975            # Section 2.1
@@ -147,8 +153,9 @@ def univariate_mcd_bruteforce(x):
 # Section 4 (random partition) and Section 5 (eq. partitionsize)
 # ----------------------------------------------------------------------------
 def block_count(n: int, p: int, omega: int = OMEGA) -> int:
-    """q = max(floor(n / (p omega)), 1)   (eq. partitionsize)."""
-    return max(n // (p * omega), 1)
+    """q = max(floor(n / (p omega)), 1)   (eq. partitionsize), at most QMAX
+    (reading R10)."""
+    return min(max(n // (p * omega), 1), QMAX)
 
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -506,19 +513,45 @@ def validate(n: int, p: int, h: int):
         raise OracleError("need [(n+p+1)/2] <= h < n")
 
 
+def block_start_unit(args):
+    """Steps 1-3 of Section 4 for one start k of one block: the initial
+    scatter S~_k (Section 3.2), its refinement (Section 3.3) and the C-steps
+    (Sections 2.1, 3.4).  Returns (S~_k, Start | None, Chain | None).  The
+    paper runs each block on its own thread; `fit` may map these units over
+    host processes."""
+    Zl, k, h_b, kappa_max, max_steps = args
+    Sk = start_wrap(Zl) if k == 0 else start_gsscm(Zl)
+    st = refine(Zl, Sk, kappa_max)
+    if st is None:
+        return Sk, None, None
+    return Sk, st, csteps(Zl, st.mu, st.Sigma, h_b, kappa_max, max_steps)
+
+
+def _column_mcd(args):
+    x, cutoff_q = args
+    return univariate_mcd(x, cutoff_q)
+
+
 def fit(X, h: int, *, omega: int = OMEGA, seed: int = 0,
         kappa_max: float = KAPPA_MAX, cutoff_q: float = CUTOFF_Q,
         max_steps: int = MAX_CSTEPS, q: int | None = None,
-        reweight_consistency: int = 1, init=None) -> Fit:
+        reweight_consistency: int = 1, init=None, map_fn=map) -> Fit:
     """init = (mu, Sigma) in X units: warm start (end of Section 4: the final
     estimate of a run as the input to step 3 of the next).  Reading R13:
     the blocks are kept (step 3 runs per block), steps 1-2 and the
     univariate standardisation are skipped; Z is standardised by the warm
     fit's own centre and diagonal, and each block runs one chain, from the
-    warm fit."""
+    warm fit.
+
+    map_fn (default: the builtin map) evaluates the independent units, the
+    column univariate MCDs and the (block, start) units of steps 1-3, in
+    order; a process pool's map runs them on several host cores with the
+    same results."""
     X = np.asarray(X, dtype=np.float64)
     n, p = X.shape
     validate(n, p, h)
+    if q is not None and not 1 <= q <= QMAX:
+        raise OracleError("need 1 <= q <= QMAX blocks (reading R10)")
     if init is not None:
         mu_uni = np.asarray(init[0], dtype=np.float64).reshape(p)
         S_init = np.asarray(init[1], dtype=np.float64).reshape(p, p)
@@ -527,7 +560,7 @@ def fit(X, h: int, *, omega: int = OMEGA, seed: int = 0,
         s_uni = np.sqrt(np.diag(S_init))
     else:
         # Section 3.1 and Section 4 (eq. standardization): whole-X univariate MCD.
-        uni = [univariate_mcd(X[:, j], cutoff_q) for j in range(p)]
+        uni = list(map_fn(_column_mcd, [(X[:, j], cutoff_q) for j in range(p)]))
         mu_uni = np.array([u.mu for u in uni])
         s_uni = np.sqrt(np.array([u.s2 for u in uni]))
     Z = (X - mu_uni) / s_uni
@@ -542,26 +575,24 @@ def fit(X, h: int, *, omega: int = OMEGA, seed: int = 0,
     alpha = h / n
     c_alpha = consistency_factor(alpha, p)
     blocks = []
+    if init is None:
+        # Steps 1-3 for every (block, start): initial scatter, refinement,
+        # C-steps; independent units.
+        units = list(map_fn(block_start_unit,
+                            [(Z[perm[l * m:(l + 1) * m]], k, h_b, kappa_max, max_steps)
+                             for l in range(q) for k in range(2)]))
     for l in range(q):
         rows = perm[l * m:(l + 1) * m]
-        Zl = Z[rows]
         if init is not None:
             # warm start: step 3 only, from the warm fit (Z units)
             S = [None, None]
             starts = [None, None]
             Sz = S_init / np.outer(s_uni, s_uni)
-            chains = [csteps(Zl, np.zeros(p), Sz, h_b, kappa_max, max_steps), None]
+            chains = [csteps(Z[rows], np.zeros(p), Sz, h_b, kappa_max, max_steps), None]
         else:
-            # Step 1: the two initial scatters; step 2: refinement; step 3: C-steps.
-            S = [start_wrap(Zl), start_gsscm(Zl)]
-            starts, chains = [], []
-            for Sk in S:
-                st = refine(Zl, Sk, kappa_max)
-                starts.append(st)
-                if st is None:
-                    chains.append(None)
-                    continue
-                chains.append(csteps(Zl, st.mu, st.Sigma, h_b, kappa_max, max_steps))
+            S = [units[2 * l][0], units[2 * l + 1][0]]
+            starts = [units[2 * l][1], units[2 * l + 1][1]]
+            chains = [units[2 * l][2], units[2 * l + 1][2]]
         # Step 4: the start with the lower determinant (start 1 on ties).
         b = Block(rows, S, starts, chains)
         ok = [k for k in range(2) if chains[k] is not None and chains[k].ok]

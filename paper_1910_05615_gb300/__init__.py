@@ -59,7 +59,8 @@ class _Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("bytes", ctypes.c_double * len(STAGES)),
                 ("launches", ctypes.c_int64 * len(STAGES)), ("csteps", ctypes.c_int32),
                 ("win_steps", ctypes.c_int32), ("win_miss", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("sel_cand", ctypes.c_int64), ("sel_band", ctypes.c_int64)]
+                ("sel_cand", ctypes.c_int64), ("sel_band", ctypes.c_int64),
+                ("flops", ctypes.c_double * len(STAGES))]
 
 
 class _Result(ctypes.Structure):
@@ -265,7 +266,7 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     if profile:
         out["profile"] = {"csteps": prof.csteps, "win_steps": prof.win_steps, "win_miss": prof.win_miss,
                           "sel_cand": prof.sel_cand, "sel_band": prof.sel_band, "stages": {
-            name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i]}
+            name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i], "flops": prof.flops[i]}
             for i, name in enumerate(STAGES)}}
     return out
 
@@ -375,14 +376,23 @@ def rtdetmcd_distances_noalloc(X, mu, Sigma, *, precision=RTD_FP32, out=None, st
     allocate when they score: no workspace, the library uses a fixed device
     array instead.  X (and out, if given) must be CUDA tensors."""
     lib = _load()
+    torch = _torch()
     ptr, n, p, ld, dev, keep = _rows(X)
     if dev is None:
         raise ValueError("rtdetmcd_distances_noalloc needs X on a CUDA device")
-    mu = np.ascontiguousarray(mu, dtype=np.float64)
-    S = np.ascontiguousarray(Sigma, dtype=np.float64)
+    if out is not None:
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        if out.device != dev or out.numel() < n:
+            raise ValueError("out must be on X's device and hold at least n = %d values" % n)
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(-1)
+    S = np.ascontiguousarray(Sigma, dtype=np.float64).reshape(-1)
+    if mu.size != p or S.size != p * p:
+        raise ValueError("mu must have p entries and Sigma p x p")
     d2 = out if out is not None else _out(n, np.float32, dev)
-    st = lib.rtdetmcd_distances_noalloc(ptr, n, p, ld, mu.ctypes.data, S.ctypes.data, precision, _ptr(d2),
-                                        _stream_ptr(dev, stream))
+    with torch.cuda.device(dev):
+        st = lib.rtdetmcd_distances_noalloc(ptr, n, p, ld, mu.ctypes.data, S.ctypes.data, precision, _ptr(d2),
+                                            _stream_ptr(dev, stream))
     del keep
     if st != 0:
         raise RtdError(st, lib.rtdetmcd_status_string(st).decode())

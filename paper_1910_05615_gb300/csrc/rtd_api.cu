@@ -19,7 +19,7 @@ namespace {
 
 constexpr int TARGET_CTAS = 304;      // row-kernel CTAs per pass (all blocks): 2 per SM
 constexpr int MIN_ROWS_PER_CTA = 256;
-constexpr int MAX_BLOCKS = 1024;
+constexpr int MAX_BLOCKS = RTD_MAX_BLOCKS;
 
 struct Region {
     size_t off, bytes;
@@ -70,7 +70,7 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (ld < p) return RTD_EINVAL;
     if (o.precision != RTD_FP32 && o.precision != RTD_FP64 && o.precision != RTD_BF16) return RTD_EINVAL;
     if (o.precision == RTD_BF16 && (p < 25 || p > 48)) return RTD_EINVAL;
-    if (o.omega < 1 || o.max_csteps < 1 || o.q_override < 0) return RTD_EINVAL;
+    if (o.omega < 1 || o.max_csteps < 1 || o.q_override < 0 || o.q_override > MAX_BLOCKS) return RTD_EINVAL;
     if (!(o.cutoff_q > 0.0 && o.cutoff_q < 1.0) || !(o.kappa_max > 1.0)) return RTD_EINVAL;
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
     if (o.select_path < 0 || o.select_path > 2) return RTD_EINVAL;
@@ -87,6 +87,8 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     S.precision = (o.precision == RTD_BF16) ? RTD_FP32 : o.precision;
     S.tc = o.precision == RTD_BF16;
     S.max_steps = o.max_csteps;
+    // eq. partitionsize, at most MAX_BLOCKS blocks (the paper caps q by the
+    // number of CPU cores instead); an explicit q above it is refused above
     long long q = o.q_override ? o.q_override : n / ((long long)p * o.omega);
     if (q < 1) q = 1;
     if (q > MAX_BLOCKS) q = MAX_BLOCKS;
@@ -175,6 +177,18 @@ bool is_device_ptr(const void* ptr) {
     cudaError_t e = cudaPointerGetAttributes(&a, ptr);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device memory of a device other than the current one (where the kernels
+// run): such pointers are refused rather than read as peer memory.
+bool on_other_device(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.device != dev;
 }
 
 #define RTD_CUDA(call)                                  \
@@ -330,8 +344,9 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         pf.end(0, 0.0);
         pf.begin(RTD_STAGE_SORT);
         sort_segments(P, keys, P.arenaB, kb, nseg, L, s);
-        // per pass: histogram read, scatter read + write
-        pf.end(3 * kb, (double)nseg * L * kb * 3.0 * kb);
+        // algorithmic bytes: every key read and written once per 8-bit pass
+        // (the histogram pass's extra read of the keys is overhead)
+        pf.end(3 * kb, (double)nseg * L * kb * 2.0 * kb);
         pf.begin(stage);
     };
     // Sections 3.1 and 4: setup, univariate MCD of every column
@@ -395,6 +410,7 @@ csteps:
             else launch_dist(P, s);
             // rows read, keys written
             pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_);
+            if (o.profile) o.profile->flops[RTD_STAGE_CDIST] += mch * p_ * (p_ + 3.0);
             pf.begin(RTD_STAGE_CSELECT);
             if (win) {
                 launch_select_win(P, s);   // a chain whose window missed takes the histogram path there
@@ -539,6 +555,11 @@ int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, co
         out->status = RTD_EWORKSPACE;
         return RTD_EWORKSPACE;
     }
+    if (on_other_device(X) || on_other_device(d2_out) || on_other_device(flags_out) ||
+        on_other_device(workspace) || on_other_device(o.subset_out) || on_other_device(o.diag_out)) {
+        out->status = RTD_EINVAL;
+        return RTD_EINVAL;
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int r = run_fit(X, S, o, workspace, s, out, d2_out, flags_out);
     out->status = r;
@@ -649,6 +670,7 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld, const d
         return RTD_EINVAL;
     size_t need = rtdetmcd_distances_workspace_size(n, p);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    if (on_other_device(X) || on_other_device(d2_out) || on_other_device(workspace)) return RTD_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Layout L;
     Region rst = L.add(sizeof(Status));
@@ -707,6 +729,8 @@ int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_
         return RTD_EINVAL;
     size_t need = rtdetmcd_grad_workspace_size(n, p);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    if (on_other_device(X) || on_other_device(wset) || on_other_device(grad_out) || on_other_device(workspace))
+        return RTD_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t slot_d = (size_t)gram_nblk(pad_p(p)) * 16 + 2;
     Layout L;

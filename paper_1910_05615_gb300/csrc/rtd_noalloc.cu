@@ -63,10 +63,16 @@ int scratch_address(void** out) {
     return RTD_OK;
 }
 
+// Device (or managed) memory that the current device's kernels may read as
+// their own: memory of another device is refused, not read as peer memory.
 bool on_device(const void* ptr) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.device == dev;
 }
 
 }  // namespace
@@ -78,7 +84,9 @@ extern "C" int rtdetmcd_distances_noalloc(const float* X, int64_t n, int32_t p, 
         (precision != RTD_FP32 && precision != RTD_FP64))
         return RTD_EINVAL;
     if (p < 1 || p > RTD_MAX_P) return RTD_EINVAL;          // beyond what the array holds
-    if (!on_device(X) || !on_device(d2_out)) return RTD_EINVAL;   // host data would need staging
+    // host data would need staging memory; another device's memory is not
+    // this device's to write
+    if (!on_device(X) || !on_device(d2_out)) return RTD_EINVAL;
     void* base = nullptr;
     int e = scratch_address(&base);
     if (e) return e;

@@ -77,6 +77,24 @@ def test_fit_rejects_before_device_work(lib, n, p, ld, h, code):
     assert st == code and res.status == code
 
 
+def test_fit_rejects_too_many_blocks(lib):
+    """An explicit block count above RTD_MAX_BLOCKS = 1024 is refused (the
+    rule's own q is capped there instead, reading R10)."""
+    import paper_1910_05615_gb300 as m
+    n, p = 100_000, 2
+    X = np.zeros((n, p), np.float32)
+    o = m._Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    for q, code in ((1025, 1), (1024, 5)):     # 5: valid, but no workspace
+        o.q_override = q
+        res = m._Result()
+        st = lib.rtdetmcd_fit(X.ctypes.data, n, p, p, (3 * n) // 4, ctypes.byref(o), None, 0, None,
+                              ctypes.byref(res), None, None)
+        assert st == code, q
+    o.q_override = 1025
+    assert lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o)) == 0
+
+
 @pytest.mark.parametrize("p", [24, 49])
 def test_bf16_form_width_range(lib, p):
     """The tensor-core Gram form covers 25 <= p <= 48 only."""

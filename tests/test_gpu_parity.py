@@ -144,6 +144,11 @@ def test_fit_main_case(rtd, main_case, form):
     for l, b in enumerate(ref.blocks):
         assert got["diag"]["blocks"][l]["chosen"] == b.chosen
         assert got["diag"]["blocks"][l]["kept"] == int(l in ref.kept)
+    # the update-based C-step (Section 3.5) is taken: some chain recomputed
+    # its Gram from scratch at fewer steps than it ran
+    ch = got["diag"]["chains"]
+    assert any(c["status"] == 0 and 0 < c["full_recomputes"] < c["steps"] for c in ch)
+    assert sum(c["steps"] - c["full_recomputes"] for c in ch) > 0
 
 
 # ------------------------------------------------------------ edge cases
@@ -193,6 +198,23 @@ def test_fit_edges(rtd, form, n, p, alpha, seed):
     ok, rep = compare_fit(got, ref, fr.X, form)
     if not ok:
         pytest.fail(str(rep))
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
+def test_fit_block_cap(rtd, form):
+    """n / (p omega) = 1250 blocks by eq. partitionsize, capped at 1024
+    (reading R10) on both sides: 1024 blocks of 39 rows."""
+    fr = datagen.contaminated_gaussian(40_000, 2, eps=0.1, kind="point", shift=9.0, seed=12)
+    ref = O.fit(fr.X, fr.h, omega=16)
+    assert ref.q == 1024 and ref.m == 39
+    got = rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, omega=16, subset=True,
+                           precision=rtd.RTD_FP32 if form == "fp32" else rtd.RTD_FP64)
+    assert got["q"] == 1024 and got["m"] == 39
+    ok, rep = compare_fit(got, ref, fr.X, form)
+    if not ok:
+        pytest.fail(str(rep))
+    with pytest.raises(rtd.RtdError):
+        rtd.rtdetmcd_fit(torch.from_numpy(fr.X).cuda(), fr.h, q=1025)
 
 
 def test_fit_deterministic(rtd):
