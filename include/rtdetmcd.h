@@ -59,10 +59,11 @@ extern "C" {
 /* arithmetic of the row passes (distances, Grams, sort keys) */
 #define RTD_FP64 0   /* plain FP64 form */
 #define RTD_FP32 1   /* FP32 row passes, FP64 p x p algebra, FP64 recompute near every threshold */
-#define RTD_BF16 2   /* the FP32 form with every Gram (starts, C-steps, reweighting) on the tensor
-                        cores: rows centred in FP32 and split into BF16 high and low parts, all four
-                        partial products with FP32 accumulation, FP64 sums every 4,096 rows;
-                        25 <= p <= 48 (RTD_EINVAL otherwise) */
+#define RTD_BF16 2   /* the FP32 form with the Grams of the starts and C-steps on the tensor
+                        cores: rows centred in FP32 and split into BF16 high, middle and low
+                        parts (24 significant bits), the six leading partial products with FP32
+                        accumulation, compensated FP32 sums every 256 rows; the reweighting Gram
+                        stays on the FP32 CUDA-core path; 25 <= p <= 48 (RTD_EINVAL otherwise) */
 
 typedef struct {
     int32_t  precision;            /* RTD_FP32 (default), RTD_FP64 or RTD_BF16 */
@@ -312,6 +313,33 @@ int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld,
                   const double* mu_host, const double* sigma_host, double c,
                   double w_logdet, double w_rd, double* value_out, float* grad_out,
                   void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Vector-Jacobian product of the reweighted fit (Section 4 steps 8-10) with
+ * the reweighting set W held fixed: for the outputs
+ *   mu = mean of the rows in W (p), Sigma = c * S_W (p x p),
+ *   log det Sigma, and RD_i = sqrt((x_i - mu)^T Sigma^-1 (x_i - mu)) (n rows),
+ * and cotangents (gmu, gSigma, g_logdet, gRD) on them, grad_out receives
+ *   d/dX [ gmu . mu + <gSigma, Sigma> + g_logdet log det Sigma + gRD . RD ].
+ * The paper has no counterpart: W and the h-subsets are discrete choices,
+ * and with them fixed the fit is smooth in the rows, which gives every row's
+ * influence on the fit.
+ *   X, wset, wbit, mu_host, sigma_host, c   as for rtdetmcd_grad
+ *   gmu_host     nullable (zero), host, p doubles
+ *   gsigma_host  nullable (zero), host, p x p doubles row-major (its
+ *                symmetric part acts, Sigma being symmetric)
+ *   grd          nullable (zero), device, n floats: cotangent on RD
+ *   grad_out     device, n x p floats (row-major, stride p)
+ * Workspace: rtdetmcd_grad_workspace_size(n, p) bytes.  Returns RTD_EINVAL
+ * for host X, wset, grd or grad_out and non-finite cotangents,
+ * RTD_EDEGENERATE when |W| < p + 1.  Rows with RD_i = 0 take the zero
+ * subgradient of their own distance.  Row arithmetic in FP32, sums across
+ * rows in FP64.
+ */
+int rtdetmcd_vjp(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t* wset, int32_t wbit,
+                 const double* mu_host, const double* sigma_host, double c, const double* gmu_host,
+                 const double* gsigma_host, double g_logdet, const float* grd, float* grad_out,
+                 void* workspace, size_t ws_bytes, void* stream);
 
 /* chi2_{p, q} quantile as used for the cutoff (computed by the library's own
    incomplete-gamma routines). */

@@ -700,4 +700,48 @@ def fixed_set_gradient(X, W, c, w_logdet=1.0, w_rd=1.0):
     return grad
 
 
+def fixed_set_outputs(X, W, c):
+    """(mu, Sigma, log det Sigma, RD) of the reweighted fit with the set W
+    held fixed (steps 8-10): mu = mean of W, Sigma = c * (covariance of W,
+    denominator |W| - 1), RD over all rows."""
+    X = np.asarray(X, dtype=np.float64)
+    Xw = X[np.asarray(W, dtype=bool)]
+    mu = Xw.mean(axis=0)
+    S = c * np.cov(Xw, rowvar=False, ddof=1).reshape(X.shape[1], X.shape[1])
+    L = np.linalg.cholesky(S)
+    Y = solve_triangular(L, (X - mu).T, lower=True)
+    return mu, S, float(2.0 * np.sum(np.log(np.diag(L)))), np.sqrt(np.sum(Y * Y, axis=0))
+
+
+def fixed_set_vjp(X, W, c, gmu=None, gSigma=None, g_logdet=0.0, gRD=None):
+    """d/dX of gmu.mu + <gSigma, Sigma> + g_logdet log det Sigma + gRD.RD for
+    the outputs of fixed_set_outputs, from the chain rule.  With
+    r_i = x_i - mu, u_i = Sigma^-1 r_i, omega_i = gRD_i / RD_i, N = |W|:
+      the cotangents reaching mu and Sigma through RD and log det are
+        gmu_t = gmu - sum_j omega_j u_j,
+        G_t   = sym(gSigma) + g_logdet Sigma^-1 - 1/2 sum_j omega_j u_j u_j^T
+      (dRD_j/dmu = -u_j/RD_j, dRD_j/dSigma = -u_j u_j^T/(2 RD_j),
+      dlogdet/dSigma = Sigma^-1); then d mu/dx_i = [i in W] I/N and
+      dSigma = c/(N-1) sum_W (dx r^T + r dx^T), so
+        grad_i = omega_i u_i + [i in W] (gmu_t / N + 2 c/(N-1) G_t r_i).
+    Rows with RD_i = 0 take the zero subgradient of their own term."""
+    X = np.asarray(X, dtype=np.float64)
+    W = np.asarray(W, dtype=bool)
+    n, p = X.shape
+    N = int(W.sum())
+    mu, S, _, rd = fixed_set_outputs(X, W, c)
+    Sinv = np.linalg.inv(S)
+    R = X - mu
+    U = R @ Sinv
+    gmu = np.zeros(p) if gmu is None else np.asarray(gmu, dtype=np.float64)
+    gS = np.zeros((p, p)) if gSigma is None else np.asarray(gSigma, dtype=np.float64)
+    gRD = np.zeros(n) if gRD is None else np.asarray(gRD, dtype=np.float64)
+    om = np.where(rd > 0, gRD / np.where(rd > 0, rd, 1.0), 0.0)
+    gmu_t = gmu - (U * om[:, None]).sum(axis=0)
+    G_t = 0.5 * (gS + gS.T) + g_logdet * Sinv - 0.5 * (U * om[:, None]).T @ U
+    grad = U * om[:, None]
+    grad[W] += gmu_t / N + (2.0 * c / (N - 1)) * (R[W] @ G_t)
+    return grad
+
+
 __all__ = [name for name in dir() if not name.startswith("_")]

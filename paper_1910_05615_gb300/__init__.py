@@ -23,7 +23,7 @@ __all__ = [
     "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
     "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
     "rtdetmcd_grad_workspace_size", "rtdetmcd_objective", "rtdetmcd_fit_batch",
-    "rtdetmcd_fit_batch_workspace_size",
+    "rtdetmcd_fit_batch_workspace_size", "rtdetmcd_vjp", "rtdetmcd_fit_outputs",
 ]
 
 RTD_FP64 = 0
@@ -118,6 +118,8 @@ def _load():
     lib.rtdetmcd_grad.argtypes = [vp, i64, i32, i64, vp, i32, vp, vp, dbl, dbl, dbl, ctypes.POINTER(dbl), vp,
                                   vp, sz, vp]
     lib.rtdetmcd_grad.restype = i32
+    lib.rtdetmcd_vjp.argtypes = [vp, i64, i32, i64, vp, i32, vp, vp, dbl, vp, vp, dbl, vp, vp, vp, sz, vp]
+    lib.rtdetmcd_vjp.restype = i32
     lib.rtdetmcd_flag.argtypes = [vp, i64, dbl, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.rtdetmcd_flag.restype = i32
     lib.rtdetmcd_chi2_quantile.argtypes = [i32, dbl]
@@ -430,6 +432,90 @@ def rtdetmcd_grad(X, wset, mu, Sigma, c, *, wbit=1, w_logdet=1.0, w_rd=1.0, grad
     if st != 0:
         raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
     return val.value, g
+
+
+def rtdetmcd_vjp(X, wset, mu, Sigma, c, *, gmu=None, gSigma=None, glogdet=0.0, gRD=None, wbit=1, stream=None,
+                 workspace=None):
+    """d/dX of gmu.mu + <gSigma, Sigma> + glogdet log det Sigma + gRD.RD for
+    the reweighted fit (mu, Sigma = c S_W, RD over all rows) with the set W
+    (bit `wbit` of wset) held fixed.  X, wset and gRD are CUDA tensors; gmu,
+    gSigma host arrays or tensors (None = zero).  Returns the n x p gradient
+    (CUDA float32)."""
+    lib = _load()
+    torch = _torch()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    if dev is None or not (isinstance(wset, torch.Tensor) and wset.is_cuda):
+        raise ValueError("rtdetmcd_vjp needs X and wset on a CUDA device")
+    if wset.dtype != torch.uint8 or wset.numel() != n or not wset.is_contiguous():
+        raise ValueError("wset must be a contiguous uint8 tensor of n bytes")
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(-1)
+    S = np.ascontiguousarray(Sigma, dtype=np.float64).reshape(-1)
+    if mu.size != p or S.size != p * p:
+        raise ValueError("mu must have p entries and Sigma p x p")
+
+    def host(a, size):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            a = a.detach().cpu().numpy()
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if a.size != size:
+            raise ValueError("cotangent of the wrong size")
+        return a
+
+    gm, gs = host(gmu, p), host(gSigma, p * p)
+    grd = None
+    if gRD is not None:
+        if not (isinstance(gRD, torch.Tensor) and gRD.is_cuda and gRD.device == dev) or gRD.numel() != n:
+            raise ValueError("gRD must be a CUDA tensor of n values on X's device")
+        grd = gRD.detach().to(torch.float32).contiguous()
+    ws = workspace if workspace is not None else _workspace(lib.rtdetmcd_grad_workspace_size(n, p), dev)
+    g = torch.empty((n, p), dtype=torch.float32, device=dev)
+    st = lib.rtdetmcd_vjp(ptr, n, p, ld, wset.data_ptr(), wbit, mu.ctypes.data, S.ctypes.data, float(c),
+                          gm.ctypes.data if gm is not None else None, gs.ctypes.data if gs is not None else None,
+                          float(glogdet), _ptr(grd), g.data_ptr(), ws.data_ptr(), ws.numel(),
+                          _stream_ptr(dev, stream))
+    del keep
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return g
+
+
+_outputs_fn = None
+
+
+def rtdetmcd_fit_outputs(X, h, **fit_kwargs):
+    """Differentiable outputs (mu, Sigma, logdet, RD) of the reweighted fit of
+    the rows of X (a CUDA float32 tensor): mu (p) and Sigma (p x p) float64,
+    logdet a 0-d float64, RD (n) float32, all on X's device.  The forward
+    pass runs rtdetmcd_fit; the backward pass holds the fit's discrete
+    choices (the h-subsets and the reweighting set W) fixed and applies
+    rtdetmcd_vjp to the incoming cotangents of all four outputs."""
+    global _outputs_fn
+    torch = _torch()
+    if _outputs_fn is None:
+        class _Outputs(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Xt, hh, kw):
+                fit = rtdetmcd_fit(Xt.detach(), hh, d2=True, flags=False, subset=True, **kw)
+                ctx.save_for_backward(Xt, fit["subset"])
+                ctx.fit = (fit["mu"], fit["Sigma"], fit["c_rew"])
+                dev = Xt.device
+                mu = torch.tensor(fit["mu"], dtype=torch.float64, device=dev)
+                S = torch.tensor(fit["Sigma"], dtype=torch.float64, device=dev)
+                ld = torch.tensor(fit["logdet"], dtype=torch.float64, device=dev)
+                return mu, S, ld, fit["d2"].clamp_min(0).sqrt()
+
+            @staticmethod
+            def backward(ctx, gmu, gS, gld, grd):
+                Xt, sub = ctx.saved_tensors
+                mu, S, c = ctx.fit
+                g = rtdetmcd_vjp(Xt.detach(), sub, mu, S, c, gmu=gmu, gSigma=gS,
+                                 glogdet=float(gld) if gld is not None else 0.0, gRD=grd)
+                return g, None, None
+
+        _outputs_fn = _Outputs
+    return _outputs_fn.apply(X, h, fit_kwargs)
 
 
 _objective_fn = None

@@ -717,19 +717,22 @@ size_t rtdetmcd_grad_workspace_size(int64_t n, int32_t p) {
     L.add((size_t)GRAD_SLOTS * slot_d * sizeof(double));
     L.add(slot_d * sizeof(double));
     L.add(sizeof(double));
+    L.add((size_t)RTD_MAX_P * (RTD_MAX_P + 1) * sizeof(double));   // cotangents on mu and Sigma
     return (L.total + 255) & ~(size_t)255;
 }
 
-int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t* wset, int32_t wbit,
-                  const double* mu_host, const double* sigma_host, double c, double w_logdet, double w_rd,
-                  double* value_out, float* grad_out, void* workspace, size_t ws_bytes, void* stream) {
-    if (!X || !wset || !mu_host || !sigma_host || n < 2 || p < 1 || p > RTD_MAX_P || ld < p || wbit < 0 ||
-        wbit > 7 || !(c > 0.0) || !std::isfinite(c) || !std::isfinite(w_logdet) || !std::isfinite(w_rd) ||
-        !is_device_ptr(X) || !is_device_ptr(wset) || (grad_out && !is_device_ptr(grad_out)))
-        return RTD_EINVAL;
+namespace {
+
+// The adjoint passes of rtdetmcd_grad and rtdetmcd_vjp: device cotangents
+// `grd` (nullable), host cotangents gmu (p) / gsig (p x p) (nullable).
+int grad_impl(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t* wset, int32_t wbit,
+              const double* mu_host, const double* sigma_host, double c, double w_logdet, double w_rd,
+              const float* grd, const double* gmu_host, const double* gsig_host, double* value_out,
+              float* grad_out, void* workspace, size_t ws_bytes, void* stream) {
     size_t need = rtdetmcd_grad_workspace_size(n, p);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
-    if (on_other_device(X) || on_other_device(wset) || on_other_device(grad_out) || on_other_device(workspace))
+    if (on_other_device(X) || on_other_device(wset) || on_other_device(grad_out) || on_other_device(workspace) ||
+        on_other_device(grd))
         return RTD_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t slot_d = (size_t)gram_nblk(pad_p(p)) * 16 + 2;
@@ -740,19 +743,31 @@ int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_
     Region rpa = L.add((size_t)GRAD_SLOTS * slot_d * sizeof(double));
     Region rto = L.add(slot_d * sizeof(double));
     Region rld = L.add(sizeof(double));
+    Region rcot = L.add((size_t)RTD_MAX_P * (RTD_MAX_P + 1) * sizeof(double));
     Status* st = at<Status>(workspace, rst);
     RowParams* rp = at<RowParams>(workspace, rrp);
     double* ms = at<double>(workspace, rms);
     double* tot = at<double>(workspace, rto);
     double* ldv = at<double>(workspace, rld);
+    double* cot = at<double>(workspace, rcot);
     int dev = 0, nsm = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     RTD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     RTD_CUDA(cudaMemsetAsync(st, 0, sizeof(Status), s));
     RTD_CUDA(cudaMemcpyAsync(ms, mu_host, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, s));
     RTD_CUDA(cudaMemcpyAsync(ms + RTD_MAX_P, sigma_host, (size_t)p * p * sizeof(double), cudaMemcpyHostToDevice, s));
+    GradCot gc{grd, nullptr, nullptr};
+    if (gmu_host) {
+        RTD_CUDA(cudaMemcpyAsync(cot, gmu_host, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, s));
+        gc.gmu = cot;
+    }
+    if (gsig_host) {
+        RTD_CUDA(cudaMemcpyAsync(cot + RTD_MAX_P, gsig_host, (size_t)p * p * sizeof(double), cudaMemcpyHostToDevice,
+                                 s));
+        gc.gsig = cot + RTD_MAX_P;
+    }
     launch_score_prep(ms, ms + RTD_MAX_P, p, rp, st, s, ldv);
-    launch_grad(X, n, p, ld, wset, (int)wbit, rp, at<double>(workspace, rpa), slot_d, tot, c, w_logdet, w_rd,
+    launch_grad(X, n, p, ld, wset, (int)wbit, rp, at<double>(workspace, rpa), slot_d, tot, c, w_logdet, w_rd, gc,
                 grad_out, nsm, s);
     RTD_CUDA(cudaGetLastError());
     double h[3];
@@ -766,6 +781,40 @@ int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_
     if (h[1] < (double)p + 1.0) return RTD_EDEGENERATE;
     if (value_out) *value_out = w_logdet * h[2] + w_rd * h[0];
     return RTD_OK;
+}
+
+bool finite_all(const double* a, size_t k) {
+    for (size_t i = 0; i < k; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+int rtdetmcd_grad(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t* wset, int32_t wbit,
+                  const double* mu_host, const double* sigma_host, double c, double w_logdet, double w_rd,
+                  double* value_out, float* grad_out, void* workspace, size_t ws_bytes, void* stream) {
+    if (!X || !wset || !mu_host || !sigma_host || n < 2 || p < 1 || p > RTD_MAX_P || ld < p || wbit < 0 ||
+        wbit > 7 || !(c > 0.0) || !std::isfinite(c) || !std::isfinite(w_logdet) || !std::isfinite(w_rd) ||
+        !is_device_ptr(X) || !is_device_ptr(wset) || (grad_out && !is_device_ptr(grad_out)))
+        return RTD_EINVAL;
+    return grad_impl(X, n, p, ld, wset, wbit, mu_host, sigma_host, c, w_logdet, w_rd, nullptr, nullptr, nullptr,
+                     value_out, grad_out, workspace, ws_bytes, stream);
+}
+
+int rtdetmcd_vjp(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t* wset, int32_t wbit,
+                 const double* mu_host, const double* sigma_host, double c, const double* gmu_host,
+                 const double* gsigma_host, double g_logdet, const float* grd, float* grad_out, void* workspace,
+                 size_t ws_bytes, void* stream) {
+    if (!X || !wset || !mu_host || !sigma_host || !grad_out || n < 2 || p < 1 || p > RTD_MAX_P || ld < p ||
+        wbit < 0 || wbit > 7 || !(c > 0.0) || !std::isfinite(c) || !std::isfinite(g_logdet) || !is_device_ptr(X) ||
+        !is_device_ptr(wset) || !is_device_ptr(grad_out) || (grd && !is_device_ptr(grd)))
+        return RTD_EINVAL;
+    if ((gmu_host && !finite_all(gmu_host, (size_t)p)) || (gsigma_host && !finite_all(gsigma_host, (size_t)p * p)))
+        return RTD_EINVAL;
+    // without a cotangent on RD its rows carry weight zero
+    return grad_impl(X, n, p, ld, wset, wbit, mu_host, sigma_host, c, g_logdet, 0.0, grd, gmu_host, gsigma_host,
+                     nullptr, grad_out, workspace, ws_bytes, stream);
 }
 
 int rtdetmcd_flag(const float* d2, int64_t n, double cutoff_d2, uint8_t* flags_out, int64_t* n_flagged,

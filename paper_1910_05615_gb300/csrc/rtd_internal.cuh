@@ -115,11 +115,20 @@ void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* 
                        Status* st, cudaStream_t s, double* logdet_out = nullptr);
 // adjoint of steps 8-10 (rtd_rows.cu): slot count of the reduction pass
 constexpr int GRAD_SLOTS = 1024;
+// Cotangents of the vector-Jacobian product of the reweighted fit (device
+// pointers, each nullable = zero): grd on RD (n floats; NULL = the scalar
+// objective's weight w_rd on every row), gmu on mu (p doubles), gsig on
+// Sigma (p x p doubles, row-major; its symmetric part is used).
+struct GradCot {
+    const float* grd;
+    const double* gmu;
+    const double* gsig;
+};
 // keys per tile of the segmented radix sort (threads x keys per thread)
 constexpr int SORT_TILE_KEYS = 4096;
 void launch_grad(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
                  const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,
-                 double w_rd, float* grad, int nsm, cudaStream_t s);
+                 double w_rd, GradCot cot, float* grad, int nsm, cudaStream_t s);
 
 // Gram partial layout: blocks (bi <= bj) of 4 x 4 over the extended vector
 // e = (v_0 .. v_{p-1}, 1, 0 ...) of length pe = pb + 4.

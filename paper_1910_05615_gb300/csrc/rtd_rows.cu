@@ -200,8 +200,9 @@ void launch_dist_win(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist_win
 void launch_band64(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, band64, P, s); }
 void launch_grad(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
                  const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,
-                 double w_rd, float* grad, int nsm, cudaStream_t s) {
-    RTD_PB_CALL(pad_p(p), grad, X, n, p, ld, wset, wbit, rp, partial, slot_d, tot, c, w_ld, w_rd, grad, nsm, s);
+                 double w_rd, GradCot cot, float* grad, int nsm, cudaStream_t s) {
+    RTD_PB_CALL(pad_p(p), grad, X, n, p, ld, wset, wbit, rp, partial, slot_d, tot, c, w_ld, w_rd, cot, grad, nsm,
+                s);
 }
 void launch_memb(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, memb, P, s); }
 void launch_rew(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, rew, P, s); }

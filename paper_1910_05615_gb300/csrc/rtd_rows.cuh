@@ -1300,11 +1300,11 @@ __global__ void __launch_bounds__(NT) k_rew(const float* __restrict__ Xp, int p,
     acc.store(reinterpret_cast<double*>(smem), partial + sl * slot_d);
 }
 
+// The reweighting Gram (steps 8-9) stays on the CUDA-core accumulator in
+// every form: the reweighted fit decides the final flags, so it carries the
+// FP32 form's error also when the starts and C-steps use the tensor cores.
 template <int PB, typename T, bool TC = false>
 void rew_t(const Plan& P, cudaStream_t s) {
-    if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
-        if (P.tc) { rew_t<PB, T, true>(P, s); return; }
-    }
     size_t sm = align16(gram_smem_bytes<PB, T>()) + PB * PB * sizeof(T);
     if (TC) sm = align128(sm) + GramPick<PB, T, TC>::extra;
     auto k = k_rew<PB, T, TC>;
@@ -1316,15 +1316,23 @@ void rew_t(const Plan& P, cudaStream_t s) {
 }
 // =====================================================================
 // Adjoint of Section 4 steps 8-10 with the reweighting set W fixed:
-// f = w_ld log det Sigma + w_rd sum_j RD_j, mu = mean of W, Sigma = c S_W.
-// With r = x - mu, y = M r (M = L^-1, Sigma = L L^T), RD = |y| and
-// u = M^T y = Sigma^-1 r:
-//   pass 1: sum over all rows of (u, 1)(u, 1)^T / RD (so that
-//           G = -1/2 sum u u^T / RD and g = -sum u / RD), sum RD and |W|;
-//   pass 2: grad = w_rd (u / RD + [W] (g / N + a G r)) + w_ld [W] a u,
-//           a = 2 c / (N - 1).
-// Rows with RD = 0 take the zero subgradient of their own term.  FP32 row
-// arithmetic, FP64 cross-CTA sums.
+// mu = mean of W, Sigma = c S_W, RD_j = |M (x_j - mu)| over all rows.  The
+// vector-Jacobian product for cotangents (gmu, gSigma, gld, gRD) on
+// (mu, Sigma, log det Sigma, RD) follows from the chain rule through
+// r = x - mu, y = M r (M = L^-1, Sigma = L L^T), RD = |y|, u = M^T y =
+// Sigma^-1 r, with omega_j = gRD_j / RD_j and N = |W|:
+//   the cotangents reaching mu and Sigma are
+//     gmu_t = gmu - sum_j omega_j u_j,
+//     G_t   = sym(gSigma) + gld Sigma^-1 - 1/2 sum_j omega_j u_j u_j^T;
+//   d mu / d x_i = [W] I / N and d Sigma = a/2 sum_W (dx r^T + r dx^T),
+//   a = 2 c / (N - 1), so that
+//     grad_i = omega_i u_i + [W] (gmu_t / N + a G_t r_i).
+//   pass 1: sum over all rows of omega (u, 1)(u, 1)^T, sum RD and |W|;
+//   pass 2: the rows' gradients.
+// The scalar objective w_ld log det Sigma + w_rd sum RD is the case
+// gRD = w_rd, gld = w_ld, gmu = gSigma = 0 (then pass 1 weights rows by
+// 1 / RD and w_rd scales its sums).  Rows with RD = 0 take the zero
+// subgradient of their own term.  FP32 row arithmetic, FP64 cross-CTA sums.
 // =====================================================================
 template <int PB>
 __device__ __forceinline__ void grad_row(const float* __restrict__ sM, const float (&c)[PB], float (&u)[PB],
@@ -1364,8 +1372,8 @@ __device__ inline void grad_load_m(const RowParams& rp, int p, float* sM, float*
 template <int PB>
 __global__ void __launch_bounds__(NT, 2) k_grad_gram(const float* __restrict__ X, long long n, int p, long long ld,
                                                   int vec4, const uint8_t* __restrict__ wset, int wbit,
-                                                  const RowParams* __restrict__ rp, double* __restrict__ partial,
-                                                  size_t slot_d) {
+                                                  const RowParams* __restrict__ rp, const float* __restrict__ grd,
+                                                  double* __restrict__ partial, size_t slot_d) {
     typedef GramShape<PB, float> S;
     extern __shared__ __align__(16) unsigned char smem[];
     float* tile = reinterpret_cast<float*>(smem);
@@ -1394,7 +1402,7 @@ __global__ void __launch_bounds__(NT, 2) k_grad_gram(const float* __restrict__ X
             for (int j = 0; j < PB; ++j) dst[j] = u[j];
             dst[PB] = 0.f; dst[PB + 1] = 0.f; dst[PB + 2] = 0.f; dst[PB + 3] = 0.f;
             dst[p] = 1.f;
-            wt[threadIdx.x] = rd > 0.f ? 1.f / rd : 0.f;
+            wt[threadIdx.x] = rd > 0.f ? (grd ? grd[row] : 1.f) / rd : 0.f;
         }
         __syncthreads();
         acc.rows(tile, wt, k);
@@ -1420,17 +1428,27 @@ template <int PB>
 __global__ void __launch_bounds__(NT) k_grad_rows(const float* __restrict__ X, long long n, int p, long long ld,
                                                   int vec4, const uint8_t* __restrict__ wset, int wbit,
                                                   const RowParams* __restrict__ rp, const double* __restrict__ tot,
-                                                  double c, double w_ld, double w_rd, float* __restrict__ grad) {
+                                                  double c, double w_ld, double w_rd, GradCot cot,
+                                                  float* __restrict__ grad) {
     typedef GramShape<PB, float> S;
     __shared__ float sM[PB * PB], sG[PB * PB], sg[PB], s_hi[PB], s_lo[PB];
     grad_load_m<PB>(*rp, p, sM, s_hi, s_lo);
     const int nb = S::NB;
+    // pass 1 summed omega (u,1)(u,1)^T with omega = gRD / RD, or 1 / RD for
+    // the scalar objective, whose weight w_rd then scales the sums here
+    const double ws = cot.grd ? 1.0 : w_rd;
     for (int e = threadIdx.x; e < PB * PB; e += NT) {
         const int i = e / PB, j = e % PB;
-        sG[e] = (i < p && j < p) ? (float)(-0.5 * gram_get(tot, i, j, nb)) : 0.f;
+        double v = 0.0;
+        if (i < p && j < p) {
+            v = -0.5 * ws * gram_get(tot, i, j, nb);
+            if (cot.gsig) v += 0.5 * (cot.gsig[i * p + j] + cot.gsig[j * p + i]);
+        }
+        sG[e] = (float)v;
     }
     const double N = tot[S::NBLK * 16 + 1];
-    for (int j = threadIdx.x; j < PB; j += NT) sg[j] = (j < p) ? (float)(-gram_get(tot, j, p, nb) / N) : 0.f;
+    for (int j = threadIdx.x; j < PB; j += NT)
+        sg[j] = (j < p) ? (float)(((cot.gmu ? cot.gmu[j] : 0.0) - ws * gram_get(tot, j, p, nb)) / N) : 0.f;
     __syncthreads();
     const float a = (float)(2.0 * c / (N - 1.0)), wl = (float)w_ld, wr = (float)w_rd;
     for (long long row = (long long)blockIdx.x * NT + threadIdx.x; row < n; row += (long long)gridDim.x * NT) {
@@ -1440,18 +1458,18 @@ __global__ void __launch_bounds__(NT) k_grad_rows(const float* __restrict__ X, l
 #pragma unroll
         for (int j = 0; j < PB; ++j) cc[j] = (x[j] - s_hi[j]) - s_lo[j];
         grad_row<PB>(sM, cc, u, rd);
-        const float inv = rd > 0.f ? 1.f / rd : 0.f;
+        const float om = rd > 0.f ? (cot.grd ? cot.grd[row] : wr) / rd : 0.f;
         const bool inW = (wset[row] >> wbit) & 1;
         float* out = grad + row * p;
 #pragma unroll
         for (int k = 0; k < PB; ++k) {
             if (k >= p) break;
-            float gk = wr * u[k] * inv;
+            float gk = om * u[k];
             if (inW) {
                 float gr = 0.f;
 #pragma unroll
                 for (int j = 0; j < PB; ++j) gr = fmaf(sG[k * PB + j], cc[j], gr);
-                gk += wr * (sg[k] + a * gr) + wl * a * u[k];
+                gk += sg[k] + a * gr + wl * a * u[k];
             }
             out[k] = gk;
         }
@@ -1460,8 +1478,8 @@ __global__ void __launch_bounds__(NT) k_grad_rows(const float* __restrict__ X, l
 
 template <int PB>
 void grad_t(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit, const RowParams* rp,
-            double* partial, size_t slot_d, double* tot, double c, double w_ld, double w_rd, float* grad, int nsm,
-            cudaStream_t s) {
+            double* partial, size_t slot_d, double* tot, double c, double w_ld, double w_rd, GradCot cot, float* grad,
+            int nsm, cudaStream_t s) {
     typedef GramShape<PB, float> S;
     const int vec4 = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     long long tiles = (n + S::TR - 1) / S::TR;
@@ -1472,13 +1490,13 @@ void grad_t(const float* X, long long n, int p, long long ld, const uint8_t* wse
     auto k1 = k_grad_gram<PB>;
     // static M (up to 16 KB) plus the dynamic tile can pass 48 KB: always opt in
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k1<<<g1, NT, sm, s>>>(X, n, p, ld, vec4, wset, wbit, rp, partial, slot_d);
+    k1<<<g1, NT, sm, s>>>(X, n, p, ld, vec4, wset, wbit, rp, cot.grd, partial, slot_d);
     const int nv = S::NBLK * 16 + 2;
     k_sum_slots<<<(nv + 255) / 256, 256, 0, s>>>(partial, g1, slot_d, nv, tot);
     if (grad) {
         long long blocks = (n + NT - 1) / NT;
         int g2 = (int)(blocks < 8LL * nsm ? blocks : 8LL * nsm);
-        k_grad_rows<PB><<<g2, NT, 0, s>>>(X, n, p, ld, vec4, wset, wbit, rp, tot, c, w_ld, w_rd, grad);
+        k_grad_rows<PB><<<g2, NT, 0, s>>>(X, n, p, ld, vec4, wset, wbit, rp, tot, c, w_ld, w_rd, cot, grad);
     }
 }
 

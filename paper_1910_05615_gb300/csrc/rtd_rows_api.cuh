@@ -13,7 +13,7 @@ namespace rtd {
     void band64_pb##N(const Plan& P, cudaStream_t s);                                               \
     void grad_pb##N(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,   \
                     const RowParams* rp, double* partial, size_t slot_d, double* tot, double c,       \
-                    double w_ld, double w_rd, float* grad, int nsm, cudaStream_t s);                   \
+                    double w_ld, double w_rd, GradCot cot, float* grad, int nsm, cudaStream_t s);      \
     void memb_pb##N(const Plan& P, cudaStream_t s);                                                 \
     void rew_pb##N(const Plan& P, cudaStream_t s);                                                  \
     void member_gram_pb##N(const Plan& P, cudaStream_t s);                                          \

@@ -33,8 +33,8 @@ void RTD_FN(dist_win_pb)(const Plan& P, cudaStream_t s) { dist_win_t<RTD_PB>(P, 
 void RTD_FN(band64_pb)(const Plan& P, cudaStream_t s) { band64_t<RTD_PB>(P, s); }
 void RTD_FN(grad_pb)(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
                      const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,
-                     double w_rd, float* grad, int nsm, cudaStream_t s) {
-    grad_t<RTD_PB>(X, n, p, ld, wset, wbit, rp, partial, slot_d, tot, c, w_ld, w_rd, grad, nsm, s);
+                     double w_rd, GradCot cot, float* grad, int nsm, cudaStream_t s) {
+    grad_t<RTD_PB>(X, n, p, ld, wset, wbit, rp, partial, slot_d, tot, c, w_ld, w_rd, cot, grad, nsm, s);
 }
 void RTD_FN(memb_pb)(const Plan& P, cudaStream_t s) {
     if (P.precision == RTD_FP64) memb_t<RTD_PB, double>(P, s);

@@ -2,14 +2,18 @@
 // the split-BF16 form (the mean and scatter of a subset, Section 3.4, with
 // the rows' products taken on the tensor cores).
 //
-// Every weighted row a = sqrt(w) e (centred in FP32) is split as
-// a = a_hi + a_lo, a_hi = bf16(a), a_lo = bf16(a - a_hi) (16 significant
-// bits together).  One 16-row step issues D += [a_hi | a_lo]^T [a_hi | a_lo]
-// (M = 128 lanes, features on the lanes; N = 2H columns, K = 16 rows), whose
-// four H x H quadrants are the products hi*hi, hi*lo, lo*hi and lo*lo, with
-// FP32 accumulation in tensor memory.  Every FLUSH_ROWS rows the accumulators
-// are read back and summed into an FP64 copy in shared memory, which bounds
-// the FP32 accumulation error to that many rows.
+// Every weighted row a = sqrt(w) e (centred in FP32) is split three ways,
+// a = a_hi + a_mid + a_lo with a_hi = bf16(a), a_mid = bf16(a - a_hi),
+// a_lo = bf16(a - a_hi - a_mid): 24 significant bits, the FP32 row itself.
+// One 16-row step issues D += [a_hi | a_mid]^T [a_hi | a_mid | a_lo]
+// (M = 128 lanes, features on the lanes; N = 3H columns, K = 16 rows), whose
+// blocks are the products hi*hi, hi*mid, hi*lo, mid*hi, mid*mid and mid*lo,
+// with FP32 accumulation in tensor memory; lo*hi and lo*mid are the
+// transposes of hi*lo and mid*lo and are recovered when the sums are
+// symmetrised.  Every FLUSH_ROWS rows the accumulators are read back and
+// summed into compensated FP32 pairs in shared memory, which bounds the
+// depth of the FP32 accumulation in tensor memory (whose additions need not
+// round to nearest).
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -93,43 +97,50 @@ __device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// split of two FP32 values into packed BF16 high and low parts
-__device__ inline void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+// split of two FP32 values into packed BF16 high, middle and low parts (the
+// differences are exact in FP32; the three parts carry 24 significant bits)
+__device__ inline void split_bf16x3(float x0, float x1, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
     __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-    const float h0 = __low2float(h), h1 = __high2float(h);
-    __nv_bfloat162 l = __floats2bfloat162_rn(x0 - h0, x1 - h1);
+    const float r0 = x0 - __low2float(h), r1 = x1 - __high2float(h);
+    __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+    __nv_bfloat162 l = __floats2bfloat162_rn(r0 - __low2float(m), r1 - __high2float(m));
     hi = *reinterpret_cast<uint32_t*>(&h);
+    mid = *reinterpret_cast<uint32_t*>(&m);
     lo = *reinterpret_cast<uint32_t*>(&l);
 }
 
 // ---------------------------------------------------------------- GramTC
 // Drop-in for GramAcc<PB, float> (same put()/rows()/store() contract, same
 // slot layout) for 25 <= p <= 48.  Rows are put by the threads that hold
-// them: a = sqrt(|w|) (v, 1, 0 ...) is split into BF16 high and low parts
-// and written as the MN-major operand [a_hi | a_lo] (2H features) of one
-// 16-row step.  The same buffer serves as A (M = 128 lanes: a_hi on lanes
-// 0 .. H-1, a_lo on lanes H .. 2H-1, the rest unused) and as B (N = 2H), so
-// one MMA per step accumulates all four partial products.  Rows of negative
-// weight (signed mode) go to a second buffer and accumulator, subtracted at
-// the flush.  Needs SMEM bytes of dynamic shared memory (16-byte aligned)
-// handed over by setup(), and 128 (256 signed) tensor-memory columns.
+// them: a = sqrt(|w|) (v, 1, 0 ...) is split into BF16 high, middle and low
+// parts and written as the MN-major operand [a_hi | a_mid | a_lo] (3H
+// features) of one 16-row step.  The buffer serves as B (N = 3H) and its
+// first 128 features as A (M = 128 lanes: a_hi on lanes 0 .. H-1, a_mid on
+// lanes H .. 2H-1, the rest unused), so one MMA per step accumulates the six
+// partial products.  Rows of negative weight (signed mode) go to a second
+// buffer and accumulator, subtracted at the flush.  Needs SMEM bytes of
+// dynamic shared memory (16-byte aligned) handed over by setup(), and 256
+// (512 signed) tensor-memory columns.
 template <int PB, int NTH, int TROWS>
 struct GramTC {
     static constexpr int PE = PB + 4;
-    static constexpr int H = ((PB + 1) + 7) / 8 * 8;        // features incl. the constant (>= p + 1)
-    static constexpr int N = 2 * H;                         // [a_hi | a_lo]
+    static constexpr int H = ((PB + 1) + 15) / 16 * 16;     // features incl. the constant (>= p + 1)
+    static constexpr int N = 3 * H;                         // [a_hi | a_mid | a_lo]
     static constexpr int TR = TROWS;                        // rows per rows() call, at most
-    static constexpr int GROUP = 32 * H;                    // bytes per 8 rows: 2H/8 chunks of 8 rows x 16 B
+    static constexpr int CH = N / 8;                        // 16-byte feature chunks per row
+    static constexpr int GROUP = CH * 128;                  // bytes per 8 rows: CH chunks of 8 rows x 16 B
     static constexpr int OPS1 = TR / 8 * GROUP;             // one operand buffer
-    static constexpr int PAD = 2048;                        // A reads 16 chunks past each group start
-    static constexpr int ACC_LD = H + 1;                    // FP64 row stride (bank spread)
+    static constexpr int PAD = 2048;
+    static constexpr int ACC_LD = H + 1;                    // pair-sum row stride (bank spread)
     static constexpr int SMEM = 2 * OPS1 + PAD + H * ACC_LD * 8;
-    static constexpr int FLUSH_ROWS = 4096;
-    static_assert(N <= 128 && N % 16 == 0, "features on at most 128 lanes, N a multiple of 16");
+    // rows accumulated in FP32 in tensor memory between two flushes
+    static constexpr int FLUSH_ROWS = 256;
+    static_assert(2 * H <= 128 && CH >= 16, "A: hi and mid on at most 128 lanes, read within one row group");
+    static_assert(N % 16 == 0 && N <= 256, "N a multiple of 16, at most 256");
     static_assert(TR % 16 == 0, "tile rows must be a multiple of 16");
 
     unsigned char* ops;
-    double* acc;
+    FF* acc;            // H x ACC_LD compensated FP32 sums
     uint32_t* s_taddr;
     uint64_t* bar;
     int* err;           // shared failure flag
@@ -142,7 +153,7 @@ struct GramTC {
 
     __device__ void setup(unsigned char* region, uint32_t* taddr_slot, uint64_t* mbar, int* err_flag) {
         ops = region;
-        acc = reinterpret_cast<double*>(region + 2 * OPS1 + PAD);
+        acc = reinterpret_cast<FF*>(region + 2 * OPS1 + PAD);
         s_taddr = taddr_slot;
         bar = mbar;
         err = err_flag;
@@ -151,8 +162,8 @@ struct GramTC {
     // all threads; signed_rows: some rows may carry negative weights
     __device__ void init(int = 0, bool signed_rows = false) {
         sgn = signed_rows ? 1 : 0;
-        tcols = sgn ? 256u : 128u;
-        for (int e = threadIdx.x; e < H * ACC_LD; e += NTH) acc[e] = 0.0;
+        tcols = sgn ? 512u : 256u;
+        for (int e = threadIdx.x; e < H * ACC_LD; e += NTH) acc[e] = FF{0.f, 0.f};
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
             mbar_init_fence();
@@ -181,33 +192,47 @@ struct GramTC {
         tc_fence_after();
     }
 
-    // tensor memory -> FP64 accumulators: lanes L < H hold a_hi rows, lanes
-    // H <= L < 2H the a_lo rows of the same features; both add into row L % H
-    // (in two phases, so that each FP64 row has one writer at a time)
+    // tensor memory -> compensated FP32 accumulators.  Lane L < H holds
+    // feature L of the a_hi rows, lane H <= L < 2H feature L - H of the a_mid
+    // rows; column c holds feature c % H of part c / H.  A lane first folds
+    // its three column parts in FP32 (the lo part twice: the symmetric part
+    // taken in store() restores the lo*hi and lo*mid blocks from hi*lo and
+    // mid*lo), then adds the folded row into row L % H of the pair sums; the
+    // hi and mid lanes of a feature add in two phases, one writer per row at
+    // a time.
     __device__ void flush() {
         wait_mma();
         if (!fresh) {
             const int w = threadIdx.x >> 5;
             const int L = threadIdx.x;
+            float t[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) t[j] = 0.f;
+            if (w < 4) {
+                const uint32_t base = *s_taddr + ((uint32_t)(w * 32) << 16);
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(base + (uint32_t)c0, v);
+                    if (sgn) {
+                        float vn[16];
+                        tmem_ld16(base + (uint32_t)(N + c0), vn);
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) v[u] -= vn[u];
+                    }
+                    const float f = (c0 >= 2 * H) ? 2.f : 1.f;   // a 16-column group lies in one part
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) t[(c0 % H) + u] = fmaf(f, v[u], t[(c0 % H) + u]);
+                }
+            }
             for (int ph = 0; ph < 2; ++ph) {
-                if (w < 4) {
-                    const uint32_t base = *s_taddr + ((uint32_t)(w * 32) << 16);
-                    const bool mine = (ph == 0) ? (L < H) : (L >= H && L < 2 * H);
-                    double* arow = acc + (L % H) * ACC_LD;
-#pragma unroll 1
-                    for (int c0 = 0; c0 < N; c0 += 16) {
-                        float v[16];
-                        tmem_ld16(base + (uint32_t)c0, v);
-                        if (sgn) {
-                            float vn[16];
-                            tmem_ld16(base + (uint32_t)(N + c0), vn);
+                const bool mine = (ph == 0) ? (L < H) : (L >= H && L < 2 * H);
+                if (mine) {
+                    FF* arow = acc + (L % H) * ACC_LD;
 #pragma unroll
-                            for (int u = 0; u < 16; ++u) v[u] -= vn[u];
-                        }
-                        if (mine) {
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) arow[(c0 + u) % H] += (double)v[u];
-                        }
+                    for (int j = 0; j < H; ++j) {
+                        const FF e = ff_two_sum(arow[j].hi, t[j]);
+                        arow[j] = FF{e.hi, arow[j].lo + e.lo};
                     }
                 }
                 __syncthreads();
@@ -233,21 +258,22 @@ struct GramTC {
         unsigned char* dst = ops + ((sgn && w < 0.f) ? OPS1 : 0) + (slot >> 3) * GROUP + (slot & 7) * 16;
 #pragma unroll
         for (int g = 0; g < H / 8; ++g) {
-            uint32_t hi[4], lo[4];
+            uint32_t hi[4], mi[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int j0 = 8 * g + 2 * q, j1 = j0 + 1;
                 const float a0 = (j0 < PB ? v[j0 < PB ? j0 : 0] : 0.f) * sw + (j0 == p ? sw : 0.f);
                 const float a1 = (j1 < PB ? v[j1 < PB ? j1 : 0] : 0.f) * sw + (j1 == p ? sw : 0.f);
-                split_bf16x2(a0, a1, hi[q], lo[q]);
+                split_bf16x3(a0, a1, hi[q], mi[q], lo[q]);
             }
             *reinterpret_cast<uint4*>(dst + g * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(dst + (H / 8 + g) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(dst + (H / 8 + g) * 128) = make_uint4(mi[0], mi[1], mi[2], mi[3]);
+            *reinterpret_cast<uint4*>(dst + (2 * H / 8 + g) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
         if (sgn) {   // the other buffer's copy of this slot is zero
             unsigned char* z = ops + ((w < 0.f) ? 0 : OPS1) + (slot >> 3) * GROUP + (slot & 7) * 16;
 #pragma unroll
-            for (int g = 0; g < 2 * H / 8; ++g) *reinterpret_cast<uint4*>(z + g * 128) = make_uint4(0, 0, 0, 0);
+            for (int g = 0; g < CH; ++g) *reinterpret_cast<uint4*>(z + g * 128) = make_uint4(0, 0, 0, 0);
         }
     }
 
@@ -258,10 +284,10 @@ struct GramTC {
         const int kpad = nks * 16;
         const int nbuf = sgn ? 2 : 1;
         // zero rows k .. kpad-1 of the last step
-        for (int e = threadIdx.x; e < (kpad - k) * (2 * H / 8) * nbuf; e += NTH) {
-            const int per = (kpad - k) * (2 * H / 8);
+        for (int e = threadIdx.x; e < (kpad - k) * CH * nbuf; e += NTH) {
+            const int per = (kpad - k) * CH;
             const int b = e / per, r = e % per;
-            const int slot = k + r / (2 * H / 8), g = r % (2 * H / 8);
+            const int slot = k + r / CH, g = r % CH;
             *reinterpret_cast<uint4*>(ops + b * OPS1 + (slot >> 3) * GROUP + (slot & 7) * 16 + g * 128) =
                 make_uint4(0, 0, 0, 0);
         }
@@ -303,7 +329,7 @@ struct GramTC {
             while (b >= NB - bi) { b -= NB - bi; ++bi; }
             const int bj = bi + b;
             const int i = 4 * bi + ((e & 15) >> 2), j = 4 * bj + (e & 3);
-            slot[e] = ((i < H && j < H) ? acc[i * ACC_LD + j] : 0.0) + bad;
+            slot[e] = ((i < H && j < H) ? 0.5 * (ff_d(acc[i * ACC_LD + j]) + ff_d(acc[j * ACC_LD + i])) : 0.0) + bad;
         }
         __syncthreads();
         if (threadIdx.x < 32) tmem_dealloc(*s_taddr, tcols);

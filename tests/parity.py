@@ -4,6 +4,8 @@ Tolerances (stated in the project's design notes):
   FP32 form: mu and Sigma within 1e-5 relative (max-abs over max-abs of the
              oracle), same final h-subsets and flags outside the tie bands.
   FP64 form: 1e-9 relative.
+  Split-BF16 form: mu and Sigma within 1e-3 relative, the same subsets and
+             flags outside the tie bands.
 Tie bands: rows whose oracle distance lies within 1e-6 relative of the h-th
 distance of their block (subsets) or of the cutoff (flags) are excluded.
 """
@@ -11,7 +13,7 @@ import numpy as np
 
 import oracle as O
 
-TOL = {"fp32": 1e-5, "fp64": 1e-9}
+TOL = {"fp32": 1e-5, "fp64": 1e-9, "bf16": 1e-3}
 TIE = 1e-6
 
 
