@@ -62,7 +62,7 @@ extern "C" {
 #define RTD_BF16 2   /* the FP32 form with the Grams of the starts and C-steps on the tensor
                         cores: rows centred in FP32 and split into BF16 high, middle and low
                         parts (24 significant bits), the six leading partial products with FP32
-                        accumulation, compensated FP32 sums every 256 rows; the reweighting Gram
+                        accumulation, compensated FP32 sums every 128 rows; the reweighting Gram
                         stays on the FP32 CUDA-core path; 25 <= p <= 48 (RTD_EINVAL otherwise) */
 
 typedef struct {
@@ -101,6 +101,11 @@ typedef struct {
        RTD_EINVAL unless finite with a positive diagonal. */
     const double* init_mu;
     const double* init_sigma;
+    int32_t  dist_path;            /* FP32 form, C-step distances from the second step on:
+                                      0 (default) tcgen05 tensor cores, split-TF32 operands;
+                                      1 CUDA-core FP32 FMAs.  Both take the same decisions (every
+                                      threshold decision near the FP32 error is made in FP64). */
+    int32_t  reserved0;
 } rtd_options;
 
 /* Stages of a fit, for rtd_profile. */

@@ -48,7 +48,8 @@ class _Options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("reweight_consistency", ctypes.c_int32),
                 ("select_path", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
                 ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p),
-                ("init_mu", ctypes.c_void_p), ("init_sigma", ctypes.c_void_p)]
+                ("init_mu", ctypes.c_void_p), ("init_sigma", ctypes.c_void_p),
+                ("dist_path", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_dist",
@@ -207,9 +208,9 @@ def rtdetmcd_status_string(code):
 
 
 def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100,
-                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, select_path=0, init=None,
-                 d2=True, flags=True, subset=False, diag=False, profile=False, stream=None, workspace=None,
-                 check=True):
+                 cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, select_path=0, dist_path=0,
+                 init=None, d2=True, flags=True, subset=False, diag=False, profile=False, stream=None,
+                 workspace=None, check=True):
     """RT-DetMCD fit of the rows of X (float32, row-major) with coverage h.
 
     X on a CUDA device: outputs are CUDA tensors on the same device.  X in
@@ -226,6 +227,7 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     o.max_csteps, o.cutoff_q, o.kappa_max = max_csteps, cutoff_q, kappa_max
     o.reweight_consistency = reweight_consistency
     o.select_path = select_path
+    o.dist_path = dist_path
     if init is not None:   # warm start: (mu, Sigma) of an earlier fit, X units
         init_mu = np.ascontiguousarray(init[0], dtype=np.float64).reshape(-1)
         init_sigma = np.ascontiguousarray(init[1], dtype=np.float64).reshape(-1)

@@ -74,6 +74,7 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (!(o.cutoff_q > 0.0 && o.cutoff_q < 1.0) || !(o.kappa_max > 1.0)) return RTD_EINVAL;
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
     if (o.select_path < 0 || o.select_path > 2) return RTD_EINVAL;
+    if (o.dist_path < 0 || o.dist_path > 1) return RTD_EINVAL;
     if ((o.init_mu == nullptr) != (o.init_sigma == nullptr)) return RTD_EINVAL;
     if (o.init_mu) {   // warm start: finite, positive diagonal (host memory)
         for (int j = 0; j < p; ++j) {
@@ -405,29 +406,34 @@ csteps:
             // predicted window, selection from the window's rows; chains whose
             // window missed take the histogram path below
             const bool win = S.precision == RTD_FP32 && it > 0 && o.select_path != 1;
+            // (the first kernel of a step also clears the counters that the
+            // membership pass and the finalize accumulate)
             pf.begin(RTD_STAGE_CDIST);
-            if (win) launch_dist_win(P, s);
-            else launch_dist(P, s);
+            if (win) {
+                if (o.dist_path == 1) launch_dist_win(P, s);
+                else launch_dist_tc(P, s);
+            } else {
+                launch_dist(P, s);
+            }
             // rows read, keys written
             pf.end(1, (double)S.m * act_blocks * p_ * 4 + mch * K_);
             if (o.profile) o.profile->flops[RTD_STAGE_CDIST] += mch * p_ * (p_ + 3.0);
             pf.begin(RTD_STAGE_CSELECT);
             if (win) {
-                launch_select_win(P, s);   // a chain whose window missed takes the histogram path there
+                // one launch: bin of the rank, FP64 range, ranking (a chain
+                // whose window missed takes the histogram path there)
+                launch_select_fast(P, s);
             } else {
                 launch_select_bucket(P, s);
                 launch_compact(P, s);
                 launch_select_finish(P, s);
+                if (S.precision == RTD_FP32) {
+                    launch_band64(P, s);
+                    launch_select_band(P, s);
+                }
             }
-            if (S.precision == RTD_FP32) {
-                launch_band64(P, s);
-                launch_select_band(P, s);
-            }
-            pf.end((win ? 1 : 3) + (S.precision == RTD_FP32 ? 2 : 0), win ? 0.0 : mch * K_);
+            pf.end(win ? 1 : 3 + (S.precision == RTD_FP32 ? 2 : 0), win ? 0.0 : mch * K_);
             pf.begin(RTD_STAGE_CUPDATE);
-            RTD_CUDA(cudaMemsetAsync(&P.st->active, 0, 3 * sizeof(int), s));
-            RTD_CUDA(cudaMemsetAsync(&P.st->gram_rows, 0, sizeof(unsigned long long), s));
-            RTD_CUDA(cudaMemsetAsync(P.blk_active, 0, (size_t)S.q * sizeof(int), s));
             launch_memb(P, s);
             launch_cstep_finalize(P, s);
             pf.end(3, mch * (K_ + 2));

@@ -109,6 +109,7 @@ struct SelRule {
     float t_prev, t_prev2;          // FP32 thresholds of the last two steps
     int bandsel;                    // histogram path: band listed, FP64 ranking pending
     int band_off;                   // offset of the band list in the chain's band buffer
+    int done;                       // CTAs of the one-launch window selection finished
     // counters over the whole fit (profiling)
     int acc_win, acc_miss;
     long long acc_cand, acc_band;

@@ -71,6 +71,7 @@ void launch_start2(const Plan& P, cudaStream_t s);
 void launch_transform(const Plan& P, int which, cudaStream_t s);
 void launch_dist(const Plan& P, cudaStream_t s);
 void launch_dist_win(const Plan& P, cudaStream_t s);
+void launch_dist_tc(const Plan& P, cudaStream_t s);
 void launch_band64(const Plan& P, cudaStream_t s);
 void launch_compact(const Plan& P, cudaStream_t s);
 void launch_memb(const Plan& P, cudaStream_t s);
@@ -94,6 +95,7 @@ void launch_select_bucket(const Plan& P, cudaStream_t s);
 void launch_select_finish(const Plan& P, cudaStream_t s);
 void launch_select_win(const Plan& P, cudaStream_t s);
 void launch_select_band(const Plan& P, cudaStream_t s);
+void launch_select_fast(const Plan& P, cudaStream_t s);
 
 // ---- small FP64 kernels (rtd_small.cu)
 void launch_setup(const Plan& P, const rtd_options& o, cudaStream_t s);

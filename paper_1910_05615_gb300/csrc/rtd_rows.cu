@@ -197,6 +197,7 @@ void launch_start2(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, start2, P,
 void launch_transform(const Plan& P, int which, cudaStream_t s) { (void)which; RTD_PB_CALL(P.pb, transform, P, s); }
 void launch_dist(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist, P, s); }
 void launch_dist_win(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist_win, P, s); }
+void launch_dist_tc(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, dist_tc, P, s); }
 void launch_band64(const Plan& P, cudaStream_t s) { RTD_PB_CALL(P.pb, band64, P, s); }
 void launch_grad(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
                  const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,

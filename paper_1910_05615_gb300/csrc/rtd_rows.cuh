@@ -640,11 +640,26 @@ __device__ inline void hist_add(unsigned* h, unsigned bin, bool valid) {
     if (valid && (__ffs(peers) - 1) == lane) atomicAdd(h + bin, (unsigned)__popc(peers));
 }
 
+// Per-step counters of the membership pass and the finalize start at zero;
+// the first kernel of a C-step clears them (stream-ordered before both).
+__device__ __forceinline__ void clear_step_counters(Status* st, int* blk) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        blk[blockIdx.y] = 0;
+        if (blockIdx.y == 0) {
+            st->active = 0;
+            st->active_blocks = 0;
+            st->done = 0;
+            st->gram_rows = 0ull;
+        }
+    }
+}
+
 template <int PB, typename T>
 __global__ void __launch_bounds__(NT, 2) k_dist(const float* __restrict__ Xp, int p, int m, int cpb,
                                                 const Chain* __restrict__ ch, T* __restrict__ dkeys,
-                                                long long qm, unsigned* __restrict__ hist) {
+                                                long long qm, unsigned* __restrict__ hist, Status* st, int* blk) {
     constexpr int R = DistRows<PB, T>::R;
+    clear_step_counters(st, blk);
     extern __shared__ __align__(16) unsigned char smem[];
     T* sMb = reinterpret_cast<T*>(smem);                                   // [2][PB*PB]
     unsigned* shb = reinterpret_cast<unsigned*>(smem + 2 * PB * PB * sizeof(T));  // [2][HIST_BINS]
@@ -714,7 +729,8 @@ void dist_t(const Plan& P, cudaStream_t s) {
     size_t sm = 2 * PB * PB * sizeof(T) + 2 * HIST_BINS * sizeof(unsigned);
     auto k = k_dist<PB, T>;
     set_smem(k, sm);
-    k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb_dist, P.ch, (T*)P.dkeys, (long long)P.q * P.m, P.hist);
+    k<<<grid, NT, sm, s>>>(P.Xp, P.p, P.m, P.cpb_dist, P.ch, (T*)P.dkeys, (long long)P.q * P.m, P.hist, P.st,
+                           P.blk_active);
 }
 // =====================================================================
 // C-step distances of the FP32 form from the second step on (Sections 2.1,
@@ -794,8 +810,9 @@ template <int PB>
 __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
     k_dist_win(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
                const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys,
-               long long qm, Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st) {
+               long long qm, Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st, int* blk) {
     typedef DistWin<PB> D;
+    clear_step_counters(st, blk);
     constexpr int R = D::R, PH = D::PH, NTW = D::NTW, NW = D::NW, WT = D::WT;
     extern __shared__ __align__(128) unsigned char smem[];
     float2* sM = reinterpret_cast<float2*>(smem + NW * D::STAGES * D::WTILE);   // [2][PB][PH]
@@ -976,7 +993,291 @@ void dist_win_t(const Plan& P, cudaStream_t s) {
     auto k = k_dist_win<PB>;
     set_smem(k, D::SMEM);
     k<<<grid, D::NTW, D::SMEM, s>>>(P.Xp, P.p, P.m, cpb, P.cs, P.ch, P.rule, (float*)P.dkeys,
-                                    (long long)P.q * P.m, P.cand, P.hist, P.st);
+                                    (long long)P.q * P.m, P.cand, P.hist, P.st, P.blk_active);
+}
+
+// =====================================================================
+// C-step distances of the FP32 form from the second step on, on the tensor
+// cores (Sections 2.1, 3.4).  For a tile of 128 rows centred at the FP32
+// univariate centre u, Y = C [M_1^T | M_2^T] (both starts of the block) is a
+// 128 x p x 2p product taken by tcgen05.mma kind::tf32 with split operands:
+// c = c_hi + c_lo, M = M_hi + M_lo (c_hi, M_hi the TF32 high parts, the low
+// parts exact FP32 differences), Y = C_hi M_hi + C_lo M_hi + C_hi M_lo, which
+// leaves about 2^-19 relative error per product against |M| |c|: far inside
+// the FP64 band of 2^-9 in which every decision is recomputed in FP64.  The
+// accumulator (FP32, tensor memory: lane = row, column = output) is read back
+// by the row's own thread, which forms d2_k = |y_k - b_k|^2 (b = M (mu - u)
+// in FP64, rounded once) and classifies the key against the chain's window
+// exactly as the CUDA-core pass does.  Rows arrive by bulk copies, two tiles
+// ahead; every wait is bounded and records an error.
+//
+// Shared-memory operands are K-major without swizzle: element (r, k) of a
+// part at ((r / 8) KCH + k / 4) 128 + (r % 8) 16 + (k % 4) 4 bytes, so that
+// core matrices along K are 128 bytes apart (LBO) and 8-row groups KCH * 128
+// bytes apart (SBO).
+// =====================================================================
+template <int PB> struct DistTC {
+    static constexpr int KP = (PB + 7) / 8 * 8;            // K padded to the TF32 step (8)
+    static constexpr int KCH = KP / 4;                     // 16-byte K chunks per row
+    static constexpr int NC = 2 * KP;                      // N: both starts' outputs
+    static constexpr int TM = 128;                         // rows per tile (M)
+    static constexpr int NTH = 128;                        // one thread per tile row
+    static constexpr int TCOLS = NC <= 32 ? 32 : (NC <= 64 ? 64 : 128);
+    static constexpr size_t RAW = (size_t)TM * PB * 4;    // one raw tile
+    static constexpr size_t AOP = (size_t)TM * KP * 4;    // one part of A
+    static constexpr size_t BOP = (size_t)NC * KP * 4;    // one part of B
+    static constexpr size_t OFF_A = (2 * RAW + 127) / 128 * 128;
+    static constexpr size_t OFF_B = OFF_A + 2 * AOP;
+    static constexpr size_t OFF_H = OFF_B + 2 * BOP;
+    static constexpr size_t SMEM = OFF_H + 2 * (size_t)WIN_BINS * 4;
+    static constexpr int BY_SMEM = (int)((227 * 1024) / (SMEM + 1024));
+    static constexpr int BY_TMEM = 512 / TCOLS;
+    static constexpr int CTAS_PER_SM = BY_SMEM < BY_TMEM ? (BY_SMEM < 4 ? (BY_SMEM < 1 ? 1 : BY_SMEM) : 4)
+                                                         : (BY_TMEM < 4 ? BY_TMEM : 4);
+    static_assert(NC % 16 == 0 && NC <= 256, "N of the MMA");
+    static_assert(SMEM + 1024 <= 227 * 1024, "operands exceed shared memory");
+};
+
+__device__ __forceinline__ unsigned kop_off(int r, int k, int kch) {
+    return (unsigned)(((r >> 3) * kch + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+template <int PB>
+__global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
+    k_dist_tc(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
+              const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys, long long qm,
+              Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st, int* blk) {
+    typedef DistTC<PB> D;
+    constexpr int KP = D::KP, KCH = D::KCH, NC = D::NC, TM = D::TM, NTH = D::NTH;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float* raw = reinterpret_cast<float*>(smem);
+    unsigned char* Ah = smem + D::OFF_A;
+    unsigned char* Al = Ah + D::AOP;
+    unsigned char* Bh = smem + D::OFF_B;
+    unsigned char* Bl = Bh + D::BOP;
+    unsigned* sh = reinterpret_cast<unsigned*>(smem + D::OFF_H);
+    __shared__ __align__(8) uint64_t bar_raw[2];
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t s_taddr;
+    __shared__ float s_nu[PB];
+    __shared__ float s_b[2][KP];
+    __shared__ unsigned s_wlo[2], s_whi[2];
+    __shared__ int s_wsh[2], s_on[2], s_below[2];
+    const int l = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    clear_step_counters(st, blk);
+    int r0, r1;
+    block_rows(m, cpb, r0, r1);
+    const int ntiles = (r1 - r0 + TM - 1) / TM;
+    if (tid < 2) {
+        const int c = 2 * l + tid;
+        s_on[tid] = ch[c].active && rule[c].win;
+        s_wlo[tid] = rule[c].w_lo;
+        s_whi[tid] = rule[c].w_hi;
+        s_wsh[tid] = rule[c].w_sh;
+        s_below[tid] = 0;
+    }
+    if (tid == 0) {
+        mbar_init(&bar_raw[0], 1);
+        mbar_init(&bar_raw[1], 1);
+        mbar_init(&bar_mma, 1);
+        mbar_init_fence();
+    }
+    for (int e = tid; e < 2 * WIN_BINS; e += NTH) sh[e] = 0u;
+    // B = [M_1^T | M_2^T]: row n = k KP + i of B is row i of M_k (zero beyond p)
+    for (int e = tid; e < NC * KP; e += NTH) {
+        const int n = e / KP, j = e % KP;
+        const int k = n / KP, i = n % KP;
+        const float v = (i < p && j <= i) ? ch[2 * l + k].rp.Mf[i * PMAX + j] : 0.f;
+        const float hi = tf32_hi(v);
+        *reinterpret_cast<float*>(Bh + kop_off(n, j, KCH)) = hi;
+        *reinterpret_cast<float*>(Bl + kop_off(n, j, KCH)) = v - hi;
+    }
+    for (int e = tid; e < 2 * KP; e += NTH) {
+        const int k = e / KP, j = e % KP;
+        s_b[k][j] = (j < p) ? ch[2 * l + k].rp.bf[j] : 0.f;
+    }
+    for (int j = tid; j < PB; j += NTH) s_nu[j] = (j < p) ? -(float)cs->mu_uni[j] : 0.f;
+    async_proxy_fence();    // B, written by threads, is read by the tensor cores
+    __syncthreads();
+    if ((!s_on[0] && !s_on[1]) || ntiles == 0) return;   // uniform; nothing issued, nothing allocated
+    if (w == 0) {
+        tmem_alloc(&s_taddr, D::TCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    auto issue = [&](int t) {   // thread 0
+        const int row0 = r0 + t * TM;
+        const int rows = min(TM, r1 - row0);
+        const unsigned bytes = (unsigned)rows * PB * (unsigned)sizeof(float);
+        mbar_expect_tx(&bar_raw[t & 1], bytes);
+        bulk_load(raw + (size_t)(t & 1) * TM * PB, Xp + (size_t)row0 * PB, bytes, &bar_raw[t & 1]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < 2 && t < ntiles; ++t) issue(t);
+    const uint32_t idesc = idesc_tf32(TM, NC);
+    const uint32_t aoff_h = smem_addr(Ah), aoff_l = smem_addr(Al), boff_h = smem_addr(Bh), boff_l = smem_addr(Bl);
+    int below0 = 0, below1 = 0;
+    int failed = 0;
+    unsigned ph_mma = 0;
+    int t = 0;
+    for (; t < ntiles; ++t) {
+        const int row0 = r0 + t * TM;
+        const int rows = min(TM, r1 - row0);
+        const bool okr = mbar_wait(&bar_raw[t & 1], (unsigned)(t >> 1) & 1u);
+        if (!__syncthreads_and(okr)) { failed = 1; break; }
+        // centre the row and split it into the two A parts
+        {
+            float c[KP];
+            const float* src = raw + (size_t)(t & 1) * TM * PB + (size_t)tid * PB;
+#pragma unroll
+            for (int q4 = 0; q4 < PB / 4; ++q4) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tid < rows) v = reinterpret_cast<const float4*>(src)[q4];
+                c[4 * q4 + 0] = v.x + s_nu[4 * q4 + 0];
+                c[4 * q4 + 1] = v.y + s_nu[4 * q4 + 1];
+                c[4 * q4 + 2] = v.z + s_nu[4 * q4 + 2];
+                c[4 * q4 + 3] = v.w + s_nu[4 * q4 + 3];
+            }
+#pragma unroll
+            for (int j = PB; j < KP; ++j) c[j] = 0.f;
+            if (tid >= rows) {
+#pragma unroll
+                for (int j = 0; j < KP; ++j) c[j] = 0.f;
+            }
+#pragma unroll
+            for (int q4 = 0; q4 < KCH; ++q4) {
+                float4 h, lo;
+                h.x = tf32_hi(c[4 * q4 + 0]); lo.x = c[4 * q4 + 0] - h.x;
+                h.y = tf32_hi(c[4 * q4 + 1]); lo.y = c[4 * q4 + 1] - h.y;
+                h.z = tf32_hi(c[4 * q4 + 2]); lo.z = c[4 * q4 + 2] - h.z;
+                h.w = tf32_hi(c[4 * q4 + 3]); lo.w = c[4 * q4 + 3] - h.w;
+                *reinterpret_cast<float4*>(Ah + kop_off(tid, 4 * q4, KCH)) = h;
+                *reinterpret_cast<float4*>(Al + kop_off(tid, 4 * q4, KCH)) = lo;
+            }
+        }
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            // the raw stage of tile t is read: refill it with tile t + 2
+            if (t + 2 < ntiles) issue(t + 2);
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < KP / 8; ++ks) {
+                const uint32_t o = (uint32_t)ks * 256u;
+                const uint64_t ah = smem_desc(aoff_h + o, 128, KCH * 128), al = smem_desc(aoff_l + o, 128, KCH * 128);
+                const uint64_t bh = smem_desc(boff_h + o, 128, KCH * 128), bl = smem_desc(boff_l + o, 128, KCH * 128);
+                mma_tf32(taddr, ah, bh, idesc, ks > 0);
+                mma_tf32(taddr, al, bh, idesc, true);
+                mma_tf32(taddr, ah, bl, idesc, true);
+            }
+            mma_commit(&bar_mma);
+        }
+        const bool okm = mbar_wait(&bar_mma, ph_mma);
+        ph_mma ^= 1u;
+        if (!__syncthreads_and(okm)) { failed = 2; break; }
+        tc_fence_after();
+        // epilogue: this thread's row is tensor-memory lane tid
+        float d2[2] = {0.f, 0.f};
+        const uint32_t lrow = taddr + ((uint32_t)(w * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < NC; c0 += 16) {
+            float v[16];
+            tmem_ld16(lrow + (uint32_t)c0, v);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int col = c0 + u, kc = col / KP, i = col % KP;
+                if (i < p) {
+                    const float y = v[u] - s_b[kc][i];
+                    d2[kc] = fmaf(y, y, d2[kc]);
+                }
+            }
+        }
+        tc_fence_before();
+        const int row = row0 + tid;
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+            if (!s_on[kc]) continue;
+            const int cidx = 2 * l + kc;
+            const unsigned wlo = s_wlo[kc], whi = s_whi[kc];
+            const int wsh = s_wsh[kc];
+            const unsigned key = __float_as_uint(d2[kc]);
+            bool cnd = false;
+            if (tid < rows) {
+                const bool in = key < wlo;
+                cnd = !in && key <= whi;
+                if (kc == 0) below0 += in ? 1 : 0; else below1 += in ? 1 : 0;
+                dkeys[(size_t)kc * qm + row] = d2[kc];
+                if (cnd) atomicAdd(&sh[kc * WIN_BINS + ((key - wlo) >> wsh)], 1u);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, cnd);
+            if (bal) {
+                const int lead = __ffs(bal) - 1;
+                int b0 = 0;
+                if (lane == lead) b0 = atomicAdd(&rule[cidx].cand, __popc(bal));
+                b0 = __shfl_sync(0xffffffffu, b0, lead);
+                if (cnd) {
+                    const int idx = b0 + __popc(bal & ((1u << lane) - 1u));
+                    if (idx < m) {
+                        Cand e;
+                        e.key = key;
+                        e.pos = (unsigned)(row - l * m);
+                        e.pad = 0;
+                        cand[(size_t)cidx * m + idx] = e;
+                    }
+                }
+            }
+        }
+    }
+    if (failed) {
+        // let copies still in flight land before the CTA's shared memory is released
+        if (tid == 0) {
+            // in flight: tiles t, t + 1 (raw wait failed) or t + 1, t + 2 (MMA wait failed)
+            const int t0 = failed == 1 ? t : t + 1;
+            for (int u = t0; u < ntiles && u < t0 + 2; ++u) (void)mbar_wait(&bar_raw[u & 1], (unsigned)(u >> 1) & 1u);
+            if (failed == 2) (void)mbar_wait(&bar_mma, ph_mma ^ 1u);
+            set_error(st, RTD_EINTERNAL);
+        }
+    }
+    below0 = warp_sum_int(below0);
+    below1 = warp_sum_int(below1);
+    if (lane == 0) {
+        if (below0) atomicAdd(&s_below[0], below0);
+        if (below1) atomicAdd(&s_below[1], below1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (w == 0) tmem_dealloc(taddr, D::TCOLS);
+    if (failed) return;
+    if (tid < 2 && s_on[tid] && s_below[tid]) atomicAdd(&rule[2 * l + tid].below, s_below[tid]);
+    for (int kc = 0; kc < 2; ++kc) {
+        if (!s_on[kc]) continue;
+        unsigned* gh = hist + (size_t)(2 * l + kc) * HIST_BINS;
+        for (int b = tid; b < WIN_BINS; b += NTH) {
+            const unsigned v = sh[kc * WIN_BINS + b];
+            if (v) atomicAdd(gh + b, v);
+        }
+    }
+}
+
+template <int PB>
+void dist_tc_t(const Plan& P, cudaStream_t s) {
+    typedef DistTC<PB> D;
+    // one resident wave, at least one tile per CTA
+    long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
+    const long long lim = ((long long)P.m + D::TM - 1) / D::TM;
+    if (cw > lim) cw = lim;
+    const int cpb = (int)(cw > 0 ? cw : 1);
+    dim3 grid(cpb, P.q);
+    auto k = k_dist_tc<PB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::SMEM);
+    k<<<grid, D::NTH, D::SMEM, s>>>(P.Xp, P.p, P.m, cpb, P.cs, P.ch, P.rule, (float*)P.dkeys,
+                                    (long long)P.q * P.m, P.cand, P.hist, P.st, P.blk_active);
 }
 
 // =====================================================================

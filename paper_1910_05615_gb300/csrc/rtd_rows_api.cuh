@@ -10,6 +10,7 @@ namespace rtd {
     void transform_pb##N(const Plan& P, cudaStream_t s);                                            \
     void dist_pb##N(const Plan& P, cudaStream_t s);                                                 \
     void dist_win_pb##N(const Plan& P, cudaStream_t s);                                             \
+    void dist_tc_pb##N(const Plan& P, cudaStream_t s);                                              \
     void band64_pb##N(const Plan& P, cudaStream_t s);                                               \
     void grad_pb##N(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,   \
                     const RowParams* rp, double* partial, size_t slot_d, double* tot, double c,       \

@@ -30,6 +30,7 @@ void RTD_FN(dist_pb)(const Plan& P, cudaStream_t s) {
     else dist_t<RTD_PB, float>(P, s);
 }
 void RTD_FN(dist_win_pb)(const Plan& P, cudaStream_t s) { dist_win_t<RTD_PB>(P, s); }
+void RTD_FN(dist_tc_pb)(const Plan& P, cudaStream_t s) { dist_tc_t<RTD_PB>(P, s); }
 void RTD_FN(band64_pb)(const Plan& P, cudaStream_t s) { band64_t<RTD_PB>(P, s); }
 void RTD_FN(grad_pb)(const float* X, long long n, int p, long long ld, const uint8_t* wset, int wbit,
                      const RowParams* rp, double* partial, size_t slot_d, double* tot, double c, double w_ld,

@@ -387,7 +387,7 @@ __device__ bool make_rowparams(const double* __restrict__ mu_z, const double* __
 // predicted from the chain's last two thresholds (none before the first
 // selection: the histogram path runs).
 __device__ inline void set_window(SelRule& R, int fp32, int path) {
-    R.below = 0; R.cand = 0; R.band = 0; R.nlo = 0;
+    R.below = 0; R.cand = 0; R.band = 0; R.nlo = 0; R.done = 0;
     R.fast = 0; R.need_hist = 0; R.bandsel = 0; R.band_off = 0;
     R.win = 0;
     if (!fp32 || path == 1 || !R.have_t || !(R.t_prev >= 0.f) || !isfinite(R.t_prev)) return;

@@ -1517,6 +1517,278 @@ __global__ void __launch_bounds__(BANDSEL_T) k_select_band(const Chain* __restri
     }
 }
 
+// =====================================================================
+// Window path of the FP32 form in one launch (from the second C-step on),
+// SF_CTAS CTAs per chain.  Every CTA finds the window bin b that holds rank
+// r = h_b - (rows below the window).  The FP64 range is that bin widened
+// by the band, [lo_b (1 - eps), hi_b (1 + eps)]: a row whose FP32 key lies
+// below it is in, above it out (the FP32 error is under eps), and a row
+// inside it is decided by its FP64 distance.  The rule needs no FP32
+// threshold: every CTA counts its share of the candidates below the range
+// and appends (FP64 d2, position) of those inside it to the chain's list;
+// the chain's last CTA ranks the list (ties to the lower position) and sets
+// the decision bits the membership pass reads.  A window that misses (the
+// rank or the range outside it) is resolved by the last CTA with the
+// histogram path over the block's keys and the same FP64 ranking.
+// =====================================================================
+constexpr int SF_T = 256;       // threads per CTA
+constexpr int SF_CTAS = 8;      // CTAs per chain
+
+// FP64 d2 = |M (x - mu)|^2 of one padded row; M (lower triangular, row
+// stride PB) and mu in shared memory.  Output rows are taken 16 at a time,
+// column by column within a block, so that every FMA of a column step feeds
+// a different accumulator and the accumulators stay in registers.
+template <int PB>
+__device__ __forceinline__ double row_d2_fp64(const float* __restrict__ xrow, const double* sM, const double* smu) {
+    constexpr int IB = 16;
+    asm volatile("" ::: "memory");   // keep M in shared memory, not hoisted into registers across rows
+    float x[PB];
+#pragma unroll
+    for (int q4 = 0; q4 < PB / 4; ++q4) {
+        const float4 v = reinterpret_cast<const float4*>(xrow)[q4];
+        x[4 * q4] = v.x; x[4 * q4 + 1] = v.y; x[4 * q4 + 2] = v.z; x[4 * q4 + 3] = v.w;
+    }
+    double d2 = 0.0;
+#pragma unroll
+    for (int i0 = 0; i0 < PB; i0 += IB) {
+        double y[IB];
+#pragma unroll
+        for (int ii = 0; ii < IB; ++ii) y[ii] = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < PB && jj < i0 + IB; ++jj) {
+            const double cj = (double)x[jj] - smu[jj];
+#pragma unroll
+            for (int ii = 0; ii < IB; ++ii)
+                if (i0 + ii < PB && i0 + ii >= jj) y[ii] = fma(sM[(i0 + ii) * PB + jj], cj, y[ii]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < IB; ++ii) y[ii] *= y[ii];
+#pragma unroll
+        for (int w2 = 1; w2 < IB; w2 <<= 1)
+#pragma unroll
+            for (int ii = 0; ii + w2 < IB; ii += 2 * w2) y[ii] += y[ii + w2];
+        d2 += y[0];
+    }
+    return d2;
+}
+
+template <int PB>
+__device__ void stage_m64(const RowParams& rp, int p, double* sM, double* smu) {
+    for (int e = threadIdx.x; e < PB * PB; e += blockDim.x) {
+        const int i = e / PB, j = e % PB;
+        sM[e] = (i < p && j <= i) ? rp.M[i * PMAX + j] : 0.0;
+    }
+    for (int j = threadIdx.x; j < PB; j += blockDim.x) smu[j] = (j < p) ? rp.mu[j] : 0.0;
+}
+
+// Rank the list (key = FP64 d2 bits, pos) and set decision bit 1 of the
+// first r1 entries in (d2, pos) order, clearing it on the others; returns
+// the d2 of entry r1 (rank r1 - 1) to every thread.  buf: SEL_SMALL entries.
+__device__ double rank_and_mark(const Cand* list, int n, int r1, uint8_t* mb, Cand* buf, Status* st) {
+    __shared__ double s_t;
+    if (r1 < 1 || r1 > n) {
+        if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
+        return 0.0;
+    }
+    if (n <= SEL_SMALL) {
+        // other CTAs wrote the list in this launch: read it from L2
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(list) + i);
+            buf[i].key = v.x;
+            buf[i].pos = (unsigned)(v.y & 0xffffffffull);
+            buf[i].pad = (unsigned)(v.y >> 32);
+        }
+        __syncthreads();
+        if (n <= 512) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const u128 v = comp(buf[i]);
+                int rank = 0;
+                for (int j = 0; j < n; ++j) rank += comp(buf[j]) < v ? 1 : 0;
+                const unsigned pos = buf[i].pos;
+                mb[pos] = (uint8_t)((mb[pos] & 1) | (rank < r1 ? 2 : 0));
+                if (rank == r1 - 1) s_t = __longlong_as_double((long long)buf[i].key);
+            }
+        } else {
+            cta_bitonic(buf, n);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const unsigned pos = buf[i].pos;
+                mb[pos] = (uint8_t)((mb[pos] & 1) | (i < r1 ? 2 : 0));
+            }
+            if (threadIdx.x == 0) s_t = __longlong_as_double((long long)buf[r1 - 1].key);
+        }
+        __syncthreads();
+        return s_t;
+    }
+    const Cand tb = cta_select_rank(list, n, r1, 64, buf, st);
+    if (tb.pad) return 0.0;
+    const u128 tv = comp(tb);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Cand e = list[i];
+        mb[e.pos] = (uint8_t)((mb[e.pos] & 1) | (comp(e) <= tv ? 2 : 0));
+    }
+    return __longlong_as_double((long long)tb.key);
+}
+
+template <int PB>
+__global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
+                                                      const float* __restrict__ Xp, const float* __restrict__ dkeys,
+                                                      long long qm, Cand* __restrict__ cand_all,
+                                                      Cand* __restrict__ band_all, unsigned* __restrict__ hist,
+                                                      uint8_t* __restrict__ memb_all, int m, int p, int hb,
+                                                      Status* st) {
+    static_assert(WIN_BINS % SF_T == 0, "window bins per thread");
+    static_assert(SEL_SMALL * sizeof(Cand) >= HIST_BINS * sizeof(unsigned), "histogram aliases buf");
+    __shared__ Cand buf[SEL_SMALL];
+    extern __shared__ double sm64[];
+    double* sM = sm64;              // PB x PB
+    double* smu = sm64 + PB * PB;   // PB
+    __shared__ unsigned wt[SF_T / 32];
+    __shared__ int s_pos[SF_T];
+    __shared__ int s_n, s_bin, s_last, s_base, s_nlo;
+    const int c = blockIdx.x;
+    if (!ch[c].active) return;
+    SelRule& R = rule[c];
+    if (!R.win) return;
+    const int l = c / 2, k = c % 2;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int C = R.cand < m ? R.cand : m;
+    const int r = hb - R.below;
+    unsigned* h = hist + (size_t)c * HIST_BINS;
+    uint8_t* mb = memb_all + (size_t)c * m;
+    // 1. the window bin of rank r (each thread owns PER consecutive bins)
+    constexpr int PER = WIN_BINS / SF_T;
+    unsigned loc[PER];
+    unsigned run = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) { loc[i] = h[tid * PER + i]; run += loc[i]; }
+    unsigned x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    if (tid == 0) { s_bin = -1; s_nlo = 0; }
+    __syncthreads();
+    unsigned cum = x - run;
+    for (int k2 = 0; k2 < w; ++k2) cum += wt[k2];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        if (r >= 1 && cum < (unsigned)r && (unsigned)r <= cum + loc[i]) s_bin = tid * PER + i;
+        cum += loc[i];
+    }
+    __syncthreads();
+    const int b = s_bin;
+    bool miss = (r < 1 || r > C || b < 0);
+    unsigned long long kb_lo = 0ull, kb_hi = 0ull;
+    if (!miss) {
+        const unsigned lo_key = R.w_lo + ((unsigned)b << R.w_sh);
+        unsigned hi_key = lo_key + ((1u << R.w_sh) - 1u);
+        if (hi_key > R.w_hi || hi_key < lo_key) hi_key = R.w_hi;
+        kb_lo = __float_as_uint(__uint_as_float(lo_key) * (float)(1.0 - BAND_EPS));
+        kb_hi = __float_as_uint(__uint_as_float(hi_key) * (float)(1.0 + BAND_EPS));
+        // rows of the FP64 range outside the window were not listed
+        if (kb_lo < (unsigned long long)R.w_lo || kb_hi > (unsigned long long)R.w_hi) miss = true;
+    }
+    // 2. this CTA's share of the candidates
+    if (!miss) {
+        stage_m64<PB>(ch[c].rp, p, sM, smu);
+        const int chunk = (C + SF_CTAS - 1) / SF_CTAS;
+        const int i0 = (int)blockIdx.y * chunk;
+        const int i1 = min(C, i0 + chunk);
+        const Cand* cand = cand_all + (size_t)c * m;
+        Cand* list = band_all + (size_t)c * m;
+        const float* Xb = Xp + (size_t)l * m * PB;
+        int nlo = 0;
+        for (int base = i0; base < i1; base += SF_T) {
+            if (tid == 0) s_n = 0;
+            __syncthreads();
+            const int i = base + tid;
+            bool take = false;
+            unsigned pos = 0;
+            if (i < i1) {
+                const Cand e = cand[i];
+                if (e.key < kb_lo) ++nlo;
+                else if (e.key <= kb_hi) { take = true; pos = e.pos; }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            int wb = 0;
+            if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (take) s_pos[wb + __popc(bal & ((1u << lane) - 1u))] = (int)pos;
+            __syncthreads();
+            const int nr = s_n;
+            if (tid == 0 && nr) s_base = atomicAdd(&R.band, nr);
+            __syncthreads();
+            if (tid < nr) {   // full warps of rows: the FP64 pipe charges per warp instruction
+                const unsigned ps = (unsigned)s_pos[tid];
+                Cand e;
+                e.key = (unsigned long long)__double_as_longlong(row_d2_fp64<PB>(Xb + (size_t)ps * PB, sM, smu));
+                e.pos = ps;
+                e.pad = 0;
+                list[s_base + tid] = e;
+            }
+        }
+        nlo = warp_sum_int(nlo);
+        if (lane == 0 && nlo) atomicAdd(&s_nlo, nlo);
+        __syncthreads();
+        if (tid == 0 && s_nlo) atomicAdd(&R.nlo, s_nlo);
+    }
+    // 3. the chain's last CTA
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&R.done, 1) == SF_CTAS - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int i = tid; i < WIN_BINS; i += SF_T) h[i] = 0u;   // every CTA has read the bins
+    if (!miss) {
+        const int n64 = atomicAdd(&R.band, 0);
+        const int nlo_all = atomicAdd(&R.nlo, 0);
+        const double t = rank_and_mark(band_all + (size_t)c * m, n64, r - nlo_all, mb, buf, st);
+        if (tid == 0) {
+            R.t_lo = kb_lo;
+            R.t_hi = kb_hi;
+            R.nlo = R.below + nlo_all;
+            R.band_off = 0;
+            R.t_prev2 = R.t_prev;
+            R.t_prev = (float)t;
+            R.fast = 1;
+            R.acc_win += 1;
+            R.acc_cand += C;
+            R.acc_band += n64;
+        }
+        return;
+    }
+    // the window missed: histogram path over the block's keys, then the
+    // band's FP64 distances and ranking in this CTA
+    if (tid == 0) { R.need_hist = 1; R.acc_win += 1; R.acc_cand += C; R.acc_miss += 1; }
+    unsigned* cnt = reinterpret_cast<unsigned*>(buf);
+    cta_hist_path(R, dkeys + (size_t)k * qm + (size_t)l * m, m, hb, cand_all + (size_t)c * m,
+                  band_all + (size_t)c * m, buf, cnt, st);
+    __syncthreads();
+    if (!R.bandsel) return;   // an error was recorded
+    stage_m64<PB>(ch[c].rp, p, sM, smu);
+    __syncthreads();
+    const int nb = R.band;
+    Cand* band = band_all + (size_t)c * m + R.band_off;
+    const float* Xb = Xp + (size_t)l * m * PB;
+    for (int i = tid; i < nb; i += SF_T)
+        band[i].key = (unsigned long long)__double_as_longlong(row_d2_fp64<PB>(Xb + (size_t)band[i].pos * PB, sM, smu));
+    __syncthreads();
+    (void)rank_and_mark(band, nb, hb - R.nlo, mb, buf, st);
+    if (tid == 0) { R.acc_band += nb; R.bandsel = 0; R.fast = 1; }
+}
+
+void launch_select_fast(const Plan& P, cudaStream_t s) {
+    RTD_PB_SWITCH(P.pb, {
+        const size_t sm = (size_t)(PB * PB + PB) * sizeof(double);
+        k_select_fast<PB><<<dim3(2 * P.q, SF_CTAS), SF_T, sm, s>>>(P.ch, P.rule, P.Xp, (const float*)P.dkeys,
+                                                                   (long long)P.q * P.m, P.cand, P.band, P.hist,
+                                                                   P.memb, P.m, P.p, P.hb, P.st);
+    });
+}
+
 void launch_select_win(const Plan& P, cudaStream_t s) {
     k_select_win<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.hist, (const float*)P.dkeys,
                                            (long long)P.q * P.m, P.m, P.hb, P.st);

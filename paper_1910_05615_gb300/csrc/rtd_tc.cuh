@@ -68,6 +68,28 @@ __host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
     return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
+// Instruction descriptor of kind::tf32: TF32 A and B (32-bit containers),
+// FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                      // D format: F32
+           | (2u << 7) | (2u << 10)       // A, B format: TF32
+           | ((uint32_t)(N >> 3) << 17)   // N / 8
+           | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ inline void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)acc)
+        : "memory");
+}
+
+// TF32 high part of an FP32 value (sign, exponent and the top 10 mantissa
+// bits); x - tf32_hi(x) is exact in FP32 and holds the rest.
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 __device__ inline void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -133,8 +155,10 @@ struct GramTC {
     static constexpr int PAD = 2048;
     static constexpr int ACC_LD = H + 1;                    // pair-sum row stride (bank spread)
     static constexpr int SMEM = 2 * OPS1 + PAD + H * ACC_LD * 8;
-    // rows accumulated in FP32 in tensor memory between two flushes
-    static constexpr int FLUSH_ROWS = 256;
+    // rows accumulated in FP32 in tensor memory between two flushes (one
+    // batch: the accumulation there need not round to nearest, so its depth
+    // is kept short)
+    static constexpr int FLUSH_ROWS = 128;
     static_assert(2 * H <= 128 && CH >= 16, "A: hi and mid on at most 128 lanes, read within one row group");
     static_assert(N % 16 == 0 && N <= 256, "N a multiple of 16, at most 256");
     static_assert(TR % 16 == 0, "tile rows must be a multiple of 16");

@@ -250,6 +250,28 @@ def test_select_paths_agree(rtd, main_case, case):
     assert p0["sel_band"] > 0
 
 
+@pytest.mark.parametrize("case", ["main", "point", "p37", "p64"])
+def test_dist_paths_agree(rtd, main_case, case):
+    """The C-step distances on the tensor cores (split-TF32 operands, the
+    default) and on the CUDA cores (FP32 FMAs) feed the same FP64-exact
+    decisions: the same subsets at every step, so bitwise the same fits."""
+    if case == "main":
+        fr = main_case[0]
+    elif case == "point":
+        fr = datagen.contaminated_gaussian(120_000, 5, eps=0.1, kind="point", shift=10.0, seed=3)
+    elif case == "p37":
+        fr = datagen.contaminated_gaussian(300_000, 37, eps=0.15, kind="cluster", shift=6.0, seed=6)
+    else:
+        fr = datagen.contaminated_gaussian(200_000, 64, eps=0.1, kind="shift", shift=7.0, seed=4)
+    X = torch.from_numpy(fr.X).cuda()
+    a = rtd.rtdetmcd_fit(X, fr.h, dist_path=0, subset=True, profile=True)
+    b = rtd.rtdetmcd_fit(X, fr.h, dist_path=1, subset=True)
+    assert torch.equal(a["subset"], b["subset"])
+    assert np.array_equal(a["mu"], b["mu"]) and np.array_equal(a["Sigma"], b["Sigma"])
+    assert np.array_equal(a["Sigma_raw"], b["Sigma_raw"]) and torch.equal(a["flags"], b["flags"])
+    assert a["profile"]["win_steps"] > 0
+
+
 def test_select_path_rejects_bad_value(rtd):
     fr = datagen.small_fp64_case()
     with pytest.raises(rtd.RtdError):
@@ -389,7 +411,7 @@ def test_fit_outputs_autograd(rtd):
     a, B, wv = rng.standard_normal(6), rng.standard_normal((6, 6)), rng.standard_normal(40_000)
     Xr = X.clone().requires_grad_(True)
     mu, S, ld, rd = rtd.rtdetmcd_fit_outputs(Xr, fr.h)
-    np.testing.assert_array_equal(mu.cpu().numpy(), fit["mu"])
+    np.testing.assert_array_equal(mu.detach().cpu().numpy(), fit["mu"])
     loss = (mu * torch.from_numpy(a).cuda()).sum() + (S * torch.from_numpy(B).cuda()).sum() + 0.3 * ld \
         + (rd.double() * torch.from_numpy(wv).cuda()).sum()
     loss.backward()
@@ -465,7 +487,7 @@ def test_grad_rejects_small_set(rtd):
 @pytest.mark.parametrize("n,p", [(400_000, 40), (200_003, 25), (200_003, 48)])
 def test_bf16_form_parity(rtd, n, p):
     """Start and C-step Grams on tcgen05 (three-way split-BF16 products, FP32
-    accumulation in tensor memory, compensated sums every 256 rows), the
+    accumulation in tensor memory, compensated sums every 128 rows), the
     reweighting Gram on the CUDA cores: mu and Sigma (raw and reweighted)
     within 1e-3 relative of the FP64 oracle, and, as for the FP32 form, the
     same final h-subsets, reweighting set and flags outside the 1e-6 tie
