@@ -249,7 +249,31 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld,
                        int32_t precision, float* d2_out,
                        void* workspace, size_t ws_bytes, void* stream);
 
-/* Size of the fixed device array used by rtdetmcd_distances_noalloc. */
+/* Bytes of workspace rtdetmcd_score needs. */
+size_t rtdetmcd_score_workspace_size(int64_t n, int32_t p);
+
+/*
+ * Scoring of rows against a fit in one pass (Section 6: the distances and
+ * flags of Section 4 step 10 for new data): d2_i = (x_i - mu)^T Sigma^-1
+ * (x_i - mu) and the flag d2_i > cutoff_d2, both written by the same
+ * streaming kernel, with the number of flagged rows.
+ *   mu_host, sigma_host  the fit (host; sigma positive definite, else
+ *                        RTD_EDEGENERATE); passed in the launch parameters,
+ *                        so no copy of them precedes the stream
+ *   cutoff_d2            e.g. rtdetmcd_chi2_quantile(p, 0.975)
+ *   precision            RTD_FP32: FP32 rows, and a row whose FP32 d2 lies
+ *                        within 2^-9 of the cutoff is decided by its FP64
+ *                        distance (so the flags equal those of FP64
+ *                        distances); RTD_FP64: FP64 rows
+ *   d2_out               nullable, n floats
+ *   flags_out            nullable, n bytes (1 = outlier)
+ *   n_flagged            nullable, host: the count (-1 without flags_out)
+ */
+int rtdetmcd_score(const float* X, int64_t n, int32_t p, int64_t ld, const double* mu_host,
+                   const double* sigma_host, double cutoff_d2, int32_t precision, float* d2_out,
+                   uint8_t* flags_out, int64_t* n_flagged, void* workspace, size_t ws_bytes, void* stream);
+
+/* Size of the fixed device array used by rtdetmcd_distances_noalloc. *//* Size of the fixed device array used by rtdetmcd_distances_noalloc. */
 #define RTD_NOALLOC_SCRATCH_BYTES (96 * 1024)
 
 /*

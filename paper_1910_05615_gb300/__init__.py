@@ -23,7 +23,8 @@ __all__ = [
     "rtdetmcd_flag", "rtdetmcd_distances_noalloc", "rtdetmcd_chi2_quantile", "rtdetmcd_status_string", "rtdetmcd_workspace_size",
     "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
     "rtdetmcd_grad_workspace_size", "rtdetmcd_objective", "rtdetmcd_fit_batch",
-    "rtdetmcd_fit_batch_workspace_size", "rtdetmcd_vjp", "rtdetmcd_fit_outputs",
+    "rtdetmcd_fit_batch_workspace_size", "rtdetmcd_vjp", "rtdetmcd_fit_outputs", "rtdetmcd_score",
+    "rtdetmcd_score_workspace_size",
 ]
 
 RTD_FP64 = 0
@@ -106,6 +107,10 @@ def _load():
     lib.rtdetmcd_distances_workspace_size.restype = sz
     lib.rtdetmcd_distances.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp, sz, vp]
     lib.rtdetmcd_distances.restype = i32
+    lib.rtdetmcd_score_workspace_size.argtypes = [i64, i32]
+    lib.rtdetmcd_score_workspace_size.restype = sz
+    lib.rtdetmcd_score.argtypes = [vp, i64, i32, i64, vp, vp, dbl, i32, vp, vp, ctypes.POINTER(i64), vp, sz, vp]
+    lib.rtdetmcd_score.restype = i32
     lib.rtdetmcd_distances_noalloc.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp]
     lib.rtdetmcd_distances_noalloc.restype = i32
     P64, P32 = ctypes.POINTER(i64), ctypes.POINTER(i32)
@@ -373,6 +378,34 @@ def rtdetmcd_distances(X, mu, Sigma, *, precision=RTD_FP32, stream=None, workspa
     if st != 0:
         raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
     return d2
+
+
+def rtdetmcd_score_workspace_size(n, p):
+    return _load().rtdetmcd_score_workspace_size(n, p)
+
+
+def rtdetmcd_score(X, mu, Sigma, cutoff_d2=None, *, precision=RTD_FP32, d2=True, flags=True, stream=None,
+                   workspace=None):
+    """Distances, flags (d2 > cutoff_d2) and their count for the rows of X
+    against the fit (mu, Sigma) in one streaming pass.  cutoff_d2 defaults to
+    chi2_{p,0.975}.  Returns (d2 or None, flags or None, n_flagged)."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(-1)
+    S = np.ascontiguousarray(Sigma, dtype=np.float64).reshape(-1)
+    if mu.size != p or S.size != p * p:
+        raise ValueError("mu must have p entries and Sigma p x p")
+    cut = rtdetmcd_chi2_quantile(p, 0.975) if cutoff_d2 is None else float(cutoff_d2)
+    ws = workspace if workspace is not None else _workspace(lib.rtdetmcd_score_workspace_size(n, p), dev)
+    d2o = _out(n, np.float32, dev) if d2 else None
+    flo = _out(n, np.uint8, dev) if flags else None
+    cnt = ctypes.c_int64(0)
+    st = lib.rtdetmcd_score(ptr, n, p, ld, mu.ctypes.data, S.ctypes.data, cut, precision, _ptr(d2o), _ptr(flo),
+                            ctypes.byref(cnt), ws.data_ptr(), ws.numel(), _stream_ptr(dev, stream))
+    del keep
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return d2o, flo, cnt.value
 
 
 def rtdetmcd_distances_noalloc(X, mu, Sigma, *, precision=RTD_FP32, out=None, stream=None):

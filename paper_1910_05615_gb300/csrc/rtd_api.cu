@@ -713,6 +713,70 @@ int rtdetmcd_distances(const float* X, int64_t n, int32_t p, int64_t ld, const d
     return hs.code;
 }
 
+size_t rtdetmcd_score_workspace_size(int64_t n, int32_t p) {
+    if (n < 1 || p < 1 || p > RTD_MAX_P) return 0;
+    Layout L;
+    L.add(sizeof(Status));
+    L.add(sizeof(RowParams));
+    L.add(sizeof(double));
+    L.add((size_t)n * p * sizeof(float));
+    L.add((size_t)n * sizeof(float));
+    L.add((size_t)n);
+    return (L.total + 255) & ~(size_t)255;
+}
+
+int rtdetmcd_score(const float* X, int64_t n, int32_t p, int64_t ld, const double* mu_host,
+                   const double* sigma_host, double cutoff_d2, int32_t precision, float* d2_out,
+                   uint8_t* flags_out, int64_t* n_flagged, void* workspace, size_t ws_bytes, void* stream) {
+    if (!X || !mu_host || !sigma_host || n < 1 || p < 1 || p > RTD_MAX_P || ld < p ||
+        (precision != RTD_FP32 && precision != RTD_FP64) || n >= (1LL << 31) || !(cutoff_d2 == cutoff_d2))
+        return RTD_EINVAL;
+    size_t need = rtdetmcd_score_workspace_size(n, p);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    if (on_other_device(X) || on_other_device(d2_out) || on_other_device(flags_out) || on_other_device(workspace))
+        return RTD_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Layout L;
+    Region rst = L.add(sizeof(Status));
+    Region rrp = L.add(sizeof(RowParams));
+    Region rcut = L.add(sizeof(double));
+    Region rxs = L.add((size_t)n * p * sizeof(float));
+    Region rds = L.add((size_t)n * sizeof(float));
+    Region rfs = L.add((size_t)n);
+    Status* st = at<Status>(workspace, rst);
+    RowParams* rp = at<RowParams>(workspace, rrp);
+    // the fit travels in the launch parameters: no copy precedes the stream
+    FitArg a;
+    for (int j = 0; j < p; ++j) a.mu[j] = mu_host[j];
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j <= i; ++j) a.tri[i * (i + 1) / 2 + j] = sigma_host[(size_t)i * p + j];
+    const float* Xd = X;
+    long long ldd = ld;
+    if (!is_device_ptr(X)) {
+        float* xs = at<float>(workspace, rxs);
+        if (ld == p)
+            RTD_CUDA(cudaMemcpyAsync(xs, X, (size_t)n * p * sizeof(float), cudaMemcpyHostToDevice, s));
+        else
+            RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)p * sizeof(float), X, (size_t)ld * sizeof(float),
+                                       (size_t)p * sizeof(float), (size_t)n, cudaMemcpyHostToDevice, s));
+        Xd = xs;
+        ldd = p;
+    }
+    const bool ddev = !d2_out || is_device_ptr(d2_out), fdev = !flags_out || is_device_ptr(flags_out);
+    float* d2 = d2_out ? (ddev ? d2_out : at<float>(workspace, rds)) : nullptr;
+    uint8_t* fl = flags_out ? (fdev ? flags_out : at<uint8_t>(workspace, rfs)) : nullptr;
+    launch_score_prep_arg(a, p, cutoff_d2, rp, st, at<double>(workspace, rcut), s);
+    launch_score_flags(Xd, n, p, ldd, rp, precision, cutoff_d2, at<double>(workspace, rcut), d2, fl,
+                       &st->n_flagged, s);
+    if (d2_out && !ddev) RTD_CUDA(cudaMemcpyAsync(d2_out, d2, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (flags_out && !fdev) RTD_CUDA(cudaMemcpyAsync(flags_out, fl, (size_t)n, cudaMemcpyDeviceToHost, s));
+    Status hs;
+    int e = fetch_status(st, s, hs);
+    if (e) return e;
+    if (n_flagged) *n_flagged = flags_out ? (int64_t)hs.n_flagged : -1;
+    return hs.code;
+}
+
 size_t rtdetmcd_grad_workspace_size(int64_t n, int32_t p) {
     if (n < 1 || p < 1 || p > RTD_MAX_P) return 0;
     const size_t slot_d = (size_t)gram_nblk(pad_p(p)) * 16 + 2;

@@ -115,6 +115,22 @@ void launch_rew_finalize(const Plan& P, cudaStream_t s);
 void launch_result(const Plan& P, rtd_result* dev_out, double* diag, cudaStream_t s);
 void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* rp,
                        Status* st, cudaStream_t s, double* logdet_out = nullptr);
+// A fit (mu and the lower triangle of Sigma, row by row) passed by value in
+// the launch parameters of the scoring preparation: no host-to-device copy
+// precedes the scoring stream.
+struct FitArg {
+    double mu[PMAX];
+    double tri[PMAX * (PMAX + 1) / 2];
+};
+// (also zeroes the status word and stores the cutoff at cut_out)
+void launch_score_prep_arg(const FitArg& a, int p, double cut, RowParams* rp, Status* st, double* cut_out,
+                           cudaStream_t s);
+// Distances and flags of the scoring call in one pass (Section 6): d2_out
+// and flags nullable; FP32 rows decide in FP64 near the cutoff.  cut_dev:
+// the cutoff in device memory (FP64 form).
+void launch_score_flags(const float* X, long long n, int p, long long ld, const RowParams* rp, int precision,
+                        double cut, const double* cut_dev, float* d2_out, uint8_t* flags,
+                        unsigned long long* count, cudaStream_t s);
 // adjoint of steps 8-10 (rtd_rows.cu): slot count of the reduction pass
 constexpr int GRAD_SLOTS = 1024;
 // Cotangents of the vector-Jacobian product of the reweighted fit (device

@@ -214,6 +214,20 @@ void launch_final(const Plan& P, float* d2_out, uint8_t* flags_out, cudaStream_t
                 d2_out, flags_out, &P.st->n_flagged, P.nsm, s);
 }
 
+void launch_score_flags(const float* X, long long n, int p, long long ld, const RowParams* rp, int precision,
+                        double cut, const double* cut_dev, float* d2_out, uint8_t* flags,
+                        unsigned long long* count, cudaStream_t s) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (precision == RTD_FP64) {   // FP64 rows decide exactly: the final pass of the fit
+        RTD_PB_CALL(pad_p(p), final, X, n, p, ld, precision, rp, cut_dev, flags ? 1 : 0, d2_out, flags, count,
+                    nsm, s);
+        return;
+    }
+    RTD_PB_CALL(pad_p(p), score, X, n, p, ld, rp, cut, d2_out, flags, count, nsm, s);
+}
+
 void launch_score(const float* X, long long n, int p, long long ld, const RowParams* rp,
                   int precision, float* d2_out, cudaStream_t s) {
     int dev = 0, nsm = 148;

@@ -1022,14 +1022,14 @@ template <int PB> struct DistTC {
     static constexpr int NC = 2 * KP;                      // N: both starts' outputs
     static constexpr int TM = 128;                         // rows per tile (M)
     static constexpr int NTH = 128;                        // one thread per tile row
-    static constexpr int TCOLS = NC <= 32 ? 32 : (NC <= 64 ? 64 : 128);
+    static constexpr int RS = PB <= 24 ? 3 : 2;            // raw tile stages (bulk copies in flight)
+    static constexpr int TCOLS = 2 * NC <= 32 ? 32 : (2 * NC <= 64 ? 64 : (2 * NC <= 128 ? 128 : 256));
     static constexpr size_t RAW = (size_t)TM * PB * 4;    // one raw tile
-    static constexpr size_t AOP = (size_t)TM * KP * 4;    // one part of A
+    static constexpr size_t AOP = (size_t)TM * KP * 4;    // one part of one A buffer
     static constexpr size_t BOP = (size_t)NC * KP * 4;    // one part of B
-    static constexpr size_t OFF_A = (2 * RAW + 127) / 128 * 128;
-    static constexpr size_t OFF_B = OFF_A + 2 * AOP;
-    static constexpr size_t OFF_H = OFF_B + 2 * BOP;
-    static constexpr size_t SMEM = OFF_H + 2 * (size_t)WIN_BINS * 4;
+    static constexpr size_t OFF_A = (RS * RAW + 127) / 128 * 128;
+    static constexpr size_t OFF_B = OFF_A + 4 * AOP;      // A: 2 buffers x (hi, lo)
+    static constexpr size_t SMEM = OFF_B + 2 * BOP;
     static constexpr int BY_SMEM = (int)((227 * 1024) / (SMEM + 1024));
     static constexpr int BY_TMEM = 512 / TCOLS;
     static constexpr int CTAS_PER_SM = BY_SMEM < BY_TMEM ? (BY_SMEM < 4 ? (BY_SMEM < 1 ? 1 : BY_SMEM) : 4)
@@ -1042,27 +1042,35 @@ __device__ __forceinline__ unsigned kop_off(int r, int k, int kch) {
     return (unsigned)(((r >> 3) * kch + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
+// 32 lanes x 16 columns of tensor memory into registers, without the wait
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 template <int PB>
 __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
     k_dist_tc(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
               const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys, long long qm,
               Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st, int* blk) {
     typedef DistTC<PB> D;
-    constexpr int KP = D::KP, KCH = D::KCH, NC = D::NC, TM = D::TM, NTH = D::NTH;
+    constexpr int KP = D::KP, KCH = D::KCH, NC = D::NC, TM = D::TM, NTH = D::NTH, RS = D::RS;
     extern __shared__ __align__(1024) unsigned char smem[];
     float* raw = reinterpret_cast<float*>(smem);
-    unsigned char* Ah = smem + D::OFF_A;
-    unsigned char* Al = Ah + D::AOP;
+    unsigned char* Abase = smem + D::OFF_A;        // [buffer][hi, lo]
     unsigned char* Bh = smem + D::OFF_B;
     unsigned char* Bl = Bh + D::BOP;
-    unsigned* sh = reinterpret_cast<unsigned*>(smem + D::OFF_H);
-    __shared__ __align__(8) uint64_t bar_raw[2];
-    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ __align__(8) uint64_t bar_raw[RS];
+    __shared__ __align__(8) uint64_t bar_mma[2];
     __shared__ uint32_t s_taddr;
     __shared__ float s_nu[PB];
     __shared__ float s_b[2][KP];
     __shared__ unsigned s_wlo[2], s_whi[2];
-    __shared__ int s_wsh[2], s_on[2], s_below[2];
+    __shared__ int s_wsh[2], s_on[2], s_below[2], s_fail;
     const int l = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     clear_step_counters(st, blk);
@@ -1078,12 +1086,12 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
         s_below[tid] = 0;
     }
     if (tid == 0) {
-        mbar_init(&bar_raw[0], 1);
-        mbar_init(&bar_raw[1], 1);
-        mbar_init(&bar_mma, 1);
+        for (int i = 0; i < RS; ++i) mbar_init(&bar_raw[i], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
         mbar_init_fence();
+        s_fail = 0;
     }
-    for (int e = tid; e < 2 * WIN_BINS; e += NTH) sh[e] = 0u;
     // B = [M_1^T | M_2^T]: row n = k KP + i of B is row i of M_k (zero beyond p)
     for (int e = tid; e < NC * KP; e += NTH) {
         const int n = e / KP, j = e % KP;
@@ -1113,87 +1121,43 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
         const int row0 = r0 + t * TM;
         const int rows = min(TM, r1 - row0);
         const unsigned bytes = (unsigned)rows * PB * (unsigned)sizeof(float);
-        mbar_expect_tx(&bar_raw[t & 1], bytes);
-        bulk_load(raw + (size_t)(t & 1) * TM * PB, Xp + (size_t)row0 * PB, bytes, &bar_raw[t & 1]);
+        mbar_expect_tx(&bar_raw[t % RS], bytes);
+        bulk_load(raw + (size_t)(t % RS) * TM * PB, Xp + (size_t)row0 * PB, bytes, &bar_raw[t % RS]);
     };
     if (tid == 0)
-        for (int t = 0; t < 2 && t < ntiles; ++t) issue(t);
+        for (int t = 0; t < RS && t < ntiles; ++t) issue(t);
     const uint32_t idesc = idesc_tf32(TM, NC);
-    const uint32_t aoff_h = smem_addr(Ah), aoff_l = smem_addr(Al), boff_h = smem_addr(Bh), boff_l = smem_addr(Bl);
+    const uint32_t abase = smem_addr(Abase), boff_h = smem_addr(Bh), boff_l = smem_addr(Bl);
     int below0 = 0, below1 = 0;
-    int failed = 0;
-    unsigned ph_mma = 0;
-    int t = 0;
-    for (; t < ntiles; ++t) {
-        const int row0 = r0 + t * TM;
-        const int rows = min(TM, r1 - row0);
-        const bool okr = mbar_wait(&bar_raw[t & 1], (unsigned)(t >> 1) & 1u);
-        if (!__syncthreads_and(okr)) { failed = 1; break; }
-        // centre the row and split it into the two A parts
-        {
-            float c[KP];
-            const float* src = raw + (size_t)(t & 1) * TM * PB + (size_t)tid * PB;
-#pragma unroll
-            for (int q4 = 0; q4 < PB / 4; ++q4) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (tid < rows) v = reinterpret_cast<const float4*>(src)[q4];
-                c[4 * q4 + 0] = v.x + s_nu[4 * q4 + 0];
-                c[4 * q4 + 1] = v.y + s_nu[4 * q4 + 1];
-                c[4 * q4 + 2] = v.z + s_nu[4 * q4 + 2];
-                c[4 * q4 + 3] = v.w + s_nu[4 * q4 + 3];
-            }
-#pragma unroll
-            for (int j = PB; j < KP; ++j) c[j] = 0.f;
-            if (tid >= rows) {
-#pragma unroll
-                for (int j = 0; j < KP; ++j) c[j] = 0.f;
-            }
-#pragma unroll
-            for (int q4 = 0; q4 < KCH; ++q4) {
-                float4 h, lo;
-                h.x = tf32_hi(c[4 * q4 + 0]); lo.x = c[4 * q4 + 0] - h.x;
-                h.y = tf32_hi(c[4 * q4 + 1]); lo.y = c[4 * q4 + 1] - h.y;
-                h.z = tf32_hi(c[4 * q4 + 2]); lo.z = c[4 * q4 + 2] - h.z;
-                h.w = tf32_hi(c[4 * q4 + 3]); lo.w = c[4 * q4 + 3] - h.w;
-                *reinterpret_cast<float4*>(Ah + kop_off(tid, 4 * q4, KCH)) = h;
-                *reinterpret_cast<float4*>(Al + kop_off(tid, 4 * q4, KCH)) = lo;
-            }
+
+    // epilogue of tile u: d2 of this thread's row from accumulator u & 1,
+    // classification against the windows
+    auto epilogue = [&](int u) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma[u & 1], (unsigned)(u >> 1) & 1u));
+        if (!ok) {
+            if (lane == 0) s_fail = 1;
+            return;
         }
-        async_proxy_fence();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            // the raw stage of tile t is read: refill it with tile t + 2
-            if (t + 2 < ntiles) issue(t + 2);
-            tc_fence_after();
-#pragma unroll
-            for (int ks = 0; ks < KP / 8; ++ks) {
-                const uint32_t o = (uint32_t)ks * 256u;
-                const uint64_t ah = smem_desc(aoff_h + o, 128, KCH * 128), al = smem_desc(aoff_l + o, 128, KCH * 128);
-                const uint64_t bh = smem_desc(boff_h + o, 128, KCH * 128), bl = smem_desc(boff_l + o, 128, KCH * 128);
-                mma_tf32(taddr, ah, bh, idesc, ks > 0);
-                mma_tf32(taddr, al, bh, idesc, true);
-                mma_tf32(taddr, ah, bl, idesc, true);
-            }
-            mma_commit(&bar_mma);
-        }
-        const bool okm = mbar_wait(&bar_mma, ph_mma);
-        ph_mma ^= 1u;
-        if (!__syncthreads_and(okm)) { failed = 2; break; }
         tc_fence_after();
-        // epilogue: this thread's row is tensor-memory lane tid
+        const int row0 = r0 + u * TM;
+        const int rows = min(TM, r1 - row0);
         float d2[2] = {0.f, 0.f};
-        const uint32_t lrow = taddr + ((uint32_t)(w * 32) << 16);
+        const uint32_t lrow = taddr + ((uint32_t)(w * 32) << 16) + (uint32_t)((u & 1) * NC);
 #pragma unroll
-        for (int c0 = 0; c0 < NC; c0 += 16) {
-            float v[16];
-            tmem_ld16(lrow + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < NC; c0 += 32) {
+            uint32_t va[16], vb[16];
+            tmem_ld16_nowait(lrow + (uint32_t)c0, va);
+            if (c0 + 16 < NC) tmem_ld16_nowait(lrow + (uint32_t)(c0 + 16), vb);
+            tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int col = c0 + u, kc = col / KP, i = col % KP;
-                if (i < p) {
-                    const float y = v[u] - s_b[kc][i];
-                    d2[kc] = fmaf(y, y, d2[kc]);
+            for (int u2 = 0; u2 < 32; ++u2) {
+                const int col = c0 + u2;
+                if (col < NC) {
+                    const int kc = col / KP, i = col % KP;
+                    if (i < p) {
+                        const float y = __uint_as_float(u2 < 16 ? va[u2] : vb[u2 - 16]) - s_b[kc][i];
+                        d2[kc] = fmaf(y, y, d2[kc]);
+                    }
                 }
             }
         }
@@ -1204,7 +1168,6 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
             if (!s_on[kc]) continue;
             const int cidx = 2 * l + kc;
             const unsigned wlo = s_wlo[kc], whi = s_whi[kc];
-            const int wsh = s_wsh[kc];
             const unsigned key = __float_as_uint(d2[kc]);
             bool cnd = false;
             if (tid < rows) {
@@ -1212,7 +1175,7 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
                 cnd = !in && key <= whi;
                 if (kc == 0) below0 += in ? 1 : 0; else below1 += in ? 1 : 0;
                 dkeys[(size_t)kc * qm + row] = d2[kc];
-                if (cnd) atomicAdd(&sh[kc * WIN_BINS + ((key - wlo) >> wsh)], 1u);
+                if (cnd) atomicAdd(hist + (size_t)cidx * HIST_BINS + ((key - wlo) >> s_wsh[kc]), 1u);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, cnd);
             if (bal) {
@@ -1232,16 +1195,81 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
                 }
             }
         }
-    }
-    if (failed) {
-        // let copies still in flight land before the CTA's shared memory is released
-        if (tid == 0) {
-            // in flight: tiles t, t + 1 (raw wait failed) or t + 1, t + 2 (MMA wait failed)
-            const int t0 = failed == 1 ? t : t + 1;
-            for (int u = t0; u < ntiles && u < t0 + 2; ++u) (void)mbar_wait(&bar_raw[u & 1], (unsigned)(u >> 1) & 1u);
-            if (failed == 2) (void)mbar_wait(&bar_mma, ph_mma ^ 1u);
-            set_error(st, RTD_EINTERNAL);
+    };
+
+    int t = 0;
+    int issued = ntiles < RS ? ntiles : RS;   // raw tiles issued so far (thread 0's view)
+    for (; t < ntiles; ++t) {
+        const int row0 = r0 + t * TM;
+        const int rows = min(TM, r1 - row0);
+        const int ab = t & 1;
+        unsigned char* Ah = Abase + (size_t)(2 * ab) * D::AOP;
+        unsigned char* Al = Ah + D::AOP;
+        const bool okr = __all_sync(0xffffffffu, mbar_wait(&bar_raw[t % RS], (unsigned)((t / RS) & 1)));
+        if (!okr && lane == 0) s_fail = 1;
+        // centre the row and split it into the two parts of A buffer t & 1
+        // (that buffer's last reader, the MMA of tile t - 2, completed before
+        // the epilogue of tile t - 2 ran)
+        if (okr) {
+            float c[KP];
+            const float* src = raw + (size_t)(t % RS) * TM * PB + (size_t)tid * PB;
+#pragma unroll
+            for (int q4 = 0; q4 < PB / 4; ++q4) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tid < rows) v = reinterpret_cast<const float4*>(src)[q4];
+                c[4 * q4 + 0] = v.x + s_nu[4 * q4 + 0];
+                c[4 * q4 + 1] = v.y + s_nu[4 * q4 + 1];
+                c[4 * q4 + 2] = v.z + s_nu[4 * q4 + 2];
+                c[4 * q4 + 3] = v.w + s_nu[4 * q4 + 3];
+            }
+#pragma unroll
+            for (int j = PB; j < KP; ++j) c[j] = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < KCH; ++q4) {
+                float4 h, lo;
+                h.x = tf32_hi(c[4 * q4 + 0]); lo.x = c[4 * q4 + 0] - h.x;
+                h.y = tf32_hi(c[4 * q4 + 1]); lo.y = c[4 * q4 + 1] - h.y;
+                h.z = tf32_hi(c[4 * q4 + 2]); lo.z = c[4 * q4 + 2] - h.z;
+                h.w = tf32_hi(c[4 * q4 + 3]); lo.w = c[4 * q4 + 3] - h.w;
+                *reinterpret_cast<float4*>(Ah + kop_off(tid, 4 * q4, KCH)) = h;
+                *reinterpret_cast<float4*>(Al + kop_off(tid, 4 * q4, KCH)) = lo;
+            }
         }
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (s_fail) break;   // uniform
+        if (tid == 0) {
+            // the raw stage of tile t is read: refill it with tile t + RS
+            if (t + RS < ntiles) { issue(t + RS); ++issued; }
+            tc_fence_after();
+            const uint32_t dcol = taddr + (uint32_t)(ab * NC);
+            const uint32_t ah0 = abase + (uint32_t)(2 * ab) * (uint32_t)D::AOP;
+            const uint32_t al0 = ah0 + (uint32_t)D::AOP;
+#pragma unroll
+            for (int ks = 0; ks < KP / 8; ++ks) {
+                const uint32_t o = (uint32_t)ks * 256u;
+                const uint64_t ah = smem_desc(ah0 + o, 128, KCH * 128), al = smem_desc(al0 + o, 128, KCH * 128);
+                const uint64_t bh = smem_desc(boff_h + o, 128, KCH * 128), bl = smem_desc(boff_l + o, 128, KCH * 128);
+                mma_tf32(dcol, ah, bh, idesc, ks > 0);
+                mma_tf32(dcol, al, bh, idesc, true);
+                mma_tf32(dcol, ah, bl, idesc, true);
+            }
+            mma_commit(&bar_mma[ab]);
+        }
+        // the MMA of tile t runs while tile t - 1 is read back
+        if (t >= 1) epilogue(t - 1);
+    }
+    if (!s_fail && ntiles >= 1) epilogue(ntiles - 1);
+    __syncthreads();
+    const int failed = s_fail;
+    if (failed && tid == 0) {
+        // let copies and MMAs still in flight finish before shared memory and
+        // tensor memory are released (each wait bounded)
+        for (int u = t; u < issued; ++u) (void)mbar_wait(&bar_raw[u % RS], (unsigned)((u / RS) & 1));
+        for (int u = (t >= 2 ? t - 2 : 0); u <= t && u < ntiles; ++u)
+            (void)mbar_wait(&bar_mma[u & 1], (unsigned)(u >> 1) & 1u);
+        set_error(st, RTD_EINTERNAL);
     }
     below0 = warp_sum_int(below0);
     below1 = warp_sum_int(below1);
@@ -1255,18 +1283,17 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
     if (w == 0) tmem_dealloc(taddr, D::TCOLS);
     if (failed) return;
     if (tid < 2 && s_on[tid] && s_below[tid]) atomicAdd(&rule[2 * l + tid].below, s_below[tid]);
-    for (int kc = 0; kc < 2; ++kc) {
-        if (!s_on[kc]) continue;
-        unsigned* gh = hist + (size_t)(2 * l + kc) * HIST_BINS;
-        for (int b = tid; b < WIN_BINS; b += NTH) {
-            const unsigned v = sh[kc * WIN_BINS + b];
-            if (v) atomicAdd(gh + b, v);
-        }
-    }
 }
+
+// widths whose double-buffered operands fit a CTA's shared memory
+template <int PB> constexpr bool dist_tc_width() { return PB <= 40; }
 
 template <int PB>
 void dist_tc_t(const Plan& P, cudaStream_t s) {
+    if constexpr (!dist_tc_width<PB>()) {   // 48, 64: the CUDA-core pass
+        dist_win_t<PB>(P, s);
+        return;
+    } else {
     typedef DistTC<PB> D;
     // one resident wave, at least one tile per CTA
     long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
@@ -1278,6 +1305,7 @@ void dist_tc_t(const Plan& P, cudaStream_t s) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::SMEM);
     k<<<grid, D::NTH, D::SMEM, s>>>(P.Xp, P.p, P.m, cpb, P.cs, P.ch, P.rule, (float*)P.dkeys,
                                     (long long)P.q * P.m, P.cand, P.hist, P.st, P.blk_active);
+    }
 }
 
 // =====================================================================
@@ -1892,6 +1920,114 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
         nflag = cta_sum_int(nflag);
         if (threadIdx.x == 0 && nflag) atomicAdd(count, (unsigned long long)nflag);
     }
+}
+
+// =====================================================================
+// Scoring of new rows in one pass (Section 6; step 10 of Section 4 against
+// a given fit): d2 (optional), the flag d2 > cutoff (optional) and the
+// count.  FP32 rows; a row whose FP32 d2 lies within the FP64 band of the
+// cutoff is queued per warp and recomputed in FP64 once the warp holds 32
+// of them (one row per lane), so no CTA-wide barrier sits in the loop.
+// Each thread keeps SR rows in flight.
+// =====================================================================
+template <int PB> struct ScoreRows { static constexpr int R = PB <= 8 ? 4 : (PB <= 24 ? 2 : 1); };
+
+template <int PB>
+__global__ void __launch_bounds__(NT) k_score(const float* __restrict__ X, long long n, int p, long long ld,
+                                              int vec4, const RowParams* __restrict__ rp, double cut,
+                                              float* __restrict__ d2_out, uint8_t* __restrict__ flags,
+                                              unsigned long long* __restrict__ count) {
+    constexpr int R = ScoreRows<PB>::R;
+    constexpr int QCAP = 32 * (R + 1);
+    __shared__ float sM[PB * PB];
+    __shared__ float s_hi[PB], s_lo[PB];
+    __shared__ long long s_q[NT / 32][QCAP];
+    for (int e = threadIdx.x; e < PB * PB; e += NT) {
+        const int i = e / PB, j = e % PB;
+        sM[e] = (i < p && j <= i) ? rp->Mf[i * PMAX + j] : 0.f;
+    }
+    for (int j = threadIdx.x; j < PB; j += NT) {
+        s_hi[j] = (j < p) ? rp->mu_hi[j] : 0.f;
+        s_lo[j] = (j < p) ? rp->mu_lo[j] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float cut_lo = (float)(cut * (1.0 - BAND_EPS)), cut_hi = (float)(cut * (1.0 + BAND_EPS));
+    const bool decide = flags != nullptr;
+    long long* q = s_q[w];
+    int qn = 0;       // warp-uniform
+    int nflag = 0;
+    auto drain = [&](int k) {   // FP64 for the first k queued rows, one per lane
+        if (lane < k) {
+            const long long i = q[lane];
+            const double d = d2_fp64(X + i * ld, *rp, p);
+            const bool out = d > cut;
+            if (d2_out) d2_out[i] = (float)d;
+            flags[i] = out ? 1 : 0;
+            nflag += out ? 1 : 0;
+        }
+        __syncwarp();
+        for (int e = lane; e + k < qn; e += 32) q[e] = q[e + k];
+        __syncwarp();
+        qn -= k;
+    };
+    const long long stride = (long long)gridDim.x * NT * R;
+    for (long long tb = (long long)blockIdx.x * NT * R; tb < n; tb += stride) {
+        float xs[R][PB];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long i = tb + (long long)r * NT + threadIdx.x;
+            if (i < n) load_row_user<PB>(X + i * ld, p, vec4 != 0, xs[r]);
+            else {
+#pragma unroll
+                for (int j = 0; j < PB; ++j) xs[r][j] = 0.f;
+            }
+        }
+        float c[R][PB];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < PB; ++j) c[r][j] = (xs[r][j] - s_hi[j]) - s_lo[j];
+        float d2[R];
+        tri_d2<PB, float, R>(sM, p, c, d2);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long i = tb + (long long)r * NT + threadIdx.x;
+            const bool valid = i < n;
+            const bool band = valid && decide && d2[r] >= cut_lo && d2[r] <= cut_hi;
+            if (valid && !band) {
+                const bool out = (double)d2[r] > cut;
+                if (d2_out) d2_out[i] = d2[r];
+                if (decide) {
+                    flags[i] = out ? 1 : 0;
+                    nflag += out ? 1 : 0;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, band);
+            if (band) q[qn + __popc(bal & ((1u << lane) - 1u))] = i;
+            qn += __popc(bal);
+        }
+        __syncwarp();
+        if (qn >= 32) drain(32);
+    }
+    __syncwarp();
+    if (qn > 0) drain(qn);
+    if (count && decide) {
+        nflag = warp_sum_int(nflag);
+        if (lane == 0 && nflag) atomicAdd(count, (unsigned long long)nflag);
+    }
+}
+
+template <int PB>
+void score_t(const float* X, long long n, int p, long long ld, const RowParams* rp, double cut, float* d2,
+             uint8_t* fl, unsigned long long* cnt, int nsm, cudaStream_t s) {
+    const int vec4 = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    constexpr int R = ScoreRows<PB>::R;
+    const long long tiles = (n + (long long)NT * R - 1) / ((long long)NT * R);
+    const long long cap = (long long)nsm * 8;   // a resident wave of 256-thread CTAs
+    int grid = (int)(tiles < cap ? tiles : cap);
+    if (grid < 1) grid = 1;
+    k_score<PB><<<grid, NT, 0, s>>>(X, n, p, ld, vec4, rp, cut, d2, fl, cnt);
 }
 
 template <int PB, typename T>

@@ -1099,6 +1099,38 @@ __global__ void __launch_bounds__(CT) k_score_prep(const double* __restrict__ mu
     if (ok && logdet_out && threadIdx.x == 0) *logdet_out = s_ld;
 }
 
+// The same from a fit passed by value; also zeroes the status word first.
+__global__ void __launch_bounds__(CT) k_score_prep_arg(const __grid_constant__ FitArg a, int p, double cut,
+                                                       RowParams* rp, Status* st, double* cut_out) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Li = sm + MAT;
+    __shared__ double one[PMAX], zero[PMAX], mu[PMAX], Sp[PMAX * PMAX];
+    __shared__ double s_ld;
+    if (threadIdx.x == 0) {
+        st->code = 0;
+        st->n_flagged = 0ull;
+        *cut_out = cut;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) { one[j] = 1.0; zero[j] = 0.0; mu[j] = a.mu[j]; }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e % p;
+        const int hi = i > j ? i : j, lo = i > j ? j : i;
+        Sp[i * PMAX + j] = a.tri[hi * (hi + 1) / 2 + lo];
+    }
+    __syncthreads();
+    const bool ok = make_rowparams(mu, Sp, zero, one, p, A, Li, *rp, &s_ld);
+    if (!ok && threadIdx.x == 0) set_error(st, RTD_EDEGENERATE);
+}
+
+void launch_score_prep_arg(const FitArg& a, int p, double cut, RowParams* rp, Status* st, double* cut_out,
+                           cudaStream_t s) {
+    size_t sm = 2 * MAT * sizeof(double);
+    auto k = k_score_prep_arg;
+    big_smem(k, sm);
+    k<<<1, CT, sm, s>>>(a, p, cut, rp, st, cut_out);
+}
+
 void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* rp, Status* st, cudaStream_t s,
                        double* logdet_out) {
     size_t sm = 2 * MAT * sizeof(double);

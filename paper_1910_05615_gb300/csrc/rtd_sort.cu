@@ -1643,7 +1643,6 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
     double* sM = sm64;              // PB x PB
     double* smu = sm64 + PB * PB;   // PB
     __shared__ unsigned wt[SF_T / 32];
-    __shared__ int s_pos[SF_T];
     __shared__ int s_n, s_bin, s_last, s_base, s_nlo;
     const int c = blockIdx.x;
     if (!ch[c].active) return;
@@ -1690,9 +1689,13 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
         // rows of the FP64 range outside the window were not listed
         if (kb_lo < (unsigned long long)R.w_lo || kb_hi > (unsigned long long)R.w_hi) miss = true;
     }
-    // 2. this CTA's share of the candidates
+    // 2. this CTA's share of the candidates: the in-range rows are listed
+    //    first (positions in buf), then their FP64 distances are taken in one
+    //    pass, one row per thread, so the FP64 latency is paid once
     if (!miss) {
         stage_m64<PB>(ch[c].rp, p, sM, smu);
+        constexpr int LCAP = (int)(SEL_SMALL * sizeof(Cand) / sizeof(int));
+        int* lst = reinterpret_cast<int*>(buf);
         const int chunk = (C + SF_CTAS - 1) / SF_CTAS;
         const int i0 = (int)blockIdx.y * chunk;
         const int i1 = min(C, i0 + chunk);
@@ -1700,34 +1703,39 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
         Cand* list = band_all + (size_t)c * m;
         const float* Xb = Xp + (size_t)l * m * PB;
         int nlo = 0;
-        for (int base = i0; base < i1; base += SF_T) {
+        // windows of at most LCAP candidates, so the list cannot overflow
+        for (int w0 = i0; w0 < i1; w0 += LCAP) {
+            const int w1 = min(i1, w0 + LCAP);
             if (tid == 0) s_n = 0;
             __syncthreads();
-            const int i = base + tid;
-            bool take = false;
-            unsigned pos = 0;
-            if (i < i1) {
-                const Cand e = cand[i];
-                if (e.key < kb_lo) ++nlo;
-                else if (e.key <= kb_hi) { take = true; pos = e.pos; }
+            for (int base = w0; base < w1; base += SF_T) {
+                const int i = base + tid;
+                bool take = false;
+                unsigned pos = 0;
+                if (i < w1) {
+                    const Cand e = cand[i];
+                    if (e.key < kb_lo) ++nlo;
+                    else if (e.key <= kb_hi) { take = true; pos = e.pos; }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                int wb = 0;
+                if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
+                wb = __shfl_sync(0xffffffffu, wb, 0);
+                if (take) lst[wb + __popc(bal & ((1u << lane) - 1u))] = (int)pos;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            int wb = 0;
-            if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
-            wb = __shfl_sync(0xffffffffu, wb, 0);
-            if (take) s_pos[wb + __popc(bal & ((1u << lane) - 1u))] = (int)pos;
             __syncthreads();
-            const int nr = s_n;
-            if (tid == 0 && nr) s_base = atomicAdd(&R.band, nr);
+            const int nl = s_n;
+            if (tid == 0 && nl) s_base = atomicAdd(&R.band, nl);
             __syncthreads();
-            if (tid < nr) {   // full warps of rows: the FP64 pipe charges per warp instruction
-                const unsigned ps = (unsigned)s_pos[tid];
+            for (int j = tid; j < nl; j += SF_T) {
+                const unsigned ps = (unsigned)lst[j];
                 Cand e;
                 e.key = (unsigned long long)__double_as_longlong(row_d2_fp64<PB>(Xb + (size_t)ps * PB, sM, smu));
                 e.pos = ps;
                 e.pad = 0;
-                list[s_base + tid] = e;
+                list[s_base + j] = e;
             }
+            __syncthreads();   // lst and s_n are reused by the next window
         }
         nlo = warp_sum_int(nlo);
         if (lane == 0 && nlo) atomicAdd(&s_nlo, nlo);
@@ -1783,6 +1791,8 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
 void launch_select_fast(const Plan& P, cudaStream_t s) {
     RTD_PB_SWITCH(P.pb, {
         const size_t sm = (size_t)(PB * PB + PB) * sizeof(double);
+        // static buffers plus M pass 48 KB at the larger widths: opt in
+        cudaFuncSetAttribute(k_select_fast<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_select_fast<PB><<<dim3(2 * P.q, SF_CTAS), SF_T, sm, s>>>(P.ch, P.rule, P.Xp, (const float*)P.dkeys,
                                                                    (long long)P.q * P.m, P.cand, P.band, P.hist,
                                                                    P.memb, P.m, P.p, P.hb, P.st);

@@ -67,6 +67,56 @@ def test_flag_bit_exact(rtd):
     assert np.array_equal(fl2.astype(bool), ref) and cnt2 == cnt
 
 
+@pytest.mark.parametrize("p", [1, 4, 20, 37, 64])
+@pytest.mark.parametrize("host", [False, True])
+def test_score_one_pass(rtd, p, host):
+    """Distances, flags and count in one pass (Section 6): the flags equal
+    those of the FP64 distances (rows within 2^-9 of the cutoff are decided
+    in FP64), the distances match the plain definition, and outside the band
+    the FP32 distances are those of rtdetmcd_distances bit for bit."""
+    rng = np.random.default_rng(100 + p)
+    n = 200_003 + 13 * p
+    X = (rng.standard_normal((n, p)) * 1.3 + 0.4).astype(np.float32)
+    X[: n // 20] += 4.0
+    mu = rng.standard_normal(p) * 0.1
+    S = _spd(p, rng, cond=30.0)
+    cut = O.chi2_ppf(0.975, p)
+    ref = O.mahalanobis_d2_plain(X, mu, S)
+    src = X if host else torch.from_numpy(X).cuda()
+    for prec, tol in ((rtd.RTD_FP32, 2e-4), (rtd.RTD_FP64, 1e-6)):
+        d2, fl, cnt = rtd.rtdetmcd_score(src, mu, S, cut, precision=prec)
+        d2, fl = to_np(d2), to_np(fl).astype(bool)
+        assert np.max(np.abs(d2 - ref) / np.maximum(ref, 1e-3)) < tol
+        decided = np.abs(ref - cut) > 1e-12 * cut
+        assert np.array_equal(fl[decided], (ref > cut)[decided]) and cnt == int(fl.sum())
+        if prec == rtd.RTD_FP32:
+            d2b = to_np(rtd.rtdetmcd_distances(src, mu, S, precision=prec))
+            outside = np.abs(d2b.astype(np.float64) - cut) > 2.0 ** -8 * cut
+            assert np.array_equal(d2[outside], d2b[outside])
+    # flags only, distances only
+    _, fl2, cnt2 = rtd.rtdetmcd_score(src, mu, S, cut, d2=False)
+    assert cnt2 == cnt and np.array_equal(to_np(fl2).astype(bool), fl)
+    d3, fl3, cnt3 = rtd.rtdetmcd_score(src, mu, S, cut, flags=False)
+    assert fl3 is None and cnt3 == -1
+
+
+def test_score_strided_and_rejects(rtd):
+    rng = np.random.default_rng(5)
+    n, p, ld = 40_001, 6, 11
+    buf = rng.standard_normal((n, ld)).astype(np.float32)
+    X = torch.from_numpy(buf).cuda()[:, :p]
+    S = _spd(p, rng)
+    d2, fl, cnt = rtd.rtdetmcd_score(X, np.zeros(p), S, 12.0)
+    ref = O.mahalanobis_d2_plain(buf[:, :p], np.zeros(p), S)
+    assert np.max(np.abs(to_np(d2) - ref) / np.maximum(ref, 1e-3)) < 2e-4
+    assert cnt == int(np.sum(ref > 12.0))
+    bad = S.copy()
+    bad[0, 0] = -1.0
+    with pytest.raises(rtd.RtdError) as e:
+        rtd.rtdetmcd_score(X, np.zeros(p), bad, 12.0)
+    assert e.value.code == 4
+
+
 # ------------------------------------------------------------- whole fits
 def _fit_both(rtd, fr, form, host=False, **kw):
     X = fr.X if host else torch.from_numpy(fr.X).cuda()
