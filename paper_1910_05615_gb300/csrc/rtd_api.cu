@@ -43,7 +43,7 @@ struct Shape {
 
 struct Regions {
     Region st, cs, ch, rule, fitrp, res, xstage, d2stage, flagstage, substage, diagstage,
-        Xp, perm, arenaA, arenaB, sort_hist, uni, uscratch, gss, dkeys, memb, cand, band, hist, swaps,
+        Xp, perm, arenaA, arenaB, sort_hist, uni, uscratch, gss, dkeys, memb, cand, segcnt, band, hist, swaps,
         blk, partial, gsum, wset, chosen, amb, kept, kl, scratch;
 };
 
@@ -152,6 +152,7 @@ size_t layout(const Shape& S, Regions& R) {
     R.dkeys = L.add(2 * qm * K);
     R.memb = L.add(2 * qm);
     R.cand = L.add(2 * qm * sizeof(Cand));
+    R.segcnt = L.add(2 * q * SEG_MAX * sizeof(int));
     R.band = L.add(2 * qm * sizeof(Cand));
     R.hist = L.add(2 * q * HIST_BINS * sizeof(unsigned));
     R.swaps = L.add(2 * q * sizeof(int));
@@ -294,6 +295,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     P.dkeys = at<void>(ws, R.dkeys);
     P.memb = at<uint8_t>(ws, R.memb);
     P.cand = at<Cand>(ws, R.cand);
+    P.segcnt = at<int>(ws, R.segcnt);
     P.band = at<Cand>(ws, R.band);
     P.hist = at<unsigned>(ws, R.hist);
     P.swaps = at<int>(ws, R.swaps);

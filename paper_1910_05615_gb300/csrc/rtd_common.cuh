@@ -110,11 +110,16 @@ struct SelRule {
     int bandsel;                    // histogram path: band listed, FP64 ranking pending
     int band_off;                   // offset of the band list in the chain's band buffer
     int done;                       // CTAs of the one-launch window selection finished
+    int nseg;                       // window candidates: segments (CTAs per block of the distance pass)
     // counters over the whole fit (profiling)
     int acc_win, acc_miss;
     long long acc_cand, acc_band;
 };
 constexpr int WIN_BINS = 1024;      // bins of the window histogram
+// Window candidates are listed per CTA of the distance pass: CTA b of a
+// block writes its candidates from its own first row's offset on (it cannot
+// have more candidates than rows) and its count to segcnt[chain][b].
+constexpr int SEG_MAX = 1024;       // CTAs per block of a distance pass, at most
 
 struct Cand {
     unsigned long long key;

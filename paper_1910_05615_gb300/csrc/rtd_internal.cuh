@@ -48,6 +48,7 @@ struct Plan {
     void* dkeys;            // C-step distance keys [2][q*m]
     uint8_t* memb;          // [2q][m] membership bytes
     Cand* cand;             // [2q][m]
+    int* segcnt;            // [2q][SEG_MAX] window candidates per distance CTA
     Cand* band;             // [2q][m]
     unsigned* hist;         // [2q][HIST_BINS]
     int* swaps;             // [2q]
@@ -93,7 +94,6 @@ size_t unimcd_scratch_doubles(int nseg, long long L);
 void launch_gsscm(const Plan& P, const void* rkeys, cudaStream_t s);
 void launch_select_bucket(const Plan& P, cudaStream_t s);
 void launch_select_finish(const Plan& P, cudaStream_t s);
-void launch_select_win(const Plan& P, cudaStream_t s);
 void launch_select_band(const Plan& P, cudaStream_t s);
 void launch_select_fast(const Plan& P, cudaStream_t s);
 

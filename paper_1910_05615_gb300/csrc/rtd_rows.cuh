@@ -810,7 +810,8 @@ template <int PB>
 __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
     k_dist_win(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
                const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys,
-               long long qm, Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st, int* blk) {
+               long long qm, Cand* __restrict__ cand, int* __restrict__ segcnt, unsigned* __restrict__ hist,
+               Status* st, int* blk) {
     typedef DistWin<PB> D;
     clear_step_counters(st, blk);
     constexpr int R = D::R, PH = D::PH, NTW = D::NTW, NW = D::NW, WT = D::WT;
@@ -821,12 +822,13 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
     __shared__ float2 s_nu[PH];
     __shared__ float s_b[2][PB];
     __shared__ unsigned s_wlo[2], s_whi[2];
-    __shared__ int s_wsh[2], s_on[2], s_below[2], s_fail;
+    __shared__ int s_wsh[2], s_on[2], s_below[2], s_ncand[2], s_fail;
     const int l = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int r0, r1;
     block_rows(m, cpb, r0, r1);
     const int ntiles = (r1 - r0 + WT - 1) / WT;      // warp tiles of the CTA
+    const int seg0 = r0 - l * m;                     // this CTA's candidate segment
     if (threadIdx.x < 2) {
         const int c = 2 * l + threadIdx.x;
         s_on[threadIdx.x] = ch[c].active && rule[c].win;
@@ -834,6 +836,7 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
         s_whi[threadIdx.x] = rule[c].w_hi;
         s_wsh[threadIdx.x] = rule[c].w_sh;
         s_below[threadIdx.x] = 0;
+        s_ncand[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) s_fail = 0;
     if (lane == 0) {
@@ -934,17 +937,14 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
                 if (bal) {
                     const int lead = __ffs(bal) - 1;
                     int b0 = 0;
-                    if (lane == lead) b0 = atomicAdd(&rule[cidx].cand, __popc(bal));
+                    if (lane == lead) b0 = atomicAdd(&s_ncand[kc], __popc(bal));
                     b0 = __shfl_sync(0xffffffffu, b0, lead);
                     if (cnd) {
-                        const int idx = b0 + __popc(bal & ((1u << lane) - 1u));
-                        if (idx < m) {
-                            Cand e;
-                            e.key = key;
-                            e.pos = (unsigned)(row - l * m);
-                            e.pad = 0;
-                            cand[(size_t)cidx * m + idx] = e;
-                        }
+                        Cand e;
+                        e.key = key;
+                        e.pos = (unsigned)(row - l * m);
+                        e.pad = 0;
+                        cand[(size_t)cidx * m + seg0 + b0 + __popc(bal & ((1u << lane) - 1u))] = e;
                     }
                 }
             }
@@ -969,8 +969,13 @@ __global__ void __launch_bounds__(DistWin<PB>::NTW, DistWin<PB>::CTAS_PER_SM)
         if (threadIdx.x == 0) set_error(st, RTD_EINTERNAL);
         return;
     }
-    if (threadIdx.x < 2 && s_on[threadIdx.x] && s_below[threadIdx.x])
-        atomicAdd(&rule[2 * l + threadIdx.x].below, s_below[threadIdx.x]);
+    if (threadIdx.x < 2 && s_on[threadIdx.x]) {
+        const int c = 2 * l + threadIdx.x;
+        if (s_below[threadIdx.x]) atomicAdd(&rule[c].below, s_below[threadIdx.x]);
+        segcnt[(size_t)c * SEG_MAX + blockIdx.x] = s_ncand[threadIdx.x];
+        if (s_ncand[threadIdx.x]) atomicAdd(&rule[c].cand, s_ncand[threadIdx.x]);
+        if (blockIdx.x == 0) rule[c].nseg = gridDim.x;
+    }
     for (int kc = 0; kc < 2; ++kc) {
         if (!s_on[kc]) continue;
         unsigned* gh = hist + (size_t)(2 * l + kc) * HIST_BINS;
@@ -988,12 +993,13 @@ void dist_win_t(const Plan& P, cudaStream_t s) {
     long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
     const long long lim = ((long long)P.m + 255) / 256;
     if (cw > lim) cw = lim;
+    if (cw > SEG_MAX) cw = SEG_MAX;
     const int cpb = (int)(cw > 0 ? cw : 1);
     dim3 grid(cpb, P.q);
     auto k = k_dist_win<PB>;
     set_smem(k, D::SMEM);
     k<<<grid, D::NTW, D::SMEM, s>>>(P.Xp, P.p, P.m, cpb, P.cs, P.ch, P.rule, (float*)P.dkeys,
-                                    (long long)P.q * P.m, P.cand, P.hist, P.st, P.blk_active);
+                                    (long long)P.q * P.m, P.cand, P.segcnt, P.hist, P.st, P.blk_active);
 }
 
 // =====================================================================
@@ -1056,7 +1062,8 @@ template <int PB>
 __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
     k_dist_tc(const float* __restrict__ Xp, int p, int m, int cpb, const Consts* __restrict__ cs,
               const Chain* __restrict__ ch, SelRule* __restrict__ rule, float* __restrict__ dkeys, long long qm,
-              Cand* __restrict__ cand, unsigned* __restrict__ hist, Status* st, int* blk) {
+              Cand* __restrict__ cand, int* __restrict__ segcnt, unsigned* __restrict__ hist, Status* st,
+              int* blk) {
     typedef DistTC<PB> D;
     constexpr int KP = D::KP, KCH = D::KCH, NC = D::NC, TM = D::TM, NTH = D::NTH, RS = D::RS;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1070,13 +1077,14 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
     __shared__ float s_nu[PB];
     __shared__ float s_b[2][KP];
     __shared__ unsigned s_wlo[2], s_whi[2];
-    __shared__ int s_wsh[2], s_on[2], s_below[2], s_fail;
+    __shared__ int s_wsh[2], s_on[2], s_below[2], s_ncand[2], s_fail;
     const int l = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     clear_step_counters(st, blk);
     int r0, r1;
     block_rows(m, cpb, r0, r1);
     const int ntiles = (r1 - r0 + TM - 1) / TM;
+    const int seg0 = r0 - l * m;                     // this CTA's candidate segment
     if (tid < 2) {
         const int c = 2 * l + tid;
         s_on[tid] = ch[c].active && rule[c].win;
@@ -1084,6 +1092,11 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
         s_whi[tid] = rule[c].w_hi;
         s_wsh[tid] = rule[c].w_sh;
         s_below[tid] = 0;
+        s_ncand[tid] = 0;
+        if (s_on[tid]) {
+            if (ntiles == 0) segcnt[(size_t)c * SEG_MAX + blockIdx.x] = 0;
+            if (blockIdx.x == 0) rule[c].nseg = gridDim.x;
+        }
     }
     if (tid == 0) {
         for (int i = 0; i < RS; ++i) mbar_init(&bar_raw[i], 1);
@@ -1181,17 +1194,14 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
             if (bal) {
                 const int lead = __ffs(bal) - 1;
                 int b0 = 0;
-                if (lane == lead) b0 = atomicAdd(&rule[cidx].cand, __popc(bal));
+                if (lane == lead) b0 = atomicAdd(&s_ncand[kc], __popc(bal));
                 b0 = __shfl_sync(0xffffffffu, b0, lead);
                 if (cnd) {
-                    const int idx = b0 + __popc(bal & ((1u << lane) - 1u));
-                    if (idx < m) {
-                        Cand e;
-                        e.key = key;
-                        e.pos = (unsigned)(row - l * m);
-                        e.pad = 0;
-                        cand[(size_t)cidx * m + idx] = e;
-                    }
+                    Cand e;
+                    e.key = key;
+                    e.pos = (unsigned)(row - l * m);
+                    e.pad = 0;
+                    cand[(size_t)cidx * m + seg0 + b0 + __popc(bal & ((1u << lane) - 1u))] = e;
                 }
             }
         }
@@ -1282,7 +1292,12 @@ __global__ void __launch_bounds__(DistTC<PB>::NTH, DistTC<PB>::CTAS_PER_SM)
     tc_fence_after();
     if (w == 0) tmem_dealloc(taddr, D::TCOLS);
     if (failed) return;
-    if (tid < 2 && s_on[tid] && s_below[tid]) atomicAdd(&rule[2 * l + tid].below, s_below[tid]);
+    if (tid < 2 && s_on[tid]) {
+        const int c = 2 * l + tid;
+        if (s_below[tid]) atomicAdd(&rule[c].below, s_below[tid]);
+        segcnt[(size_t)c * SEG_MAX + blockIdx.x] = s_ncand[tid];
+        if (s_ncand[tid]) atomicAdd(&rule[c].cand, s_ncand[tid]);
+    }
 }
 
 // widths whose double-buffered operands fit a CTA's shared memory
@@ -1299,12 +1314,13 @@ void dist_tc_t(const Plan& P, cudaStream_t s) {
     long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
     const long long lim = ((long long)P.m + D::TM - 1) / D::TM;
     if (cw > lim) cw = lim;
+    if (cw > SEG_MAX) cw = SEG_MAX;
     const int cpb = (int)(cw > 0 ? cw : 1);
     dim3 grid(cpb, P.q);
     auto k = k_dist_tc<PB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::SMEM);
     k<<<grid, D::NTH, D::SMEM, s>>>(P.Xp, P.p, P.m, cpb, P.cs, P.ch, P.rule, (float*)P.dkeys,
-                                    (long long)P.q * P.m, P.cand, P.hist, P.st, P.blk_active);
+                                    (long long)P.q * P.m, P.cand, P.segcnt, P.hist, P.st, P.blk_active);
     }
 }
 

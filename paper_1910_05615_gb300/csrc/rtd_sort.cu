@@ -1314,165 +1314,6 @@ void launch_select_finish(const Plan& P, cudaStream_t s) {
                                               P.precision == RTD_FP32, P.st);
 }
 
-// =====================================================================
-// Window path of the FP32 form (from the second C-step on).  The distance
-// pass has counted the rows below the window, listed the rows inside it and
-// binned them in WIN_BINS bins.  The bin of rank h_b gives a key range that
-// holds the threshold t; the candidates within the FP64 band of that range
-// (a few hundred rows) are the only ones the selection has to order.  The
-// rule is the histogram path's: rows below [t (1 - eps), t (1 + eps)] are
-// in, band rows are ranked by their FP64 distance (ties to the lower
-// position).  The band list goes to the upper half of the chain's band
-// buffer (the lower half holds the rows of the bin's range).  A chain whose
-// rank or band falls outside the window is marked need_hist and left to the
-// histogram path.
-// =====================================================================
-__device__ void select_win_body(SelRule& R, Cand* cand, Cand* band_all_c, unsigned* h, int m, int hb,
-                                Cand* buf, unsigned* cnt, Status* st);
-
-__global__ void __launch_bounds__(SEL_T) k_select_win(const Chain* __restrict__ ch, SelRule* __restrict__ rule,
-                                                       Cand* __restrict__ cand_all, Cand* __restrict__ band_all,
-                                                       unsigned* __restrict__ hist, const float* __restrict__ dkeys,
-                                                       long long qm, int m, int hb, Status* st) {
-    static_assert(WIN_BINS == SEL_T, "one window bin per thread");
-    __shared__ Cand buf[SEL_SMALL];
-    static_assert(SEL_SMALL * sizeof(Cand) >= HIST_BINS * sizeof(unsigned), "histogram aliases buf");
-    // the bin counts are dead before the ranking reuses buf
-    unsigned* cnt = reinterpret_cast<unsigned*>(buf);
-    const int c = blockIdx.x;
-    if (!ch[c].active) return;
-    SelRule& R = rule[c];
-    if (!R.win) return;
-    select_win_body(R, cand_all + (size_t)c * m, band_all + (size_t)c * m, hist + (size_t)c * HIST_BINS, m, hb,
-                    buf, cnt, st);
-    __syncthreads();
-    if (R.need_hist) {   // the window missed: the histogram path, in this CTA
-        const int l = c / 2, k = c % 2;
-        cta_hist_path(R, dkeys + (size_t)k * qm + (size_t)l * m, m, hb, cand_all + (size_t)c * m,
-                      band_all + (size_t)c * m, buf, cnt, st);
-    }
-}
-
-__device__ void select_win_body(SelRule& R, Cand* cand_w, Cand* band_all_c, unsigned* h, int m, int hb,
-                                Cand* buf, unsigned* cnt, Status* st) {
-    __shared__ int s_bin, s_ns, s_nslo, s_nb, s_nlo;
-    const int lane = threadIdx.x & 31;
-    // window histogram: inclusive scan, bins reset for the next use
-    const unsigned own = h[threadIdx.x];
-    h[threadIdx.x] = 0u;
-    cnt[threadIdx.x] = own;
-    if (threadIdx.x == 0) { s_bin = -1; s_ns = 0; s_nslo = 0; s_nb = 0; s_nlo = 0; }
-    __syncthreads();
-    for (int o = 1; o < WIN_BINS; o <<= 1) {
-        unsigned v = threadIdx.x >= o ? cnt[threadIdx.x - o] : 0u;
-        __syncthreads();
-        cnt[threadIdx.x] += v;
-        __syncthreads();
-    }
-    const int C = R.cand < m ? R.cand : m;
-    const int r = hb - R.below;
-    if (threadIdx.x == 0) { R.acc_win += 1; R.acc_cand += C; }
-    if (r < 1 || r > C) {
-        if (threadIdx.x == 0) R.need_hist = 1;
-        return;
-    }
-    {
-        const unsigned incl = cnt[threadIdx.x], excl = incl - own;
-        if (excl < (unsigned)r && (unsigned)r <= incl) s_bin = threadIdx.x;
-    }
-    __syncthreads();
-    const int b = s_bin;
-    if (b < 0) {   // the counts disagree with the list: take the histogram path
-        if (threadIdx.x == 0) R.need_hist = 1;
-        return;
-    }
-    // key range of bin b and its FP64 band
-    const unsigned lo_key = R.w_lo + ((unsigned)b << R.w_sh);
-    unsigned hi_key = lo_key + ((1u << R.w_sh) - 1u);
-    if (hi_key > R.w_hi || hi_key < lo_key) hi_key = R.w_hi;
-    const unsigned long long kb_lo = __float_as_uint(__uint_as_float(lo_key) * (float)(1.0 - BAND_EPS));
-    const unsigned long long kb_hi = __float_as_uint(__uint_as_float(hi_key) * (float)(1.0 + BAND_EPS));
-    // candidates inside [kb_lo, kb_hi] -> lower half of the band buffer
-    const Cand* cand = cand_w;
-    Cand* sub = band_all_c;
-    const int cap = m / 2;
-    int nlo = 0;
-    constexpr int CU = 4;   // candidates per thread and round, loaded before they are used
-    for (int base = 0; base < C; base += CU * blockDim.x) {
-        Cand e[CU];
-#pragma unroll
-        for (int u = 0; u < CU; ++u) {
-            const int i = base + u * blockDim.x + threadIdx.x;
-            if (i < C) e[u] = cand[i];
-        }
-#pragma unroll
-        for (int u = 0; u < CU; ++u) {
-            const int i = base + u * blockDim.x + threadIdx.x;
-            bool in = false;
-            if (i < C) {
-                if (e[u].key < kb_lo) ++nlo;
-                else in = e[u].key <= kb_hi;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, in);
-            int wb = 0;
-            if (lane == 0 && bal) wb = atomicAdd(&s_ns, __popc(bal));
-            wb = __shfl_sync(0xffffffffu, wb, 0);
-            if (in) {
-                const int idx = wb + __popc(bal & ((1u << lane) - 1u));
-                if (idx < cap) sub[idx] = e[u];
-            }
-        }
-    }
-    nlo = warp_sum_int(nlo);
-    if (lane == 0 && nlo) atomicAdd(&s_nslo, nlo);
-    __syncthreads();
-    const int ns = s_ns, r1 = r - s_nslo;
-    if (ns > cap || r1 < 1 || r1 > ns) {
-        if (threadIdx.x == 0) R.need_hist = 1;
-        return;
-    }
-    Cand t = cta_select_rank(sub, ns, r1, 32, buf, st);
-    if (t.pad) return;
-    const float tf = __uint_as_float((unsigned)t.key);
-    const unsigned long long t_lo = __float_as_uint(tf * (float)(1.0 - BAND_EPS));
-    const unsigned long long t_hi = __float_as_uint(tf * (float)(1.0 + BAND_EPS));
-    if (t_lo < (unsigned long long)R.w_lo || t_hi > (unsigned long long)R.w_hi) {
-        if (threadIdx.x == 0) R.need_hist = 1;
-        return;
-    }
-    // band rows -> upper half; rows of the range below the band
-    Cand* band = band_all_c + cap;
-    int blo = 0;
-    for (int base = 0; base < ns; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        bool inb = false;
-        Cand e;
-        if (i < ns) {
-            e = sub[i];
-            if (e.key < t_lo) ++blo;
-            else inb = e.key <= t_hi;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, inb);
-        int wb = 0;
-        if (lane == 0 && bal) wb = atomicAdd(&s_nb, __popc(bal));
-        wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (inb) band[wb + __popc(bal & ((1u << lane) - 1u))] = e;
-    }
-    blo = warp_sum_int(blo);
-    if (lane == 0 && blo) atomicAdd(&s_nlo, blo);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        R.t_lo = t_lo;
-        R.t_hi = t_hi;
-        R.band = s_nb;
-        R.nlo = R.below + s_nslo + s_nlo;
-        R.band_off = cap;
-        R.t_prev2 = R.t_prev;
-        R.t_prev = tf;
-        R.fast = 1;
-    }
-}
-
 // Band ranking of the FP32 form (both paths): the band rows whose FP64
 // (d2, position) is at most that of rank h_b - (rows below the band) get the
 // decision bit (bit 1) the membership pass reads.
@@ -1634,8 +1475,8 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
                                                       const float* __restrict__ Xp, const float* __restrict__ dkeys,
                                                       long long qm, Cand* __restrict__ cand_all,
                                                       Cand* __restrict__ band_all, unsigned* __restrict__ hist,
-                                                      uint8_t* __restrict__ memb_all, int m, int p, int hb,
-                                                      Status* st) {
+                                                      uint8_t* __restrict__ memb_all, const int* __restrict__ segcnt,
+                                                      int m, int p, int hb, Status* st) {
     static_assert(WIN_BINS % SF_T == 0, "window bins per thread");
     static_assert(SEL_SMALL * sizeof(Cand) >= HIST_BINS * sizeof(unsigned), "histogram aliases buf");
     __shared__ Cand buf[SEL_SMALL];
@@ -1696,34 +1537,16 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
         stage_m64<PB>(ch[c].rp, p, sM, smu);
         constexpr int LCAP = (int)(SEL_SMALL * sizeof(Cand) / sizeof(int));
         int* lst = reinterpret_cast<int*>(buf);
-        const int chunk = (C + SF_CTAS - 1) / SF_CTAS;
-        const int i0 = (int)blockIdx.y * chunk;
-        const int i1 = min(C, i0 + chunk);
         const Cand* cand = cand_all + (size_t)c * m;
         Cand* list = band_all + (size_t)c * m;
         const float* Xb = Xp + (size_t)l * m * PB;
+        // the candidates sit in segments, one per CTA of the distance pass
+        // (segment b from the first row of that CTA's range on)
+        const int nseg = R.nseg;
+        const int segw = nseg > 0 ? (m + nseg - 1) / nseg : m;
         int nlo = 0;
-        // windows of at most LCAP candidates, so the list cannot overflow
-        for (int w0 = i0; w0 < i1; w0 += LCAP) {
-            const int w1 = min(i1, w0 + LCAP);
-            if (tid == 0) s_n = 0;
-            __syncthreads();
-            for (int base = w0; base < w1; base += SF_T) {
-                const int i = base + tid;
-                bool take = false;
-                unsigned pos = 0;
-                if (i < w1) {
-                    const Cand e = cand[i];
-                    if (e.key < kb_lo) ++nlo;
-                    else if (e.key <= kb_hi) { take = true; pos = e.pos; }
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, take);
-                int wb = 0;
-                if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
-                wb = __shfl_sync(0xffffffffu, wb, 0);
-                if (take) lst[wb + __popc(bal & ((1u << lane) - 1u))] = (int)pos;
-            }
-            __syncthreads();
+        // FP64 distances of the listed rows, one per thread, appended to the chain's list
+        auto flush = [&]() {
             const int nl = s_n;
             if (tid == 0 && nl) s_base = atomicAdd(&R.band, nl);
             __syncthreads();
@@ -1735,8 +1558,34 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
                 e.pad = 0;
                 list[s_base + j] = e;
             }
-            __syncthreads();   // lst and s_n are reused by the next window
+            __syncthreads();
+            if (tid == 0) s_n = 0;
+            __syncthreads();
+        };
+        if (tid == 0) s_n = 0;
+        __syncthreads();
+        for (int b = (int)blockIdx.y; b < nseg; b += SF_CTAS) {
+            const int base = b * segw;
+            const int cnt = segcnt[(size_t)c * SEG_MAX + b];
+            for (int off = 0; off < cnt; off += SF_T) {
+                const int i = off + tid;
+                bool take = false;
+                unsigned pos = 0;
+                if (i < cnt) {
+                    const Cand e = cand[base + i];
+                    if (e.key < kb_lo) ++nlo;
+                    else if (e.key <= kb_hi) { take = true; pos = e.pos; }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                int wb = 0;
+                if (lane == 0 && bal) wb = atomicAdd(&s_n, __popc(bal));
+                wb = __shfl_sync(0xffffffffu, wb, 0);
+                if (take) lst[wb + __popc(bal & ((1u << lane) - 1u))] = (int)pos;
+                __syncthreads();
+                if (s_n > LCAP - SF_T) flush();   // room for the next round
+            }
         }
+        flush();
         nlo = warp_sum_int(nlo);
         if (lane == 0 && nlo) atomicAdd(&s_nlo, nlo);
         __syncthreads();
@@ -1795,14 +1644,10 @@ void launch_select_fast(const Plan& P, cudaStream_t s) {
         cudaFuncSetAttribute(k_select_fast<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_select_fast<PB><<<dim3(2 * P.q, SF_CTAS), SF_T, sm, s>>>(P.ch, P.rule, P.Xp, (const float*)P.dkeys,
                                                                    (long long)P.q * P.m, P.cand, P.band, P.hist,
-                                                                   P.memb, P.m, P.p, P.hb, P.st);
+                                                                   P.memb, P.segcnt, P.m, P.p, P.hb, P.st);
     });
 }
 
-void launch_select_win(const Plan& P, cudaStream_t s) {
-    k_select_win<<<2 * P.q, SEL_T, 0, s>>>(P.ch, P.rule, P.cand, P.band, P.hist, (const float*)P.dkeys,
-                                           (long long)P.q * P.m, P.m, P.hb, P.st);
-}
 void launch_select_band(const Plan& P, cudaStream_t s) {
     k_select_band<<<2 * P.q, BANDSEL_T, 0, s>>>(P.ch, P.rule, P.band, P.memb, P.m, P.hb, P.st);
 }
