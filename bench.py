@@ -449,6 +449,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: each fit as one captured CUDA graph with device-side control flow (cached and "
+                         "relaunched); 0: stream launches with host loop control")
+    ap.add_argument("--dist-path", type=int, default=0, help="C-step distances: 0 CUDA cores, 1 tensor cores")
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16"],
                     help="form of the timed fits (the headline is fp32; bf16 needs 25 <= p <= 48)")
     args = ap.parse_args()
@@ -488,9 +492,16 @@ def main():
                         device=dev) if args.fp64_steps > 0 else None)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    d2_buf = torch.empty(n, dtype=torch.float32, device=dev)
+    fl_buf = torch.empty(n, dtype=torch.uint8, device=dev)
+
     def fit(Xin, prec, ws, profile=False):
-        return rtd.rtdetmcd_fit(Xin, h, precision=prec, workspace=ws, profile=profile,
-                                stream=stream.cuda_stream)
+        if Xin.is_cuda:   # device rows: preallocated outputs, so a captured graph is relaunched
+            return rtd.rtdetmcd_fit(Xin, h, precision=prec, workspace=ws, profile=profile,
+                                    stream=stream.cuda_stream, graph=bool(args.graph) and not profile,
+                                    dist_path=args.dist_path, d2_out=d2_buf, flags_out=fl_buf)
+        return rtd.rtdetmcd_fit(Xin, h, precision=prec, workspace=ws, profile=profile, stream=stream.cuda_stream,
+                                dist_path=args.dist_path)
 
     def timed(Xin, prec, ws, k, profile=False):
         out, profs = [], []
@@ -617,6 +628,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.form == "fp32" else "bf16x2 products, f32 rows", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "p": p, "h": h, "q": r32["q"], "form": args.form,
+                   "launch": "captured CUDA graph, device-side C-step loop" if args.graph else "stream launches",
+                   "cstep_distances": "tensor cores (split TF32)" if args.dist_path else "CUDA cores (FP32)",
                    "l2": "512 MiB write between timed steps (input 80 MB < L2)",
                    "parallelism": f"{ws_n} independent replica(s)"},
         "fp64_form": ({"value": n / (statistics.mean(t64) / 1e3), "unit": "rows/s",

@@ -102,10 +102,19 @@ typedef struct {
     const double* init_mu;
     const double* init_sigma;
     int32_t  dist_path;            /* FP32 form, C-step distances from the second step on:
-                                      0 (default) tcgen05 tensor cores, split-TF32 operands;
-                                      1 CUDA-core FP32 FMAs.  Both take the same decisions (every
-                                      threshold decision near the FP32 error is made in FP64). */
-    int32_t  reserved0;
+                                      0 (default) CUDA-core FP32 FMAs;
+                                      1 tcgen05 tensor cores with split-TF32 operands (p <= 40;
+                                      wider rows take the CUDA-core pass).  Both take the same
+                                      decisions (every threshold decision near the FP32 error is
+                                      made in FP64). */
+    int32_t  graph;                /* 0 (default): stream launches, the host reads a status word
+                                      between the stages and after every C-step;
+                                      1: the whole fit as one captured CUDA graph with its control
+                                      flow on the device (conditional nodes: the C-step loop runs
+                                      while a chain iterates, later stages only if no error), kept
+                                      per host thread and relaunched when the same arguments come
+                                      again.  Needs device rows and outputs, no profile and no warm
+                                      start (the stream path is taken otherwise). */
 } rtd_options;
 
 /* Stages of a fit, for rtd_profile. */

@@ -50,7 +50,7 @@ class _Options(ctypes.Structure):
                 ("select_path", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
                 ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p),
                 ("init_mu", ctypes.c_void_p), ("init_sigma", ctypes.c_void_p),
-                ("dist_path", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("dist_path", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_dist",
@@ -214,8 +214,8 @@ def rtdetmcd_status_string(code):
 
 def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100,
                  cutoff_q=0.975, kappa_max=1000.0, reweight_consistency=1, select_path=0, dist_path=0,
-                 init=None, d2=True, flags=True, subset=False, diag=False, profile=False, stream=None,
-                 workspace=None, check=True):
+                 graph=False, init=None, d2=True, flags=True, subset=False, diag=False, profile=False,
+                 stream=None, workspace=None, d2_out=None, flags_out=None, check=True):
     """RT-DetMCD fit of the rows of X (float32, row-major) with coverage h.
 
     X on a CUDA device: outputs are CUDA tensors on the same device.  X in
@@ -233,6 +233,7 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     o.reweight_consistency = reweight_consistency
     o.select_path = select_path
     o.dist_path = dist_path
+    o.graph = 1 if graph else 0
     if init is not None:   # warm start: (mu, Sigma) of an earlier fit, X units
         init_mu = np.ascontiguousarray(init[0], dtype=np.float64).reshape(-1)
         init_sigma = np.ascontiguousarray(init[1], dtype=np.float64).reshape(-1)
@@ -243,8 +244,11 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
     if ws_need == 0:
         raise RtdError(1, "invalid n, p or options")
     ws = workspace if workspace is not None else _workspace(ws_need, dev)
-    d2_out = _out(n, np.float32, dev) if d2 else None
-    fl_out = _out(n, np.uint8, dev) if flags else None
+    if d2_out is None:
+        d2_out = _out(n, np.float32, dev) if d2 else None
+    fl_out = flags_out
+    if fl_out is None:
+        fl_out = _out(n, np.uint8, dev) if flags else None
     sub_out = _out(n, np.uint8, dev) if subset else None
     o.subset_out = _ptr(sub_out)
     qq = q if q else max(min(n // (p * omega), 1024), 1)

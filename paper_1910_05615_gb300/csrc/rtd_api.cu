@@ -75,6 +75,7 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
     if (o.select_path < 0 || o.select_path > 2) return RTD_EINVAL;
     if (o.dist_path < 0 || o.dist_path > 1) return RTD_EINVAL;
+    if (o.graph < 0 || o.graph > 1) return RTD_EINVAL;
     if ((o.init_mu == nullptr) != (o.init_sigma == nullptr)) return RTD_EINVAL;
     if (o.init_mu) {   // warm start: finite, positive diagonal (host memory)
         for (int j = 0; j < p; ++j) {
@@ -262,11 +263,8 @@ struct Prof {
     ~Prof() { collect(); }
 };
 
-int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s,
-            rtd_result* out, float* d2_out, uint8_t* flags_out) {
-    Regions R;
-    layout(S, R);
-    Plan P;
+// The work decomposition of one fit over the caller's workspace.
+int make_plan(const float* X, const Shape& S, const rtd_options& o, void* ws, const Regions& R, Plan& P) {
     memset(&P, 0, sizeof(P));
     P.n = S.n; P.h = S.h; P.ld = S.ld; P.p = S.p; P.pb = S.pb; P.q = S.q; P.m = S.m; P.hb = S.hb;
     P.precision = S.precision; P.tc = S.tc; P.cpb = S.cpb; P.max_steps = S.max_steps; P.key_bytes = S.key_bytes;
@@ -279,6 +277,7 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         P.cpb_dist = (int)(cd < lim ? (cd > 0 ? cd : 1) : lim);
     }
     feistel_setup(P.F, S.n, o.seed, S.q == 1);
+    P.X = X;
     P.st = at<Status>(ws, R.st);
     P.cs = at<Consts>(ws, R.cs);
     P.ch = at<Chain>(ws, R.ch);
@@ -309,6 +308,15 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     P.kept = at<int>(ws, R.kept);
     P.kl = at<double>(ws, R.kl);
     P.scratch = at<double>(ws, R.scratch);
+    return RTD_OK;
+}
+
+int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s,
+            rtd_result* out, float* d2_out, uint8_t* flags_out) {
+    Regions R;
+    layout(S, R);
+    Plan P;
+    { int e = make_plan(X, S, o, ws, R, P); if (e) return e; }
 
     // rows: stage host data through the workspace
     if (is_device_ptr(X)) {
@@ -412,8 +420,8 @@ csteps:
             // membership pass and the finalize accumulate)
             pf.begin(RTD_STAGE_CDIST);
             if (win) {
-                if (o.dist_path == 1) launch_dist_win(P, s);
-                else launch_dist_tc(P, s);
+                if (o.dist_path == 1) launch_dist_tc(P, s);
+                else launch_dist_win(P, s);
             } else {
                 launch_dist(P, s);
             }
@@ -524,6 +532,311 @@ finish:
     return out->status;
 }
 
+// =====================================================================
+// The fit as one captured CUDA graph.  The kernel sequence of run_fit is
+// issued into a graph whose control flow stays on the device:
+//   - an IF node after the univariate stage (a data error ends the fit),
+//   - a WHILE node for the C-step loop, whose condition the finalize
+//     kernel's last CTA sets (chains still iterating, no error),
+//   - IF nodes before the aggregation and before the final pass.
+// No value comes back to the host until the result record.  Executable
+// graphs are kept per host thread, keyed by every argument they bake in, so
+// a repeated call is one graph launch and one read of the result.
+// =====================================================================
+struct GraphKey {
+    const float* X;
+    long long n, ld, h;
+    int p, dev;
+    void* ws;
+    float* d2;
+    uint8_t* fl;
+    uint8_t* sub;
+    double* diag;
+    int precision, omega, q_override, max_csteps, rew, select_path, dist_path;
+    double cutoff_q, kappa_max;
+    unsigned long long seed;
+};
+
+bool key_equal(const GraphKey& a, const GraphKey& b) { return memcmp(&a, &b, sizeof(GraphKey)) == 0; }
+
+// What fixes a graph's topology (its nodes and conditionals): graphs of the
+// same topology differ only in their nodes' parameters, so one executable
+// graph can be updated in place from the capture of another call.
+struct TopoKey {
+    int pb, single_block, precision, tc, select_path, dist_path, subset, dev;
+};
+
+TopoKey topo_of(const GraphKey& k, const Shape& S) {
+    TopoKey t;
+    memset(&t, 0, sizeof(t));
+    t.pb = S.pb;
+    t.single_block = S.q == 1;
+    t.precision = S.precision;
+    t.tc = S.tc;
+    t.select_path = k.select_path;
+    t.dist_path = k.dist_path;
+    t.subset = k.sub != nullptr;
+    t.dev = k.dev;
+    return t;
+}
+
+struct GraphEntry {
+    GraphKey key;
+    TopoKey topo;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long used = 0;
+};
+
+constexpr int GRAPH_CACHE = 8;
+
+struct GraphThreadState {
+    GraphEntry entries[GRAPH_CACHE];
+    unsigned long long clock = 0;
+    cudaStream_t cap = nullptr;        // capture stream
+    cudaStream_t body[3] = {nullptr, nullptr, nullptr};   // conditional bodies, by nesting depth
+    ~GraphThreadState() {
+        for (GraphEntry& e : entries)
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (cap) cudaStreamDestroy(cap);
+        for (cudaStream_t b : body)
+            if (b) cudaStreamDestroy(b);
+    }
+};
+
+GraphThreadState& graph_state() {
+    static thread_local GraphThreadState g;
+    return g;
+}
+
+// A conditional handle of the graph being captured on `s`.
+int cond_handle(cudaStream_t s, unsigned def, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    RTD_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cst != cudaStreamCaptureStatusActive) return RTD_ECUDA;
+    RTD_CUDA(cudaGraphConditionalHandleCreate(h, g, def, cudaGraphCondAssignDefault));
+    return RTD_OK;
+}
+
+// Append a conditional node to the capture on `s` and start capturing its
+// body on `body`.
+int cond_open(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaStream_t body) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    RTD_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &nd));
+    if (cst != cudaStreamCaptureStatusActive) return RTD_ECUDA;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    RTD_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    RTD_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    RTD_CUDA(cudaStreamBeginCaptureToGraph(body, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    return RTD_OK;
+}
+
+int cond_close(cudaStream_t body) {
+    cudaGraph_t g = nullptr;
+    RTD_CUDA(cudaStreamEndCapture(body, &g));
+    return RTD_OK;
+}
+
+// One C-step of run_fit (window or histogram selection), then the finalize
+// that sets the loop condition hloop.
+void issue_cstep(const Plan& P, const Shape& S, const rtd_options& o, bool win, unsigned long long hloop,
+                 cudaStream_t s) {
+    if (win) {
+        if (o.dist_path == 1) launch_dist_tc(P, s);
+        else launch_dist_win(P, s);
+        launch_select_fast(P, s);
+    } else {
+        launch_dist(P, s);
+        launch_select_bucket(P, s);
+        launch_compact(P, s);
+        launch_select_finish(P, s);
+        if (S.precision == RTD_FP32) {
+            launch_band64(P, s);
+            launch_select_band(P, s);
+        }
+    }
+    launch_memb(P, s);
+    launch_cstep_finalize(P, s, hloop);
+}
+
+// Capture the whole fit into a graph (device rows and outputs, no profile,
+// no warm start); dres and diag receive the result record.
+int capture_fit(Plan& P, const Shape& S, const rtd_options& o, const Regions& R, void* ws, float* d2,
+                uint8_t* fl, rtd_result* dres, double* diag, cudaGraph_t* graph_out) {
+    GraphThreadState& G = graph_state();
+    for (int i = 0; i < 3; ++i)
+        if (!G.body[i]) RTD_CUDA(cudaStreamCreateWithFlags(&G.body[i], cudaStreamNonBlocking));
+    cudaStream_t s = G.cap;
+    RTD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int e = RTD_OK;
+    auto body = [&]() -> int {
+        const size_t q2 = 2 * (size_t)S.q, qm = (size_t)S.q * S.m;
+        RTD_CUDA(cudaMemsetAsync(P.st, 0, sizeof(Status), s));
+        RTD_CUDA(cudaMemsetAsync(P.cs, 0, sizeof(Consts), s));
+        RTD_CUDA(cudaMemsetAsync(P.ch, 0, q2 * sizeof(Chain), s));
+        RTD_CUDA(cudaMemsetAsync(P.rule, 0, q2 * sizeof(SelRule), s));
+        RTD_CUDA(cudaMemsetAsync(P.hist, 0, q2 * HIST_BINS * sizeof(unsigned), s));
+        RTD_CUDA(cudaMemsetAsync(P.memb, 0, 2 * qm, s));
+        RTD_CUDA(cudaMemsetAsync(P.wset, 0, qm, s));
+        RTD_CUDA(cudaMemsetAsync(P.swaps, 0, q2 * sizeof(int), s));
+        launch_gather(P, s);
+        launch_setup(P, o, s);
+        launch_col_keys(P, (uint32_t*)P.arenaA, s);
+        sort_segments(P, P.arenaA, P.arenaB, 4, S.p, S.n, s);
+        launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
+        launch_uni_finish(P, s);
+        // the rest of the fit runs only if the rows passed the checks so far
+        cudaGraphConditionalHandle hA, hW, hB, hC;
+        int r = cond_handle(s, 0, &hA);
+        if (r) return r;
+        launch_cond_ok(hA, P.st, s);
+        if ((r = cond_open(s, hA, cudaGraphCondTypeIf, G.body[0]))) return r;
+        {
+            cudaStream_t b1 = G.body[0];
+            launch_start1(P, b1);
+            sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, S.q, S.m, b1);
+            launch_gsscm(P, P.arenaA, b1);
+            launch_start2(P, b1);
+            launch_start_reduce(P, b1);
+            launch_refine_eigen(P, b1);
+            launch_transform(P, 0, b1);
+            sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, b1);
+            launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, b1);
+            launch_refine_mid(P, b1);
+            launch_transform(P, 1, b1);
+            sort_segments(P, P.arenaA, P.arenaB, S.key_bytes, 2 * S.p * S.q, S.m, b1);
+            launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, b1);
+            launch_refine_end(P, b1);
+            launch_chol_prep(P, b1);
+            // the C-step loop: the first step, then steps while a chain
+            // iterates (condition set by each finalize)
+            if ((r = cond_handle(b1, 0, &hW))) return r;
+            issue_cstep(P, S, o, false, hW, b1);
+            if ((r = cond_open(b1, hW, cudaGraphCondTypeWhile, G.body[1]))) return r;
+            issue_cstep(P, S, o, S.precision == RTD_FP32 && o.select_path != 1, hW, G.body[1]);
+            if ((r = cond_close(G.body[1]))) return r;
+            // Section 4 steps 4-9, then step 10
+            if ((r = cond_handle(b1, 0, &hB))) return r;
+            launch_cond_ok(hB, P.st, b1);
+            if ((r = cond_open(b1, hB, cudaGraphCondTypeIf, G.body[1]))) return r;
+            {
+                cudaStream_t b2 = G.body[1];
+                launch_block_choose(P, b2);
+                if (S.precision == RTD_FP32) launch_rechoose(P, b2);
+                launch_aggregate(P, b2);
+                launch_fit_prep(P, 0, b2);
+                launch_rew(P, b2);
+                launch_rew_finalize(P, b2);
+                launch_fit_prep(P, 1, b2);
+                if ((r = cond_handle(b2, 0, &hC))) return r;
+                launch_cond_ok(hC, P.st, b2);
+                if ((r = cond_open(b2, hC, cudaGraphCondTypeIf, G.body[2]))) return r;
+                launch_final(P, d2, fl, G.body[2]);
+                if (o.subset_out) {
+                    RTD_CUDA(cudaMemsetAsync(o.subset_out, 0, (size_t)S.n, G.body[2]));
+                    launch_subset_out(P, o.subset_out, G.body[2]);
+                }
+                if ((r = cond_close(G.body[2]))) return r;
+            }
+            if ((r = cond_close(G.body[1]))) return r;
+        }
+        if ((r = cond_close(G.body[0]))) return r;
+        RTD_CUDA(cudaMemsetAsync(dres, 0, sizeof(rtd_result), s));
+        launch_result(P, dres, diag, s);
+        return RTD_OK;
+    };
+    e = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (e || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return e ? e : RTD_ECUDA;
+    }
+    *graph_out = g;
+    return RTD_OK;
+}
+
+// run_fit through a cached executable graph.  Returns -1 when the call does
+// not qualify (host rows or outputs, a profile, a warm start), so that the
+// caller takes the stream path.
+int run_fit_graph(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s,
+                  rtd_result* out, float* d2_out, uint8_t* flags_out) {
+    if (o.profile || o.init_mu || !is_device_ptr(X) || (d2_out && !is_device_ptr(d2_out)) ||
+        (flags_out && !is_device_ptr(flags_out)) || (o.subset_out && !is_device_ptr(o.subset_out)) ||
+        (o.diag_out && !is_device_ptr(o.diag_out)))
+        return -1;
+    GraphThreadState& G = graph_state();
+    if (!G.cap) RTD_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    GraphKey k;
+    memset(&k, 0, sizeof(k));
+    k.X = X; k.n = S.n; k.ld = S.ld; k.h = S.h; k.p = S.p;
+    RTD_CUDA(cudaGetDevice(&k.dev));
+    k.ws = ws; k.d2 = d2_out; k.fl = flags_out; k.sub = o.subset_out; k.diag = o.diag_out;
+    k.precision = o.precision; k.omega = o.omega; k.q_override = o.q_override; k.max_csteps = o.max_csteps;
+    k.rew = o.reweight_consistency; k.select_path = o.select_path; k.dist_path = o.dist_path;
+    k.cutoff_q = o.cutoff_q; k.kappa_max = o.kappa_max; k.seed = o.seed;
+    Regions R;
+    layout(S, R);
+    rtd_result* dres = at<rtd_result>(ws, R.res);
+    GraphEntry* hit = nullptr;
+    for (GraphEntry& e : G.entries)
+        if (e.exec && key_equal(e.key, k)) hit = &e;
+    if (!hit) {
+        Plan P;
+        int e = make_plan(X, S, o, ws, R, P);
+        if (e) return e;
+        cudaGraph_t g = nullptr;
+        e = capture_fit(P, S, o, R, ws, d2_out, flags_out, dres, o.diag_out, &g);
+        if (e) return -1;   // not capturable here: the stream path
+        const TopoKey tk = topo_of(k, S);
+        // an executable graph of the same topology is updated in place
+        for (GraphEntry& en : G.entries) {
+            if (!en.exec || memcmp(&en.topo, &tk, sizeof(TopoKey)) != 0) continue;
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(en.exec, g, &info) == cudaSuccess) {
+                en.key = k;
+                hit = &en;
+                break;
+            }
+            cudaGetLastError();
+        }
+        if (!hit) {
+            GraphEntry* slot = &G.entries[0];
+            for (GraphEntry& en : G.entries) {
+                if (!en.exec) { slot = &en; break; }
+                if (en.used < slot->used) slot = &en;
+            }
+            if (slot->exec) { cudaGraphExecDestroy(slot->exec); slot->exec = nullptr; }
+            cudaError_t ie = cudaGraphInstantiate(&slot->exec, g, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(g);
+                cudaGetLastError();
+                slot->exec = nullptr;
+                return -1;
+            }
+            slot->key = k;
+            slot->topo = tk;
+            hit = slot;
+        }
+        cudaGraphDestroy(g);
+    }
+    hit->used = ++G.clock;
+    RTD_CUDA(cudaGraphLaunch(hit->exec, s));
+    RTD_CUDA(cudaMemcpyAsync(out, dres, sizeof(rtd_result), cudaMemcpyDeviceToHost, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    RTD_CUDA(cudaGetLastError());
+    return out->status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -569,7 +882,9 @@ int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, co
         return RTD_EINVAL;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int r = run_fit(X, S, o, workspace, s, out, d2_out, flags_out);
+    int r = -1;
+    if (o.graph == 1) r = run_fit_graph(X, S, o, workspace, s, out, d2_out, flags_out);
+    if (r == -1) r = run_fit(X, S, o, workspace, s, out, d2_out, flags_out);
     out->status = r;
     return r;
 }
@@ -640,8 +955,11 @@ int rtdetmcd_fit_batch(int32_t nframes, const float* const* X, const int64_t* n,
             cudaSetDevice(dev);
             void* wsw = static_cast<unsigned char*>(workspace) + slice * (size_t)w;
             for (int f = next.fetch_add(1); f < nframes; f = next.fetch_add(1)) {
-                int r = run_fit(X[f], shapes[f], o, wsw, ss[w], &out[f], d2_out ? d2_out[f] : nullptr,
-                                flags_out ? flags_out[f] : nullptr);
+                float* d2f = d2_out ? d2_out[f] : nullptr;
+                uint8_t* flf = flags_out ? flags_out[f] : nullptr;
+                int r = -1;
+                if (o.graph == 1) r = run_fit_graph(X[f], shapes[f], o, wsw, ss[w], &out[f], d2f, flf);
+                if (r == -1) r = run_fit(X[f], shapes[f], o, wsw, ss[w], &out[f], d2f, flf);
                 out[f].status = r;
             }
         };

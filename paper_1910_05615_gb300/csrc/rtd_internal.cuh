@@ -106,7 +106,10 @@ void launch_refine_mid(const Plan& P, cudaStream_t s);
 void launch_refine_end(const Plan& P, cudaStream_t s);
 void launch_warm_start(const Plan& P, const double* init, cudaStream_t s);
 void launch_chol_prep(const Plan& P, cudaStream_t s);
-void launch_cstep_finalize(const Plan& P, cudaStream_t s);
+// hloop: conditional handle of a captured C-step loop (0: none)
+void launch_cstep_finalize(const Plan& P, cudaStream_t s, unsigned long long hloop = 0);
+// sets a captured conditional node's condition to (no error so far)
+void launch_cond_ok(unsigned long long h, const Status* st, cudaStream_t s);
 void launch_block_choose(const Plan& P, cudaStream_t s);
 void launch_rechoose(const Plan& P, cudaStream_t s);
 void launch_aggregate(const Plan& P, cudaStream_t s);

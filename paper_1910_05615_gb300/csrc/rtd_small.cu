@@ -481,8 +481,11 @@ void launch_chol_prep(const Plan& P, cudaStream_t s) {
 // or a fresh sum), new mu and Sigma = Lambda/(h_b-1) (eqs. cstep4a/b),
 // convergence when H_new = H_old (no swaps).
 // =====================================================================
-// Last of the 2q finalize CTAs: count the blocks that still iterate.
-__device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Status* st) {
+// Last of the 2q finalize CTAs: count the blocks that still iterate; under a
+// captured graph, also set the C-step loop's condition (chains still
+// iterating and no error).
+__device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Status* st,
+                                           cudaGraphConditionalHandle hloop) {
     __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -498,7 +501,13 @@ __device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Sta
         a += b[l] > 0 ? 1 : 0;
     }
     a = (int)cta_sum((double)a);
-    if (threadIdx.x == 0) st->active_blocks = a;
+    if (threadIdx.x == 0) {
+        st->active_blocks = a;
+        if (hloop) {
+            volatile Status* vs = st;
+            cudaGraphSetConditional(hloop, (vs->active > 0 && vs->code == 0) ? 1u : 0u);
+        }
+    }
 }
 
 // End of a C-step and start of the next one: fold the Gram partials into
@@ -507,7 +516,8 @@ __device__ inline void count_active_blocks(const Chain* ch, int q, int* blk, Sta
 // (no swaps); a chain that goes on gets its next row parameters and window.
 __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* __restrict__ cs,
                                                        const double* __restrict__ gsum, size_t slot_d,
-                                                       int* swaps, int* blk, SelRule* rule, Status* st) {
+                                                       int* swaps, int* blk, SelRule* rule, Status* st,
+                                                       cudaGraphConditionalHandle hloop) {
     extern __shared__ double sm[];
     __shared__ double dmu[PMAX], inv_s[PMAX], Ss[PMAX];
     __shared__ double s_m2;
@@ -516,7 +526,7 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
     Chain& C = ch[c];
     if (!C.active) {
         if (threadIdx.x == 0) clear_rule(rule[c]);
-        count_active_blocks(ch, cs->q, blk, st);
+        count_active_blocks(ch, cs->q, blk, st, hloop);
         return;
     }
     const int p = cs->p, nb = gram_nb(cs->pb);
@@ -598,15 +608,27 @@ __global__ void __launch_bounds__(CT) k_cstep_finalize(Chain* ch, const Consts* 
             atomicAdd(&blk[l], 1);
         }
     }
-    count_active_blocks(ch, cs->q, blk, st);
+    count_active_blocks(ch, cs->q, blk, st, hloop);
 }
 
-void launch_cstep_finalize(const Plan& P, cudaStream_t s) {
+void launch_cstep_finalize(const Plan& P, cudaStream_t s, unsigned long long hloop) {
     launch_reduce_slots(P, 0, s);
     size_t sm = 3 * MAT * sizeof(double);
     auto k = k_cstep_finalize;
     big_smem(k, sm);
-    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles, P.swaps, P.blk_active, P.rule, P.st);
+    k<<<2 * P.q, CT, sm, s>>>(P.ch, P.cs, P.gsum, P.slot_doubles, P.swaps, P.blk_active, P.rule, P.st,
+                              (cudaGraphConditionalHandle)hloop);
+}
+
+// Condition of a captured graph's conditional node: no error so far.
+__global__ void k_cond_ok(cudaGraphConditionalHandle h, const Status* st) {
+    if (threadIdx.x == 0) {
+        volatile const Status* vs = st;
+        cudaGraphSetConditional(h, vs->code == 0 ? 1u : 0u);
+    }
+}
+void launch_cond_ok(unsigned long long h, const Status* st, cudaStream_t s) {
+    k_cond_ok<<<1, 32, 0, s>>>((cudaGraphConditionalHandle)h, st);
 }
 
 // =====================================================================

@@ -302,8 +302,8 @@ def test_select_paths_agree(rtd, main_case, case):
 
 @pytest.mark.parametrize("case", ["main", "point", "p37", "p64"])
 def test_dist_paths_agree(rtd, main_case, case):
-    """The C-step distances on the tensor cores (split-TF32 operands, the
-    default) and on the CUDA cores (FP32 FMAs) feed the same FP64-exact
+    """The C-step distances on the CUDA cores (FP32 FMAs, the default) and on
+    the tensor cores (split-TF32 operands) feed the same FP64-exact
     decisions: the same subsets at every step, so bitwise the same fits."""
     if case == "main":
         fr = main_case[0]
@@ -320,6 +320,60 @@ def test_dist_paths_agree(rtd, main_case, case):
     assert np.array_equal(a["mu"], b["mu"]) and np.array_equal(a["Sigma"], b["Sigma"])
     assert np.array_equal(a["Sigma_raw"], b["Sigma_raw"]) and torch.equal(a["flags"], b["flags"])
     assert a["profile"]["win_steps"] > 0
+
+
+@pytest.mark.parametrize("case", ["main", "blocks", "point", "fp64", "bf16", "maxsteps"])
+def test_graph_fit_equals_stream_fit(rtd, main_case, case):
+    """The fit captured as one CUDA graph with device-side control flow (the
+    C-step loop as a conditional WHILE node) issues the same kernels on the
+    same data as the stream path: bitwise the same results."""
+    kw = {}
+    if case == "main":
+        fr = main_case[0]
+    elif case == "blocks":
+        fr = datagen.contaminated_gaussian(184_331, 5, eps=0.15, kind="shift", shift=6.0, seed=4)
+    elif case == "point":
+        fr = datagen.contaminated_gaussian(120_000, 5, eps=0.1, kind="point", shift=10.0, seed=3)
+    elif case == "fp64":
+        fr = datagen.contaminated_gaussian(50_000, 8, eps=0.2, kind="cluster", shift=7.0, seed=9)
+        kw = {"precision": rtd.RTD_FP64}
+    elif case == "bf16":
+        fr = datagen.large_case(n=200_003, p=32, seed=5)
+        kw = {"precision": rtd.RTD_BF16}
+    else:
+        fr = datagen.contaminated_gaussian(60_000, 6, eps=0.15, kind="cluster", shift=6.0, seed=21)
+        kw = {"max_csteps": 2}
+    X = torch.from_numpy(fr.X).cuda()
+    a = rtd.rtdetmcd_fit(X, fr.h, subset=True, diag=True, **kw)
+    sub = torch.empty(X.shape[0], dtype=torch.uint8, device="cuda")
+    d2 = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    fl = torch.empty(X.shape[0], dtype=torch.uint8, device="cuda")
+    for rep in range(2):      # the second call relaunches the cached graph
+        d2.fill_(-1.0)
+        b = rtd.rtdetmcd_fit(X, fr.h, graph=True, subset=True, diag=True, d2_out=d2, flags_out=fl, **kw)
+        assert b["status"] == 0 and b["warnings"] == a["warnings"]
+        assert np.array_equal(a["mu"], b["mu"]) and np.array_equal(a["Sigma"], b["Sigma"])
+        assert np.array_equal(a["Sigma_raw"], b["Sigma_raw"]) and a["csteps_max"] == b["csteps_max"]
+        assert torch.equal(a["d2"], d2) and torch.equal(a["flags"], fl)
+        assert torch.equal(a["subset"], b["subset"])
+        da, db = a["diag"], b["diag"]
+        assert [c["steps"] for c in da["chains"]] == [c["steps"] for c in db["chains"]]
+
+
+@pytest.mark.parametrize("bad", ["nan", "degenerate"])
+def test_graph_fit_data_errors(rtd, bad):
+    """Data errors end the captured fit on the device (the conditional nodes
+    skip the later stages) with the stream path's status."""
+    fr = datagen.contaminated_gaussian(5000, 4, eps=0.0, kind="point", shift=0.0, seed=0)
+    X = fr.X.copy()
+    if bad == "nan":
+        X[1234, 2] = np.nan
+    else:
+        X[:3000, 1] = 1.0
+    Xd = torch.from_numpy(X).cuda()
+    a = rtd.rtdetmcd_fit(Xd, fr.h, check=False)
+    b = rtd.rtdetmcd_fit(Xd, fr.h, graph=True, check=False)
+    assert a["status"] == b["status"] == (2 if bad == "nan" else 4)
 
 
 def test_select_path_rejects_bad_value(rtd):
