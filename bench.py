@@ -182,22 +182,40 @@ def batched_leg(rtd, torch, datagen, dev, stream, nstreams=16, reps=2):
         hs.append(int(np.floor(0.75 * n)))
     rows = sum(int(X.shape[0]) for X in frames)
     ws = torch.empty(rtd.rtdetmcd_fit_batch_workspace_size(frames, nstreams), dtype=torch.uint8, device=dev)
-    rtd.rtdetmcd_fit_batch(frames, hs, nstreams=nstreams, workspace=ws, stream=stream.cuda_stream)   # warm-up
-    ts = []
-    for i in range(reps):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = rtd.rtdetmcd_fit_batch(frames, hs, nstreams=nstreams, workspace=ws, stream=stream.cuda_stream)
-        e1.record(stream)
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    t = statistics.median(ts)
+    def run(graph):
+        return rtd.rtdetmcd_fit_batch(frames, hs, nstreams=nstreams, workspace=ws, stream=stream.cuda_stream,
+                                      graph=graph, autotune=1)
+
+    res_by = {}
+    for graph in (1, 0):
+        run(graph)   # warm-up (graph: captures, instantiates and tunes each width class)
+        ts = []
+        for i in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = run(graph)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res_by[graph] = (statistics.median(ts), out)
+    t, out = res_by[1]
+    t_stream = res_by[0][0]
+    tuned = {}
+    for pp in (8, 16, 24, 32, 40):
+        for nn in (4000, 25000):
+            tv = rtd.rtdetmcd_tuned(nn, pp)
+            if tv:
+                tuned[f"p={pp},n~{nn}"] = {"win_rows": tv["win_rows"], "sel_ctas": tv["sel_ctas"]}
     res = {"workload": f"{BATCH_FRAMES} frames, n ~ U[2000, 50000], p ~ U{{8,16,24,32,40}}, 0-25% point "
                        f"outliers at 10 v_min, FP32 form, q = 1 per frame ({rows:,} rows, inputs larger than L2)",
            "frames_per_s": BATCH_FRAMES / (t / 1e3), "rows_per_s": rows / (t / 1e3), "ms_per_batch": t,
            "nstreams": nstreams, "flagged_total": int(sum(o["n_flagged"] for o in out)),
-           "form": "concurrent single fits on streams (host worker threads), not yet one persistent launch"}
+           "form": "each frame one captured CUDA graph (device-side C-step loop), updated in place from frame "
+                   "to frame, frames concurrent on streams from host worker threads; launch shapes autotuned "
+                   "per width class",
+           "stream_launches": {"ms_per_batch": t_stream, "frames_per_s": BATCH_FRAMES / (t_stream / 1e3)},
+           "tuned_shapes": tuned}
     del frames, ws
     torch.cuda.empty_cache()
     return res
@@ -520,6 +538,10 @@ def main():
             last = r
         return out, profs, last
 
+    tuning = None
+    if args.graph:   # launch shapes of this problem picked by the autotuner (values unchanged)
+        tuning = rtd.rtdetmcd_autotune(X, h, precision=FORM, dist_path=args.dist_path, workspace=ws32,
+                                       stream=stream.cuda_stream)
     for _ in range(args.warmup):
         fit(X, FORM, ws32)
     barrier()
@@ -637,6 +659,7 @@ def main():
                        "fp32_speedup": statistics.mean(t64) / (tot32 / args.steps),
                        "roofline": fp64_roofline(prof64[0])} if t64 else None),
         "roofline": roof, "roofline_cstep": roof_c, "stages": stages, "csteps": prof32[-1]["csteps"],
+        "autotuned_shape": tuning,
         "selection": selection_stats(prof32[-1]),
         "profiled_ms_per_step": statistics.mean(tprof),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "scoring": scoring,

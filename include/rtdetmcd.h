@@ -115,6 +115,10 @@ typedef struct {
                                       per host thread and relaunched when the same arguments come
                                       again.  Needs device rows and outputs, no profile and no warm
                                       start (the stream path is taken otherwise). */
+    int32_t  autotune;             /* rtdetmcd_fit_batch with graph = 1: 1 (default) tunes each class
+                                      of frames without a tuned launch shape first (see
+                                      rtdetmcd_autotune); 0 uses the tuned or default shapes */
+    int32_t  reserved1;
 } rtd_options;
 
 /* Stages of a fit, for rtd_profile. */
@@ -382,6 +386,34 @@ int rtdetmcd_vjp(const float* X, int64_t n, int32_t p, int64_t ld, const uint8_t
 /* chi2_{p, q} quantile as used for the cutoff (computed by the library's own
    incomplete-gamma routines). */
 double rtdetmcd_chi2_quantile(int32_t p, double q);
+
+/* Launch shapes of a fit picked by the autotuner. */
+typedef struct {
+    int32_t win_rows;     /* rows per CTA, at least, of the C-step distance pass (0: the pass's own) */
+    int32_t sel_ctas;     /* CTAs per chain of the one-launch window selection */
+    int32_t candidates;   /* shapes timed */
+    int32_t reserved;
+    double  ms_best;      /* median fit time under the chosen shape */
+    double  ms_default;   /* median fit time under the default shape */
+} rtd_tuning;
+
+/*
+ * Autotuner of the launch shapes (a part of this engine, not of the paper):
+ * times whole fits of these rows (one warm-up and three timed fits per
+ * candidate, CUDA events on `stream`) under each candidate shape of the
+ * C-step distance pass (rows per CTA) and of the window selection (CTAs per
+ * chain), and keeps the fastest for later fits with the same padded width,
+ * block count, block length class, form and paths, in this process.  Neither
+ * shape changes any value a fit computes, so tuned and untuned fits are
+ * equal bit for bit.  Arguments as for rtdetmcd_fit (device rows; the fits'
+ * outputs are not kept); `out` (nullable, host) receives the choice.
+ */
+int rtdetmcd_autotune(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                      void* workspace, size_t ws_bytes, void* stream, rtd_tuning* out);
+
+/* The tuned shape for fits of this size and these options: 1 and *out filled
+   if one is kept, 0 otherwise. */
+int rtdetmcd_tuned(int64_t n, int32_t p, const rtd_options* opt, rtd_tuning* out);
 
 /* Human-readable name of a status code. */
 const char* rtdetmcd_status_string(int status);

@@ -24,7 +24,7 @@ __all__ = [
     "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
     "rtdetmcd_grad_workspace_size", "rtdetmcd_objective", "rtdetmcd_fit_batch",
     "rtdetmcd_fit_batch_workspace_size", "rtdetmcd_vjp", "rtdetmcd_fit_outputs", "rtdetmcd_score",
-    "rtdetmcd_score_workspace_size",
+    "rtdetmcd_score_workspace_size", "rtdetmcd_autotune", "rtdetmcd_tuned",
 ]
 
 RTD_FP64 = 0
@@ -50,7 +50,13 @@ class _Options(ctypes.Structure):
                 ("select_path", ctypes.c_int32), ("subset_out", ctypes.c_void_p),
                 ("diag_out", ctypes.c_void_p), ("profile", ctypes.c_void_p),
                 ("init_mu", ctypes.c_void_p), ("init_sigma", ctypes.c_void_p),
-                ("dist_path", ctypes.c_int32), ("graph", ctypes.c_int32)]
+                ("dist_path", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("win_rows", ctypes.c_int32), ("sel_ctas", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ms_best", ctypes.c_double), ("ms_default", ctypes.c_double)]
 
 
 STAGES = ["partition", "univariate", "starts", "refine", "cstep_prep", "cstep_dist",
@@ -128,6 +134,11 @@ def _load():
     lib.rtdetmcd_vjp.restype = i32
     lib.rtdetmcd_flag.argtypes = [vp, i64, dbl, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.rtdetmcd_flag.restype = i32
+    lib.rtdetmcd_autotune.argtypes = [vp, i64, i32, i64, i64, ctypes.POINTER(_Options), vp, sz, vp,
+                                      ctypes.POINTER(_Tuning)]
+    lib.rtdetmcd_autotune.restype = i32
+    lib.rtdetmcd_tuned.argtypes = [i64, i32, ctypes.POINTER(_Options), ctypes.POINTER(_Tuning)]
+    lib.rtdetmcd_tuned.restype = i32
     lib.rtdetmcd_chi2_quantile.argtypes = [i32, dbl]
     lib.rtdetmcd_chi2_quantile.restype = dbl
     lib.rtdetmcd_status_string.argtypes = [i32]
@@ -282,6 +293,45 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
             name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i], "flops": prof.flops[i]}
             for i, name in enumerate(STAGES)}}
     return out
+
+
+def _tuning_dict(t):
+    return {"win_rows": t.win_rows, "sel_ctas": t.sel_ctas, "candidates": t.candidates, "ms_best": t.ms_best,
+            "ms_default": t.ms_default}
+
+
+def rtdetmcd_autotune(X, h, *, precision=RTD_FP32, graph=True, dist_path=0, select_path=0, stream=None,
+                      workspace=None, **opts):
+    """Time the candidate launch shapes of the C-step distance pass and the
+    window selection on fits of the rows X (a CUDA tensor) and keep the
+    fastest for later fits of this class; returns the choice."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    if dev is None:
+        raise ValueError("rtdetmcd_autotune needs X on a CUDA device")
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision, o.graph, o.dist_path, o.select_path = precision, 1 if graph else 0, dist_path, select_path
+    for k, v in opts.items():
+        setattr(o, k, v)
+    ws = workspace if workspace is not None else _workspace(lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o)), dev)
+    t = _Tuning()
+    st = lib.rtdetmcd_autotune(ptr, n, p, ld, h, ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream_ptr(dev, stream),
+                               ctypes.byref(t))
+    del keep
+    if st != 0:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+    return _tuning_dict(t)
+
+
+def rtdetmcd_tuned(n, p, *, precision=RTD_FP32, dist_path=0, select_path=0):
+    """The tuned launch shape kept for fits of this size, or None."""
+    lib = _load()
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision, o.dist_path, o.select_path = precision, dist_path, select_path
+    t = _Tuning()
+    return _tuning_dict(t) if lib.rtdetmcd_tuned(n, p, ctypes.byref(o), ctypes.byref(t)) else None
 
 
 def rtdetmcd_fit_batch_workspace_size(frames, nstreams=8, precision=RTD_FP32):

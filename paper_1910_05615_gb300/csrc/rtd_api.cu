@@ -1,7 +1,9 @@
 #include <vector>
 #include <cmath>
 #include <atomic>
+#include <mutex>
 #include <thread>
+#include <algorithm>
 // rtd_api.cu - C ABI entry points and host orchestration of RT-DetMCD.
 //
 // The host validates arguments, lays out the caller's workspace, and issues
@@ -20,6 +22,7 @@ namespace {
 constexpr int TARGET_CTAS = 304;      // row-kernel CTAs per pass (all blocks): 2 per SM
 constexpr int MIN_ROWS_PER_CTA = 256;
 constexpr int MAX_BLOCKS = RTD_MAX_BLOCKS;
+constexpr int SF_CTAS_DEFAULT = 8;    // CTAs per chain of the window selection unless tuned
 
 struct Region {
     size_t off, bytes;
@@ -61,6 +64,7 @@ rtd_options defaults() {
     o.subset_out = nullptr;
     o.diag_out = nullptr;
     o.profile = nullptr;
+    o.autotune = 1;
     return o;
 }
 
@@ -75,7 +79,7 @@ int make_shape(long long n, int p, long long ld, long long h, const rtd_options&
     if (o.reweight_consistency < 0 || o.reweight_consistency > 2) return RTD_EINVAL;
     if (o.select_path < 0 || o.select_path > 2) return RTD_EINVAL;
     if (o.dist_path < 0 || o.dist_path > 1) return RTD_EINVAL;
-    if (o.graph < 0 || o.graph > 1) return RTD_EINVAL;
+    if (o.graph < 0 || o.graph > 1 || o.autotune < 0 || o.autotune > 1) return RTD_EINVAL;
     if ((o.init_mu == nullptr) != (o.init_sigma == nullptr)) return RTD_EINVAL;
     if (o.init_mu) {   // warm start: finite, positive diagonal (host memory)
         for (int j = 0; j < p; ++j) {
@@ -263,6 +267,58 @@ struct Prof {
     ~Prof() { collect(); }
 };
 
+// ---------------------------------------------------------------- autotuner
+// Launch shapes picked by timing: rows per CTA of the window distance pass
+// and CTAs per chain of the window selection.  Neither changes any value a
+// fit computes (distances are per row, counts are exact sums, and the
+// selection ranks its list in FP64 whatever order it was filled in), so a
+// tuned fit equals an untuned one bit for bit.  Choices are kept per
+// process, keyed by what the best shape depends on.
+struct TuneKey {
+    int pb, q, mbucket, precision, tc, dist_path, select_path, dev;
+};
+struct TuneVal {
+    int win_rows, sel_ctas;
+};
+std::mutex g_tune_lock;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+thread_local const TuneVal* t_force = nullptr;   // a candidate under test on this thread
+
+int m_bucket(long long m) {   // pairs of octaves of the block length
+    int b = 0;
+    while ((1LL << (2 * (b + 1))) <= m) ++b;
+    return b;
+}
+
+TuneKey tune_key(const Shape& S, const rtd_options& o, int dev) {
+    TuneKey k;
+    memset(&k, 0, sizeof(k));
+    k.pb = S.pb; k.q = S.q; k.mbucket = m_bucket(S.m); k.precision = S.precision; k.tc = S.tc;
+    k.dist_path = o.dist_path; k.select_path = o.select_path; k.dev = dev;
+    return k;
+}
+
+bool tune_get(const TuneKey& k, TuneVal& v) {
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    for (auto& e : g_tune)
+        if (memcmp(&e.first, &k, sizeof(TuneKey)) == 0) { v = e.second; return true; }
+    return false;
+}
+
+void tune_put(const TuneKey& k, const TuneVal& v) {
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    for (auto& e : g_tune)
+        if (memcmp(&e.first, &k, sizeof(TuneKey)) == 0) { e.second = v; return; }
+    g_tune.push_back({k, v});
+}
+
+TuneVal resolve_tuning(const Shape& S, const rtd_options& o, int dev) {
+    TuneVal v{0, 0};
+    if (t_force) v = *t_force;
+    else tune_get(tune_key(S, o, dev), v);
+    return v;
+}
+
 // The work decomposition of one fit over the caller's workspace.
 int make_plan(const float* X, const Shape& S, const rtd_options& o, void* ws, const Regions& R, Plan& P) {
     memset(&P, 0, sizeof(P));
@@ -271,6 +327,11 @@ int make_plan(const float* X, const Shape& S, const rtd_options& o, void* ws, co
     int dev = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     RTD_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, dev));
+    {
+        const TuneVal tv = resolve_tuning(S, o, dev);
+        P.win_rows = tv.win_rows;
+        P.sel_ctas = tv.sel_ctas;
+    }
     {   // distance pass: one resident wave (two CTAs per SM), at least 512 rows each
         long long cd = (2LL * P.nsm + S.q - 1) / S.q;
         long long lim = (S.m + 511) / 512;
@@ -553,6 +614,7 @@ struct GraphKey {
     uint8_t* sub;
     double* diag;
     int precision, omega, q_override, max_csteps, rew, select_path, dist_path;
+    int win_rows, sel_ctas;
     double cutoff_q, kappa_max;
     unsigned long long seed;
 };
@@ -784,6 +846,11 @@ int run_fit_graph(const float* X, const Shape& S, const rtd_options& o, void* ws
     k.precision = o.precision; k.omega = o.omega; k.q_override = o.q_override; k.max_csteps = o.max_csteps;
     k.rew = o.reweight_consistency; k.select_path = o.select_path; k.dist_path = o.dist_path;
     k.cutoff_q = o.cutoff_q; k.kappa_max = o.kappa_max; k.seed = o.seed;
+    {
+        const TuneVal tv = resolve_tuning(S, o, k.dev);
+        k.win_rows = tv.win_rows;
+        k.sel_ctas = tv.sel_ctas;
+    }
     Regions R;
     layout(S, R);
     rtd_result* dres = at<rtd_result>(ws, R.res);
@@ -835,6 +902,70 @@ int run_fit_graph(const float* X, const Shape& S, const rtd_options& o, void* ws
     RTD_CUDA(cudaStreamSynchronize(s));
     RTD_CUDA(cudaGetLastError());
     return out->status;
+}
+
+// One fit through the graph path (or the stream path when it does not
+// qualify).
+int fit_once(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s, rtd_result* out,
+             float* d2, uint8_t* fl) {
+    int r = -1;
+    if (o.graph == 1) r = run_fit_graph(X, S, o, ws, s, out, d2, fl);
+    if (r == -1) r = run_fit(X, S, o, ws, s, out, d2, fl);
+    return r;
+}
+
+// Time every candidate launch shape on this problem (one warm-up and three
+// timed fits each, CUDA events on the stream) and keep the fastest.
+int autotune_shape(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s,
+                   rtd_tuning* res) {
+    static const int WROWS[3] = {0, 1024, 4096};
+    static const int SCTAS[3] = {2, 4, 8};
+    int dev = 0;
+    RTD_CUDA(cudaGetDevice(&dev));
+    cudaEvent_t e0, e1;
+    RTD_CUDA(cudaEventCreate(&e0));
+    RTD_CUDA(cudaEventCreate(&e1));
+    rtd_result tmp;
+    TuneVal best{0, 0};
+    float best_ms = 1e30f, dflt_ms = -1.f;
+    int ncand = 0, err = RTD_OK;
+    for (int a = 0; a < 3 && !err; ++a) {
+        for (int b = 0; b < 3 && !err; ++b) {
+            const TuneVal cand{WROWS[a], SCTAS[b]};
+            t_force = &cand;
+            err = fit_once(X, S, o, ws, s, &tmp, nullptr, nullptr);   // warm-up (captures the graph)
+            float ms[3];
+            for (int r = 0; r < 3 && !err; ++r) {
+                cudaEventRecord(e0, s);
+                err = fit_once(X, S, o, ws, s, &tmp, nullptr, nullptr);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms[r], e0, e1);
+            }
+            t_force = nullptr;
+            if (err) break;
+            // median of three
+            float lo = fminf(ms[0], fminf(ms[1], ms[2])), hi = fmaxf(ms[0], fmaxf(ms[1], ms[2]));
+            const float med = ms[0] + ms[1] + ms[2] - lo - hi;
+            ++ncand;
+            if (cand.win_rows == 0 && cand.sel_ctas == SF_CTAS_DEFAULT) dflt_ms = med;
+            if (med < best_ms) { best_ms = med; best = cand; }
+        }
+    }
+    t_force = nullptr;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err) return err;
+    tune_put(tune_key(S, o, dev), best);
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->win_rows = best.win_rows;
+        res->sel_ctas = best.sel_ctas;
+        res->candidates = ncand;
+        res->ms_best = best_ms;
+        res->ms_default = dflt_ms;
+    }
+    return RTD_OK;
 }
 
 }  // namespace
@@ -934,6 +1065,30 @@ int rtdetmcd_fit_batch(int32_t nframes, const float* const* X, const int64_t* n,
     int dev = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    if (o.graph == 1 && o.autotune == 1) {
+        // tune each class of frames (same tuning key) that has no choice yet,
+        // on the frame of median size in the class, before the pool starts
+        std::vector<int> todo;
+        for (int f = 0; f < nframes; ++f) {
+            TuneVal v;
+            if (!tune_get(tune_key(shapes[f], o, dev), v)) todo.push_back(f);
+        }
+        while (!todo.empty()) {
+            const TuneKey k0 = tune_key(shapes[todo[0]], o, dev);
+            std::vector<int> cls, rest;
+            for (int f : todo) {
+                const TuneKey kf = tune_key(shapes[f], o, dev);
+                (memcmp(&kf, &k0, sizeof(TuneKey)) == 0 ? cls : rest).push_back(f);
+            }
+            std::sort(cls.begin(), cls.end(), [&](int a, int b) { return n[a] < n[b]; });
+            const int f = cls[cls.size() / 2];
+            if (is_device_ptr(X[f])) {
+                const int e = autotune_shape(X[f], shapes[f], o, workspace, caller, nullptr);
+                if (e) return e;
+            }
+            todo.swap(rest);
+        }
+    }
     // the workers' streams start after the caller's earlier work
     cudaEvent_t ready;
     RTD_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
@@ -1235,6 +1390,40 @@ int rtdetmcd_flag(const float* d2, int64_t n, double cutoff_d2, uint8_t* flags_o
     if (e) return e;
     if (n_flagged) *n_flagged = (int64_t)hs.n_flagged;
     return hs.code;
+}
+
+int rtdetmcd_autotune(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                      void* workspace, size_t ws_bytes, void* stream, rtd_tuning* out) {
+    rtd_options o = opt ? *opt : defaults();
+    o.subset_out = nullptr;
+    o.diag_out = nullptr;
+    o.profile = nullptr;
+    Shape S;
+    int e = make_shape(n, p, ld, h, o, S);
+    if (!e) e = check_h(S);
+    if (!X || !is_device_ptr(X)) e = RTD_EINVAL;
+    if (e) return e;
+    Regions R;
+    size_t need = layout(S, R);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    if (on_other_device(X) || on_other_device(workspace)) return RTD_EINVAL;
+    return autotune_shape(X, S, o, workspace, reinterpret_cast<cudaStream_t>(stream), out);
+}
+
+int rtdetmcd_tuned(int64_t n, int32_t p, const rtd_options* opt, rtd_tuning* out) {
+    rtd_options o = opt ? *opt : defaults();
+    Shape S;
+    if (make_shape(n, p, p, (n + p + 1) / 2, o, S) != RTD_OK) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    TuneVal v;
+    if (!tune_get(tune_key(S, o, dev), v)) return 0;
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->win_rows = v.win_rows;
+        out->sel_ctas = v.sel_ctas;
+    }
+    return 1;
 }
 
 double rtdetmcd_chi2_quantile(int32_t p, double q) {

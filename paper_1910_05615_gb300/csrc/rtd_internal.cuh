@@ -28,6 +28,8 @@ struct Plan {
     int p, pb, q, m, hb, precision, cpb, nsm, max_steps;
     int cpb_dist;           // CTAs per block of the distance and compaction passes
     int tc;                 // Grams on the tensor cores (split-BF16 form)
+    int win_rows;           // rows per CTA, at least, of the window distance pass (0: the kernel's own)
+    int sel_ctas;           // CTAs per chain of the window selection (0: 8)
     int key_bytes;          // 4 (FP32 form) or 8 (FP64 form) for refinement sorts
     Feistel F;
     // device buffers

@@ -991,7 +991,8 @@ void dist_win_t(const Plan& P, cudaStream_t s) {
     typedef DistWin<PB> D;
     // one resident wave, at least 256 rows per CTA
     long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
-    const long long lim = ((long long)P.m + 255) / 256;
+    const long long rpc = P.win_rows > 256 ? P.win_rows : 256;
+    const long long lim = ((long long)P.m + rpc - 1) / rpc;
     if (cw > lim) cw = lim;
     if (cw > SEG_MAX) cw = SEG_MAX;
     const int cpb = (int)(cw > 0 ? cw : 1);
@@ -1312,7 +1313,8 @@ void dist_tc_t(const Plan& P, cudaStream_t s) {
     typedef DistTC<PB> D;
     // one resident wave, at least one tile per CTA
     long long cw = (long long)D::CTAS_PER_SM * P.nsm / P.q;
-    const long long lim = ((long long)P.m + D::TM - 1) / D::TM;
+    const long long rpc = P.win_rows > D::TM ? P.win_rows : D::TM;
+    const long long lim = ((long long)P.m + rpc - 1) / rpc;
     if (cw > lim) cw = lim;
     if (cw > SEG_MAX) cw = SEG_MAX;
     const int cpb = (int)(cw > 0 ? cw : 1);

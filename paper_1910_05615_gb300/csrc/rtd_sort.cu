@@ -1360,7 +1360,7 @@ __global__ void __launch_bounds__(BANDSEL_T) k_select_band(const Chain* __restri
 
 // =====================================================================
 // Window path of the FP32 form in one launch (from the second C-step on),
-// SF_CTAS CTAs per chain.  Every CTA finds the window bin b that holds rank
+// gridDim.y CTAs per chain.  Every CTA finds the window bin b that holds rank
 // r = h_b - (rows below the window).  The FP64 range is that bin widened
 // by the band, [lo_b (1 - eps), hi_b (1 + eps)]: a row whose FP32 key lies
 // below it is in, above it out (the FP32 error is under eps), and a row
@@ -1373,7 +1373,7 @@ __global__ void __launch_bounds__(BANDSEL_T) k_select_band(const Chain* __restri
 // histogram path over the block's keys and the same FP64 ranking.
 // =====================================================================
 constexpr int SF_T = 256;       // threads per CTA
-constexpr int SF_CTAS = 8;      // CTAs per chain
+constexpr int SF_CTAS = 8;      // CTAs per chain unless tuned
 
 // FP64 d2 = |M (x - mu)|^2 of one padded row; M (lower triangular, row
 // stride PB) and mu in shared memory.  Output rows are taken 16 at a time,
@@ -1564,7 +1564,7 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
         };
         if (tid == 0) s_n = 0;
         __syncthreads();
-        for (int b = (int)blockIdx.y; b < nseg; b += SF_CTAS) {
+        for (int b = (int)blockIdx.y; b < nseg; b += (int)gridDim.y) {
             const int base = b * segw;
             const int cnt = segcnt[(size_t)c * SEG_MAX + b];
             for (int off = 0; off < cnt; off += SF_T) {
@@ -1594,7 +1594,7 @@ __global__ void __launch_bounds__(SF_T) k_select_fast(const Chain* __restrict__ 
     // 3. the chain's last CTA
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&R.done, 1) == SF_CTAS - 1);
+    if (tid == 0) s_last = (atomicAdd(&R.done, 1) == (int)gridDim.y - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -1642,7 +1642,7 @@ void launch_select_fast(const Plan& P, cudaStream_t s) {
         const size_t sm = (size_t)(PB * PB + PB) * sizeof(double);
         // static buffers plus M pass 48 KB at the larger widths: opt in
         cudaFuncSetAttribute(k_select_fast<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_select_fast<PB><<<dim3(2 * P.q, SF_CTAS), SF_T, sm, s>>>(P.ch, P.rule, P.Xp, (const float*)P.dkeys,
+        k_select_fast<PB><<<dim3(2 * P.q, P.sel_ctas > 0 ? P.sel_ctas : SF_CTAS), SF_T, sm, s>>>(P.ch, P.rule, P.Xp, (const float*)P.dkeys,
                                                                    (long long)P.q * P.m, P.cand, P.band, P.hist,
                                                                    P.memb, P.segcnt, P.m, P.p, P.hb, P.st);
     });

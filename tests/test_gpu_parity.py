@@ -650,6 +650,36 @@ def test_fit_batch_matches_single_fits_and_oracle(rtd):
         assert ok, (f, rep)
 
 
+def test_autotune_keeps_every_value(rtd):
+    """The autotuner changes launch shapes only: fits under the tuned shape
+    equal the untuned ones bit for bit, and the choice is kept."""
+    fr = datagen.contaminated_gaussian(150_000, 12, eps=0.15, kind="cluster", shift=6.0, seed=31)
+    X = torch.from_numpy(fr.X).cuda()
+    a = rtd.rtdetmcd_fit(X, fr.h, subset=True)
+    t = rtd.rtdetmcd_autotune(X, fr.h)
+    assert t["candidates"] == 9 and t["ms_best"] > 0 and t["ms_best"] <= t["ms_default"]
+    assert rtd.rtdetmcd_tuned(150_000, 12) == {**t, "candidates": 0, "ms_best": 0.0, "ms_default": 0.0}
+    for graph in (False, True):
+        b = rtd.rtdetmcd_fit(X, fr.h, subset=True, graph=graph)
+        assert np.array_equal(a["mu"], b["mu"]) and np.array_equal(a["Sigma"], b["Sigma"])
+        assert torch.equal(a["subset"], b["subset"]) and torch.equal(a["flags"], b["flags"])
+
+
+def test_fit_batch_graph_matches_single_fits(rtd):
+    """Many frames, each a captured graph updated in place from frame to frame
+    (device-side C-step loop), with per-class autotuning: every result equals
+    the single stream fit bit for bit."""
+    frames = [datagen.batched_frame(f) for f in range(40, 72)]
+    Xs = [torch.from_numpy(fr.X).cuda() for fr in frames]
+    got = rtd.rtdetmcd_fit_batch(Xs, [fr.h for fr in frames], nstreams=4, graph=1, autotune=1)
+    for f, fr in enumerate(frames):
+        one = rtd.rtdetmcd_fit(Xs[f], fr.h)
+        g = got[f]
+        assert g["status"] == 0
+        assert np.array_equal(g["mu"], one["mu"]) and np.array_equal(g["Sigma"], one["Sigma"])
+        assert torch.equal(g["d2"], one["d2"]) and torch.equal(g["flags"], one["flags"])
+
+
 def test_fit_batch_host_frames(rtd):
     frames = [datagen.batched_frame(f) for f in range(20, 26)]
     got = rtd.rtdetmcd_fit_batch([fr.X for fr in frames], [fr.h for fr in frames], nstreams=3)
