@@ -213,6 +213,79 @@ int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h,
                  const rtd_options* opt, void* workspace, size_t ws_bytes,
                  void* stream, rtd_result* out, float* d2_out, uint8_t* flags_out);
 
+/*
+ * The fit in stages, for one fit sharded over G processes (one GPU each).
+ * Section 4 groups into stages whose exchanges are small:
+ *   - the univariate MCD of each column (Section 3.1, eq. standardization):
+ *     columns are independent;
+ *   - steps 2-4 (starts, refinement, C-steps, choice of start) of each block:
+ *     blocks are independent (the paper runs one thread per block);
+ *   - steps 5-7 read only the q block fits (p + p^2 + 2 doubles each);
+ *   - steps 8-9 sum over the rows of all blocks: count, sum and centred
+ *     cross-products of the reweighting set (1 + p + p^2 doubles);
+ *   - step 10 treats each row alone.
+ * A process takes a range of columns, a range of blocks and a range of rows;
+ * between the stages the processes all-gather the column results and the
+ * block fits and sum the moments.  Called with the whole ranges in one process
+ * the stages give rtdetmcd_fit's results, up to the order of the FP64 sums of
+ * the moments (which can move the reweighted fit by a few units in the last
+ * place).
+ * Every stage call: X is the whole n x p matrix (device or host; host rows are
+ * copied in every call), h and opt as for rtdetmcd_fit and equal in every call
+ * and process (opt->init_mu must be NULL; graph, subset_out, diag_out and
+ * profile are ignored); the workspace has at least
+ * rtdetmcd_workspace_size(n, p, opt) bytes; results may go to host or device
+ * memory; the call returns when they are written.  Returns RTD_EINVAL for a
+ * range outside [0, p), [0, q) or [0, n) or a missing pointer, and the status
+ * of the stage's data otherwise (RTD_ENONFINITE, RTD_EDEGENERATE, ...).
+ */
+#define RTD_BLOCK_FIT_DOUBLES(p) (2 + (p) + (p) * (p))
+#define RTD_MOMENT_DOUBLES(p) (1 + (p) + (p) * (p))
+
+/* Block count q and rows per block m of the partition of Section 4
+   (eq. partitionsize) for these arguments. */
+int rtdetmcd_partition(int64_t n, int32_t p, int64_t h, const rtd_options* opt, int32_t* q, int64_t* m);
+
+/* Univariate reweighted MCD (Section 3.1) of columns [col_lo, col_hi) over
+   all n rows, and the non-finite check of those columns: uni_out receives
+   2 (col_hi - col_lo) doubles, the locations then the scales (mu_uni, s_uni
+   of eq. standardization). */
+int rtdetmcd_standardize(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                         int32_t col_lo, int32_t col_hi, void* workspace, size_t ws_bytes, void* stream,
+                         double* uni_out);
+
+/* Section 4 steps 2-4 for blocks [blk_lo, blk_hi) of the partition, with the
+   standardisation uni (2p doubles: all locations, then all scales).
+   fits_out receives one record of RTD_BLOCK_FIT_DOUBLES(p) doubles per block:
+     chosen start (0 wrapping, 1 GSSCM; -1 when neither gave a fit),
+     log det Sigma_l, mu_l[p], Sigma_l[p^2] row-major
+   in Z units, Sigma_l = Lambda/(h_b - 1) without c(alpha).  An empty range
+   does nothing. */
+int rtdetmcd_fit_blocks(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                        const double* uni, int32_t blk_lo, int32_t blk_hi, void* workspace, size_t ws_bytes,
+                        void* stream, double* fits_out);
+
+/* Steps 5-7 from the records of all q blocks (fits, block order), then the
+   step-8 distances to the raw fit of the rows of blocks [blk_lo, blk_hi):
+   moments_out receives RTD_MOMENT_DOUBLES(p) doubles, the count of the rows
+   of the reweighting set W, the sum of x - c and the sum of (x - c)(x - c)^T
+   over them (row-major), with c the raw centre in X units (the same in every
+   process, since steps 5-7 are).  An empty range gives zeros.
+   RTD_EILLCOND if no block has a fit; RTD_EINVAL for a malformed record. */
+int rtdetmcd_reweight_moments(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                              const double* uni, const double* fits, int32_t blk_lo, int32_t blk_hi,
+                              void* workspace, size_t ws_bytes, void* stream, double* moments_out);
+
+/* Step 9 from the moments summed over all blocks (every process's
+   rtdetmcd_reweight_moments added entrywise), then step 10 for the original
+   rows [row_lo, row_hi): out (host) as for rtdetmcd_fit, with n_flagged
+   counting those rows only and csteps_max, chains_ok zero; d2_out and
+   flags_out (nullable) receive row_hi - row_lo entries. */
+int rtdetmcd_reweight_finish(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                             const double* uni, const double* fits, const double* moments, int64_t row_lo,
+                             int64_t row_hi, void* workspace, size_t ws_bytes, void* stream, rtd_result* out,
+                             float* d2_out, uint8_t* flags_out);
+
 /* Largest number of concurrent streams of rtdetmcd_fit_batch. */
 #define RTD_BATCH_MAX_STREAMS 64
 

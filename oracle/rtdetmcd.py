@@ -513,6 +513,40 @@ def validate(n: int, p: int, h: int):
         raise OracleError("need [(n+p+1)/2] <= h < n")
 
 
+def choose_start(chains) -> int:
+    """Section 4 step 4: of the starts whose C-steps gave a fit, the one with
+    the lower determinant; start 1 on ties (reading R11).  Returns 0, 1, or
+    -1 when neither start gave a fit."""
+    ok = [k for k in range(2) if chains[k] is not None and chains[k].ok]
+    if not ok:
+        return -1
+    if len(ok) == 1:
+        return ok[0]
+    ld = [np.linalg.slogdet(chains[k].Sigma)[1] for k in range(2)]
+    return 0 if ld[0] <= ld[1] else 1
+
+
+def aggregate(fits, h_b: int, c_alpha: float):
+    """Section 4 steps 5-7 from the block fits: fits[l] = (mu_l, c(alpha)
+    Sigma_l) in Z units, or None for a block without a fit.  Entrywise
+    median of the fitted blocks, KL deviation of each from it, keep the
+    ceil(q_f/2) closest (stable order by KL), pool their h_b-subsets
+    (reading R7).  With one block (q = 1) the raw fit is that block's.
+    Returns (mu_raw, Sigma_raw, kept, kl); kl lists the fitted blocks."""
+    fitted = [l for l in range(len(fits)) if fits[l] is not None]
+    if not fitted:
+        raise OracleError("every start of every block was ill-conditioned")
+    if len(fits) == 1:
+        return fits[0][0], fits[0][1], [0], np.zeros(1)
+    mu_med = entrywise_median([fits[l][0] for l in fitted])
+    S_med = entrywise_median([fits[l][1] for l in fitted])
+    kl = np.array([kl_deviation(mu_med, S_med, fits[l][0], fits[l][1]) for l in fitted])
+    order = np.argsort(kl, kind="stable")
+    kept = [fitted[i] for i in order[: (len(fitted) + 1) // 2]]
+    mu_raw, Sigma_raw, _ = pool([(fits[l][0], fits[l][1], h_b) for l in kept], c_alpha)
+    return mu_raw, Sigma_raw, kept, kl
+
+
 def block_start_unit(args):
     """Steps 1-3 of Section 4 for one start k of one block: the initial
     scatter S~_k (Section 3.2), its refinement (Section 3.3) and the C-steps
@@ -593,34 +627,14 @@ def fit(X, h: int, *, omega: int = OMEGA, seed: int = 0,
             S = [units[2 * l][0], units[2 * l + 1][0]]
             starts = [units[2 * l][1], units[2 * l + 1][1]]
             chains = [units[2 * l][2], units[2 * l + 1][2]]
-        # Step 4: the start with the lower determinant (start 1 on ties).
         b = Block(rows, S, starts, chains)
-        ok = [k for k in range(2) if chains[k] is not None and chains[k].ok]
-        if ok:
-            if len(ok) == 2:
-                ld = [np.linalg.slogdet(chains[k].Sigma)[1] for k in range(2)]
-                b.chosen = 0 if ld[0] <= ld[1] else 1
-            else:
-                b.chosen = ok[0]
+        b.chosen = choose_start(chains)
+        if b.chosen >= 0:
             ch = chains[b.chosen]
             b.mu, b.Sigma = ch.mu, c_alpha * ch.Sigma
         blocks.append(b)
-    fitted = [l for l in range(q) if blocks[l].chosen >= 0]
-    if not fitted:
-        raise OracleError("every start of every block was ill-conditioned")
-    # Steps 5-7: entrywise median, KL deviations, keep ceil(q/2), pool.
-    if q == 1:
-        mu_raw, Sigma_raw = blocks[0].mu, blocks[0].Sigma
-        kept, kl = [0], np.zeros(1)
-    else:
-        mu_med = entrywise_median([blocks[l].mu for l in fitted])
-        S_med = entrywise_median([blocks[l].Sigma for l in fitted])
-        kl = np.array([kl_deviation(mu_med, S_med, blocks[l].mu, blocks[l].Sigma)
-                       for l in fitted])
-        order = np.argsort(kl, kind="stable")
-        kept = [fitted[i] for i in order[: (len(fitted) + 1) // 2]]
-        mu_raw, Sigma_raw, _ = pool([(blocks[l].mu, blocks[l].Sigma, h_b)
-                                     for l in kept], c_alpha)
+    mu_raw, Sigma_raw, kept, kl = aggregate(
+        [(b.mu, b.Sigma) if b.chosen >= 0 else None for b in blocks], h_b, c_alpha)
     # Steps 8-9: reweighting over the rows of all blocks.
     cutoff_d2 = chi2_ppf(cutoff_q, p)
     used = perm[: q * m]

@@ -24,7 +24,8 @@ __all__ = [
     "rtdetmcd_diag_size", "rtdetmcd_distances_workspace_size", "parse_diag", "rtdetmcd_grad",
     "rtdetmcd_grad_workspace_size", "rtdetmcd_objective", "rtdetmcd_fit_batch",
     "rtdetmcd_fit_batch_workspace_size", "rtdetmcd_vjp", "rtdetmcd_fit_outputs", "rtdetmcd_score",
-    "rtdetmcd_score_workspace_size", "rtdetmcd_autotune", "rtdetmcd_tuned",
+    "rtdetmcd_score_workspace_size", "rtdetmcd_autotune", "rtdetmcd_tuned", "rtdetmcd_partition",
+    "rtdetmcd_standardize", "rtdetmcd_fit_blocks", "rtdetmcd_reweight_moments", "rtdetmcd_reweight_finish",
 ]
 
 RTD_FP64 = 0
@@ -120,6 +121,21 @@ def _load():
     lib.rtdetmcd_distances_noalloc.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp]
     lib.rtdetmcd_distances_noalloc.restype = i32
     P64, P32 = ctypes.POINTER(i64), ctypes.POINTER(i32)
+    lib.rtdetmcd_partition.argtypes = [i64, i32, i64, ctypes.POINTER(_Options), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i64)]
+    lib.rtdetmcd_partition.restype = i32
+    lib.rtdetmcd_standardize.argtypes = [vp, i64, i32, i64, i64, ctypes.POINTER(_Options), i32, i32, vp, sz, vp,
+                                         vp]
+    lib.rtdetmcd_standardize.restype = i32
+    lib.rtdetmcd_fit_blocks.argtypes = [vp, i64, i32, i64, i64, ctypes.POINTER(_Options), vp, i32, i32, vp, sz,
+                                        vp, vp]
+    lib.rtdetmcd_fit_blocks.restype = i32
+    lib.rtdetmcd_reweight_moments.argtypes = [vp, i64, i32, i64, i64, ctypes.POINTER(_Options), vp, vp, i32, i32,
+                                              vp, sz, vp, vp]
+    lib.rtdetmcd_reweight_moments.restype = i32
+    lib.rtdetmcd_reweight_finish.argtypes = [vp, i64, i32, i64, i64, ctypes.POINTER(_Options), vp, vp, vp, i64,
+                                             i64, vp, sz, vp, ctypes.POINTER(_Result), vp, vp]
+    lib.rtdetmcd_reweight_finish.restype = i32
     lib.rtdetmcd_fit_batch_workspace_size.argtypes = [i32, P64, P32, vp, i32]
     lib.rtdetmcd_fit_batch_workspace_size.restype = sz
     lib.rtdetmcd_fit_batch.argtypes = [i32, ctypes.POINTER(vp), P64, P32, P64, P64, vp, vp, sz, vp, i32,
@@ -293,6 +309,142 @@ def rtdetmcd_fit(X, h, *, precision=RTD_FP32, omega=4096, q=0, seed=0, max_cstep
             name: {"ms": prof.ms[i], "bytes": prof.bytes[i], "launches": prof.launches[i], "flops": prof.flops[i]}
             for i, name in enumerate(STAGES)}}
     return out
+
+
+# ------------------------------------------------- the fit in stages
+def _stage_options(lib, precision=RTD_FP32, omega=4096, q=0, seed=0, max_csteps=100, cutoff_q=0.975,
+                   kappa_max=1000.0, reweight_consistency=1, select_path=0, dist_path=0):
+    o = _Options()
+    lib.rtdetmcd_default_options(ctypes.byref(o))
+    o.precision, o.omega, o.q_override, o.seed = precision, omega, q, seed
+    o.max_csteps, o.cutoff_q, o.kappa_max = max_csteps, cutoff_q, kappa_max
+    o.reweight_consistency, o.select_path, o.dist_path = reweight_consistency, select_path, dist_path
+    o.graph = 0
+    return o
+
+
+def _f64(a, size, name):
+    """(pointer, keepalive) of a float64 array of `size` values: a numpy
+    array or a contiguous torch tensor (host or device)."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != size:
+            raise ValueError(f"{name} must be a contiguous float64 tensor of {size} values")
+        return a.data_ptr(), a
+    A = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if A.size != size:
+        raise ValueError(f"{name} must hold {size} values")
+    return A.ctypes.data, A
+
+
+def _stage_ws(lib, n, p, o, dev, workspace):
+    need = lib.rtdetmcd_workspace_size(n, p, ctypes.byref(o))
+    if need == 0:
+        raise RtdError(1, "invalid n, p or options")
+    return workspace if workspace is not None else _workspace(need, dev)
+
+
+def _status(lib, st, check):
+    if st != 0 and check:
+        raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
+
+
+def rtdetmcd_partition(n, p, h, **options):
+    """(q, m): block count and rows per block of the partition (Section 4)."""
+    lib = _load()
+    o = _stage_options(lib, **options)
+    q, m = ctypes.c_int32(0), ctypes.c_int64(0)
+    st = lib.rtdetmcd_partition(n, p, h, ctypes.byref(o), ctypes.byref(q), ctypes.byref(m))
+    _status(lib, st, True)
+    return q.value, m.value
+
+
+def rtdetmcd_standardize(X, h, col_lo, col_hi, *, stream=None, workspace=None, check=True, **options):
+    """Univariate MCD of columns [col_lo, col_hi): float64 (2, k) array of
+    locations and scales (host numpy).  Returns (status, array)."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    o = _stage_options(lib, **options)
+    ws = _stage_ws(lib, n, p, o, dev, workspace)
+    k = max(col_hi - col_lo, 0)
+    out = np.zeros((2, k), dtype=np.float64)
+    st = lib.rtdetmcd_standardize(ptr, n, p, ld, h, ctypes.byref(o), col_lo, col_hi, ws.data_ptr(), ws.numel(),
+                                  _stream_ptr(dev, stream), out.ctypes.data)
+    del keep
+    _status(lib, st, check)
+    return st, out
+
+
+def rtdetmcd_fit_blocks(X, h, uni, blk_lo, blk_hi, *, stream=None, workspace=None, check=True, **options):
+    """Steps 2-4 of blocks [blk_lo, blk_hi) given uni = (mu_uni, s_uni):
+    float64 (blk_hi - blk_lo, 2 + p + p^2) block-fit records (host numpy).
+    Returns (status, records)."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    o = _stage_options(lib, **options)
+    ws = _stage_ws(lib, n, p, o, dev, workspace)
+    up, ukeep = _f64(uni, 2 * p, "uni")
+    k = max(blk_hi - blk_lo, 0)
+    out = np.zeros((k, 2 + p + p * p), dtype=np.float64)
+    st = lib.rtdetmcd_fit_blocks(ptr, n, p, ld, h, ctypes.byref(o), up, blk_lo, blk_hi, ws.data_ptr(), ws.numel(),
+                                 _stream_ptr(dev, stream), out.ctypes.data)
+    del keep, ukeep
+    _status(lib, st, check)
+    return st, out
+
+
+def rtdetmcd_reweight_moments(X, h, uni, fits, blk_lo, blk_hi, *, stream=None, workspace=None, check=True,
+                              **options):
+    """Steps 5-7 from all q block-fit records, then the reweighting moments
+    (count, sum, centred cross-products) of the rows of blocks
+    [blk_lo, blk_hi): float64 (1 + p + p^2,) host array.  Returns (status,
+    moments)."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    o = _stage_options(lib, **options)
+    q, _ = rtdetmcd_partition(n, p, h, **options)
+    ws = _stage_ws(lib, n, p, o, dev, workspace)
+    up, ukeep = _f64(uni, 2 * p, "uni")
+    fp, fkeep = _f64(fits, q * (2 + p + p * p), "fits")
+    out = np.zeros(1 + p + p * p, dtype=np.float64)
+    st = lib.rtdetmcd_reweight_moments(ptr, n, p, ld, h, ctypes.byref(o), up, fp, blk_lo, blk_hi, ws.data_ptr(),
+                                       ws.numel(), _stream_ptr(dev, stream), out.ctypes.data)
+    del keep, ukeep, fkeep
+    _status(lib, st, check)
+    return st, out
+
+
+def rtdetmcd_reweight_finish(X, h, uni, fits, moments, row_lo, row_hi, *, d2=True, flags=True, stream=None,
+                             workspace=None, check=True, **options):
+    """Step 9 from the summed moments, then step 10 for rows [row_lo, row_hi).
+    Returns (status, dict) with the reweighted and raw fits (X units) and the
+    rows' squared distances and flags (on X's device, or numpy for host X);
+    n_flagged counts those rows."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    o = _stage_options(lib, **options)
+    q, _ = rtdetmcd_partition(n, p, h, **options)
+    ws = _stage_ws(lib, n, p, o, dev, workspace)
+    up, ukeep = _f64(uni, 2 * p, "uni")
+    fp, fkeep = _f64(fits, q * (2 + p + p * p), "fits")
+    mp_, mkeep = _f64(moments, 1 + p + p * p, "moments")
+    k = max(row_hi - row_lo, 0)
+    d2_out = _out(k, np.float32, dev) if d2 else None
+    fl_out = _out(k, np.uint8, dev) if flags else None
+    res = _Result()
+    st = lib.rtdetmcd_reweight_finish(ptr, n, p, ld, h, ctypes.byref(o), up, fp, mp_, row_lo, row_hi, ws.data_ptr(),
+                                      ws.numel(), _stream_ptr(dev, stream), ctypes.byref(res), _ptr(d2_out),
+                                      _ptr(fl_out))
+    del keep, ukeep, fkeep, mkeep
+    _status(lib, st, check)
+    return st, {
+        "status": st, "warnings": res.warnings, "n": res.n, "p": res.p, "q": res.q, "m": res.m, "h": res.h,
+        "h_b": res.h_b, "mu": np.array(res.mu[:p]), "Sigma": np.array(res.sigma[:p * p]).reshape(p, p),
+        "mu_raw": np.array(res.mu_raw[:p]), "Sigma_raw": np.array(res.sigma_raw[:p * p]).reshape(p, p),
+        "logdet": res.logdet, "logdet_raw": res.logdet_raw, "cutoff_d2": res.cutoff_d2,
+        "n_flagged": res.n_flagged, "n_reweight": res.n_reweight, "c_rew": res.c_rew,
+        "rows": (row_lo, row_hi), "d2": d2_out, "flags": fl_out,
+    }
 
 
 def _tuning_dict(t):

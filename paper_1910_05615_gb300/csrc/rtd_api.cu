@@ -47,7 +47,7 @@ struct Shape {
 struct Regions {
     Region st, cs, ch, rule, fitrp, res, xstage, d2stage, flagstage, substage, diagstage,
         Xp, perm, arenaA, arenaB, sort_hist, uni, uscratch, gss, dkeys, memb, cand, segcnt, band, hist, swaps,
-        blk, partial, gsum, wset, chosen, amb, kept, kl, scratch;
+        blk, partial, gsum, wset, chosen, amb, kept, kl, scratch, fits, moments;
 };
 
 rtd_options defaults() {
@@ -170,6 +170,8 @@ size_t layout(const Shape& S, Regions& R) {
     R.kept = L.add(q * sizeof(int));
     R.kl = L.add(q * sizeof(double));
     R.scratch = L.add(((p + p * p) * (q + 1) + 64) * sizeof(double));
+    R.fits = L.add(q * (2 + p + p * p) * sizeof(double));
+    R.moments = L.add((1 + p + p * p) * sizeof(double));
     return (L.total + 255) & ~(size_t)255;
 }
 
@@ -319,25 +321,31 @@ TuneVal resolve_tuning(const Shape& S, const rtd_options& o, int dev) {
     return v;
 }
 
-// The work decomposition of one fit over the caller's workspace.
-int make_plan(const float* X, const Shape& S, const rtd_options& o, void* ws, const Regions& R, Plan& P) {
+// The work decomposition of one fit over the caller's workspace.  With
+// q_full > 0, S.q blocks starting at permuted position t0 of a partition
+// into q_full blocks (the launch shapes are those of the whole partition).
+int make_plan(const float* X, const Shape& S, const rtd_options& o, void* ws, const Regions& R, Plan& P,
+              int q_full = 0, long long t0 = 0) {
     memset(&P, 0, sizeof(P));
+    Shape SF = S;
+    if (q_full) SF.q = q_full;
+    P.t0 = t0;
     P.n = S.n; P.h = S.h; P.ld = S.ld; P.p = S.p; P.pb = S.pb; P.q = S.q; P.m = S.m; P.hb = S.hb;
     P.precision = S.precision; P.tc = S.tc; P.cpb = S.cpb; P.max_steps = S.max_steps; P.key_bytes = S.key_bytes;
     int dev = 0;
     RTD_CUDA(cudaGetDevice(&dev));
     RTD_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, dev));
     {
-        const TuneVal tv = resolve_tuning(S, o, dev);
+        const TuneVal tv = resolve_tuning(SF, o, dev);
         P.win_rows = tv.win_rows;
         P.sel_ctas = tv.sel_ctas;
     }
     {   // distance pass: one resident wave (two CTAs per SM), at least 512 rows each
-        long long cd = (2LL * P.nsm + S.q - 1) / S.q;
+        long long cd = (2LL * P.nsm + SF.q - 1) / SF.q;
         long long lim = (S.m + 511) / 512;
         P.cpb_dist = (int)(cd < lim ? (cd > 0 ? cd : 1) : lim);
     }
-    feistel_setup(P.F, S.n, o.seed, S.q == 1);
+    feistel_setup(P.F, S.n, o.seed, SF.q == 1);
     P.X = X;
     P.st = at<Status>(ws, R.st);
     P.cs = at<Consts>(ws, R.cs);
@@ -968,6 +976,270 @@ int autotune_shape(const float* X, const Shape& S, const rtd_options& o, void* w
     return RTD_OK;
 }
 
+// =====================================================================
+// The fit in stages, for a fit sharded over processes (one per GPU).
+// Section 4's steps grouped by what they need from the other processes:
+//   STAGE_UNI      the univariate MCD of a range of columns (step
+//                  "standardization"; each column alone),
+//   STAGE_BLOCKS   steps 2-4 of a range of blocks (each block alone),
+//   STAGE_MOMENTS  steps 5-7 from all q block fits, then the step-8
+//                  distances and the reweighting moments of the rows of a
+//                  range of blocks,
+//   STAGE_FINISH   step 9 from the moments summed over all blocks, then
+//                  step 10 for a range of the original rows.
+// =====================================================================
+enum { STAGE_UNI = 1, STAGE_BLOCKS = 2, STAGE_MOMENTS = 3, STAGE_FINISH = 4 };
+
+struct StageArgs {
+    int kind;
+    long long lo, hi;        // columns (UNI), blocks (BLOCKS, MOMENTS) or rows (FINISH)
+    const double* uni;       // 2p: mu_uni then s_uni
+    const double* fits;      // q block-fit records
+    const double* moments;   // reweighting moments summed over all blocks
+    double* out;             // uni (UNI), records (BLOCKS) or moments (MOMENTS)
+    rtd_result* res;         // FINISH
+    float* d2;               // FINISH, nullable: hi - lo floats
+    uint8_t* fl;             // FINISH, nullable: hi - lo bytes
+};
+
+size_t fit_record_doubles(int p) { return 2 + (size_t)p + (size_t)p * p; }
+size_t moment_doubles(int p) { return 1 + (size_t)p + (size_t)p * p; }
+
+// Rows on the device: as given, or staged through the workspace.
+int device_rows(const float* X, const Shape& S, void* ws, const Regions& R, Plan& P, cudaStream_t s) {
+    if (is_device_ptr(X)) {
+        P.X = X;
+        return RTD_OK;
+    }
+    float* xs = at<float>(ws, R.xstage);
+    if (S.ld == S.p)
+        RTD_CUDA(cudaMemcpyAsync(xs, X, (size_t)S.n * S.p * sizeof(float), cudaMemcpyHostToDevice, s));
+    else
+        RTD_CUDA(cudaMemcpy2DAsync(xs, (size_t)S.p * sizeof(float), X, (size_t)S.ld * sizeof(float),
+                                   (size_t)S.p * sizeof(float), (size_t)S.n, cudaMemcpyHostToDevice, s));
+    P.X = xs;
+    P.ld = S.p;
+    return RTD_OK;
+}
+
+int clear_plan(const Plan& P, cudaStream_t s) {
+    const size_t q2 = 2 * (size_t)P.q, qm = (size_t)P.q * P.m;
+    RTD_CUDA(cudaMemsetAsync(P.st, 0, sizeof(Status), s));
+    RTD_CUDA(cudaMemsetAsync(P.cs, 0, sizeof(Consts), s));
+    RTD_CUDA(cudaMemsetAsync(P.ch, 0, q2 * sizeof(Chain), s));
+    RTD_CUDA(cudaMemsetAsync(P.rule, 0, q2 * sizeof(SelRule), s));
+    RTD_CUDA(cudaMemsetAsync(P.hist, 0, q2 * HIST_BINS * sizeof(unsigned), s));
+    RTD_CUDA(cudaMemsetAsync(P.memb, 0, 2 * qm, s));
+    RTD_CUDA(cudaMemsetAsync(P.wset, 0, qm, s));
+    RTD_CUDA(cudaMemsetAsync(P.swaps, 0, q2 * sizeof(int), s));
+    return RTD_OK;
+}
+
+// The given standardisation (2p doubles, host or device memory) into the
+// constants of the plan; scales must be positive and finite.
+int set_uni(const Plan& P, const double* uni, cudaStream_t s) {
+    const int p = P.p;
+    std::vector<double> h(2 * (size_t)p);
+    RTD_CUDA(cudaMemcpyAsync(h.data(), uni, h.size() * sizeof(double), cudaMemcpyDefault, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < p; ++j)
+        if (!std::isfinite(h[j]) || !std::isfinite(h[p + j]) || !(h[p + j] > 0.0)) return RTD_EINVAL;
+    char* cs = reinterpret_cast<char*>(P.cs);
+    RTD_CUDA(cudaMemcpyAsync(cs + offsetof(Consts, mu_uni), h.data(), p * sizeof(double), cudaMemcpyHostToDevice, s));
+    RTD_CUDA(cudaMemcpyAsync(cs + offsetof(Consts, s_uni), h.data() + p, p * sizeof(double), cudaMemcpyHostToDevice, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    return RTD_OK;
+}
+
+// Host copy of `count` doubles (host or device memory), all finite.
+int host_finite(const double* src, size_t count, cudaStream_t s, std::vector<double>& h) {
+    h.resize(count);
+    RTD_CUDA(cudaMemcpyAsync(h.data(), src, count * sizeof(double), cudaMemcpyDefault, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    for (double v : h)
+        if (!std::isfinite(v)) return RTD_EINVAL;
+    return RTD_OK;
+}
+
+// Steps 5-7 from the q records a.fits (whole-partition plan P); leaves the
+// raw fit's row parameters in P.fitrp[0].  Records are checked on the host
+// first: start -1, 0 or 1 and finite values.
+int pool_blocks(const Plan& P, const Regions& R, void* ws, const StageArgs& a, cudaStream_t s) {
+    const size_t rd = fit_record_doubles(P.p);
+    std::vector<double> h;
+    { int e = host_finite(a.fits, (size_t)P.q * rd, s, h); if (e) return e; }
+    for (int l = 0; l < P.q; ++l) {
+        const double c = h[(size_t)l * rd];
+        if (c != -1.0 && c != 0.0 && c != 1.0) return RTD_EINVAL;
+    }
+    double* rec = at<double>(ws, R.fits);
+    RTD_CUDA(cudaMemcpyAsync(rec, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    launch_block_fits_in(P, rec, s);
+    launch_aggregate(P, s);
+    launch_fit_prep(P, 0, s);
+    return RTD_OK;
+}
+
+int run_stage(const float* X, const Shape& S, const rtd_options& o, void* ws, cudaStream_t s, const StageArgs& a) {
+    Regions R;
+    layout(S, R);
+    Plan P;
+    { int e = make_plan(X, S, o, ws, R, P); if (e) return e; }
+    { int e = device_rows(X, S, ws, R, P, s); if (e) return e; }
+    const bool ranged = a.kind == STAGE_BLOCKS || a.kind == STAGE_MOMENTS;
+    Plan PL = P;   // the block range: blocks [lo, hi) of the q-block partition
+    if (ranged && a.hi > a.lo) {
+        Shape SL = S;
+        SL.q = (int)(a.hi - a.lo);
+        int e = make_plan(X, SL, o, ws, R, PL, S.q, a.lo * (long long)S.m);
+        if (e) return e;
+        PL.X = P.X;
+        PL.ld = P.ld;
+    }
+    const int p = S.p;
+    Status hs;
+    if (a.kind == STAGE_UNI) {
+        { int e = clear_plan(P, s); if (e) return e; }
+        launch_setup(P, o, s);
+        Plan PC = P;   // columns [lo, hi) as a matrix of their own
+        PC.X = P.X + a.lo;
+        PC.p = (int)(a.hi - a.lo);
+        launch_col_keys(PC, (uint32_t*)P.arenaA, s);   // also the non-finite check
+        sort_segments(PC, P.arenaA, P.arenaB, 4, PC.p, S.n, s);
+        launch_unimcd(PC, P.arenaA, 4, PC.p, S.n, 0, P.uni, s);
+        launch_uni_finish(PC, s);
+        char* cs = reinterpret_cast<char*>(P.cs);
+        RTD_CUDA(cudaMemcpyAsync(a.out, cs + offsetof(Consts, mu_uni), PC.p * sizeof(double), cudaMemcpyDefault, s));
+        RTD_CUDA(cudaMemcpyAsync(a.out + PC.p, cs + offsetof(Consts, s_uni), PC.p * sizeof(double),
+                                 cudaMemcpyDefault, s));
+        int e = fetch_status(P.st, s, hs);
+        return e ? e : hs.code;
+    }
+    if (a.kind == STAGE_BLOCKS) {
+        if (a.hi == a.lo) return RTD_OK;
+        { int e = clear_plan(PL, s); if (e) return e; }
+        launch_setup(PL, o, s);
+        { int e = set_uni(PL, a.uni, s); if (e) return e; }
+        launch_col_keys(P, (uint32_t*)P.arenaA, s);   // the non-finite check: no further work on bad rows
+        { int e = fetch_status(PL.st, s, hs); if (e) return e; }
+        if (hs.code) return hs.code;
+        launch_gather(PL, s);
+        // Section 3.2: initial estimators; Section 3.3: refinement
+        launch_start1(PL, s);
+        sort_segments(PL, PL.arenaA, PL.arenaB, S.key_bytes, PL.q, S.m, s);
+        launch_gsscm(PL, PL.arenaA, s);
+        launch_start2(PL, s);
+        launch_start_reduce(PL, s);
+        launch_refine_eigen(PL, s);
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_transform(PL, pass, s);
+            sort_segments(PL, PL.arenaA, PL.arenaB, S.key_bytes, 2 * p * PL.q, S.m, s);
+            launch_unimcd(PL, PL.arenaA, S.key_bytes, 2 * p * PL.q, S.m, 1, PL.uni, s);
+            if (pass == 0) launch_refine_mid(PL, s);
+        }
+        launch_refine_end(PL, s);
+        launch_chol_prep(PL, s);
+        { int e = fetch_status(PL.st, s, hs); if (e) return e; }
+        if (hs.code) return hs.code;
+        // Sections 2.1, 3.4, 3.5: C-steps until every chain has stopped
+        for (int it = 0; it <= S.max_steps; ++it) {
+            const bool win = S.precision == RTD_FP32 && it > 0 && o.select_path != 1;
+            issue_cstep(PL, S, o, win, 0, s);
+            int e = fetch_status(PL.st, s, hs);
+            if (e) return e;
+            if (hs.code || hs.active == 0) break;
+        }
+        if (hs.code) return hs.code;
+        // step 4
+        launch_block_choose(PL, s);
+        if (S.precision == RTD_FP32) launch_rechoose(PL, s);
+        double* rec = at<double>(ws, R.fits);
+        launch_block_fits_out(PL, rec, s);
+        RTD_CUDA(cudaMemcpyAsync(a.out, rec, (size_t)PL.q * fit_record_doubles(p) * sizeof(double),
+                                 cudaMemcpyDefault, s));
+        int e = fetch_status(PL.st, s, hs);
+        return e ? e : hs.code;
+    }
+    // steps 5-7 on the whole partition
+    { int e = clear_plan(P, s); if (e) return e; }
+    launch_setup(P, o, s);
+    { int e = set_uni(P, a.uni, s); if (e) return e; }
+    { int e = pool_blocks(P, R, ws, a, s); if (e) return e; }
+    { int e = fetch_status(P.st, s, hs); if (e) return e; }
+    if (hs.code) return hs.code;
+    double* mo = at<double>(ws, R.moments);
+    if (a.kind == STAGE_MOMENTS) {
+        if (a.hi > a.lo) {
+            launch_gather(PL, s);
+            launch_rew(PL, s);
+            launch_moments_out(PL, mo, s);
+        } else {
+            RTD_CUDA(cudaMemsetAsync(mo, 0, moment_doubles(p) * sizeof(double), s));
+        }
+        RTD_CUDA(cudaMemcpyAsync(a.out, mo, moment_doubles(p) * sizeof(double), cudaMemcpyDefault, s));
+        int e = fetch_status(P.st, s, hs);
+        return e ? e : hs.code;
+    }
+    // STAGE_FINISH: step 9, then step 10 for rows [lo, hi)
+    {
+        std::vector<double> h;
+        int e = host_finite(a.moments, moment_doubles(p), s, h);
+        if (e) return e;
+        RTD_CUDA(cudaMemcpyAsync(mo, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        RTD_CUDA(cudaStreamSynchronize(s));
+    }
+    launch_moments_finalize(P, mo, s);
+    launch_fit_prep(P, 1, s);
+    { int e = fetch_status(P.st, s, hs); if (e) return e; }
+    if (!hs.code && a.hi > a.lo) {
+        const long long nr = a.hi - a.lo;
+        Plan PR = P;
+        PR.X = P.X + a.lo * P.ld;
+        PR.n = nr;
+        const bool d2dev = is_device_ptr(a.d2), fldev = is_device_ptr(a.fl);
+        float* d2 = a.d2 ? (d2dev ? a.d2 : at<float>(ws, R.d2stage)) : nullptr;
+        uint8_t* fl = a.fl ? (fldev ? a.fl : at<uint8_t>(ws, R.flagstage)) : nullptr;
+        launch_final(PR, d2, fl, s);
+        if (a.d2 && !d2dev) RTD_CUDA(cudaMemcpyAsync(a.d2, d2, nr * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (a.fl && !fldev) RTD_CUDA(cudaMemcpyAsync(a.fl, fl, nr, cudaMemcpyDeviceToHost, s));
+    }
+    rtd_result* dres = at<rtd_result>(ws, R.res);
+    RTD_CUDA(cudaMemsetAsync(dres, 0, sizeof(rtd_result), s));
+    launch_result(P, dres, nullptr, s);
+    RTD_CUDA(cudaGetLastError());
+    RTD_CUDA(cudaMemcpyAsync(a.res, dres, sizeof(rtd_result), cudaMemcpyDeviceToHost, s));
+    RTD_CUDA(cudaStreamSynchronize(s));
+    RTD_CUDA(cudaGetLastError());
+    return a.res->status;
+}
+
+// Validation shared by the stage entry points.
+int stage_call(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+               void* workspace, size_t ws_bytes, void* stream, const StageArgs& a) {
+    rtd_options o = opt ? *opt : defaults();
+    o.graph = 0;
+    Shape S;
+    int e = make_shape(n, p, ld, h, o, S);
+    if (!e) e = check_h(S);
+    if (e) return e;
+    if (!X || o.init_mu) return RTD_EINVAL;
+    long long top = a.kind == STAGE_UNI ? p : a.kind == STAGE_FINISH ? n : S.q;
+    if (a.lo < 0 || a.hi < a.lo || a.hi > top) return RTD_EINVAL;
+    if (a.kind == STAGE_UNI && a.hi == a.lo) return RTD_EINVAL;
+    if (a.kind != STAGE_UNI && !a.uni) return RTD_EINVAL;
+    if ((a.kind == STAGE_MOMENTS || a.kind == STAGE_FINISH) && !a.fits) return RTD_EINVAL;
+    if (a.kind == STAGE_FINISH && (!a.moments || !a.res)) return RTD_EINVAL;
+    if (a.kind != STAGE_FINISH && !a.out && !(a.kind == STAGE_BLOCKS && a.hi == a.lo)) return RTD_EINVAL;
+    Regions R;
+    size_t need = layout(S, R);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RTD_EWORKSPACE;
+    if (on_other_device(X) || on_other_device(workspace) || on_other_device(a.uni) || on_other_device(a.fits) ||
+        on_other_device(a.moments) || on_other_device(a.out) || on_other_device(a.d2) || on_other_device(a.fl))
+        return RTD_EINVAL;
+    return run_stage(X, S, o, workspace, reinterpret_cast<cudaStream_t>(stream), a);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1016,6 +1288,59 @@ int rtdetmcd_fit(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, co
     int r = -1;
     if (o.graph == 1) r = run_fit_graph(X, S, o, workspace, s, out, d2_out, flags_out);
     if (r == -1) r = run_fit(X, S, o, workspace, s, out, d2_out, flags_out);
+    out->status = r;
+    return r;
+}
+
+int rtdetmcd_partition(int64_t n, int32_t p, int64_t h, const rtd_options* opt, int32_t* q, int64_t* m) {
+    rtd_options o = opt ? *opt : defaults();
+    Shape S;
+    int e = make_shape(n, p, p, h, o, S);
+    if (!e) e = check_h(S);
+    if (e) return e;
+    if (q) *q = S.q;
+    if (m) *m = S.m;
+    return RTD_OK;
+}
+
+int rtdetmcd_standardize(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                         int32_t col_lo, int32_t col_hi, void* workspace, size_t ws_bytes, void* stream,
+                         double* uni_out) {
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kind = STAGE_UNI; a.lo = col_lo; a.hi = col_hi; a.out = uni_out;
+    return stage_call(X, n, p, ld, h, opt, workspace, ws_bytes, stream, a);
+}
+
+int rtdetmcd_fit_blocks(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                        const double* uni, int32_t blk_lo, int32_t blk_hi, void* workspace, size_t ws_bytes,
+                        void* stream, double* fits_out) {
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kind = STAGE_BLOCKS; a.lo = blk_lo; a.hi = blk_hi; a.uni = uni; a.out = fits_out;
+    return stage_call(X, n, p, ld, h, opt, workspace, ws_bytes, stream, a);
+}
+
+int rtdetmcd_reweight_moments(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                              const double* uni, const double* fits, int32_t blk_lo, int32_t blk_hi,
+                              void* workspace, size_t ws_bytes, void* stream, double* moments_out) {
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kind = STAGE_MOMENTS; a.lo = blk_lo; a.hi = blk_hi; a.uni = uni; a.fits = fits; a.out = moments_out;
+    return stage_call(X, n, p, ld, h, opt, workspace, ws_bytes, stream, a);
+}
+
+int rtdetmcd_reweight_finish(const float* X, int64_t n, int32_t p, int64_t ld, int64_t h, const rtd_options* opt,
+                             const double* uni, const double* fits, const double* moments, int64_t row_lo,
+                             int64_t row_hi, void* workspace, size_t ws_bytes, void* stream, rtd_result* out,
+                             float* d2_out, uint8_t* flags_out) {
+    if (!out) return RTD_EINVAL;
+    memset(out, 0, sizeof(*out));
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kind = STAGE_FINISH; a.lo = row_lo; a.hi = row_hi; a.uni = uni; a.fits = fits; a.moments = moments;
+    a.res = out; a.d2 = d2_out; a.fl = flags_out;
+    int r = stage_call(X, n, p, ld, h, opt, workspace, ws_bytes, stream, a);
     out->status = r;
     return r;
 }

@@ -31,6 +31,7 @@ struct Plan {
     int win_rows;           // rows per CTA, at least, of the window distance pass (0: the kernel's own)
     int sel_ctas;           // CTAs per chain of the window selection (0: 8)
     int key_bytes;          // 4 (FP32 form) or 8 (FP64 form) for refinement sorts
+    long long t0;           // first permuted position of block 0 (a block range of a larger partition)
     Feistel F;
     // device buffers
     Status* st;
@@ -79,6 +80,11 @@ void launch_band64(const Plan& P, cudaStream_t s);
 void launch_compact(const Plan& P, cudaStream_t s);
 void launch_memb(const Plan& P, cudaStream_t s);
 void launch_rew(const Plan& P, cudaStream_t s);
+// ---- the fit in stages (rtd_small.cu)
+void launch_block_fits_out(const Plan& P, double* out, cudaStream_t s);
+void launch_block_fits_in(const Plan& P, const double* in, cudaStream_t s);
+void launch_moments_out(const Plan& P, double* out, cudaStream_t s);
+void launch_moments_finalize(const Plan& P, const double* in, cudaStream_t s);
 void launch_final(const Plan& P, float* d2_out, uint8_t* flags_out, cudaStream_t s);
 void launch_subset_out(const Plan& P, uint8_t* out, cudaStream_t s);
 void launch_member_gram(const Plan& P, cudaStream_t s);

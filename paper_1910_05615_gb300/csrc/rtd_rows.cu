@@ -8,12 +8,12 @@ namespace rtd {
 // =====================================================================
 // Partition (Section 4): permuted, padded copy of the rows.
 // =====================================================================
-__global__ void k_gather(const float* __restrict__ X, long long ld, int p, int pb, long long nq,
+__global__ void k_gather(const float* __restrict__ X, long long ld, int p, int pb, long long nq, long long t0,
                          Feistel F, float* __restrict__ Xp, int* __restrict__ perm, Status* st) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const bool vec = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += stride) {
-        long long src = feistel_perm(F, t);
+        long long src = feistel_perm(F, t0 + t);
         float4* dst = reinterpret_cast<float4*>(Xp + t * pb);
         if (src < 0) {
             set_error(st, RTD_EINTERNAL);
@@ -41,7 +41,7 @@ __global__ void k_gather(const float* __restrict__ X, long long ld, int p, int p
 void launch_gather(const Plan& P, cudaStream_t s) {
     long long nq = (long long)P.q * P.m;
     int grid = P.nsm * 8;
-    k_gather<<<grid, NT, 0, s>>>(P.X, P.ld, P.p, P.pb, nq, P.F, P.Xp, P.perm, P.st);
+    k_gather<<<grid, NT, 0, s>>>(P.X, P.ld, P.p, P.pb, nq, P.t0, P.F, P.Xp, P.perm, P.st);
 }
 
 // =====================================================================

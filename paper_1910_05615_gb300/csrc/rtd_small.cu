@@ -1161,4 +1161,107 @@ void launch_score_prep(const double* mu, const double* Sigma, int p, RowParams* 
     k<<<1, CT, sm, s>>>(mu, Sigma, p, rp, st, logdet_out);
 }
 
+// =====================================================================
+// The fit in stages (a fit sharded over processes).  A block-fit record is
+// [chosen start (-1 none, 0, 1), log det Sigma_l, mu_l[p], Sigma_l[p^2]] in
+// Z units, Sigma_l = Lambda/(h_b - 1) without c(alpha): what steps 5-7 read
+// of each block (Section 4 steps 4-7).
+// =====================================================================
+__global__ void k_block_fits_out(const Chain* __restrict__ ch, const Consts* __restrict__ cs,
+                                 const int* __restrict__ chosen, double* out) {
+    const int l = blockIdx.x, p = cs->p;
+    const size_t rd = 2 + (size_t)p + (size_t)p * p;
+    double* r = out + (size_t)l * rd;
+    const int c = chosen[l];
+    if (c < 0) {
+        for (size_t e = threadIdx.x; e < rd; e += blockDim.x) r[e] = (e == 0) ? -1.0 : 0.0;
+        return;
+    }
+    const Chain& C = ch[2 * l + c];
+    if (threadIdx.x == 0) { r[0] = (double)c; r[1] = C.logdet; }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) r[2 + j] = C.mu[j];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) r[2 + p + e] = C.Sigma[(e / p) * PMAX + e % p];
+}
+
+void launch_block_fits_out(const Plan& P, double* out, cudaStream_t s) {
+    k_block_fits_out<<<P.q, 128, 0, s>>>(P.ch, P.cs, P.chosen, out);
+}
+
+// Records of all q blocks into the chains that steps 5-7 read; a record
+// whose start is not -1, 0 or 1, or whose values are not finite, is refused.
+__global__ void k_block_fits_in(Chain* ch, const Consts* __restrict__ cs, int* chosen, const double* __restrict__ in,
+                                Status* st) {
+    const int l = blockIdx.x, p = cs->p;
+    const size_t rd = 2 + (size_t)p + (size_t)p * p;
+    const double* r = in + (size_t)l * rd;
+    const double cd = r[0];
+    const int c = (cd == 0.0) ? 0 : (cd == 1.0) ? 1 : (cd == -1.0) ? -1 : -2;
+    if (c == -2) {
+        if (threadIdx.x == 0) { chosen[l] = -1; set_error(st, RTD_EINVAL); }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        chosen[l] = c;
+        if (c < 0) set_warning(st, RTD_WARN_NO_BLOCK_FIT);
+    }
+    if (c < 0) return;
+    Chain& C = ch[2 * l + c];
+    bool bad = false;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        C.mu[j] = r[2 + j];
+        bad |= !isfinite(r[2 + j]);
+    }
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        C.Sigma[(e / p) * PMAX + e % p] = r[2 + p + e];
+        bad |= !isfinite(r[2 + p + e]);
+    }
+    if (bad) set_error(st, RTD_EINVAL);
+    if (threadIdx.x == 0) { C.logdet = r[1]; C.status = CH_OK; C.started = 1; }
+}
+
+void launch_block_fits_in(const Plan& P, const double* in, cudaStream_t s) {
+    k_block_fits_in<<<P.q, 128, 0, s>>>(P.ch, P.cs, P.chosen, in, P.st);
+}
+
+// Reweighting moments [count, sum of (x - c), sum of (x - c)(x - c)^T] with
+// c the raw centre in X units, from / to the extended Gram of the
+// reweighting pass (entry (i, p) is the sum of coordinate i, (p, p) the
+// count).
+__global__ void k_moments_out(const Consts* __restrict__ cs, const double* __restrict__ gsum, double* out) {
+    const int p = cs->p, nb = gram_nb(cs->pb);
+    for (int e = threadIdx.x; e < 1 + p + p * p; e += blockDim.x) {
+        double v;
+        if (e == 0) v = gram_get(gsum, p, p, nb);
+        else if (e <= p) v = gram_get(gsum, e - 1, p, nb);
+        else v = gram_get(gsum, (e - 1 - p) / p, (e - 1 - p) % p, nb);
+        out[e] = v;
+    }
+}
+
+void launch_moments_out(const Plan& P, double* out, cudaStream_t s) {
+    launch_reduce_slots(P, 1, s);
+    k_moments_out<<<1, 256, 0, s>>>(P.cs, P.gsum, out);
+}
+
+__global__ void k_moments_in(const Consts* __restrict__ cs, const double* __restrict__ in, double* gsum,
+                             size_t slot_d) {
+    const int p = cs->p, nb = gram_nb(cs->pb);
+    for (size_t e = threadIdx.x; e < slot_d; e += blockDim.x) gsum[e] = 0.0;
+    __syncthreads();
+    const int pe = p + 1;
+    for (int e = threadIdx.x; e < pe * pe; e += blockDim.x) {
+        const int i = e / pe, j = e % pe;
+        if (i > j) continue;
+        double v;
+        if (j == p) v = (i == p) ? in[0] : in[1 + i];
+        else v = in[1 + p + i * p + j];
+        gsum[gram_blk_index(i >> 2, j >> 2, nb) * 16 + (i & 3) * 4 + (j & 3)] = v;
+    }
+}
+
+void launch_moments_finalize(const Plan& P, const double* in, cudaStream_t s) {
+    k_moments_in<<<1, 256, 0, s>>>(P.cs, in, P.gsum, P.slot_doubles);
+    k_rew_finalize<<<1, 256, 0, s>>>(P.cs, P.fitrp, P.gsum, P.st);
+}
+
 }  // namespace rtd

@@ -192,3 +192,44 @@ def test_fit_batch_rejects_before_device_work(lib):
     assert one > 0 and lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 2) == 2 * one
     assert lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 8) == 3 * one   # at most one slice per frame
     assert lib.rtdetmcd_fit_batch_workspace_size(F, n, p, None, 0) == 0
+
+
+def test_stage_calls_reject_before_device_work(lib):
+    """The stage entry points of a sharded fit refuse ranges outside
+    [0, p), [0, q), [0, n) and missing pointers (RTD_EINVAL) before looking
+    at the workspace (RTD_EWORKSPACE when it is missing)."""
+    n, p, h = 40_000, 3, 30_000
+    X = np.zeros((n, p), np.float32)
+    q, m = ctypes.c_int32(0), ctypes.c_int64(0)
+    assert lib.rtdetmcd_partition(n, p, h, None, ctypes.byref(q), ctypes.byref(m)) == 0
+    assert (q.value, m.value) == (3, n // 3)
+    assert lib.rtdetmcd_partition(n, p, n, None, ctypes.byref(q), ctypes.byref(m)) == 1   # h = n
+    out = np.zeros(4 * p * p + 64)
+    uni = np.concatenate([np.zeros(p), np.ones(p)])
+    fits = np.zeros(3 * (2 + p + p * p))
+    mom = np.zeros(1 + p + p * p)
+    x = X.ctypes.data
+    std = lambda lo, hi, o: lib.rtdetmcd_standardize(x, n, p, p, h, None, lo, hi, None, 0, None, o)  # noqa: E731
+    assert std(0, 0, out.ctypes.data) == 1            # empty column range
+    assert std(1, p + 1, out.ctypes.data) == 1
+    assert std(0, p, None) == 1
+    assert std(0, p, out.ctypes.data) == 5            # valid: only the workspace is missing
+    blk = lambda lo, hi, u: lib.rtdetmcd_fit_blocks(x, n, p, p, h, None, u, lo, hi, None, 0, None,  # noqa: E731
+                                                   out.ctypes.data)
+    assert blk(0, 4, uni.ctypes.data) == 1
+    assert blk(2, 1, uni.ctypes.data) == 1
+    assert blk(0, 3, None) == 1
+    assert blk(3, 3, uni.ctypes.data) == 5
+    mo = lambda lo, hi, f: lib.rtdetmcd_reweight_moments(x, n, p, p, h, None, uni.ctypes.data, f, lo, hi,  # noqa
+                                                         None, 0, None, out.ctypes.data)
+    assert mo(-1, 2, fits.ctypes.data) == 1
+    assert mo(0, 2, None) == 1
+    assert mo(0, 3, fits.ctypes.data) == 5
+    import paper_1910_05615_gb300 as M
+    m_res = M._Result()
+    fin = lambda lo, hi, mm: lib.rtdetmcd_reweight_finish(x, n, p, p, h, None, uni.ctypes.data,  # noqa: E731
+                                                          fits.ctypes.data, mm, lo, hi, None, 0, None,
+                                                          ctypes.byref(m_res), None, None)
+    assert fin(0, n + 1, mom.ctypes.data) == 1 and m_res.status == 1
+    assert fin(0, n, None) == 1
+    assert fin(5, n, mom.ctypes.data) == 5
