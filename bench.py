@@ -37,8 +37,8 @@ CPU_SAMPLE_ROWS = 655_360
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_dist_win launch at
-# n=1e6, p=20 with both chains of every block active (80.22 MB + 3.35 MB)
-K_DIST_TRAFFIC = 83.57e6
+# n=1e6, p=20 with both chains of every block active (80.22 MB + 3.64 MB)
+K_DIST_TRAFFIC = 83.86e6
 
 
 def selection_stats(pp):

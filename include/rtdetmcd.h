@@ -359,7 +359,7 @@ int rtdetmcd_score(const float* X, int64_t n, int32_t p, int64_t ld, const doubl
                    const double* sigma_host, double cutoff_d2, int32_t precision, float* d2_out,
                    uint8_t* flags_out, int64_t* n_flagged, void* workspace, size_t ws_bytes, void* stream);
 
-/* Size of the fixed device array used by rtdetmcd_distances_noalloc. *//* Size of the fixed device array used by rtdetmcd_distances_noalloc. */
+/* Size of the fixed device array used by rtdetmcd_distances_noalloc. */
 #define RTD_NOALLOC_SCRATCH_BYTES (96 * 1024)
 
 /*

@@ -47,7 +47,7 @@ struct Shape {
 struct Regions {
     Region st, cs, ch, rule, fitrp, res, xstage, d2stage, flagstage, substage, diagstage,
         Xp, perm, arenaA, arenaB, sort_hist, uni, uscratch, gss, dkeys, memb, cand, segcnt, band, hist, swaps,
-        blk, partial, gsum, wset, chosen, amb, kept, kl, scratch, fits, moments;
+        blk, partial, gsum, wset, chosen, amb, kept, kl, scratch, fits, moments, sort_tot;
 };
 
 rtd_options defaults() {
@@ -146,6 +146,7 @@ size_t layout(const Shape& S, Regions& R) {
     size_t h2 = 2 * p * q * 256 * tiles_of(S.m);
     if (h2 > hs) hs = h2;
     R.sort_hist = L.add(hs * sizeof(unsigned));
+    R.sort_tot = L.add(2 * (2 * p * q > p ? 2 * p * q : p) * 256 * sizeof(unsigned));
     R.uni = L.add(4 * ((2 * p * q > p) ? 2 * p * q : p) * sizeof(double));
     {
         size_t a = unimcd_scratch_doubles((int)p, S.n), b = unimcd_scratch_doubles(2 * (int)(p * q), S.m);
@@ -357,6 +358,7 @@ int make_plan(const float* X, const Shape& S, const rtd_options& o, void* ws, co
     P.arenaA = at<void>(ws, R.arenaA);
     P.arenaB = at<void>(ws, R.arenaB);
     P.sort_hist = at<unsigned>(ws, R.sort_hist);
+    P.sort_tot = at<unsigned>(ws, R.sort_tot);
     P.uni = at<double>(ws, R.uni);
     P.uscratch = at<double>(ws, R.uscratch);
     P.gss = at<double>(ws, R.gss);

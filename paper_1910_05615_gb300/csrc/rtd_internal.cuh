@@ -45,6 +45,7 @@ struct Plan {
     void* arenaA;           // sort arena (ping)
     void* arenaB;           // sort arena (pong)
     unsigned* sort_hist;
+    unsigned* sort_tot;     // [2][segments][256] digit totals of the sort passes
     double* uni;            // per-segment univariate MCD results (4 doubles)
     double* uscratch;       // univariate MCD chunk sums and window argmins
     double* gss;            // per-block GSSCM cutoffs (A, B)

@@ -18,7 +18,7 @@ constexpr int SKPW = STILE / SW;        // keys per warp
 
 template <typename K>
 __global__ void __launch_bounds__(ST) k_sort_hist(const K* __restrict__ keys, long long L, int tiles,
-                                                  int shift, unsigned* __restrict__ hist) {
+                                                  int shift, unsigned* __restrict__ hist, unsigned* __restrict__ tot) {
     __shared__ unsigned h[256];
     const int seg = blockIdx.y, tile = blockIdx.x;
     h[threadIdx.x] = 0;
@@ -28,16 +28,33 @@ __global__ void __launch_bounds__(ST) k_sort_hist(const K* __restrict__ keys, lo
     const K* in = keys + (long long)seg * L + t0;
     for (int i = threadIdx.x; i < cnt; i += ST) atomicAdd(&h[(unsigned)(in[i] >> shift) & 255u], 1u);
     __syncthreads();
-    hist[((size_t)seg * 256 + threadIdx.x) * tiles + tile] = h[threadIdx.x];
+    const unsigned c = h[threadIdx.x];
+    hist[((size_t)seg * 256 + threadIdx.x) * tiles + tile] = c;
+    if (c) atomicAdd(&tot[(size_t)seg * 256 + threadIdx.x], c);   // the segment's digit totals
 }
 
-// Exclusive scan of one segment's 256 * tiles counters (one CTA per segment):
-// per-thread runs, then warp-shuffle scans of the run totals.
-__global__ void __launch_bounds__(1024) k_sort_scan(unsigned* __restrict__ hist, int tiles) {
+// Exclusive scan of one segment's 256 * tiles counters in (digit, tile)
+// order, by CTAs of dpc digits each: a CTA starts at the sum of the digit
+// totals before its first digit (from k_sort_hist) and scans its dpc * tiles
+// counters (per-thread runs, then warp-shuffle scans of the run totals).
+// It also clears its digits' totals for the next pass (tot_next).
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned* __restrict__ hist, int tiles, int dpc,
+                                                    const unsigned* __restrict__ tot, unsigned* __restrict__ tot_next) {
     __shared__ unsigned wsum[32];
-    const long long N = 256LL * tiles;
-    unsigned* a = hist + (size_t)blockIdx.x * N;
+    __shared__ unsigned s_base;
+    const int seg = blockIdx.y, d0 = blockIdx.x * dpc;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    {
+        unsigned v = threadIdx.x < d0 ? tot[(size_t)seg * 256 + threadIdx.x] : 0u;   // d0 < 256 <= threads
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) s_base = 0u;
+        __syncthreads();
+        if (lane == 0 && v) atomicAdd(&s_base, v);
+        if (threadIdx.x < dpc) tot_next[(size_t)seg * 256 + d0 + threadIdx.x] = 0u;
+    }
+    const long long N = (long long)dpc * tiles;
+    unsigned* a = hist + ((size_t)seg * 256 + d0) * tiles;
     long long per = (N + blockDim.x - 1) / blockDim.x;
     long long b = threadIdx.x * per, e = b + per < N ? b + per : N;
     unsigned s = 0;
@@ -62,7 +79,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(unsigned* __restrict__ hist,
         if (lane < nw) wsum[lane] = z - t;
     }
     __syncthreads();
-    unsigned run = wsum[w] + x - s;
+    unsigned run = s_base + wsum[w] + x - s;
     for (long long i = b; i < e; ++i) {
         unsigned v = a[i];
         a[i] = run;
@@ -175,10 +192,16 @@ static void sort_t(const Plan& P, K* keys, K* tmp, int nseg, long long L, cudaSt
     const int passes = (int)sizeof(K);
     K* a = keys;
     K* b = tmp;
+    // digit totals of the passes, in two alternating buffers (the scan of
+    // one pass clears the other for the next)
+    unsigned* tot[2] = {P.sort_tot, P.sort_tot + (size_t)nseg * 256};
+    cudaMemsetAsync(P.sort_tot, 0, 2 * (size_t)nseg * 256 * sizeof(unsigned), s);
+    int dpc = 1;   // digits per scan CTA: about 4096 counters each
+    while (dpc < 256 && (long long)dpc * tiles < 4096) dpc <<= 1;
     for (int ps = 0; ps < passes; ++ps) {
         int shift = 8 * ps;
-        k_sort_hist<K><<<grid, ST, 0, s>>>(a, L, tiles, shift, P.sort_hist);
-        k_sort_scan<<<nseg, 1024, 0, s>>>(P.sort_hist, tiles);
+        k_sort_hist<K><<<grid, ST, 0, s>>>(a, L, tiles, shift, P.sort_hist, tot[ps & 1]);
+        k_sort_scan<<<dim3(256 / dpc, nseg), 1024, 0, s>>>(P.sort_hist, tiles, dpc, tot[ps & 1], tot[(ps + 1) & 1]);
         k_sort_scatter<K><<<grid, ST, 0, s>>>(a, b, L, tiles, shift, P.sort_hist);
         K* t = a; a = b; b = t;
     }

@@ -144,6 +144,28 @@ def test_fit_small_case(rtd, form):
 
 
 @pytest.mark.parametrize("form", ["fp32", "fp64"])
+def test_fit_column_of_close_values(rtd, form):
+    """A column whose values all share their high 24 key bits (1 + j 2^-23,
+    j < 256, in random order, heavy ties) and a column with one value in 30%
+    of the rows: long runs of keys that differ only in the lowest digit, and
+    long runs of equal keys, in every sort pass."""
+    import types
+    rng = np.random.default_rng(21)
+    n, p = 30_011, 3
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    X[:, 1] = (1.0 + rng.integers(0, 256, n) * 2.0 ** -23).astype(np.float32)
+    X[rng.random(n) < 0.3, 2] = np.float32(0.75)
+    fr = types.SimpleNamespace(X=X, h=(3 * n) // 4)
+    got, ref = _fit_both(rtd, fr, form, q=3)
+    d = got["diag"]
+    np.testing.assert_allclose(d["mu_uni"], ref.mu_uni, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(d["sigma_uni"], ref.s_uni, rtol=1e-10)
+    ok, rep = compare_fit(got, ref, X, form)
+    if not ok:
+        pytest.fail(str(rep))
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp64"])
 def test_fit_blocks(rtd, form):
     """Parallel algorithm: q = 9 blocks of a ragged n (discarded rows)."""
     fr = datagen.contaminated_gaussian(184_331, 5, eps=0.15, kind="shift", shift=6.0, seed=4)
