@@ -359,6 +359,31 @@ int rtdetmcd_score(const float* X, int64_t n, int32_t p, int64_t ld, const doubl
                    const double* sigma_host, double cutoff_d2, int32_t precision, float* d2_out,
                    uint8_t* flags_out, int64_t* n_flagged, void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * Scoring many batches of rows against one fit (Section 6: every image of a
+ * sorting line scored with the same fit).  rtdetmcd_score_prepare factorises
+ * the fit (mu, sigma as for rtdetmcd_score, row-major p x p, host memory)
+ * once into `prepared`: device memory of the current device, at least
+ * rtdetmcd_prepared_size() bytes, 256-byte aligned, owned by the caller.  It
+ * waits for the factorisation and returns its status (RTD_EDEGENERATE when
+ * sigma is not positive definite; a prepared fit in that state makes the
+ * FP32 scoring pass write nothing).
+ * rtdetmcd_score_prepared then scores n rows in one kernel launch on `stream`
+ * and returns without waiting for it: the d2_out, flags_out and count of
+ * rtdetmcd_score (d2 and flags nullable), all device memory of the current
+ * device; count (nullable, needs flags_out) is one 64-bit counter to which
+ * the pass adds its number of flagged rows (the caller zeroes it).  p must be
+ * the prepared fit's.  Argument errors come back at once; the pass has no
+ * data-dependent errors.  Calls may overlap on several streams: the prepared
+ * fit is only read.
+ */
+size_t rtdetmcd_prepared_size(void);
+int rtdetmcd_score_prepare(const double* mu_host, const double* sigma_host, int32_t p, double cutoff_d2,
+                           void* prepared, void* stream);
+int rtdetmcd_score_prepared(const float* X, int64_t n, int32_t p, int64_t ld, const void* prepared,
+                            int32_t precision, float* d2_out, uint8_t* flags_out, unsigned long long* count,
+                            void* stream);
+
 /* Size of the fixed device array used by rtdetmcd_distances_noalloc. */
 #define RTD_NOALLOC_SCRATCH_BYTES (96 * 1024)
 

@@ -26,6 +26,7 @@ __all__ = [
     "rtdetmcd_fit_batch_workspace_size", "rtdetmcd_vjp", "rtdetmcd_fit_outputs", "rtdetmcd_score",
     "rtdetmcd_score_workspace_size", "rtdetmcd_autotune", "rtdetmcd_tuned", "rtdetmcd_partition",
     "rtdetmcd_standardize", "rtdetmcd_fit_blocks", "rtdetmcd_reweight_moments", "rtdetmcd_reweight_finish",
+    "rtdetmcd_prepared_size", "rtdetmcd_score_prepare", "rtdetmcd_score_prepared",
 ]
 
 RTD_FP64 = 0
@@ -118,6 +119,12 @@ def _load():
     lib.rtdetmcd_score_workspace_size.restype = sz
     lib.rtdetmcd_score.argtypes = [vp, i64, i32, i64, vp, vp, dbl, i32, vp, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.rtdetmcd_score.restype = i32
+    lib.rtdetmcd_prepared_size.argtypes = []
+    lib.rtdetmcd_prepared_size.restype = sz
+    lib.rtdetmcd_score_prepare.argtypes = [vp, vp, i32, dbl, vp, vp]
+    lib.rtdetmcd_score_prepare.restype = i32
+    lib.rtdetmcd_score_prepared.argtypes = [vp, i64, i32, i64, vp, i32, vp, vp, vp, vp]
+    lib.rtdetmcd_score_prepared.restype = i32
     lib.rtdetmcd_distances_noalloc.argtypes = [vp, i64, i32, i64, vp, vp, i32, vp, vp]
     lib.rtdetmcd_distances_noalloc.restype = i32
     P64, P32 = ctypes.POINTER(i64), ctypes.POINTER(i32)
@@ -612,6 +619,52 @@ def rtdetmcd_score(X, mu, Sigma, cutoff_d2=None, *, precision=RTD_FP32, d2=True,
     if st != 0:
         raise RtdError(st, lib.rtdetmcd_status_string(st).decode())
     return d2o, flo, cnt.value
+
+
+def rtdetmcd_prepared_size():
+    return _load().rtdetmcd_prepared_size()
+
+
+def rtdetmcd_score_prepare(mu, Sigma, cutoff_d2=None, *, device=None, stream=None, out=None):
+    """Factorise the fit (mu, Sigma; X units) once for scoring many batches
+    (Section 6): returns the prepared fit, a uint8 CUDA tensor (or fills
+    `out`).  Raises RtdError if Sigma is not positive definite."""
+    torch = _torch()
+    lib = _load()
+    mu_c = np.ascontiguousarray(mu, dtype=np.float64).reshape(-1)
+    p = mu_c.size
+    S_c = np.ascontiguousarray(Sigma, dtype=np.float64).reshape(p, p)
+    if cutoff_d2 is None:
+        cutoff_d2 = rtdetmcd_chi2_quantile(p, 0.975)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    prep = out if out is not None else torch.empty(lib.rtdetmcd_prepared_size(), dtype=torch.uint8, device=dev)
+    st = lib.rtdetmcd_score_prepare(mu_c.ctypes.data, S_c.ctypes.data, p, float(cutoff_d2), prep.data_ptr(),
+                                    _stream_ptr(prep.device, stream))
+    _status(lib, st, True)
+    return prep
+
+
+def rtdetmcd_score_prepared(X, prepared, *, precision=RTD_FP32, d2=True, flags=True, count=None, stream=None,
+                            d2_out=None, flags_out=None):
+    """Score the rows of X (a CUDA tensor) against a prepared fit with one
+    kernel launch and no wait: returns (d2, flags) CUDA tensors (None where
+    not asked for).  `count` (int64 CUDA tensor of one element, nullable)
+    receives the number of flagged rows added to its value."""
+    lib = _load()
+    ptr, n, p, ld, dev, keep = _rows(X)
+    if dev is None:
+        raise ValueError("rtdetmcd_score_prepared needs X on a CUDA device")
+    if d2_out is None and d2:
+        d2_out = _out(n, np.float32, dev)
+    if flags_out is None and flags:
+        flags_out = _out(n, np.uint8, dev)
+    if count is not None and (count.dtype != _torch().int64 or count.numel() != 1 or not count.is_cuda):
+        raise ValueError("count must be a one-element int64 CUDA tensor")
+    st = lib.rtdetmcd_score_prepared(ptr, n, p, ld, prepared.data_ptr(), precision, _ptr(d2_out), _ptr(flags_out),
+                                     _ptr(count), _stream_ptr(dev, stream))
+    del keep
+    _status(lib, st, True)
+    return d2_out, flags_out
 
 
 def rtdetmcd_distances_noalloc(X, mu, Sigma, *, precision=RTD_FP32, out=None, stream=None):

@@ -1568,7 +1568,7 @@ int rtdetmcd_score(const float* X, int64_t n, int32_t p, int64_t ld, const doubl
     float* d2 = d2_out ? (ddev ? d2_out : at<float>(workspace, rds)) : nullptr;
     uint8_t* fl = flags_out ? (fdev ? flags_out : at<uint8_t>(workspace, rfs)) : nullptr;
     launch_score_prep_arg(a, p, cutoff_d2, rp, st, at<double>(workspace, rcut), s);
-    launch_score_flags(Xd, n, p, ldd, rp, precision, cutoff_d2, at<double>(workspace, rcut), d2, fl,
+    launch_score_flags(Xd, n, p, ldd, rp, precision, at<double>(workspace, rcut), st, d2, fl,
                        &st->n_flagged, s);
     if (d2_out && !ddev) RTD_CUDA(cudaMemcpyAsync(d2_out, d2, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (flags_out && !fdev) RTD_CUDA(cudaMemcpyAsync(flags_out, fl, (size_t)n, cudaMemcpyDeviceToHost, s));
@@ -1577,6 +1577,65 @@ int rtdetmcd_score(const float* X, int64_t n, int32_t p, int64_t ld, const doubl
     if (e) return e;
     if (n_flagged) *n_flagged = flags_out ? (int64_t)hs.n_flagged : -1;
     return hs.code;
+}
+
+// A prepared fit: the status word, the row parameters and the cutoff, laid
+// out as the first three regions of the scoring workspace.
+size_t rtdetmcd_prepared_size(void) {
+    Layout L;
+    L.add(sizeof(Status));
+    L.add(sizeof(RowParams));
+    L.add(sizeof(double));
+    return (L.total + 255) & ~(size_t)255;
+}
+
+int rtdetmcd_score_prepare(const double* mu_host, const double* sigma_host, int32_t p, double cutoff_d2,
+                           void* prepared, void* stream) {
+    if (!mu_host || !sigma_host || p < 1 || p > RTD_MAX_P || !std::isfinite(cutoff_d2)) return RTD_EINVAL;
+    if (!prepared || (reinterpret_cast<uintptr_t>(prepared) & 255) || !is_device_ptr(prepared) ||
+        on_other_device(prepared))
+        return RTD_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Layout L;
+    Region rst = L.add(sizeof(Status));
+    Region rrp = L.add(sizeof(RowParams));
+    Region rcut = L.add(sizeof(double));
+    FitArg a;
+    for (int j = 0; j < p; ++j) a.mu[j] = mu_host[j];
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j <= i; ++j) a.tri[i * (i + 1) / 2 + j] = sigma_host[(size_t)i * p + j];
+    Status* st = at<Status>(prepared, rst);
+    launch_score_prep_arg(a, p, cutoff_d2, at<RowParams>(prepared, rrp), st, at<double>(prepared, rcut), s);
+    Status hs;
+    int e = fetch_status(st, s, hs);
+    return e ? e : hs.code;
+}
+
+int rtdetmcd_score_prepared(const float* X, int64_t n, int32_t p, int64_t ld, const void* prepared,
+                            int32_t precision, float* d2_out, uint8_t* flags_out, unsigned long long* count,
+                            void* stream) {
+    if (!X || !prepared || n < 1 || n >= (1LL << 31) || p < 1 || p > RTD_MAX_P || ld < p ||
+        (precision != RTD_FP32 && precision != RTD_FP64) || (reinterpret_cast<uintptr_t>(prepared) & 255))
+        return RTD_EINVAL;
+    if (count && !flags_out) return RTD_EINVAL;
+    int dev = 0;
+    RTD_CUDA(cudaGetDevice(&dev));
+    const void* dev_ptrs[5] = {X, prepared, d2_out, flags_out, count};
+    for (const void* q : dev_ptrs) {   // device memory of the current device, one query each
+        if (!q) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) { cudaGetLastError(); return RTD_EINVAL; }
+        if (a.type != cudaMemoryTypeDevice || a.device != dev) return RTD_EINVAL;
+    }
+    Layout L;
+    Region rst = L.add(sizeof(Status));
+    Region rrp = L.add(sizeof(RowParams));
+    Region rcut = L.add(sizeof(double));
+    void* pp = const_cast<void*>(prepared);
+    launch_score_flags(X, n, p, ld, at<RowParams>(pp, rrp), precision, at<double>(pp, rcut), at<Status>(pp, rst),
+                       d2_out, flags_out, count, reinterpret_cast<cudaStream_t>(stream));
+    RTD_CUDA(cudaGetLastError());
+    return RTD_OK;
 }
 
 size_t rtdetmcd_grad_workspace_size(int64_t n, int32_t p) {

@@ -139,9 +139,10 @@ void launch_score_prep_arg(const FitArg& a, int p, double cut, RowParams* rp, St
                            cudaStream_t s);
 // Distances and flags of the scoring call in one pass (Section 6): d2_out
 // and flags nullable; FP32 rows decide in FP64 near the cutoff.  cut_dev:
-// the cutoff in device memory (FP64 form).
+// the cutoff in device memory; st: the status word of the fit's
+// preparation (the FP32 pass writes nothing when it holds an error).
 void launch_score_flags(const float* X, long long n, int p, long long ld, const RowParams* rp, int precision,
-                        double cut, const double* cut_dev, float* d2_out, uint8_t* flags,
+                        const double* cut_dev, const Status* st, float* d2_out, uint8_t* flags,
                         unsigned long long* count, cudaStream_t s);
 // adjoint of steps 8-10 (rtd_rows.cu): slot count of the reduction pass
 constexpr int GRAD_SLOTS = 1024;

@@ -1,5 +1,7 @@
 // rtd_rows.cu - row kernels that do not depend on the padded width, and the
 // dispatch of the width-templated ones (instantiated in rtd_rows_pb*.cu).
+#include <atomic>
+
 #include "rtd_rows.cuh"
 #include "rtd_rows_api.cuh"
 
@@ -137,8 +139,10 @@ void launch_compact(const Plan& P, cudaStream_t s) {
 
 // ---------------------------------------------------------------- flags
 // Four distances per thread and step (one 16-byte load, one 4-byte store)
-// when d2 and flags are 16- and 4-byte aligned; one otherwise.
-__global__ void k_flag(const float* __restrict__ d2, long long n, double cut, uint8_t* __restrict__ flags,
+// when d2 and flags are 16- and 4-byte aligned; one otherwise.  cut_f is
+// the largest float not above the cutoff, so x > cut_f exactly when the
+// float x exceeds the FP64 cutoff (one FP32 compare per distance).
+__global__ void k_flag(const float* __restrict__ d2, long long n, float cut, uint8_t* __restrict__ flags,
                        unsigned long long* __restrict__ count) {
     int nf = 0;
     const bool vec = ((reinterpret_cast<uintptr_t>(d2) & 15) == 0) &&
@@ -147,12 +151,12 @@ __global__ void k_flag(const float* __restrict__ d2, long long n, double cut, ui
     const long long stride = (long long)gridDim.x * NT;
     for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < nv; v += stride) {
         const float4 q = __ldg(reinterpret_cast<const float4*>(d2) + v);
-        const unsigned o0 = (double)q.x > cut, o1 = (double)q.y > cut, o2 = (double)q.z > cut, o3 = (double)q.w > cut;
+        const unsigned o0 = q.x > cut, o1 = q.y > cut, o2 = q.z > cut, o3 = q.w > cut;
         if (flags) reinterpret_cast<unsigned*>(flags)[v] = o0 | (o1 << 8) | (o2 << 16) | (o3 << 24);
         nf += (int)(o0 + o1 + o2 + o3);
     }
     for (long long i = 4 * nv + (long long)blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
-        const bool o = (double)d2[i] > cut;
+        const bool o = d2[i] > cut;
         if (flags) flags[i] = o ? 1 : 0;
         nf += o ? 1 : 0;
     }
@@ -168,7 +172,9 @@ void launch_flag(const float* d2, long long n, double cut, uint8_t* flags, unsig
     long long blocks = (n + NT - 1) / NT;
     int grid = (int)(blocks < (long long)nsm * 16 ? blocks : (long long)nsm * 16);
     if (grid < 1) grid = 1;
-    k_flag<<<grid, NT, 0, s>>>(d2, n, cut, flags, count);
+    float cut_f = (float)cut;   // the largest float not above cut
+    if ((double)cut_f > cut) cut_f = std::nextafter(cut_f, -INFINITY);
+    k_flag<<<grid, NT, 0, s>>>(d2, n, cut_f, flags, count);
 }
 
 // ------------------------------------------------------- subset output
@@ -214,18 +220,32 @@ void launch_final(const Plan& P, float* d2_out, uint8_t* flags_out, cudaStream_t
                 d2_out, flags_out, &P.st->n_flagged, P.nsm, s);
 }
 
-void launch_score_flags(const float* X, long long n, int p, long long ld, const RowParams* rp, int precision,
-                        double cut, const double* cut_dev, float* d2_out, uint8_t* flags,
-                        unsigned long long* count, cudaStream_t s) {
-    int dev = 0, nsm = 148;
+// SM count of the current device, looked up once per device (the scoring
+// calls are launched per batch of rows, where every host microsecond shows)
+static int sm_count_here() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        v = 148;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+void launch_score_flags(const float* X, long long n, int p, long long ld, const RowParams* rp, int precision,
+                        const double* cut_dev, const Status* st, float* d2_out, uint8_t* flags,
+                        unsigned long long* count, cudaStream_t s) {
+    const int nsm = sm_count_here();
     if (precision == RTD_FP64) {   // FP64 rows decide exactly: the final pass of the fit
         RTD_PB_CALL(pad_p(p), final, X, n, p, ld, precision, rp, cut_dev, flags ? 1 : 0, d2_out, flags, count,
                     nsm, s);
         return;
     }
-    RTD_PB_CALL(pad_p(p), score, X, n, p, ld, rp, cut, d2_out, flags, count, nsm, s);
+    RTD_PB_CALL(pad_p(p), score, X, n, p, ld, rp, cut_dev, st, d2_out, flags, count, nsm, s);
 }
 
 void launch_score(const float* X, long long n, int p, long long ld, const RowParams* rp,

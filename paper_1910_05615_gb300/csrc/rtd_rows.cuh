@@ -1923,9 +1923,10 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
                 s_band[atomicAdd(&s_nb, 1)] = (int)i;   // decided in band_pass
                 continue;
             }
-            const double d = (double)d2[r];
-            const bool out = d > cut;
-            if (d2_out) d2_out[i] = (float)d;
+            // outside the FP64 band of the FP32 form, d2 > cut exactly when
+            // d2 lies above the band (one FP32 compare, no FP64 operation)
+            const bool out = fp32 ? (d2[r] > cut_hi) : ((double)d2[r] > cut);
+            if (d2_out) d2_out[i] = (float)d2[r];
             if (flags) flags[i] = out ? 1 : 0;
             nflag += out ? 1 : 0;
         }
@@ -1948,14 +1949,20 @@ __global__ void __launch_bounds__(NT) k_final(const float* __restrict__ X, long 
 // of them (one row per lane), so no CTA-wide barrier sits in the loop.
 // Each thread keeps SR rows in flight.
 // =====================================================================
-template <int PB> struct ScoreRows { static constexpr int R = PB <= 8 ? 4 : (PB <= 24 ? 2 : 1); };
+template <int PB> struct ScoreRows { static constexpr int R = PB <= 4 ? 8 : (PB <= 8 ? 4 : (PB <= 24 ? 2 : 1)); };
 
+// The fit's row parameters and the cutoff come from device memory (cutp),
+// and nothing is written when the status word holds an error (a fit that
+// could not be factorised).
 template <int PB>
 __global__ void __launch_bounds__(NT) k_score(const float* __restrict__ X, long long n, int p, long long ld,
-                                              int vec4, const RowParams* __restrict__ rp, double cut,
+                                              int vec4, const RowParams* __restrict__ rp,
+                                              const double* __restrict__ cutp, const Status* __restrict__ st,
                                               float* __restrict__ d2_out, uint8_t* __restrict__ flags,
                                               unsigned long long* __restrict__ count) {
     constexpr int R = ScoreRows<PB>::R;
+    if (st->code) return;
+    const double cut = *cutp;
     constexpr int QCAP = 32 * (R + 1);
     __shared__ float sM[PB * PB];
     __shared__ float s_hi[PB], s_lo[PB];
@@ -2014,7 +2021,7 @@ __global__ void __launch_bounds__(NT) k_score(const float* __restrict__ X, long 
             const bool valid = i < n;
             const bool band = valid && decide && d2[r] >= cut_lo && d2[r] <= cut_hi;
             if (valid && !band) {
-                const bool out = (double)d2[r] > cut;
+                const bool out = d2[r] > cut_hi;   // outside the band: exact in FP32
                 if (d2_out) d2_out[i] = d2[r];
                 if (decide) {
                     flags[i] = out ? 1 : 0;
@@ -2036,16 +2043,302 @@ __global__ void __launch_bounds__(NT) k_score(const float* __restrict__ X, long 
     }
 }
 
+// The same pass for p = 4 with float4 rows: each thread scores G = 4
+// consecutive rows, so their distances leave in one float4 store and their
+// flags in one 4-byte store.  The products follow tri_d2's order (the same
+// FP32 distances as k_score and the fit's passes).  A band row's FP32
+// distance and flag are written first and overwritten by the warp's FP64
+// pass later in the same warp.
+template <int G>
+__global__ void __launch_bounds__(NT, 8) k_score4(const float* __restrict__ X, long long n, long long ld,
+                                               const RowParams* __restrict__ rp, const double* __restrict__ cutp,
+                                               const Status* __restrict__ st, float* __restrict__ d2_out,
+                                               uint8_t* __restrict__ flags, unsigned long long* __restrict__ count) {
+    static_assert(G == 4, "four rows per thread: one float4 of distances, one 4-byte word of flags");
+    constexpr int QCAP = 32 * (G + 1);
+    __shared__ long long s_q[NT / 32][QCAP];
+    if (st->code) return;
+    const double cut = *cutp;
+    float M[4][4], hi[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) M[i][j] = (j <= i) ? rp->Mf[i * PMAX + j] : 0.f;
+        hi[i] = rp->mu_hi[i];
+        lo[i] = rp->mu_lo[i];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float cut_lo = (float)(cut * (1.0 - BAND_EPS)), cut_hi = (float)(cut * (1.0 + BAND_EPS));
+    const bool decide = flags != nullptr;
+    long long* q = s_q[w];
+    int qn = 0;       // warp-uniform
+    int nflag = 0;
+    auto drain = [&](int k) {   // FP64 for the first k queued rows, one per lane
+        if (lane < k) {
+            const long long i = q[lane];
+            const double d = d2_fp64(X + i * ld, *rp, 4);
+            const bool out = d > cut;
+            if (d2_out) d2_out[i] = (float)d;
+            flags[i] = out ? 1 : 0;
+            nflag += out ? 1 : 0;
+        }
+        __syncwarp();
+        for (int e = lane; e + k < qn; e += 32) q[e] = q[e + k];
+        __syncwarp();
+        qn -= k;
+    };
+    const long long ngroups = (n + G - 1) / G;
+    const long long stride = (long long)gridDim.x * NT;
+    for (long long g0 = (long long)blockIdx.x * NT; g0 < ngroups; g0 += stride) {   // CTA-uniform bounds
+        const long long g = g0 + threadIdx.x;
+        const long long r0 = g * G;
+        float4 v[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {   // all loads in flight first
+            const long long i = r0 + k;
+            v[k] = (g < ngroups && i < n) ? __ldg(reinterpret_cast<const float4*>(X + i * ld))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float dd[G];
+        bool band[G], valid[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            valid[k] = g < ngroups && r0 + k < n;
+            const float c[4] = {(v[k].x - hi[0]) - lo[0], (v[k].y - hi[1]) - lo[1], (v[k].z - hi[2]) - lo[2],
+                                (v[k].w - hi[3]) - lo[3]};
+            float d2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float acc = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc += M[i][u] * c[u];
+                d2 += acc * acc;
+            }
+            dd[k] = d2;
+            band[k] = valid[k] && decide && d2 >= cut_lo && d2 <= cut_hi;
+        }
+        if (g < ngroups) {
+            uint8_t f[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const bool out = dd[k] > cut_hi;   // exact outside the band; band rows are rewritten
+                f[k] = out ? 1 : 0;
+                nflag += (valid[k] && decide && !band[k] && out) ? 1 : 0;
+            }
+            if (r0 + G <= n) {
+                if (d2_out) *reinterpret_cast<float4*>(d2_out + r0) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                if (decide)
+                    *reinterpret_cast<uchar4*>(flags + r0) = make_uchar4(f[0], f[1], f[2], f[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (!valid[k]) continue;
+                    if (d2_out) d2_out[r0 + k] = dd[k];
+                    if (decide) flags[r0 + k] = f[k];
+                }
+            }
+        }
+        __syncwarp();   // the provisional band values are stored before the FP64 pass rewrites them
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const unsigned bal = __ballot_sync(0xffffffffu, band[k]);
+            if (band[k]) q[qn + __popc(bal & ((1u << lane) - 1u))] = r0 + k;
+            qn += __popc(bal);
+        }
+        __syncwarp();
+        while (qn >= 32) drain(32);
+    }
+    __syncwarp();
+    if (qn > 0) drain(qn);
+    if (count && decide) {
+        nflag = warp_sum_int(nflag);
+        if (lane == 0 && nflag) atomicAdd(count, (unsigned long long)nflag);
+    }
+}
+
+// The same pass for p = 4 with contiguous rows (ld = 4): a persistent grid
+// whose CTAs take every gridDim-th tile of SS_T rows and keep SS_S tiles in
+// flight by bulk asynchronous copies into shared memory (one mbarrier per
+// stage), so the bytes in flight do not depend on the number of threads.
+// Rows are then scored from shared memory as in k_score (tri_d2's order,
+// band rows to a per-warp FP64 queue).  Every wait is bounded: a copy that
+// has not landed after ASYNC_WAIT_NS sets *err, the CTA waits (bounded) for
+// its other copies and returns.
+constexpr int SS_T = 1024;   // rows per tile (16 KB)
+constexpr int SS_S = 4;      // tiles in flight per CTA
+
+template <int G>
+__global__ void __launch_bounds__(NT, 2) k_score_stream(const float* __restrict__ X, long long n,
+                                                        const RowParams* __restrict__ rp,
+                                                        const double* __restrict__ cutp, const Status* st, int* err,
+                                                        float* __restrict__ d2_out, uint8_t* __restrict__ flags,
+                                                        unsigned long long* __restrict__ count) {
+    static_assert(G == 4, "rows of four floats");
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* sx = reinterpret_cast<float4*>(smem);                       // [SS_S][SS_T]
+    __shared__ uint64_t bar[SS_S];
+    __shared__ long long s_q[NT / 32][64];
+    __shared__ int s_fail;
+    if (st->code) return;
+    const double cut = *cutp;
+    float M[4][4], hi[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) M[i][j] = (j <= i) ? rp->Mf[i * PMAX + j] : 0.f;
+        hi[i] = rp->mu_hi[i];
+        lo[i] = rp->mu_lo[i];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float cut_lo = (float)(cut * (1.0 - BAND_EPS)), cut_hi = (float)(cut * (1.0 + BAND_EPS));
+    const bool decide = flags != nullptr;
+    const long long ntiles = (n + SS_T - 1) / SS_T;
+    auto tile_bytes = [&](long long t) -> unsigned {
+        const long long r = n - t * SS_T;
+        return (unsigned)((r < SS_T ? r : SS_T) * 16);
+    };
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int k = 0; k < SS_S; ++k) mbar_init(&bar[k], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < SS_S; ++k) {
+            const long long t = blockIdx.x + (long long)k * gridDim.x;
+            if (t < ntiles) {
+                mbar_expect_tx(&bar[k], tile_bytes(t));
+                bulk_load(sx + (size_t)k * SS_T, X + t * SS_T * 4, tile_bytes(t), &bar[k]);
+            }
+        }
+    }
+    long long* q = s_q[w];
+    int qn = 0;       // warp-uniform
+    int nflag = 0;
+    auto drain = [&](int k) {   // FP64 for the first k queued rows, one per lane
+        if (lane < k) {
+            const long long i = q[lane];
+            const double d = d2_fp64(X + i * 4, *rp, 4);
+            const bool out = d > cut;
+            if (d2_out) d2_out[i] = (float)d;
+            flags[i] = out ? 1 : 0;
+            nflag += out ? 1 : 0;
+        }
+        __syncwarp();
+        for (int e = lane; e + k < qn; e += 32) q[e] = q[e + k];
+        __syncwarp();
+        qn -= k;
+    };
+    long long it = 0;
+    for (;; ++it) {
+        const long long t = blockIdx.x + it * gridDim.x;
+        if (t >= ntiles) break;
+        const int sidx = (int)(it % SS_S);
+        const unsigned parity = (unsigned)((it / SS_S) & 1);
+        const bool ok = mbar_wait(&bar[sidx], parity);
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const float4* tx = sx + (size_t)sidx * SS_T;
+        const long long r0 = t * SS_T;
+#pragma unroll
+        for (int k = 0; k < SS_T / NT; ++k) {
+            const int j = k * NT + threadIdx.x;
+            const long long i = r0 + j;
+            const bool valid = i < n;
+            const float4 v = valid ? tx[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float c[4] = {(v.x - hi[0]) - lo[0], (v.y - hi[1]) - lo[1], (v.z - hi[2]) - lo[2],
+                                (v.w - hi[3]) - lo[3]};
+            float d2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float acc = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc += M[a][u] * c[u];
+                d2 += acc * acc;
+            }
+            const bool band = valid && decide && d2 >= cut_lo && d2 <= cut_hi;
+            if (valid && !band) {
+                const bool out = d2 > cut_hi;   // outside the band: exact in FP32
+                if (d2_out) d2_out[i] = d2;
+                if (decide) {
+                    flags[i] = out ? 1 : 0;
+                    nflag += out ? 1 : 0;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, band);
+            if (bal) {
+                if (band) q[qn + __popc(bal & ((1u << lane) - 1u))] = i;
+                qn += __popc(bal);
+                __syncwarp();
+                if (qn >= 32) drain(32);
+            }
+        }
+        __syncthreads();   // the stage is consumed
+        if (threadIdx.x == 0) {
+            const long long t2 = t + (long long)SS_S * gridDim.x;
+            if (t2 < ntiles) {
+                async_proxy_fence();
+                mbar_expect_tx(&bar[sidx], tile_bytes(t2));
+                bulk_load(sx + (size_t)sidx * SS_T, X + t2 * SS_T * 4, tile_bytes(t2), &bar[sidx]);
+            }
+        }
+    }
+    if (s_fail) {   // let this CTA's copies land (bounded) before leaving
+        if (threadIdx.x == 0) {
+            atomicExch(err, RTD_ECUDA);
+            for (long long k = it; k < it + SS_S; ++k) {
+                const long long t = blockIdx.x + k * gridDim.x;
+                if (t >= ntiles) break;
+                mbar_wait(&bar[(int)(k % SS_S)], (unsigned)((k / SS_S) & 1));
+            }
+        }
+        return;
+    }
+    __syncwarp();
+    if (qn > 0) drain(qn);
+    if (count && decide) {
+        nflag = warp_sum_int(nflag);
+        if (lane == 0 && nflag) atomicAdd(count, (unsigned long long)nflag);
+    }
+}
+
 template <int PB>
-void score_t(const float* X, long long n, int p, long long ld, const RowParams* rp, double cut, float* d2,
-             uint8_t* fl, unsigned long long* cnt, int nsm, cudaStream_t s) {
+void score_t(const float* X, long long n, int p, long long ld, const RowParams* rp, const double* cutp,
+             const Status* st, float* d2, uint8_t* fl, unsigned long long* cnt, int nsm, cudaStream_t s) {
     const int vec4 = (p % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const long long cap = (long long)nsm * 8;   // a resident wave of 256-thread CTAs
+    if constexpr (PB == 4) {
+        if (vec4 && p == 4 && ld == 4) {   // contiguous rows: streamed by bulk copies
+            const long long ntiles = (n + SS_T - 1) / SS_T;
+            const long long cs = (long long)nsm * 2;
+            const int grids = (int)(ntiles < cs ? ntiles : cs);
+            const size_t sm = (size_t)SS_S * SS_T * sizeof(float4);
+            auto k = k_score_stream<4>;
+            static bool attr_set[64] = {};   // the attribute is per device; setting it twice is harmless
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (dev >= 0 && dev < 64) attr_set[dev] = true;
+            }
+            k<<<grids > 0 ? grids : 1, NT, sm, s>>>(X, n, rp, cutp, st, const_cast<int*>(&st->code), d2, fl, cnt);
+            return;
+        }
+        if (vec4 && p == 4 && (reinterpret_cast<uintptr_t>(d2) & 15) == 0 &&
+            (reinterpret_cast<uintptr_t>(fl) & 3) == 0) {
+            const long long groups = (n + 3) / 4;
+            const long long ctas = (groups + NT - 1) / NT;
+            const int grid4 = (int)(ctas < cap ? ctas : cap);
+            k_score4<4><<<grid4 > 0 ? grid4 : 1, NT, 0, s>>>(X, n, ld, rp, cutp, st, d2, fl, cnt);
+            return;
+        }
+    }
     constexpr int R = ScoreRows<PB>::R;
     const long long tiles = (n + (long long)NT * R - 1) / ((long long)NT * R);
-    const long long cap = (long long)nsm * 8;   // a resident wave of 256-thread CTAs
     int grid = (int)(tiles < cap ? tiles : cap);
     if (grid < 1) grid = 1;
-    k_score<PB><<<grid, NT, 0, s>>>(X, n, p, ld, vec4, rp, cut, d2, fl, cnt);
+    k_score<PB><<<grid, NT, 0, s>>>(X, n, p, ld, vec4, rp, cutp, st, d2, fl, cnt);
 }
 
 template <int PB, typename T>

@@ -18,8 +18,9 @@ namespace rtd {
     void memb_pb##N(const Plan& P, cudaStream_t s);                                                 \
     void rew_pb##N(const Plan& P, cudaStream_t s);                                                  \
     void member_gram_pb##N(const Plan& P, cudaStream_t s);                                          \
-    void score_pb##N(const float* X, long long n, int p, long long ld, const RowParams* rp, double cut, \
-                     float* d2, uint8_t* fl, unsigned long long* cnt, int nsm, cudaStream_t s);         \
+    void score_pb##N(const float* X, long long n, int p, long long ld, const RowParams* rp,          \
+                     const double* cutp, const Status* st, float* d2, uint8_t* fl,                  \
+                     unsigned long long* cnt, int nsm, cudaStream_t s);                             \
     void final_pb##N(const float* X, long long n, int p, long long ld, int precision,               \
                      const RowParams* rp, const double* cutp, int decide, float* d2, uint8_t* fl,   \
                      unsigned long long* cnt, int nsm, cudaStream_t s);

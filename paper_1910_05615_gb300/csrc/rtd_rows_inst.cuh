@@ -46,9 +46,9 @@ void RTD_FN(rew_pb)(const Plan& P, cudaStream_t s) {
     else rew_t<RTD_PB, float>(P, s);
 }
 void RTD_FN(member_gram_pb)(const Plan& P, cudaStream_t s) { member_gram_t<RTD_PB>(P, s); }
-void RTD_FN(score_pb)(const float* X, long long n, int p, long long ld, const RowParams* rp, double cut, float* d2,
-                      uint8_t* fl, unsigned long long* cnt, int nsm, cudaStream_t s) {
-    score_t<RTD_PB>(X, n, p, ld, rp, cut, d2, fl, cnt, nsm, s);
+void RTD_FN(score_pb)(const float* X, long long n, int p, long long ld, const RowParams* rp, const double* cutp,
+                      const Status* st, float* d2, uint8_t* fl, unsigned long long* cnt, int nsm, cudaStream_t s) {
+    score_t<RTD_PB>(X, n, p, ld, rp, cutp, st, d2, fl, cnt, nsm, s);
 }
 void RTD_FN(final_pb)(const float* X, long long n, int p, long long ld, int precision, const RowParams* rp,
                       const double* cutp, int decide, float* d2, uint8_t* fl, unsigned long long* cnt,

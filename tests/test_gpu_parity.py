@@ -100,6 +100,73 @@ def test_score_one_pass(rtd, p, host):
     assert fl3 is None and cnt3 == -1
 
 
+@pytest.mark.parametrize("p", [1, 4, 20, 37, 64])
+def test_score_prepared(rtd, p):
+    """A fit prepared once scores two batches with one launch each: the
+    distances and flags equal those of rtdetmcd_score bit for bit (the same
+    factorisation and pass), in both forms, and the device counter adds up
+    both calls' flags."""
+    rng = np.random.default_rng(300 + p)
+    mu = rng.standard_normal(p) * 0.1
+    S = _spd(p, rng, cond=30.0)
+    cut = O.chi2_ppf(0.975, p)
+    prep = rtd.rtdetmcd_score_prepare(mu, S, cut)
+    for prec in (rtd.RTD_FP32, rtd.RTD_FP64):
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        total = 0
+        for k in range(2):
+            n = 100_003 + 7919 * k
+            X = (rng.standard_normal((n, p)) * 1.3 + 0.4).astype(np.float32)
+            X[: n // 20] += 4.0
+            Xd = torch.from_numpy(X).cuda()
+            d2, fl = rtd.rtdetmcd_score_prepared(Xd, prep, precision=prec, count=count)
+            d2r, flr, cntr = rtd.rtdetmcd_score(Xd, mu, S, cut, precision=prec)
+            assert torch.equal(d2, d2r) and torch.equal(fl, flr)
+            total += cntr
+            ref = O.mahalanobis_d2_plain(X, mu, S)
+            decided = np.abs(ref - cut) > 1e-12 * cut
+            assert np.array_equal(to_np(fl).astype(bool)[decided], (ref > cut)[decided])
+        torch.cuda.synchronize()
+        assert int(count.item()) == total
+    if p == 4:   # rows of stride 8, a ragged last group of four rows
+        buf = (rng.standard_normal((50_001, 8)) * 1.3).astype(np.float32)
+        Xs = torch.from_numpy(buf).cuda()[:, :4]
+        d2, fl = rtd.rtdetmcd_score_prepared(Xs, prep)
+        ref = O.mahalanobis_d2_plain(buf[:, :4], mu, S)
+        assert np.max(np.abs(to_np(d2) - ref) / np.maximum(ref, 1e-3)) < 2e-4
+        decided = np.abs(ref - cut) > 1e-12 * cut
+        assert np.array_equal(to_np(fl).astype(bool)[decided], (ref > cut)[decided])
+
+
+def test_score_prepared_rejects(rtd):
+    """A scatter that is not positive definite is refused at preparation, and
+    the FP32 pass of such a prepared fit writes nothing; host rows, a count
+    without flags and a misaligned prepared fit are argument errors."""
+    p = 4
+    bad = np.eye(p)
+    bad[3, 3] = 0.0
+    prep = torch.empty(rtd.rtdetmcd_prepared_size(), dtype=torch.uint8, device="cuda")
+    with pytest.raises(rtd.RtdError) as e:
+        rtd.rtdetmcd_score_prepare(np.zeros(p), bad, out=prep)
+    assert e.value.code == 4
+    X = torch.randn(5000, p, device="cuda")
+    d2 = torch.full((5000,), -7.0, device="cuda")
+    fl = torch.full((5000,), 9, dtype=torch.uint8, device="cuda")
+    rtd.rtdetmcd_score_prepared(X, prep, d2_out=d2, flags_out=fl)
+    torch.cuda.synchronize()
+    assert bool((d2 == -7.0).all()) and bool((fl == 9).all())
+    good = rtd.rtdetmcd_score_prepare(np.zeros(p), np.eye(p))
+    lib = rtd._load()
+    Xh = np.zeros((5000, p), np.float32)
+    assert lib.rtdetmcd_score_prepared(Xh.ctypes.data, 5000, p, p, good.data_ptr(), rtd.RTD_FP32, d2.data_ptr(),
+                                       fl.data_ptr(), None, None) == 1
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert lib.rtdetmcd_score_prepared(X.data_ptr(), 5000, p, p, good.data_ptr(), rtd.RTD_FP32, d2.data_ptr(),
+                                       None, cnt.data_ptr(), None) == 1
+    assert lib.rtdetmcd_score_prepared(X.data_ptr(), 5000, p, p, good.data_ptr() + 8, rtd.RTD_FP32,
+                                       d2.data_ptr(), fl.data_ptr(), None, None) == 1
+
+
 def test_score_strided_and_rejects(rtd):
     rng = np.random.default_rng(5)
     n, p, ld = 40_001, 6, 11
