@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(NT) k_start1(const float* __restrict__ Xp, int
     int r0, r1;
     block_rows(m, cpb, r0, r1);
     typename GramPick<PB, T, TC>::type acc;
-    gram_setup(acc, smem + align128(gram_smem_bytes<PB, T>()));
+    gram_setup(acc, smem + (TC ? 0 : align128(gram_smem_bytes<PB, T>())));   // the tensor-core Gram stages its own rows
     acc.init();
     for (int base = r0; base < r1; base += S::TR) {
         int row = base + threadIdx.x;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(NT) k_start2(const float* __restrict__ Xp, int
     int r0, r1;
     block_rows(m, cpb, r0, r1);
     typename GramPick<PB, T, TC>::type acc;
-    gram_setup(acc, smem + align128(gram_smem_bytes<PB, T>()));
+    gram_setup(acc, smem + (TC ? 0 : align128(gram_smem_bytes<PB, T>())));   // the tensor-core Gram stages its own rows
     acc.init();
     for (int base = r0; base < r1; base += S::TR) {
         int row = base + threadIdx.x;
@@ -497,7 +497,7 @@ void start1_t(const Plan& P, cudaStream_t s) {
     if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
         if (P.tc) { start1_t<PB, T, K, true>(P, s); return; }
     }
-    size_t sm = TC ? align128(gram_smem_bytes<PB, T>()) + GramPick<PB, T, TC>::extra : gram_smem_bytes<PB, T>();
+    size_t sm = TC ? GramPick<PB, T, TC>::extra : gram_smem_bytes<PB, T>();
     auto k = k_start1<PB, T, K, TC>;
     if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     else set_smem(k, sm);
@@ -509,7 +509,7 @@ void start2_t(const Plan& P, cudaStream_t s) {
     if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
         if (P.tc) { start2_t<PB, T, K, true>(P, s); return; }
     }
-    size_t sm = TC ? align128(gram_smem_bytes<PB, T>()) + GramPick<PB, T, TC>::extra : gram_smem_bytes<PB, T>();
+    size_t sm = TC ? GramPick<PB, T, TC>::extra : gram_smem_bytes<PB, T>();
     auto k = k_start2<PB, T, K, TC>;
     if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     else set_smem(k, sm);
@@ -1443,7 +1443,10 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
     extern __shared__ __align__(16) unsigned char smem[];
     T* tile = reinterpret_cast<T*>(smem);
     T* wt = tile + S::TR * S::PE;
-    int* lst = reinterpret_cast<int*>(smem + align16(gram_smem_bytes<PB, T>()));
+    // the tensor-core Gram stages its rows itself: the CUDA-core tile and
+    // reduction scratch are not laid out then
+    constexpr size_t lead = TC ? 0 : align16(gram_smem_bytes<PB, T>());
+    int* lst = reinterpret_cast<int*>(smem + lead);
     __shared__ T s_hi[PB], s_lo[PB];
     const int l = blockIdx.y;
     int r0, r1;
@@ -1464,7 +1467,7 @@ __global__ void __launch_bounds__(NT) k_memb(const float* __restrict__ Xp, const
         const T* keys = dkeys + (size_t)k * qm;
         uint8_t* mb = memb + (size_t)c * m;
         typename GramPick<PB, T, TC>::type acc;
-        gram_setup(acc, smem + align128(memb_smem_bytes<PB, T>()));
+        gram_setup(acc, smem + align128(lead + MEMB_CHUNK * sizeof(int)));
         acc.init(full ? S::G : 1, !full);   // few swapped rows: one group; swapped-out rows subtract
         int nswap = 0;
         for (int c0 = r0; c0 < r1; c0 += MEMB_CHUNK) {
@@ -1532,7 +1535,7 @@ void memb_t(const Plan& P, cudaStream_t s) {
     if constexpr (!TC && tc_width<PB>() && sizeof(T) == 4) {
         if (P.tc) { memb_t<PB, T, true>(P, s); return; }
     }
-    size_t sm = TC ? align128(memb_smem_bytes<PB, T>()) + GramPick<PB, T, TC>::extra : memb_smem_bytes<PB, T>();
+    size_t sm = TC ? align128(MEMB_CHUNK * sizeof(int)) + GramPick<PB, T, TC>::extra : memb_smem_bytes<PB, T>();
     auto k = k_memb<PB, T, TC>;
     if (TC) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     else set_smem(k, sm);

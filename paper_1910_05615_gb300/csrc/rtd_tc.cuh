@@ -139,10 +139,12 @@ __device__ inline void split_bf16x3(float x0, float x1, uint32_t& hi, uint32_t& 
 // features) of one 16-row step.  The buffer serves as B (N = 3H) and its
 // first 128 features as A (M = 128 lanes: a_hi on lanes 0 .. H-1, a_mid on
 // lanes H .. 2H-1, the rest unused), so one MMA per step accumulates the six
-// partial products.  Rows of negative weight (signed mode) go to a second
-// buffer and accumulator, subtracted at the flush.  Needs SMEM bytes of
-// dynamic shared memory (16-byte aligned) handed over by setup(), and 256
-// (512 signed) tensor-memory columns.
+// partial products.  In signed mode (rows of weight -1, the swapped-out rows
+// of the update C-step) A is a buffer of its own holding s [a_hi | a_mid]
+// with s the weight's sign (BF16 negation is exact), so one accumulator
+// takes rows of both signs.  Needs SMEM bytes of dynamic shared memory
+// (16-byte aligned) handed over by setup(), and 256 tensor-memory columns:
+// two CTAs of an SM can hold their accumulators at once.
 template <int PB, int NTH, int TROWS>
 struct GramTC {
     static constexpr int PE = PB + 4;
@@ -151,10 +153,13 @@ struct GramTC {
     static constexpr int TR = TROWS;                        // rows per rows() call, at most
     static constexpr int CH = N / 8;                        // 16-byte feature chunks per row
     static constexpr int GROUP = CH * 128;                  // bytes per 8 rows: CH chunks of 8 rows x 16 B
-    static constexpr int OPS1 = TR / 8 * GROUP;             // one operand buffer
+    static constexpr int OPS1 = TR / 8 * GROUP;             // the B operand buffer
+    static constexpr int CHA = 16;                          // A: 128 features, 16 chunks
+    static constexpr int GROUP_A = CHA * 128;
+    static constexpr int OPS_A = TR / 8 * GROUP_A;          // the signed A operand buffer
     static constexpr int PAD = 2048;
     static constexpr int ACC_LD = H + 1;                    // pair-sum row stride (bank spread)
-    static constexpr int SMEM = 2 * OPS1 + PAD + H * ACC_LD * 8;
+    static constexpr int SMEM = OPS1 + OPS_A + PAD + H * ACC_LD * 8;
     // rows accumulated in FP32 in tensor memory between two flushes (one
     // batch: the accumulation there need not round to nearest, so its depth
     // is kept short)
@@ -177,7 +182,7 @@ struct GramTC {
 
     __device__ void setup(unsigned char* region, uint32_t* taddr_slot, uint64_t* mbar, int* err_flag) {
         ops = region;
-        acc = reinterpret_cast<FF*>(region + 2 * OPS1 + PAD);
+        acc = reinterpret_cast<FF*>(region + OPS1 + OPS_A + PAD);
         s_taddr = taddr_slot;
         bar = mbar;
         err = err_flag;
@@ -186,8 +191,16 @@ struct GramTC {
     // all threads; signed_rows: some rows may carry negative weights
     __device__ void init(int = 0, bool signed_rows = false) {
         sgn = signed_rows ? 1 : 0;
-        tcols = sgn ? 512u : 256u;
+        tcols = 256u;
         for (int e = threadIdx.x; e < H * ACC_LD; e += NTH) acc[e] = FF{0.f, 0.f};
+        if (sgn) {   // A's lanes 2H .. 127 (never read back) hold zeros
+            constexpr int c0 = 2 * H / 8, nz = CHA - c0;
+            for (int e = threadIdx.x; e < TR * nz; e += NTH) {
+                const int slot = e / nz, c = c0 + e % nz;
+                *reinterpret_cast<uint4*>(ops + OPS1 + (slot >> 3) * GROUP_A + (slot & 7) * 16 + c * 128) =
+                    make_uint4(0, 0, 0, 0);
+            }
+        }
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
             mbar_init_fence();
@@ -238,12 +251,6 @@ struct GramTC {
                 for (int c0 = 0; c0 < N; c0 += 16) {
                     float v[16];
                     tmem_ld16(base + (uint32_t)c0, v);
-                    if (sgn) {
-                        float vn[16];
-                        tmem_ld16(base + (uint32_t)(N + c0), vn);
-#pragma unroll
-                        for (int u = 0; u < 16; ++u) v[u] -= vn[u];
-                    }
                     const float f = (c0 >= 2 * H) ? 2.f : 1.f;   // a 16-column group lies in one part
 #pragma unroll
                     for (int u = 0; u < 16; ++u) t[(c0 % H) + u] = fmaf(f, v[u], t[(c0 % H) + u]);
@@ -279,7 +286,9 @@ struct GramTC {
     // beyond p), weight w
     __device__ void put(float*, float*, int slot, const float (&v)[PB], int p, float w) {
         const float sw = sqrtf(fabsf(w));
-        unsigned char* dst = ops + ((sgn && w < 0.f) ? OPS1 : 0) + (slot >> 3) * GROUP + (slot & 7) * 16;
+        unsigned char* dst = ops + (slot >> 3) * GROUP + (slot & 7) * 16;
+        unsigned char* da = ops + OPS1 + (slot >> 3) * GROUP_A + (slot & 7) * 16;
+        const uint32_t neg = (sgn && w < 0.f) ? 0x80008000u : 0u;   // sign bits of both BF16 halves
 #pragma unroll
         for (int g = 0; g < H / 8; ++g) {
             uint32_t hi[4], mi[4], lo[4];
@@ -293,11 +302,12 @@ struct GramTC {
             *reinterpret_cast<uint4*>(dst + g * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(dst + (H / 8 + g) * 128) = make_uint4(mi[0], mi[1], mi[2], mi[3]);
             *reinterpret_cast<uint4*>(dst + (2 * H / 8 + g) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        }
-        if (sgn) {   // the other buffer's copy of this slot is zero
-            unsigned char* z = ops + ((w < 0.f) ? 0 : OPS1) + (slot >> 3) * GROUP + (slot & 7) * 16;
-#pragma unroll
-            for (int g = 0; g < CH; ++g) *reinterpret_cast<uint4*>(z + g * 128) = make_uint4(0, 0, 0, 0);
+            if (sgn) {
+                *reinterpret_cast<uint4*>(da + g * 128) =
+                    make_uint4(hi[0] ^ neg, hi[1] ^ neg, hi[2] ^ neg, hi[3] ^ neg);
+                *reinterpret_cast<uint4*>(da + (H / 8 + g) * 128) =
+                    make_uint4(mi[0] ^ neg, mi[1] ^ neg, mi[2] ^ neg, mi[3] ^ neg);
+            }
         }
     }
 
@@ -306,14 +316,19 @@ struct GramTC {
         if (k <= 0) return;
         const int nks = (k + 15) >> 4;
         const int kpad = nks * 16;
-        const int nbuf = sgn ? 2 : 1;
-        // zero rows k .. kpad-1 of the last step
-        for (int e = threadIdx.x; e < (kpad - k) * CH * nbuf; e += NTH) {
-            const int per = (kpad - k) * CH;
-            const int b = e / per, r = e % per;
-            const int slot = k + r / CH, g = r % CH;
-            *reinterpret_cast<uint4*>(ops + b * OPS1 + (slot >> 3) * GROUP + (slot & 7) * 16 + g * 128) =
-                make_uint4(0, 0, 0, 0);
+        // zero rows k .. kpad-1 of the last step (B, and A's hi and mid in
+        // signed mode)
+        for (int e = threadIdx.x; e < (kpad - k) * CH; e += NTH) {
+            const int slot = k + e / CH, g = e % CH;
+            *reinterpret_cast<uint4*>(ops + (slot >> 3) * GROUP + (slot & 7) * 16 + g * 128) = make_uint4(0, 0, 0, 0);
+        }
+        if (sgn) {
+            constexpr int ca = 2 * H / 8;
+            for (int e = threadIdx.x; e < (kpad - k) * ca; e += NTH) {
+                const int slot = k + e / ca, g = e % ca;
+                *reinterpret_cast<uint4*>(ops + OPS1 + (slot >> 3) * GROUP_A + (slot & 7) * 16 + g * 128) =
+                    make_uint4(0, 0, 0, 0);
+            }
         }
         async_proxy_fence();
         __syncthreads();
@@ -324,13 +339,10 @@ struct GramTC {
             const uint32_t base = smem_addr(ops);
             for (int s = 0; s < nks; ++s) {
                 const bool accum = !(fresh && s == 0);
-                const uint32_t a = base + (uint32_t)(s * 2 * GROUP);
-                const uint64_t d = smem_desc(a, GROUP, 128);
-                mma_bf16(t, d, d, id, accum);
-                if (sgn) {
-                    const uint64_t dn = smem_desc(a + OPS1, GROUP, 128);
-                    mma_bf16(t + (uint32_t)N, dn, dn, id, accum);
-                }
+                const uint32_t b = base + (uint32_t)(s * 2 * GROUP);
+                const uint64_t db = smem_desc(b, GROUP, 128);
+                const uint64_t da = sgn ? smem_desc(base + (uint32_t)(OPS1 + s * 2 * GROUP_A), GROUP_A, 128) : db;
+                mma_bf16(t, da, db, id, accum);
             }
             mma_commit(bar);
         }
