@@ -445,10 +445,10 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
         pf.end(3, n_ * p_ * (4 + 4));
     } else {
         sorted_(P.arenaA, 4, S.p, S.n, RTD_STAGE_UNIVARIATE);
-        launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
+        const int nl = launch_unimcd(P, P.arenaA, 4, S.p, S.n, 0, P.uni, s);
         launch_uni_finish(P, s);
         // rows read, keys written, window search (chunk sums read the keys once)
-        pf.end(9, n_ * p_ * (4 + 4 + 4 + 4));
+        pf.end(3 + nl, n_ * p_ * (4 + 4 + 4 + 4));
     }
     { int e = fetch_status(P.st, s, hs); if (e) return e; }
     pf.collect();
@@ -467,13 +467,15 @@ int run_fit(const float* X, const Shape& S, const rtd_options& o, void* ws, cuda
     launch_refine_eigen(P, s);
     launch_transform(P, 0, s);
     sorted_(P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, RTD_STAGE_REFINE);
-    launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
-    launch_refine_mid(P, s);
-    launch_transform(P, 1, s);
-    sorted_(P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, RTD_STAGE_REFINE);
-    launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
-    launch_refine_end(P, s);
-    pf.end(17, 2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * 2));
+    {
+        int nl = launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
+        launch_refine_mid(P, s);
+        launch_transform(P, 1, s);
+        sorted_(P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, RTD_STAGE_REFINE);
+        nl += launch_unimcd(P, P.arenaA, S.key_bytes, 2 * S.p * S.q, S.m, 1, P.uni, s);
+        launch_refine_end(P, s);
+        pf.end(5 + nl, 2 * (qm_ * p_ * 4 + 2 * p_ * qm_ * K_ * 2));
+    }
     // Sections 2.1, 3.4, 3.5: C-steps of every chain until all have stopped
 csteps:
     {

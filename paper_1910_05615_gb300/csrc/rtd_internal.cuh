@@ -97,8 +97,9 @@ void launch_flag(const float* d2, long long n, double cut, uint8_t* flags,
 // ---- sort / select (rtd_sort.cu)
 void sort_segments(const Plan& P, void* keys, void* tmp, int key_bytes, int nseg,
                    long long L, cudaStream_t s);
-void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L,
-                   int which_c1, double* out, cudaStream_t s);
+// returns the number of kernels it launched
+int launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L,
+                  int which_c1, double* out, cudaStream_t s);
 size_t unimcd_scratch_doubles(int nseg, long long L);
 void launch_gsscm(const Plan& P, const void* rkeys, cudaStream_t s);
 void launch_select_bucket(const Plan& P, cudaStream_t s);

@@ -15,6 +15,9 @@ constexpr int SW = ST / 32;             // warps
 constexpr int SITEMS = SORT_TILE_KEYS / ST;   // rounds per warp
 constexpr int STILE = ST * SITEMS;      // keys per tile
 constexpr int SKPW = STILE / SW;        // keys per warp
+#ifndef RTD_SORT_MIN_CTAS
+#define RTD_SORT_MIN_CTAS 4                // resident scatter CTAs per SM (32-bit keys)
+#endif
 
 template <typename K>
 __global__ void __launch_bounds__(ST) k_sort_hist(const K* __restrict__ keys, long long L, int tiles,
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(unsigned* __restrict__ hist,
 }
 
 template <typename K>
-__global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K* __restrict__ out, long long L,
+__global__ void __launch_bounds__(ST, sizeof(K) == 4 ? RTD_SORT_MIN_CTAS : 2) k_sort_scatter(const K* __restrict__ in, K* __restrict__ out, long long L,
                                                      int tiles, int shift, const unsigned* __restrict__ offs) {
     __shared__ unsigned wcnt[SW][256];
     __shared__ unsigned goff[256];
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
     int cnt = (int)((L - t0) < STILE ? (L - t0) : STILE);
     const K* src = in + (long long)seg * L + t0;
     K key[SITEMS];
-    unsigned rank[SITEMS];
+    unsigned rank[(SITEMS + 1) / 2];   // two 16-bit ranks per word (a rank is below SKPW)
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < SITEMS; ++r) {     // all loads in flight before the ranking
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
         const int leader = __ffs(peers) - 1;
         unsigned base = (valid && lane == leader) ? wcnt[w][d] : 0u;
         base = __shfl_sync(0xffffffffu, base, leader);
-        rank[r] = base + __popc(peers & lt);
+        const unsigned rk = base + __popc(peers & lt);
+        rank[r >> 1] = (r & 1) ? (rank[r >> 1] | (rk << 16)) : rk;
         if (valid && lane == leader) wcnt[w][d] = base + __popc(peers);
         __syncwarp();
     }
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const K* __restrict__ in, K
         int idx = w * SKPW + r * 32 + lane;
         if (idx < cnt) {
             unsigned d = (unsigned)(key[r] >> shift) & 255u;
-            stage[wcnt[w][d] + rank[r]] = key[r];
+            stage[wcnt[w][d] + ((rank[r >> 1] >> ((r & 1) * 16)) & 0xffffu)] = key[r];
         }
     }
     __syncthreads();
@@ -488,6 +492,22 @@ __global__ void __launch_bounds__(UT) k_uni_bound(const K* __restrict__ sorted, 
         o[0] = lb;
         o[1] = qa;
     }
+}
+
+// U3 finish, 32-bit keys, for segments of many ranges: the range bounds from
+// the partial-chunk pairs, one thread per range over several CTAs per
+// segment (the FP64 arithmetic of one segment's ranges would otherwise run
+// on one SM's FP64 pipe).
+__global__ void __launch_bounds__(UT) k_uni_ubfin(double* __restrict__ wb, int nwr, const float4* __restrict__ part,
+                                                  const double* __restrict__ cpre_all, long long L, int nch) {
+    const int seg = blockIdx.y;
+    const int r = blockIdx.x * UT + threadIdx.x;
+    if (r >= nwr) return;
+    const double* cpre = cpre_all + (size_t)seg * (nch + 1) * 2;
+    const float4 v = part[(size_t)seg * nwr + r];
+    const long long k = ((long long)r * UW + L / 2 + 1) / UC;
+    const D2 pb{cpre[2 * k] + ff_d(FF{v.x, v.y}), cpre[2 * k + 1] + ff_d(FF{v.z, v.w})};
+    uni_bound_out(cpre, L, r, nwr, pb, wb + ((size_t)seg * nwr + r) * 2);
 }
 
 // U4: least first-window q of each segment.
@@ -834,8 +854,8 @@ inline UniDims uni_dims(long long L) {
 }
 
 template <typename K>
-static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int which_c1, double* out,
-                     cudaStream_t s) {
+static int unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int which_c1, double* out,
+                    cudaStream_t s) {
     const UniDims D = uni_dims(L);
     double* csum = P.uscratch;
     double* cpre = csum + (size_t)nseg * D.nch * 2;
@@ -856,6 +876,12 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     } else {
         k_uni_bound<K><<<dim3((D.nwr + wpb - 1) / wpb, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb);
     }
+    int launches = 6;
+    if (part && D.nwr > UT) {
+        k_uni_ubfin<<<dim3((D.nwr + UT - 1) / UT, nseg), UT, 0, s>>>(wb, D.nwr, part, cpre, L, D.nch);
+        part = nullptr;
+        ++launches;
+    }
     k_uni_ub<<<nseg, UT, 0, s>>>(wb, D.nwr, ub, wres, list, count, part, cpre, L, D.nch);
     if (sizeof(K) == 4) {
         long long g = (long long)nseg * D.nwr;
@@ -864,12 +890,13 @@ static void unimcd_t(const Plan& P, const K* keys, int nseg, long long L, int wh
     } else
         k_uni_eval<K><<<dim3(D.nwr, nseg), UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wb, ub, wres);
     k_uni_finish_seg<K><<<nseg, UT, 0, s>>>(keys, L, D.nch, D.nwr, cpre, wres, P.cs, which_c1, out);
+    return launches;
 }
 
-void launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L, int which_c1,
-                   double* out, cudaStream_t s) {
-    if (key_bytes == 8) unimcd_t<unsigned long long>(P, (const unsigned long long*)keys, nseg, L, which_c1, out, s);
-    else unimcd_t<uint32_t>(P, (const uint32_t*)keys, nseg, L, which_c1, out, s);
+int launch_unimcd(const Plan& P, const void* keys, int key_bytes, int nseg, long long L, int which_c1,
+                  double* out, cudaStream_t s) {
+    if (key_bytes == 8) return unimcd_t<unsigned long long>(P, (const unsigned long long*)keys, nseg, L, which_c1, out, s);
+    return unimcd_t<uint32_t>(P, (const uint32_t*)keys, nseg, L, which_c1, out, s);
 }
 
 size_t unimcd_scratch_doubles(int nseg, long long L) {
@@ -931,7 +958,7 @@ __device__ double kth_absdev(const K* s, long long L, long long s0, double m3, l
 
 // One warp per block.
 template <typename K>
-__global__ void k_gsscm(const K* __restrict__ rs, int q, long long m, double* __restrict__ AB) {
+__global__ void __launch_bounds__(32) k_gsscm(const K* __restrict__ rs, int q, long long m, double* __restrict__ AB) {
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (l >= q) return;
     const K* s = rs + (size_t)l * m;
@@ -955,7 +982,9 @@ __global__ void k_gsscm(const K* __restrict__ rs, int q, long long m, double* __
 }
 
 void launch_gsscm(const Plan& P, const void* rkeys, cudaStream_t s) {
-    int th = 128, bl = (P.q * 32 + th - 1) / th;
+    // one warp per CTA: the searches are chains of FP64 powers, and warps
+    // sharing an SM would share its FP64 pipe
+    int th = 32, bl = P.q;
     if (P.key_bytes == 8) k_gsscm<unsigned long long><<<bl, th, 0, s>>>((const unsigned long long*)rkeys, P.q, P.m, P.gss);
     else k_gsscm<uint32_t><<<bl, th, 0, s>>>((const uint32_t*)rkeys, P.q, P.m, P.gss);
 }
