@@ -8,7 +8,7 @@ namespace rtd {
 // Segmented LSD radix sort of equal-length segments (keys only, 8-bit
 // digits, stable).  Per pass: tile histograms, per-segment exclusive scan
 // in (digit, tile) order, stable scatter.  A tile is SORT_TILE_KEYS keys:
-// 8 warps, ranked with warp ballots in rounds of 32.
+// 8 warps, ranked in rounds of 32 by warp matches and warp ballots.
 // =====================================================================
 constexpr int ST = 256;                 // threads
 constexpr int SW = ST / 32;             // warps
@@ -18,6 +18,10 @@ constexpr int SKPW = STILE / SW;        // keys per warp
 #ifndef RTD_SORT_MIN_CTAS
 #define RTD_SORT_MIN_CTAS 4                // resident scatter CTAs per SM (32-bit keys)
 #endif
+// Ranking pipes: even rounds find a lane's digit peers by one warp match
+// (the MIO pipe), odd rounds by eight ballots (the ALU pipe), so that neither
+// pipe limits the pass alone.
+constexpr int SMATCH = 2;
 
 template <typename K>
 __global__ void __launch_bounds__(ST) k_sort_hist(const K* __restrict__ keys, long long L, int tiles,
@@ -118,14 +122,20 @@ __global__ void __launch_bounds__(ST, sizeof(K) == 4 ? RTD_SORT_MIN_CTAS : 2) k_
         int idx = w * SKPW + r * 32 + lane;
         bool valid = idx < cnt;
         unsigned d = (unsigned)(key[r] >> shift) & 255u;
-        // lanes holding the same digit: the intersection over the digit's 8
-        // bits of the ballots that agree with this lane's bit
-        unsigned peers = __ballot_sync(0xffffffffu, valid);
-        if (!valid) peers = 1u << lane;
+        // lanes holding the same digit: a warp match (a lane past the end
+        // matches no other), or the intersection over the digit's 8 bits of
+        // the ballots that agree with this lane's bit
+        unsigned peers;
+        if (r % SMATCH == 0) {
+            peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
+        } else {
+            peers = __ballot_sync(0xffffffffu, valid);
+            if (!valid) peers = 1u << lane;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bb : ~bb;
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bb : ~bb;
+            }
         }
         // the group's first lane reads and advances the warp's digit count
         const int leader = __ffs(peers) - 1;
