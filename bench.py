@@ -654,7 +654,7 @@ def main():
     roof["dominant_stage"] = dominant
     # ncu DRAM bytes of one launch, taken on the current kernels (null when a
     # kernel changed after its capture); the summaries live under profiles/
-    roof["traffic_note"] = ("k_sort_scatter alone: 283.2 MB DRAM per refinement pass of 40 M keys "
+    roof["traffic_note"] = ("k_sort_scatter alone: 286.1 MB DRAM per refinement pass of 40 M keys "
                             "(320 MB algorithmic), profiles/k_sort_scatter_refine_n1e6_p20.md")
     roof_c = stage_roof("cstep_dist", "k_dist_win (C-step distances from step 2 on, k_dist at step 1; "
                         "per row 4p B read + 4 B per active chain written)")
