@@ -22,6 +22,7 @@ constexpr int SKPW = STILE / SW;        // keys per warp
 // (the MIO pipe), odd rounds by eight ballots (the ALU pipe), so that neither
 // pipe limits the pass alone.
 constexpr int SMATCH = 2;
+static_assert(SKPW <= 65536, "scatter ranks are packed in 16 bits");
 
 template <typename K>
 __global__ void __launch_bounds__(ST) k_sort_hist(const K* __restrict__ keys, long long L, int tiles,
