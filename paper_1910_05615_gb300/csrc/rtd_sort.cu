@@ -316,10 +316,21 @@ __device__ inline double ucenter(const unsigned long long* s, long long L) { ret
 
 // Sum of (s_i - c, (s_i - c)^2) over [a, b) by one warp / by the CTA
 // (pairs for 32-bit keys, FP64 for 64-bit keys), returned as doubles.
+// Each lane sums its elements' high parts by TwoSum and adds the low parts
+// and the TwoSum errors in plain FP32 (a lane holds a few elements, so the
+// error sum keeps the pair's precision); the lanes' pairs are then combined
+// by the float-float warp reduction.
 __device__ inline FF2 ff_range_sum(const uint32_t* s, float c, long long a, long long b) {
-    FF2 acc = ff_zero2();
-    for (long long i = a + (threadIdx.x & 31); i < b; i += 32) acc = ff_add2(acc, ff_elem(s[i], c));
-    return ff_warp_sum2(acc);
+    float sa = 0.f, ea = 0.f, sb = 0.f, eb = 0.f;
+    for (long long i = a + (threadIdx.x & 31); i < b; i += 32) {
+        const FF2 x = ff_elem(s[i], c);
+        const FF ta = ff_two_sum(sa, x.a.hi), tb = ff_two_sum(sb, x.b.hi);
+        sa = ta.hi;
+        ea += ta.lo + x.a.lo;
+        sb = tb.hi;
+        eb += tb.lo + x.b.lo;
+    }
+    return ff_warp_sum2(FF2{ff_two_sum(sa, ea), ff_two_sum(sb, eb)});
 }
 __device__ inline D2 warp_range_sum(const uint32_t* s, float c, long long a, long long b) {
     const FF2 acc = ff_range_sum(s, c, a, b);
